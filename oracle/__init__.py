@@ -1,0 +1,206 @@
+"""FP64 CPU oracle of the IMEX-DG pressure operator and IMEX step.
+
+TEST INFRASTRUCTURE.  The oracle is the independent, plain and slow checker
+of the CUDA library (arXiv:2505.00384, Sec. 2 and Sec. 3).  Only ``tests/``,
+``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference``
+legs of ``bench.py`` may import it.  It shares no code with the CUDA path and
+the CUDA path never imports it.
+
+This module is argument marshalling only (ctypes over ``liboracle.so``, built
+from ``orc.c`` / ``orc_imex.c`` on first use) plus small dense-algebra helpers
+used by the pinning tests.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class OrcMesh(C.Structure):
+    """Mirror of ``orc_mesh`` in orc.c."""
+
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("r", C.c_int), ("q", C.c_int), ("terrain", C.c_int), ("bc_lateral", C.c_int), ("pad", C.c_int),
+        ("Lx", C.c_double), ("Ly", C.c_double), ("Lz", C.c_double),
+        ("hc", C.c_double), ("ac", C.c_double), ("xc", C.c_double), ("yc", C.c_double),
+    ]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        _lib = C.CDLL(path)
+    return _lib
+
+
+def _dp(a):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def make_mesh(nx, ny, nz, r, Lx=1000.0, Ly=1000.0, Lz=1000.0, q=None, terrain=0, hc=0.0, ac=1000.0,
+              xc=None, yc=None, bc_lateral=0):
+    """Structured hexahedral mesh on [0,Lx]x[0,Ly]x[0,Lz] (terrain-following
+    in z when ``terrain`` > 0).  ``q`` defaults to the consistent rule 2r+1."""
+    m = OrcMesh()
+    m.nx, m.ny, m.nz, m.r = nx, ny, nz, r
+    m.q = 2 * r + 1 if q is None else q
+    m.terrain, m.bc_lateral = terrain, bc_lateral
+    m.Lx, m.Ly, m.Lz = Lx, Ly, Lz
+    m.hc, m.ac = hc, ac
+    m.xc = Lx / 2 if xc is None else xc
+    m.yc = Ly / 2 if yc is None else yc
+    return m
+
+
+def ndofs(m):
+    return m.nx * m.ny * m.nz * (m.r + 1) ** 3
+
+
+def gauss(q):
+    x = np.zeros(q); w = np.zeros(q)
+    assert lib().orc_gauss(q, _dp(x), _dp(w)) == 0
+    return x, w
+
+
+def gll(n):
+    x = np.zeros(n); w = np.zeros(n)
+    assert lib().orc_gll(n, _dp(x), _dp(w)) == 0
+    return x, w
+
+
+def lagrange(nodes, x):
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+    n = len(nodes)
+    l = np.zeros(n); dl = np.zeros(n)
+    lib().orc_lagrange(n, _dp(nodes), C.c_double(x), _dp(l), _dp(dl))
+    return l, dl
+
+
+def terrain_height(m, x, y):
+    f = lib().orc_terrain_height
+    f.restype = C.c_double
+    return f(C.byref(m), C.c_double(x), C.c_double(y))
+
+
+def node_coords(m):
+    X = np.zeros(3 * ndofs(m))
+    assert lib().orc_node_coords(C.byref(m), _dp(X)) == 0
+    return X.reshape(3, -1)
+
+
+def apply_B(m, alpha, p):
+    out = np.zeros(3 * ndofs(m))
+    assert lib().orc_apply_B(C.byref(m), C.c_double(alpha), _dp(np.ascontiguousarray(p, dtype=np.float64)), _dp(out)) == 0
+    return out
+
+
+def apply_A(m, rho, V):
+    out = np.zeros(3 * ndofs(m))
+    assert lib().orc_apply_A(C.byref(m), _dp(np.ascontiguousarray(rho, dtype=np.float64)),
+                             _dp(np.ascontiguousarray(V, dtype=np.float64)), _dp(out)) == 0
+    return out
+
+
+def apply_Ainv(m, rho, V):
+    out = np.zeros(3 * ndofs(m))
+    assert lib().orc_apply_Ainv(C.byref(m), _dp(np.ascontiguousarray(rho, dtype=np.float64)),
+                                _dp(np.ascontiguousarray(V, dtype=np.float64)), _dp(out)) == 0
+    return out
+
+
+def apply_C(m, alpha, gamma, pk, V):
+    out = np.zeros(ndofs(m))
+    assert lib().orc_apply_C(C.byref(m), C.c_double(alpha), C.c_double(gamma),
+                             _dp(np.ascontiguousarray(pk, dtype=np.float64)),
+                             _dp(np.ascontiguousarray(V, dtype=np.float64)), _dp(out)) == 0
+    return out
+
+
+def apply_M(m, f, scale=1.0):
+    out = np.zeros(ndofs(m))
+    assert lib().orc_apply_M(C.byref(m), C.c_double(scale), _dp(np.ascontiguousarray(f, dtype=np.float64)), _dp(out)) == 0
+    return out
+
+
+def apply_D(m, gamma, p):
+    return apply_M(m, p, 1.0 / (gamma - 1.0))
+
+
+def apply_S(m, alpha, gamma, rho, pk, p, cells=None):
+    """y = S p = D p - C A^-1 B p.  With ``cells`` (indices), only those
+    cells' entries are computed; the rest of y is NaN."""
+    N = ndofs(m)
+    y = np.zeros(N)
+    args = [C.byref(m), C.c_double(alpha), C.c_double(gamma), _dp(np.ascontiguousarray(rho, dtype=np.float64)),
+            _dp(np.ascontiguousarray(pk, dtype=np.float64)), _dp(np.ascontiguousarray(p, dtype=np.float64))]
+    if cells is None:
+        assert lib().orc_apply_S_masked(*args, None, _dp(y)) == 0
+        return y
+    y[:] = np.nan
+    mask = np.zeros(m.nx * m.ny * m.nz, dtype=np.uint8)
+    mask[np.asarray(cells)] = 1
+    assert lib().orc_apply_S_masked(*args, mask.ctypes.data_as(C.c_void_p), _dp(y)) == 0
+    return y
+
+
+PC_NONE, PC_HELMHOLTZ, PC_INTERNAL_ENERGY = 0, 1, 2
+
+
+def precond_diag(m, kind, alpha, gamma, rho, pk):
+    d = np.zeros(ndofs(m))
+    assert lib().orc_precond_diag(C.byref(m), kind, C.c_double(alpha), C.c_double(gamma),
+                                  _dp(np.ascontiguousarray(rho, dtype=np.float64)),
+                                  _dp(np.ascontiguousarray(pk, dtype=np.float64)), _dp(d)) == 0
+    return d
+
+
+def solve(m, alpha, gamma, rho, pk, b, method="fgmres", pc=PC_HELMHOLTZ, tol=1e-10, restart=30, maxit=1000, x0=None):
+    """Solve S x = b.  Returns (x, status, iterations, relative residual)."""
+    N = ndofs(m)
+    x = np.zeros(N) if x0 is None else np.array(x0, dtype=np.float64)
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    pk = np.ascontiguousarray(pk, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    dinv = None
+    if pc != PC_NONE:
+        dinv = 1.0 / precond_diag(m, pc, alpha, gamma, rho, pk)
+    its = C.c_int(0)
+    rel = C.c_double(0.0)
+    dptr = _dp(dinv) if dinv is not None else None
+    if method == "fgmres":
+        st = lib().orc_fgmres(C.byref(m), C.c_double(alpha), C.c_double(gamma), _dp(rho), _dp(pk), dptr, _dp(b),
+                              _dp(x), C.c_double(tol), restart, maxit, C.byref(its), C.byref(rel))
+    elif method == "cg":
+        st = lib().orc_cg(C.byref(m), C.c_double(alpha), C.c_double(gamma), _dp(rho), _dp(pk), dptr, _dp(b),
+                          _dp(x), C.c_double(tol), maxit, C.byref(its), C.byref(rel))
+    else:
+        raise ValueError(method)
+    return x, st, its.value, rel.value
+
+
+def max_threads():
+    return lib().orc_max_threads()
+
+
+def set_threads(n):
+    lib().orc_set_threads(int(n))
+
+
+# ---------------------------------------------------------------- dense helpers
+def assemble(apply, n_in, n_out):
+    """Dense matrix of a linear map by applying it to unit vectors (the
+    unit-vector construction of Sec. 3.1).  For tiny meshes only."""
+    Mx = np.zeros((n_out, n_in))
+    e = np.zeros(n_in)
+    for j in range(n_in):
+        e[j] = 1.0
+        Mx[:, j] = apply(e)
+        e[j] = 0.0
+    return Mx
