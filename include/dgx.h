@@ -1,0 +1,180 @@
+/*
+ * dgx.h -- C ABI of the GB300 (sm_103a) library for the pressure solve and the
+ * explicit fluxes of the IMEX discontinuous-Galerkin compressible-Euler
+ * scheme of Orlando, Benacchio & Bonaventura, "Improving the scalability of a
+ * high-order atmospheric dynamics solver based on the deal.II library"
+ * (arXiv:2505.00384).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Unknowns are nodal DG fields of degree r on the (r+1)^3 Gauss-Lobatto
+ *    points of each hexahedral cell (Sec. 2).  DoF index
+ *    cell * (r+1)^3 + a + (r+1) b + (r+1)^2 c (x fastest), with
+ *    cell = cx + nx (cy + ny cz).  N = nx ny nz (r+1)^3.  Vector fields are
+ *    three consecutive N-blocks (x, y, z components).
+ *  - Every array argument is a DEVICE pointer on the context's device unless
+ *    the comment says host.  Arrays are contiguous; the element type is
+ *    double for DGX_F64 and float for DGX_F32.  The caller owns every array
+ *    it passes; the library never frees or keeps them beyond the call except
+ *    where stated (dgx_set_coefficients copies).
+ *  - The library owns its workspace (geometry tables, coefficient copies,
+ *    preconditioner diagonals, Krylov bases) and frees it in dgx_destroy.
+ *  - Calls are enqueued on the stream given to dgx_create and return before
+ *    the GPU finishes, except dgx_solve_pressure and dgx_imex_step, which
+ *    return after the solve because they fill an info struct.
+ *  - Return value: 0 = success, > 0 = soft status (DGX_NOT_CONVERGED), < 0 =
+ *    error (nothing useful was written).  dgx_last_error gives a message.
+ */
+#ifndef DGX_H
+#define DGX_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DGX_OK 0
+#define DGX_NOT_CONVERGED 1
+#define DGX_FALLBACK_USED 2
+#define DGX_ERR_ARG (-1)
+#define DGX_ERR_OOM (-2)
+#define DGX_ERR_CUDA (-3)
+#define DGX_ERR_BREAKDOWN (-4)
+#define DGX_ERR_DEVICE_TIMEOUT (-5)
+#define DGX_ERR_STATE (-6)
+
+/* Arithmetic of an operator application. */
+#define DGX_F64 0
+#define DGX_F32 1
+
+/* Jacobi preconditioners of Sec. 3.1. */
+#define DGX_PC_NONE 0
+#define DGX_PC_HELMHOLTZ 1       /* inverse diagonal of S~ (Helmholtz preconditioner)        */
+#define DGX_PC_INTERNAL_ENERGY 2 /* inverse diagonal of D (internal-energy preconditioner)  */
+
+/* Krylov methods (Sec. 3.1: GMRES for the non-symmetric Schur system, CG
+ * for the symmetric positive definite case). */
+#define DGX_SOLVER_FGMRES 0 /* flexible GMRES in FP64                                         */
+#define DGX_SOLVER_CG 1     /* preconditioned CG in FP64 (S must be SPD)                       */
+#define DGX_SOLVER_MIXED 2  /* FP64 flexible GMRES whose preconditioner is an FP32 GMRES solve */
+
+typedef struct dgx_ctx dgx_ctx;
+
+/* Mesh of Sec. 3: structured hexahedra on [0,Lx] x [0,Ly] x [0,Lz],
+ * terrain-following in z (z = zeta + h(x,y) (1 - zeta/Lz), zeta uniform).
+ * terrain: 0 flat; 1 bell h = h_c / (1 + ((x-x_c)^2 + (y-y_c)^2)/a_c^2);
+ *          2 bell of Sec. 3, h = h_c [1 + ((x-x_c)^2 + (y-y_c)^2)/a_c^2]^(-3/2).
+ * bc_lateral: 0 slip walls on the four lateral faces, 1 far field (the
+ * explicit flux sees the background plus (u_bar,0,0); the pressure operator
+ * is transmissive there).  Bottom and top are slip walls.
+ * n_q: Gauss points per direction of the consistent rule; 0 selects 2r+1
+ * (Sec. 3.3), the only value the GPU kernels accept. */
+typedef struct {
+  int nx, ny, nz;
+  int degree;
+  int n_q;
+  int terrain;
+  int bc_lateral;
+  int reserved;
+  double Lx, Ly, Lz;
+  double h_c, a_c, x_c, y_c;
+} dgx_mesh_desc;
+
+/* Hydrostatic background (Sec. 3): kind 0 isothermal at T (p = p0 exp(-g z/(R T))),
+ * kind 1 the constant-buoyancy-frequency state of Sec. 3 with N_bv, T = T_ref. */
+typedef struct {
+  int kind;
+  int reserved;
+  double T, p0, N_bv, R, gamma, g, u_bar;
+} dgx_background;
+
+typedef struct {
+  int method;        /* DGX_SOLVER_*                                                     */
+  int pc;            /* DGX_PC_* (right preconditioning)                                 */
+  int restart;       /* FGMRES restart length m (<= 64)                                  */
+  int maxit;         /* maximum outer iterations                                         */
+  double tol;        /* relative residual ||b - S x||_2 / ||b||_2 checked in FP64        */
+  int inner_restart; /* DGX_SOLVER_MIXED: FP32 GMRES restart length                      */
+  int inner_maxit;   /* DGX_SOLVER_MIXED: FP32 iterations per outer iteration            */
+  double inner_tol;  /* DGX_SOLVER_MIXED: relative tolerance of the FP32 inner solve      */
+  int use_x0;        /* 1: x holds the initial guess; 0: start from zero                  */
+  int reserved;
+} dgx_solve_opts;
+
+typedef struct {
+  int status;          /* DGX_OK or DGX_NOT_CONVERGED                                    */
+  int iterations;      /* outer (FP64) Krylov iterations                                 */
+  int inner_iterations;/* FP32 iterations (DGX_SOLVER_MIXED)                             */
+  int operator_f64;    /* FP64 operator applications                                     */
+  int operator_f32;    /* FP32 operator applications                                     */
+  int reserved;
+  double relres;       /* final true relative residual in FP64                            */
+  double seconds;      /* wall time of the call                                          */
+} dgx_solve_info;
+
+/* Create a context on CUDA device `device`, enqueueing all work on
+ * `cuda_stream` (a cudaStream_t; NULL = legacy default stream). */
+int dgx_create(dgx_ctx **ctx, int device, void *cuda_stream);
+void dgx_destroy(dgx_ctx *ctx);
+const char *dgx_last_error(const dgx_ctx *ctx);
+
+/* Build the mesh and its geometry tables (per-column terrain heights and
+ * their derivatives at the quadrature points), Sec. 2-3.  Replaces any
+ * earlier mesh and drops coefficients and diagonals. */
+int dgx_mesh_build(dgx_ctx *ctx, const dgx_mesh_desc *desc);
+/* N, the number of pressure DoFs; -1 without a mesh. */
+long long dgx_num_dofs(const dgx_ctx *ctx);
+/* Physical coordinates of all DoF nodes: X (device, 3N doubles). */
+int dgx_node_coords(dgx_ctx *ctx, double *X);
+
+/* Background state (Sec. 3); needed by the IMEX step. */
+int dgx_set_background(dgx_ctx *ctx, const dgx_background *bg);
+/* Nodal background density and pressure (device, N doubles each). */
+int dgx_background_fields(dgx_ctx *ctx, double *rho_bar, double *p_bar);
+
+/* Coefficients of the Schur operator of one fixed-point iteration (Sec. 2):
+ * rho_l = rho^(l) (nodal, N doubles), p_k = total pressure of the previous
+ * fixed-point iterate (nodal, N doubles), a_dt = a~_ll * dt, gamma.  The
+ * library copies both fields (FP64 and FP32 copies) and rebuilds the
+ * Helmholtz and internal-energy diagonals (Sec. 3.1). */
+int dgx_set_coefficients(dgx_ctx *ctx, const double *rho_l, const double *p_k, double a_dt, double gamma);
+
+/* y = S x = D x - C A^-1 B x, the matrix-free Schur operator of the
+ * fixed-point equation of Sec. 2 with the fast block-diagonal inverse of
+ * Sec. 3.3; x, y: N elements of type `prec`.  x and y must not alias. */
+int dgx_apply_operator(dgx_ctx *ctx, int prec, const void *x, void *y);
+/* V = A^-1 B p (the pressure-gradient step, 3N out) and y = D p - C V
+ * (the divergence step, N out): the two halves of dgx_apply_operator. */
+int dgx_apply_grad(dgx_ctx *ctx, int prec, const void *p, void *V);
+int dgx_apply_div(dgx_ctx *ctx, int prec, const void *V, const void *p, void *y);
+/* out = A_rho^-1 in (3N -> 3N), fast inverse S^-T J^-1 S^-1 of Sec. 3.3. */
+int dgx_apply_mass_inverse(dgx_ctx *ctx, int prec, const void *in, void *out);
+/* y = P^-1 x for the Jacobi preconditioner `pc` (Sec. 3.1). */
+int dgx_apply_preconditioner(dgx_ctx *ctx, int pc, int prec, const void *x, void *y);
+/* The (non-inverted) diagonal of `pc` (FP64, N doubles). */
+int dgx_preconditioner_diagonal(dgx_ctx *ctx, int pc, double *d);
+
+/* Solve S x = b (Sec. 3.1) to ||b - S x|| <= tol ||b|| in FP64.  b, x:
+ * device, N doubles.  Returns DGX_OK, DGX_NOT_CONVERGED (x holds the last
+ * iterate) or an error (DGX_ERR_BREAKDOWN on a NaN or zero Krylov scalar). */
+int dgx_solve_pressure(dgx_ctx *ctx, const double *b, double *x, const dgx_solve_opts *opts,
+                       dgx_solve_info *info);
+
+/* Default options: FGMRES(30), Helmholtz preconditioner, tol 1e-8. */
+void dgx_default_solve_opts(dgx_solve_opts *opts);
+
+/* Algorithmic work of one dgx_apply_operator call for the current mesh (host
+ * pointers, any may be NULL): floating-point operations of the implemented
+ * sum-factorisation sweeps of the gradient kernel (V = A^-1 B p) and of the
+ * divergence kernel (y = D p - C V), and the HBM floor of the whole
+ * application in bytes (p, rho, p_k read once, y written once: 32 bytes per
+ * DoF in FP64). */
+int dgx_operator_cost(const dgx_ctx *ctx, double *flops_grad, double *flops_div, double *bytes_f64);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * contexts); a diagnostic counter for benchmarks. */
+long long dgx_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,965 @@
+// C ABI of the dgx library: context, mesh and geometry set-up, background,
+// coefficients, operator / preconditioner application and the Krylov
+// pressure solvers (arXiv:2505.00384, Sec. 2 and Sec. 3.1).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "dgx_common.cuh"
+
+namespace dgx {
+
+int set_error(dgx_ctx *c, int code, const char *fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return code;
+}
+
+int check_cuda(dgx_ctx *c, cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return 0;
+  return set_error(c, e == cudaErrorMemoryAllocation ? DGX_ERR_OOM : DGX_ERR_CUDA, "%s: %s", what,
+                   cudaGetErrorString(e));
+}
+
+namespace {
+
+// ---------------------------------------------------------------- 1D rules
+// Legendre P_k and P_{k-1} at x by the three-term recurrence.
+void legendre_pair(int k, double x, double &Pk, double &Pkm1) {
+  double a = 1.0, b = x;  // P_0, P_1
+  if (k == 0) { Pk = 1.0; Pkm1 = 0.0; return; }
+  for (int j = 2; j <= k; ++j) {
+    const double c = ((2 * j - 1) * x * b - (j - 1) * a) / j;
+    a = b;
+    b = c;
+  }
+  Pk = b;
+  Pkm1 = a;
+}
+
+// Gauss-Legendre rule on [0,1]: Newton on P_q from the guess cos(pi (4i-1)/(4q+2)).
+void gauss_rule(int q, std::vector<double> &x, std::vector<double> &w) {
+  x.assign(q, 0.0);
+  w.assign(q, 0.0);
+  for (int i = 1; i <= q; ++i) {
+    double t = std::cos(M_PI * (4.0 * i - 1.0) / (4.0 * q + 2.0));
+    double dP = 1.0;
+    for (int it = 0; it < 200; ++it) {
+      double P, Pm;
+      legendre_pair(q, t, P, Pm);
+      dP = q * (Pm - t * P) / (1.0 - t * t);  // (1-t^2) P_q' = q (P_{q-1} - t P_q)
+      const double dt = P / dP;
+      t -= dt;
+      if (std::fabs(dt) <= 1e-16 * std::max(1.0, std::fabs(t))) break;
+    }
+    double P, Pm;
+    legendre_pair(q, t, P, Pm);
+    dP = q * (Pm - t * P) / (1.0 - t * t);
+    x[q - i] = 0.5 * (1.0 + t);
+    w[q - i] = 1.0 / ((1.0 - t * t) * dP * dP);
+  }
+}
+
+// Gauss-Lobatto rule on [0,1] with n points: the zeros of
+// f(x) = x P_k - P_{k-1} (k = n-1), which vanishes at +-1 and at the zeros of
+// P_k'; Newton with f'(x) = (k+1) P_k from Chebyshev-Gauss-Lobatto guesses.
+void gll_rule(int n, std::vector<double> &x, std::vector<double> &w) {
+  const int k = n - 1;
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double t = -std::cos(M_PI * i / k);
+    if (i > 0 && i < k) {
+      for (int it = 0; it < 200; ++it) {
+        double P, Pm;
+        legendre_pair(k, t, P, Pm);
+        const double dt = (t * P - Pm) / ((k + 1) * P);
+        t -= dt;
+        if (std::fabs(dt) <= 1e-16) break;
+      }
+    }
+    double P, Pm;
+    legendre_pair(k, t, P, Pm);
+    x[i] = 0.5 * (1.0 + t);
+    w[i] = 1.0 / (k * (k + 1.0) * P * P);
+  }
+  x[0] = 0.0;
+  x[k] = 1.0;
+}
+
+// Barycentric Lagrange interpolation on nodes xn: values l_j(x) and
+// derivatives through the nodal differentiation matrix.
+struct Lagrange {
+  std::vector<double> xn, lam, Dn;  // Dn[i*n+j] = l_j'(x_i)
+  int n;
+  explicit Lagrange(const std::vector<double> &nodes) : xn(nodes), n((int)nodes.size()) {
+    lam.assign(n, 1.0);
+    for (int j = 0; j < n; ++j)
+      for (int k = 0; k < n; ++k)
+        if (k != j) lam[j] /= (xn[j] - xn[k]);
+    Dn.assign(n * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int j = 0; j < n; ++j)
+        if (j != i) {
+          Dn[i * n + j] = (lam[j] / lam[i]) / (xn[i] - xn[j]);
+          s += Dn[i * n + j];
+        }
+      Dn[i * n + i] = -s;
+    }
+  }
+  void eval(double x, double *l, double *dl) const {
+    int hit = -1;
+    for (int j = 0; j < n; ++j)
+      if (std::fabs(x - xn[j]) < 1e-15) hit = j;
+    if (hit >= 0) {
+      for (int j = 0; j < n; ++j) l[j] = j == hit ? 1.0 : 0.0;
+    } else {
+      double s = 0.0;
+      for (int j = 0; j < n; ++j) s += lam[j] / (x - xn[j]);
+      for (int j = 0; j < n; ++j) l[j] = (lam[j] / (x - xn[j])) / s;
+    }
+    if (dl)
+      for (int j = 0; j < n; ++j) {
+        double d = 0.0;
+        for (int i = 0; i < n; ++i) d += l[i] * Dn[i * n + j];
+        dl[j] = d;
+      }
+  }
+};
+
+bool invert(int n, std::vector<double> A, std::vector<double> &inv) {
+  inv.assign(n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[r * n + c]) > std::fabs(A[p * n + c])) p = r;
+    if (A[p * n + c] == 0.0) return false;
+    for (int j = 0; j < n; ++j) {
+      std::swap(A[c * n + j], A[p * n + j]);
+      std::swap(inv[c * n + j], inv[p * n + j]);
+    }
+    const double d = A[c * n + c];
+    for (int j = 0; j < n; ++j) {
+      A[c * n + j] /= d;
+      inv[c * n + j] /= d;
+    }
+    for (int r = 0; r < n; ++r)
+      if (r != c) {
+        const double f = A[r * n + c];
+        for (int j = 0; j < n; ++j) {
+          A[r * n + j] -= f * A[c * n + j];
+          inv[r * n + j] -= f * inv[c * n + j];
+        }
+      }
+  }
+  return true;
+}
+
+// Per-degree 1D table block (layout in dgx_common.cuh).
+struct Tables1D {
+  int N, Q;
+  std::vector<double> gll, gllw, gq, gw, ga, gaw;
+  std::vector<double> tab;
+};
+
+bool make_tables(int r, Tables1D &T) {
+  const int N = r + 1, Q = 2 * r + 1;
+  T.N = N;
+  T.Q = Q;
+  gll_rule(N, T.gll, T.gllw);
+  gauss_rule(Q, T.gq, T.gw);
+  gauss_rule(N, T.ga, T.gaw);
+  Lagrange L(T.gll);
+  T.tab.assign(tab_size(N, Q), 0.0);
+  double *t = T.tab.data();
+  std::vector<double> l(N), dl(N);
+  for (int q = 0; q < Q; ++q) {
+    L.eval(T.gq[q], l.data(), dl.data());
+    for (int a = 0; a < N; ++a) {
+      t[tab_off_I(N, Q) + q * N + a] = l[a];
+      t[tab_off_D(N, Q) + q * N + a] = dl[a];
+      t[tab_off_IT(N, Q) + a * Q + q] = l[a];
+      t[tab_off_DT(N, Q) + a * Q + q] = dl[a];
+      t[tab_off_IIT(N, Q) + a * Q + q] = l[a] * l[a];
+      t[tab_off_DDT(N, Q) + a * Q + q] = dl[a] * dl[a];
+      t[tab_off_IDT(N, Q) + a * Q + q] = l[a] * dl[a];
+    }
+    t[tab_off_wq(N, Q) + q] = T.gw[q];
+    t[tab_off_gq(N, Q) + q] = T.gq[q];
+  }
+  std::vector<double> Ia(N * N), P;
+  for (int q = 0; q < N; ++q) {
+    L.eval(T.ga[q], l.data(), nullptr);
+    for (int a = 0; a < N; ++a) Ia[q * N + a] = l[a];
+    t[tab_off_wa(N, Q) + q] = T.gaw[q];
+  }
+  if (!invert(N, Ia, P)) return false;  // P[a][q] = (Ia^-1)[a][q]
+  for (int i = 0; i < N * N; ++i) t[tab_off_Ia(N, Q) + i] = Ia[i];
+  for (int a = 0; a < N; ++a)
+    for (int q = 0; q < N; ++q) {
+      t[tab_off_P(N, Q) + a * N + q] = P[a * N + q];
+      t[tab_off_PT(N, Q) + q * N + a] = P[a * N + q];
+    }
+  return true;
+}
+
+double terrain_h(const dgx_mesh_desc &m, double x, double y) {
+  if (m.terrain == 0) return 0.0;
+  const double s = 1.0 + ((x - m.x_c) * (x - m.x_c) + (y - m.y_c) * (y - m.y_c)) / (m.a_c * m.a_c);
+  return m.terrain == 1 ? m.h_c / s : m.h_c * std::pow(s, -1.5);
+}
+
+// ---------------------------------------------------------------- device helpers
+struct NodeP {
+  int nx, ny, n, terrain;
+  double dx, dy, dz, H, hc, ac, xc, yc;
+  double gll[8];
+};
+
+__device__ double dev_terrain(const NodeP &p, double x, double y) {
+  if (p.terrain == 0) return 0.0;
+  const double s = 1.0 + ((x - p.xc) * (x - p.xc) + (y - p.yc) * (y - p.yc)) / (p.ac * p.ac);
+  return p.terrain == 1 ? p.hc / s : p.hc * pow(s, -1.5);
+}
+
+__global__ void k_node_coords(NodeP p, long long N, double *__restrict__ X) {
+  const int n3 = p.n * p.n * p.n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const long long cell = i / n3;
+    const int node = (int)(i % n3);
+    const int a = node % p.n, b = (node / p.n) % p.n, c = node / (p.n * p.n);
+    const long long cx = cell % p.nx, cy = (cell / p.nx) % p.ny, cz = cell / ((long long)p.nx * p.ny);
+    const double x = (cx + p.gll[a]) * p.dx, y = (cy + p.gll[b]) * p.dy, zeta = (cz + p.gll[c]) * p.dz;
+    X[i] = x;
+    X[N + i] = y;
+    X[2 * N + i] = zeta + dev_terrain(p, x, y) * (1.0 - zeta / p.H);
+  }
+}
+
+struct BgP {
+  int kind;
+  double T, p0, Nbv, R, gamma, g;
+};
+
+// Hydrostatic background at height z (Sec. 3): isothermal, or the
+// constant-buoyancy-frequency state with rho_ref = p_ref / (R T_ref).
+__global__ void k_background(BgP b, long long N, const double *__restrict__ X, double *__restrict__ rho,
+                             double *__restrict__ p) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double z = X[2 * N + i];
+    double pv, rv;
+    if (b.kind == 0) {
+      pv = b.p0 * exp(-b.g * z / (b.R * b.T));
+      rv = pv / (b.R * b.T);
+    } else {
+      const double G = (b.gamma - 1.0) / b.gamma;
+      const double rref = b.p0 / (b.R * b.T);
+      const double e = exp(-b.Nbv * b.Nbv * z / b.g);
+      pv = b.p0 * pow(1.0 - b.g / (b.Nbv * b.Nbv) * G * rref / b.p0 * (1.0 - e), 1.0 / G);
+      rv = rref * pow(pv / b.p0, 1.0 / b.gamma) * e;
+    }
+    p[i] = pv;
+    rho[i] = rv;
+  }
+}
+
+int ensure_red(dgx_ctx *c) {
+  if (c->red) return 0;
+  const size_t np = (size_t)vec_partials() * 130;
+  if (int e = check_cuda(c, cudaMalloc(&c->red, np * sizeof(double)), "cudaMalloc red")) return e;
+  if (int e = check_cuda(c, cudaMalloc(&c->red_out, 256 * sizeof(double)), "cudaMalloc red_out")) return e;
+  if (int e = check_cuda(c, cudaMallocHost(&c->host_red, 256 * sizeof(double)), "cudaMallocHost")) return e;
+  c->red_elems = np;
+  return 0;
+}
+
+void free_mesh(dgx_ctx *c) {
+  for (void *p : c->owned) cudaFree(p);
+  c->owned.clear();
+  c->tab64 = nullptr;
+  c->tab32 = nullptr;
+  c->col64 = nullptr;
+  c->col32 = nullptr;
+  c->rho_bar = c->p_bar = nullptr;
+  c->rho64 = c->pk64 = nullptr;
+  c->rho32 = c->pk32 = nullptr;
+  for (int i = 0; i < 3; ++i) {
+    c->diag64[i] = c->dinv64[i] = nullptr;
+    c->dinv32[i] = nullptr;
+  }
+  c->V64 = nullptr;
+  c->V32 = nullptr;
+  if (c->kry64) cudaFree(c->kry64);
+  if (c->kry32) cudaFree(c->kry32);
+  c->kry64 = nullptr;
+  c->kry32 = nullptr;
+  c->kry64_elems = c->kry32_elems = 0;
+  c->has_mesh = c->has_coef = c->has_bg = false;
+}
+
+template <typename T>
+int dalloc(dgx_ctx *c, T **p, size_t elems) {
+  void *q = nullptr;
+  if (int e = check_cuda(c, cudaMalloc(&q, std::max<size_t>(1, elems) * sizeof(T)), "cudaMalloc")) return e;
+  c->owned.push_back(q);
+  *p = reinterpret_cast<T *>(q);
+  return 0;
+}
+
+int grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)std::min<long long>(std::max<long long>(b, 1), 4 * 152);
+}
+
+NodeP node_params(const dgx_ctx *c, const Tables1D *T = nullptr) {
+  NodeP p{};
+  p.nx = c->mesh.nx;
+  p.ny = c->mesh.ny;
+  p.n = c->n;
+  p.terrain = c->mesh.terrain;
+  p.dx = c->mesh.Lx / c->mesh.nx;
+  p.dy = c->mesh.Ly / c->mesh.ny;
+  p.dz = c->mesh.Lz / c->mesh.nz;
+  p.H = c->mesh.Lz;
+  p.hc = c->mesh.h_c;
+  p.ac = c->mesh.a_c;
+  p.xc = c->mesh.x_c;
+  p.yc = c->mesh.y_c;
+  std::vector<double> x, w;
+  gll_rule(c->n, x, w);
+  for (int i = 0; i < c->n; ++i) p.gll[i] = x[i];
+  (void)T;
+  return p;
+}
+
+// y = S x through the context's V scratch buffer
+template <typename T>
+int apply_S(dgx_ctx *c, const T *x, T *y) {
+  T *V;
+  const T *rho, *pk;
+  if constexpr (sizeof(T) == 8) {
+    V = reinterpret_cast<T *>(c->V64);
+    rho = reinterpret_cast<const T *>(c->rho64);
+    pk = reinterpret_cast<const T *>(c->pk64);
+  } else {
+    V = reinterpret_cast<T *>(c->V32);
+    rho = reinterpret_cast<const T *>(c->rho32);
+    pk = reinterpret_cast<const T *>(c->pk32);
+  }
+  if (int e = launch_grad<T>(c, x, rho, V, c->stream)) return e;
+  return launch_div<T>(c, V, x, pk, y, c->stream);
+}
+
+int check_ready(dgx_ctx *c, bool need_coef) {
+  if (!c) return DGX_ERR_ARG;
+  if (!c->has_mesh) return set_error(c, DGX_ERR_STATE, "no mesh (call dgx_mesh_build)");
+  if (need_coef && !c->has_coef) return set_error(c, DGX_ERR_STATE, "no coefficients (call dgx_set_coefficients)");
+  return 0;
+}
+
+// ---------------------------------------------------------------- Krylov
+struct Clock {
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double s() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+};
+
+template <typename T>
+int grow(dgx_ctx *c, size_t elems) {
+  if constexpr (sizeof(T) == 8) {
+    if (c->kry64_elems >= elems) return 0;
+    if (c->kry64) cudaFree(c->kry64);
+    c->kry64 = nullptr;
+    c->kry64_elems = 0;
+    if (int e = check_cuda(c, cudaMalloc(&c->kry64, elems * sizeof(double)), "cudaMalloc Krylov")) return e;
+    c->kry64_elems = elems;
+  } else {
+    if (c->kry32_elems >= elems) return 0;
+    if (c->kry32) cudaFree(c->kry32);
+    c->kry32 = nullptr;
+    c->kry32_elems = 0;
+    if (int e = check_cuda(c, cudaMalloc(&c->kry32, elems * sizeof(float)), "cudaMalloc Krylov")) return e;
+    c->kry32_elems = elems;
+  }
+  return 0;
+}
+
+// Read `count` reduced scalars from the device.
+int fetch(dgx_ctx *c, int count) {
+  if (int e = check_cuda(c, cudaMemcpyAsync(c->host_red, c->red_out, count * sizeof(double),
+                                            cudaMemcpyDeviceToHost, c->stream), "memcpy")) return e;
+  return check_cuda(c, cudaStreamSynchronize(c->stream), "sync");
+}
+
+double dev_norm(dgx_ctx *c, long long n, const double *x, int *err) {
+  vec_dot<double>(n, x, x, c->red, c->red_out, c->stream);
+  *err = fetch(c, 1);
+  return std::sqrt(c->host_red[0]);
+}
+
+// Givens-rotation least squares of Saad's GMRES on a host Hessenberg matrix.
+struct Hess {
+  int m;
+  std::vector<double> H, cs, sn, g, y;
+  explicit Hess(int m_) : m(m_), H((m_ + 1) * m_, 0.0), cs(m_), sn(m_), g(m_ + 1), y(m_) {}
+  double &h(int i, int j) { return H[i * m + j]; }
+  // new column j holds h(0..j+1, j); returns |residual estimate|
+  double add_column(int j) {
+    for (int i = 0; i < j; ++i) {
+      const double a = h(i, j), b = h(i + 1, j);
+      h(i, j) = cs[i] * a + sn[i] * b;
+      h(i + 1, j) = -sn[i] * a + cs[i] * b;
+    }
+    const double a = h(j, j), b = h(j + 1, j);
+    const double r = std::hypot(a, b);
+    cs[j] = r == 0.0 ? 1.0 : a / r;
+    sn[j] = r == 0.0 ? 0.0 : b / r;
+    h(j, j) = r;
+    h(j + 1, j) = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    return std::fabs(g[j + 1]);
+  }
+  void solve(int k) {
+    for (int i = k - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int l = i + 1; l < k; ++l) s -= h(i, l) * y[l];
+      y[i] = s / h(i, i);
+    }
+  }
+};
+
+// One Arnoldi step on the basis V (columns 0..j) with w = S z_j already in
+// `w`: classical Gram-Schmidt twice.  Fills H column j, normalises V_{j+1}.
+// Returns hn (the subdiagonal) or NaN on error (err set).
+template <typename T>
+double arnoldi(dgx_ctx *c, long long N, int j, T *V, T *w, Hess &H, int *err) {
+  double *h1 = c->red_out, *h2 = c->red_out + 64, *nrm = c->red_out + 128;
+  vec_mdot<T>(N, j + 1, V, N, w, c->red, h1, c->stream);
+  vec_mupdate<T>(N, j + 1, V, N, h1, w, c->red, nullptr, c->stream);
+  vec_mdot<T>(N, j + 1, V, N, w, c->red, h2, c->stream);
+  vec_mupdate<T>(N, j + 1, V, N, h2, w, c->red, nrm, c->stream);
+  *err = fetch(c, 129);
+  if (*err) return NAN;
+  for (int i = 0; i <= j; ++i) H.h(i, j) = c->host_red[i] + c->host_red[64 + i];
+  const double hn = std::sqrt(c->host_red[128]);
+  H.h(j + 1, j) = hn;
+  return hn;
+}
+
+// Inner FP32 GMRES (single cycle of up to `maxit` iterations, zero initial
+// guess, right Jacobi preconditioning): z32 ~= S32^-1 v32.
+int inner_gmres32(dgx_ctx *c, const float *v, float *z, const float *dinv, int maxit, double tol, int *its) {
+  const long long N = c->N;
+  const int m = std::max(1, std::min(maxit, 64));
+  float *Vb = c->kry32, *w = Vb + (size_t)(m + 1) * N, *u = w + N;
+  Hess H(m);
+  int err = 0;
+  vec_dot<float>(N, v, v, c->red, c->red_out, c->stream);
+  if ((err = fetch(c, 1))) return err;
+  const double beta = std::sqrt(c->host_red[0]);
+  *its = 0;
+  if (!(beta > 0.0)) {
+    cudaMemsetAsync(z, 0, N * sizeof(float), c->stream);
+    return std::isnan(beta) ? set_error(c, DGX_ERR_BREAKDOWN, "inner GMRES: NaN right-hand side") : 0;
+  }
+  vec_scale_by_inv_sqrt<float>(N, c->red_out, v, Vb, c->stream);
+  H.g.assign(m + 1, 0.0);
+  H.g[0] = beta;
+  int jj = 0;
+  for (int j = 0; j < m; ++j) {
+    vec_mul<float>(N, dinv, Vb + (size_t)j * N, u, c->stream);
+    if ((err = apply_S<float>(c, u, w))) return err;
+    const double hn = arnoldi<float>(c, N, j, Vb, w, H, &err);
+    if (err) return err;
+    if (std::isnan(hn)) return set_error(c, DGX_ERR_BREAKDOWN, "inner GMRES: NaN in Arnoldi");
+    const double res = H.add_column(j);
+    jj = j + 1;
+    ++*its;
+    if (hn <= 1e-300 || res <= tol * beta) break;
+    vec_scale_by_inv_sqrt<float>(N, c->red_out + 128, w, Vb + (size_t)(j + 1) * N, c->stream);
+  }
+  H.solve(jj);
+  // z = dinv .* (V y)
+  if ((err = check_cuda(c, cudaMemcpyAsync(c->red_out + 192, H.y.data(), jj * sizeof(double),
+                                           cudaMemcpyHostToDevice, c->stream), "memcpy"))) return err;
+  cudaMemsetAsync(u, 0, N * sizeof(float), c->stream);
+  vec_lincomb<float, float>(N, jj, Vb, N, c->red_out + 192, u, c->stream);
+  vec_mul<float>(N, dinv, u, z, c->stream);
+  // H.y lives on the host stack frame: make sure the copy finished before returning
+  return check_cuda(c, cudaStreamSynchronize(c->stream), "sync");
+}
+
+// Flexible GMRES(m) in FP64 (Saad), right preconditioned.  pc_kind selects
+// the Jacobi diagonal; mixed = FP32 GMRES preconditioner.
+int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dgx_solve_info &info) {
+  const long long N = c->N;
+  const int m = std::max(1, std::min(o.restart, 64));
+  const bool mixed = o.method == DGX_SOLVER_MIXED;
+  if (int e = grow<double>(c, (size_t)(2 * m + 3) * N)) return e;
+  if (mixed) {
+    const int mi = std::max(1, std::min(o.inner_maxit, 64));
+    if (int e = grow<float>(c, (size_t)(mi + 4) * N)) return e;
+  }
+  double *Vb = c->kry64, *Zb = Vb + (size_t)(m + 1) * N, *w = Zb + (size_t)m * N;
+  const double *dinv = o.pc == DGX_PC_NONE ? nullptr : c->dinv64[o.pc];
+  const float *dinv32 = o.pc == DGX_PC_NONE ? nullptr : c->dinv32[o.pc];
+  // FP32 right-hand side / solution of the inner solve, after the inner basis (V, w, u)
+  float *io32 = mixed ? c->kry32 + (size_t)(std::max(1, std::min(o.inner_maxit, 64)) + 3) * N : nullptr;
+  if (mixed && !dinv32) return set_error(c, DGX_ERR_ARG, "mixed solver needs a Jacobi preconditioner");
+  int err = 0;
+  const double bn = dev_norm(c, N, b, &err);
+  if (err) return err;
+  if (std::isnan(bn)) return set_error(c, DGX_ERR_BREAKDOWN, "NaN in right-hand side");
+  if (!o.use_x0) cudaMemsetAsync(x, 0, N * sizeof(double), c->stream);
+  if (bn == 0.0) {
+    cudaMemsetAsync(x, 0, N * sizeof(double), c->stream);
+    info.relres = 0.0;
+    info.status = DGX_OK;
+    return 0;
+  }
+  Hess H(m);
+  int its = 0;
+  for (;;) {
+    if ((err = apply_S<double>(c, x, w))) return err;
+    ++info.operator_f64;
+    vec_axpby<double>(N, 1.0, b, -1.0, w, c->stream);  // w = b - S x
+    const double beta = dev_norm(c, N, w, &err);
+    if (err) return err;
+    info.relres = beta / bn;
+    if (std::isnan(beta)) return set_error(c, DGX_ERR_BREAKDOWN, "NaN residual");
+    if (info.relres <= o.tol) {
+      info.status = DGX_OK;
+      break;
+    }
+    if (its >= o.maxit) {
+      info.status = DGX_NOT_CONVERGED;
+      break;
+    }
+    vec_scale_by_inv_sqrt<double>(N, c->red_out, w, Vb, c->stream);
+    std::fill(H.g.begin(), H.g.end(), 0.0);
+    H.g[0] = beta;
+    int jj = 0;
+    for (int j = 0; j < m; ++j) {
+      double *vj = Vb + (size_t)j * N, *zj = Zb + (size_t)j * N;
+      if (mixed) {
+        // z_j ~= S^-1 v_j by FP32 GMRES on the FP32 operator and diagonal
+        vec_convert<float, double>(N, vj, io32, c->stream);
+        int iits = 0;
+        if ((err = inner_gmres32(c, io32, io32, dinv32, o.inner_maxit, o.inner_tol, &iits))) return err;
+        info.inner_iterations += iits;
+        info.operator_f32 += iits;
+        vec_convert<double, float>(N, io32, zj, c->stream);
+      } else if (dinv) {
+        vec_mul<double>(N, dinv, vj, zj, c->stream);
+      } else {
+        cudaMemcpyAsync(zj, vj, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+      }
+      if ((err = apply_S<double>(c, zj, w))) return err;
+      ++info.operator_f64;
+      const double hn = arnoldi<double>(c, N, j, Vb, w, H, &err);
+      if (err) return err;
+      if (std::isnan(hn)) return set_error(c, DGX_ERR_BREAKDOWN, "NaN in Arnoldi");
+      const double res = H.add_column(j);
+      ++its;
+      jj = j + 1;
+      if (hn <= 1e-300) break;  // happy breakdown
+      vec_scale_by_inv_sqrt<double>(N, c->red_out + 128, w, Vb + (size_t)(j + 1) * N, c->stream);
+      if (res <= o.tol * bn || its >= o.maxit) break;
+    }
+    H.solve(jj);
+    for (int k = 0; k < jj; ++k)
+      if (std::isnan(H.y[k])) return set_error(c, DGX_ERR_BREAKDOWN, "NaN in least-squares solution");
+    if ((err = check_cuda(c, cudaMemcpyAsync(c->red_out + 192, H.y.data(), jj * sizeof(double),
+                                             cudaMemcpyHostToDevice, c->stream), "memcpy"))) return err;
+    vec_lincomb<double, double>(N, jj, Zb, N, c->red_out + 192, x, c->stream);
+    if ((err = check_cuda(c, cudaStreamSynchronize(c->stream), "sync"))) return err;
+  }
+  info.iterations = its;
+  return 0;
+}
+
+// Preconditioned CG in FP64 (S symmetric positive definite).
+int cg64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dgx_solve_info &info) {
+  const long long N = c->N;
+  if (int e = grow<double>(c, (size_t)4 * N)) return e;
+  double *r = c->kry64, *z = r + N, *p = z + N, *q = p + N;
+  const double *dinv = o.pc == DGX_PC_NONE ? nullptr : c->dinv64[o.pc];
+  int err = 0;
+  double bn = dev_norm(c, N, b, &err);
+  if (err) return err;
+  if (!o.use_x0) cudaMemsetAsync(x, 0, N * sizeof(double), c->stream);
+  if (bn == 0.0) bn = 1.0;
+  if ((err = apply_S<double>(c, x, q))) return err;
+  ++info.operator_f64;
+  cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  vec_axpby<double>(N, -1.0, q, 1.0, r, c->stream);
+  auto precond = [&](const double *in, double *out) {
+    if (dinv) vec_mul<double>(N, dinv, in, out, c->stream);
+    else cudaMemcpyAsync(out, in, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  };
+  precond(r, z);
+  cudaMemcpyAsync(p, z, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  vec_dot<double>(N, r, z, c->red, c->red_out, c->stream);
+  vec_dot<double>(N, r, r, c->red, c->red_out + 1, c->stream);
+  if ((err = fetch(c, 2))) return err;
+  double rz = c->host_red[0];
+  info.relres = std::sqrt(c->host_red[1]) / bn;
+  int its = 0;
+  info.status = info.relres <= o.tol ? DGX_OK : DGX_NOT_CONVERGED;
+  while (info.status != DGX_OK && its < o.maxit) {
+    if ((err = apply_S<double>(c, p, q))) return err;
+    ++info.operator_f64;
+    vec_dot<double>(N, p, q, c->red, c->red_out, c->stream);
+    if ((err = fetch(c, 1))) return err;
+    const double pq = c->host_red[0];
+    if (!(pq > 0.0)) return set_error(c, DGX_ERR_BREAKDOWN, "CG: p^T S p = %g (not SPD or NaN)", pq);
+    const double a = rz / pq;
+    vec_axpby<double>(N, a, p, 1.0, x, c->stream);
+    vec_axpby<double>(N, -a, q, 1.0, r, c->stream);
+    ++its;
+    precond(r, z);
+    vec_dot<double>(N, r, z, c->red, c->red_out, c->stream);
+    vec_dot<double>(N, r, r, c->red, c->red_out + 1, c->stream);
+    if ((err = fetch(c, 2))) return err;
+    const double rz2 = c->host_red[0];
+    info.relres = std::sqrt(c->host_red[1]) / bn;
+    if (std::isnan(info.relres)) return set_error(c, DGX_ERR_BREAKDOWN, "CG: NaN residual");
+    if (info.relres <= o.tol) {
+      info.status = DGX_OK;
+      break;
+    }
+    vec_axpby<double>(N, 1.0, z, rz2 / rz, p, c->stream);  // p = z + beta p
+    rz = rz2;
+  }
+  info.iterations = its;
+  return 0;
+}
+
+}  // namespace
+}  // namespace dgx
+
+using namespace dgx;
+
+extern "C" {
+
+int dgx_create(dgx_ctx **out, int device, void *stream) {
+  if (!out) return DGX_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return DGX_ERR_CUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return DGX_ERR_CUDA;
+  dgx_ctx *c = new dgx_ctx();
+  c->device = device;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  if (ensure_red(c)) {
+    delete c;
+    return DGX_ERR_OOM;
+  }
+  *out = c;
+  return DGX_OK;
+}
+
+void dgx_destroy(dgx_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  free_mesh(c);
+  if (c->red) cudaFree(c->red);
+  if (c->red_out) cudaFree(c->red_out);
+  if (c->host_red) cudaFreeHost(c->host_red);
+  delete c;
+}
+
+const char *dgx_last_error(const dgx_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+void dgx_default_solve_opts(dgx_solve_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->method = DGX_SOLVER_FGMRES;
+  o->pc = DGX_PC_HELMHOLTZ;
+  o->restart = 30;
+  o->maxit = 1000;
+  o->tol = 1e-8;
+  o->inner_restart = 30;
+  o->inner_maxit = 30;
+  o->inner_tol = 1e-4;
+  o->use_x0 = 0;
+}
+
+int dgx_mesh_build(dgx_ctx *c, const dgx_mesh_desc *d) {
+  if (!c || !d) return DGX_ERR_ARG;
+  const int r = d->degree;
+  if (r < 1 || r > kMaxDegree) return set_error(c, DGX_ERR_ARG, "degree %d outside 1..%d", r, kMaxDegree);
+  if (d->nx < 1 || d->ny < 1 || d->nz < 1) return set_error(c, DGX_ERR_ARG, "mesh extents must be >= 1");
+  if (!(d->Lx > 0 && d->Ly > 0 && d->Lz > 0)) return set_error(c, DGX_ERR_ARG, "domain lengths must be > 0");
+  if (d->n_q != 0 && d->n_q != 2 * r + 1)
+    return set_error(c, DGX_ERR_ARG, "n_q must be 0 or 2r+1 = %d (consistent integration)", 2 * r + 1);
+  if (d->terrain < 0 || d->terrain > 2) return set_error(c, DGX_ERR_ARG, "terrain kind %d", d->terrain);
+  if (d->terrain > 0 && !(d->a_c > 0)) return set_error(c, DGX_ERR_ARG, "terrain half-width a_c must be > 0");
+  if (d->bc_lateral < 0 || d->bc_lateral > 1) return set_error(c, DGX_ERR_ARG, "bc_lateral %d", d->bc_lateral);
+  const long long ncell = (long long)d->nx * d->ny * d->nz;
+  if (ncell > 2000000000LL) return set_error(c, DGX_ERR_ARG, "too many cells");
+  if (cudaSetDevice(c->device) != cudaSuccess) return set_error(c, DGX_ERR_CUDA, "cudaSetDevice");
+  cudaStreamSynchronize(c->stream);
+  free_mesh(c);
+  c->mesh = *d;
+  c->mesh.n_q = 2 * r + 1;
+  c->n = r + 1;
+  c->q = 2 * r + 1;
+  c->ncell = ncell;
+  c->N = ncell * c->n * c->n * c->n;
+  c->curved = d->terrain != 0;
+  Tables1D T;
+  if (!make_tables(r, T)) return set_error(c, DGX_ERR_ARG, "table construction failed");
+  const int N = c->n, Q = c->q;
+  int e;
+  if ((e = dalloc(c, &c->tab64, T.tab.size())) || (e = dalloc(c, &c->tab32, T.tab.size()))) return e;
+  std::vector<float> t32(T.tab.begin(), T.tab.end());
+  cudaMemcpy(c->tab64, T.tab.data(), T.tab.size() * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->tab32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (c->curved) {
+    const int CS = col_size(N, Q);
+    const long long ncol = (long long)d->nx * d->ny;
+    std::vector<double> col((size_t)ncol * CS);
+    Lagrange L(T.gll);
+    std::vector<double> lq(Q * N), dq(Q * N), la(N * N), l0(N), l1(N);
+    for (int q = 0; q < Q; ++q) L.eval(T.gq[q], &lq[q * N], &dq[q * N]);
+    for (int q = 0; q < N; ++q) L.eval(T.ga[q], &la[q * N], nullptr);
+    const double dx = d->Lx / d->nx, dy = d->Ly / d->ny;
+    std::vector<double> hn(N * N);
+    for (long long cy = 0; cy < d->ny; ++cy)
+      for (long long cx = 0; cx < d->nx; ++cx) {
+        for (int b = 0; b < N; ++b)
+          for (int a = 0; a < N; ++a) hn[a + N * b] = terrain_h(*d, (cx + T.gll[a]) * dx, (cy + T.gll[b]) * dy);
+        double *cp = &col[(size_t)(cx + d->nx * cy) * CS];
+        for (int j = 0; j < Q; ++j)
+          for (int i = 0; i < Q; ++i) {
+            double h = 0, h1 = 0, h2 = 0;
+            for (int b = 0; b < N; ++b)
+              for (int a = 0; a < N; ++a) {
+                const double v = hn[a + N * b];
+                h += lq[i * N + a] * lq[j * N + b] * v;
+                h1 += dq[i * N + a] * lq[j * N + b] * v;
+                h2 += lq[i * N + a] * dq[j * N + b] * v;
+              }
+            cp[col_off_hq(N, Q) + i + Q * j] = h;
+            cp[col_off_h1q(N, Q) + i + Q * j] = h1;
+            cp[col_off_h2q(N, Q) + i + Q * j] = h2;
+          }
+        for (int s = 0; s < 2; ++s)
+          for (int j = 0; j < Q; ++j) {
+            double hx = 0, hy = 0;
+            const int e0 = s ? N - 1 : 0;
+            for (int m = 0; m < N; ++m) {
+              hx += lq[j * N + m] * hn[e0 + N * m];
+              hy += lq[j * N + m] * hn[m + N * e0];
+            }
+            cp[col_off_hx(N, Q, s) + j] = hx;
+            cp[col_off_hy(N, Q, s) + j] = hy;
+          }
+        for (int j = 0; j < N; ++j)
+          for (int i = 0; i < N; ++i) {
+            double h = 0;
+            for (int b = 0; b < N; ++b)
+              for (int a = 0; a < N; ++a) h += la[i * N + a] * la[j * N + b] * hn[a + N * b];
+            cp[col_off_hqa(N, Q) + i + N * j] = h;
+          }
+      }
+    // each column must keep positive cell heights: h < Lz at every point
+    for (long long i = 0; i < ncol; ++i)
+      for (int k = 0; k < Q * Q; ++k)
+        if (col[(size_t)i * CS + k] >= d->Lz) return set_error(c, DGX_ERR_ARG, "terrain reaches the model top");
+    std::vector<float> c32(col.begin(), col.end());
+    if ((e = dalloc(c, &c->col64, col.size())) || (e = dalloc(c, &c->col32, col.size()))) return e;
+    cudaMemcpy(c->col64, col.data(), col.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->col32, c32.data(), c32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  const size_t Nn = (size_t)c->N;
+  if ((e = dalloc(c, &c->V64, 3 * Nn)) || (e = dalloc(c, &c->V32, 3 * Nn)) || (e = dalloc(c, &c->rho64, Nn)) ||
+      (e = dalloc(c, &c->pk64, Nn)) || (e = dalloc(c, &c->rho32, Nn)) || (e = dalloc(c, &c->pk32, Nn)))
+    return e;
+  for (int k = 1; k < 3; ++k)
+    if ((e = dalloc(c, &c->diag64[k], Nn)) || (e = dalloc(c, &c->dinv64[k], Nn)) || (e = dalloc(c, &c->dinv32[k], Nn)))
+      return e;
+  if ((e = check_cuda(c, cudaDeviceSynchronize(), "mesh upload"))) return e;
+  c->has_mesh = true;
+  return DGX_OK;
+}
+
+long long dgx_num_dofs(const dgx_ctx *c) { return (c && c->has_mesh) ? c->N : -1; }
+
+int dgx_node_coords(dgx_ctx *c, double *X) {
+  if (int e = check_ready(c, false)) return e;
+  if (!X) return set_error(c, DGX_ERR_ARG, "null output");
+  count_launch();
+  k_node_coords<<<grid_for(c->N), 256, 0, c->stream>>>(node_params(c), c->N, X);
+  return check_cuda(c, cudaGetLastError(), "k_node_coords");
+}
+
+int dgx_set_background(dgx_ctx *c, const dgx_background *bg) {
+  if (int e = check_ready(c, false)) return e;
+  if (!bg || bg->kind < 0 || bg->kind > 1 || !(bg->R > 0) || !(bg->T > 0) || !(bg->p0 > 0) || !(bg->gamma > 1))
+    return set_error(c, DGX_ERR_ARG, "invalid background");
+  if (bg->kind == 1 && !(bg->N_bv > 0)) return set_error(c, DGX_ERR_ARG, "stratified background needs N_bv > 0");
+  int e;
+  if (!c->rho_bar) {
+    if ((e = dalloc(c, &c->rho_bar, c->N)) || (e = dalloc(c, &c->p_bar, c->N))) return e;
+  }
+  double *X = c->V64;  // 3N scratch
+  count_launch();
+  k_node_coords<<<grid_for(c->N), 256, 0, c->stream>>>(node_params(c), c->N, X);
+  BgP b{bg->kind, bg->T, bg->p0, bg->N_bv, bg->R, bg->gamma, bg->g};
+  count_launch();
+  k_background<<<grid_for(c->N), 256, 0, c->stream>>>(b, c->N, X, c->rho_bar, c->p_bar);
+  if ((e = check_cuda(c, cudaGetLastError(), "k_background"))) return e;
+  c->bg = *bg;
+  c->has_bg = true;
+  return DGX_OK;
+}
+
+int dgx_background_fields(dgx_ctx *c, double *rho_bar, double *p_bar) {
+  if (int e = check_ready(c, false)) return e;
+  if (!c->has_bg) return set_error(c, DGX_ERR_STATE, "no background (call dgx_set_background)");
+  if (rho_bar) cudaMemcpyAsync(rho_bar, c->rho_bar, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  if (p_bar) cudaMemcpyAsync(p_bar, c->p_bar, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  return check_cuda(c, cudaGetLastError(), "background copy");
+}
+
+int dgx_set_coefficients(dgx_ctx *c, const double *rho, const double *pk, double a_dt, double gamma) {
+  if (int e = check_ready(c, false)) return e;
+  if (!rho || !pk) return set_error(c, DGX_ERR_ARG, "null coefficient field");
+  if (!(gamma > 1.0) || !(a_dt >= 0.0)) return set_error(c, DGX_ERR_ARG, "need gamma > 1 and a_dt >= 0");
+  const long long N = c->N;
+  cudaMemcpyAsync(c->rho64, rho, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(c->pk64, pk, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  vec_convert<float, double>(N, rho, c->rho32, c->stream);
+  vec_convert<float, double>(N, pk, c->pk32, c->stream);
+  c->alpha = a_dt;
+  c->gamma = gamma;
+  if (int e = launch_diag(c, c->rho64, c->pk64, c->diag64[DGX_PC_HELMHOLTZ], c->diag64[DGX_PC_INTERNAL_ENERGY],
+                          c->stream))
+    return e;
+  for (int k = 1; k < 3; ++k) vec_inv(N, c->diag64[k], c->dinv64[k], c->dinv32[k], c->stream);
+  if (int e = check_cuda(c, cudaGetLastError(), "set_coefficients")) return e;
+  c->has_coef = true;
+  return DGX_OK;
+}
+
+int dgx_apply_operator(dgx_ctx *c, int prec, const void *x, void *y) {
+  if (int e = check_ready(c, true)) return e;
+  if (!x || !y || x == y) return set_error(c, DGX_ERR_ARG, "x, y must be distinct non-null arrays");
+  if (prec == DGX_F64) return apply_S<double>(c, (const double *)x, (double *)y);
+  if (prec == DGX_F32) return apply_S<float>(c, (const float *)x, (float *)y);
+  return set_error(c, DGX_ERR_ARG, "precision %d", prec);
+}
+
+int dgx_apply_grad(dgx_ctx *c, int prec, const void *p, void *V) {
+  if (int e = check_ready(c, true)) return e;
+  if (!p || !V) return set_error(c, DGX_ERR_ARG, "null array");
+  if (prec == DGX_F64) return launch_grad<double>(c, (const double *)p, c->rho64, (double *)V, c->stream);
+  if (prec == DGX_F32) return launch_grad<float>(c, (const float *)p, c->rho32, (float *)V, c->stream);
+  return set_error(c, DGX_ERR_ARG, "precision %d", prec);
+}
+
+int dgx_apply_div(dgx_ctx *c, int prec, const void *V, const void *p, void *y) {
+  if (int e = check_ready(c, true)) return e;
+  if (!p || !V || !y) return set_error(c, DGX_ERR_ARG, "null array");
+  if (prec == DGX_F64) return launch_div<double>(c, (const double *)V, (const double *)p, c->pk64, (double *)y, c->stream);
+  if (prec == DGX_F32) return launch_div<float>(c, (const float *)V, (const float *)p, c->pk32, (float *)y, c->stream);
+  return set_error(c, DGX_ERR_ARG, "precision %d", prec);
+}
+
+int dgx_apply_mass_inverse(dgx_ctx *c, int prec, const void *in, void *out) {
+  if (int e = check_ready(c, true)) return e;
+  if (!in || !out) return set_error(c, DGX_ERR_ARG, "null array");
+  if (prec == DGX_F64) return launch_mass_inverse<double>(c, (const double *)in, c->rho64, (double *)out, c->stream);
+  if (prec == DGX_F32) return launch_mass_inverse<float>(c, (const float *)in, c->rho32, (float *)out, c->stream);
+  return set_error(c, DGX_ERR_ARG, "precision %d", prec);
+}
+
+int dgx_apply_preconditioner(dgx_ctx *c, int pc, int prec, const void *x, void *y) {
+  if (int e = check_ready(c, true)) return e;
+  if (!x || !y) return set_error(c, DGX_ERR_ARG, "null array");
+  if (pc < 0 || pc > 2) return set_error(c, DGX_ERR_ARG, "preconditioner %d", pc);
+  const long long N = c->N;
+  if (prec == DGX_F64) {
+    if (pc == DGX_PC_NONE) cudaMemcpyAsync(y, x, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    else vec_mul<double>(N, c->dinv64[pc], (const double *)x, (double *)y, c->stream);
+  } else if (prec == DGX_F32) {
+    if (pc == DGX_PC_NONE) cudaMemcpyAsync(y, x, N * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+    else vec_mul<float>(N, c->dinv32[pc], (const float *)x, (float *)y, c->stream);
+  } else {
+    return set_error(c, DGX_ERR_ARG, "precision %d", prec);
+  }
+  return check_cuda(c, cudaGetLastError(), "apply_preconditioner");
+}
+
+int dgx_preconditioner_diagonal(dgx_ctx *c, int pc, double *d) {
+  if (int e = check_ready(c, true)) return e;
+  if (pc != DGX_PC_HELMHOLTZ && pc != DGX_PC_INTERNAL_ENERGY) return set_error(c, DGX_ERR_ARG, "pc %d", pc);
+  if (!d) return set_error(c, DGX_ERR_ARG, "null array");
+  cudaMemcpyAsync(d, c->diag64[pc], c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  return check_cuda(c, cudaGetLastError(), "diagonal copy");
+}
+
+int dgx_solve_pressure(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts *opts, dgx_solve_info *info) {
+  if (int e = check_ready(c, true)) return e;
+  if (!b || !x || b == x) return set_error(c, DGX_ERR_ARG, "b, x must be distinct non-null arrays");
+  dgx_solve_opts o;
+  if (opts) o = *opts;
+  else dgx_default_solve_opts(&o);
+  if (o.pc < 0 || o.pc > 2) return set_error(c, DGX_ERR_ARG, "preconditioner %d", o.pc);
+  if (o.restart < 1 || o.restart > 64 || o.maxit < 0 || !(o.tol > 0))
+    return set_error(c, DGX_ERR_ARG, "need 1 <= restart <= 64, maxit >= 0, tol > 0");
+  if (o.method == DGX_SOLVER_MIXED && (o.inner_maxit < 1 || o.inner_maxit > 64 || !(o.inner_tol > 0)))
+    return set_error(c, DGX_ERR_ARG, "need 1 <= inner_maxit <= 64 and inner_tol > 0");
+  dgx_solve_info inf;
+  std::memset(&inf, 0, sizeof(inf));
+  Clock clk;
+  int e;
+  if (o.method == DGX_SOLVER_FGMRES || o.method == DGX_SOLVER_MIXED) e = fgmres64(c, b, x, o, inf);
+  else if (o.method == DGX_SOLVER_CG) e = cg64(c, b, x, o, inf);
+  else return set_error(c, DGX_ERR_ARG, "solver %d", o.method);
+  if (!e) e = check_cuda(c, cudaStreamSynchronize(c->stream), "solve sync");
+  inf.seconds = clk.s();
+  if (info) *info = inf;
+  if (e) return e;
+  return inf.status;
+}
+
+int dgx_operator_cost(const dgx_ctx *c, double *flops_grad, double *flops_div, double *b64) {
+  if (!c || !c->has_mesh) return DGX_ERR_STATE;
+  const double N = c->n, Q = c->q;
+  const double N2 = N * N, N3 = N2 * N, Q2 = Q * Q, Q3 = Q2 * Q;
+  const bool cv = c->curved;
+  // sum-factorisation sweep costs (2 flops per multiply-add)
+  const double fwd = 2 * N * (Q * N2 + Q2 * N + Q3);  // N^3 -> Q^3, one field
+  const double bwd = 2 * Q * (Q2 * N + Q * N2 + N3);  // Q^3 -> N^3, one field
+  const double fface = 2 * N * (Q * N + Q2);           // N^2 -> Q^2
+  const double bface = 2 * Q * (N * Q + N2);           // Q^2 -> N^2
+  const double fast = 2 * N * 3 * N3;                  // one N^3 -> N^3 tensor sweep triple
+  const int nfv = cv ? 5 : 3, nfp = cv ? 10 : 6, nsl = cv ? 32 : 24;
+  const double k1 = fwd + (cv ? 14 : 6) * Q3 + nfv * bwd + 6 * fface + nfp * (4 * Q2 + bface) + fast +
+                    3 * (2 * fast + 6 * N3);
+  const double k2 = 5 * fwd + (cv ? 22 : 14) * Q3 + 4 * bwd + nsl * fface + 6 * (10 * Q2) + 6 * bface;
+  if (flops_grad) *flops_grad = k1 * c->ncell;
+  if (flops_div) *flops_div = k2 * c->ncell;
+  if (b64) *b64 = 32.0 * c->N;
+  return 0;
+}
+
+long long dgx_kernel_launches(void) { return dgx::launch_count(); }
+
+}  // extern "C"

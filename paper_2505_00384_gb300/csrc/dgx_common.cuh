@@ -1,0 +1,174 @@
+// Internal declarations of the dgx library (not part of the C ABI).
+//
+// Discretisation (arXiv:2505.00384, Sec. 2 and 3): nodal DG of degree r on the
+// (r+1)^3 Gauss-Lobatto points of each hexahedron; every volume and face
+// integral uses the consistent Gauss rule with Q = 2r+1 points per direction
+// (Sec. 3.3); the density-weighted velocity mass A is inverted with the
+// r+1 point Gauss rule as S^-T J^-1 S^-1 (Sec. 3.3).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dgx.h"
+
+namespace dgx {
+
+constexpr int kMaxDegree = 6;  // r = 1..6, N = r+1 <= 7, Q = 2r+1 <= 13
+
+// ---------------------------------------------------------------- 1D tables
+// Layout of the per-degree table block (element type T), N = r+1, Q = 2r+1:
+//   I  [Q][N]  l_a(g_q)              D  [Q][N]  l_a'(g_q)
+//   IT [N][Q]  transpose of I        DT [N][Q]  transpose of D
+//   Ia [N][N]  l_a(ga_q)  (r+1 point Gauss rule of the fast inverse)
+//   P  [N][N]  Ia^-1 stored [a][q]   PT [N][N]  its transpose [q][a]
+//   IIT[N][Q]  l_a(g_q)^2            DDT[N][Q]  l_a'(g_q)^2     IDT[N][Q] l_a l_a'
+//   wq [Q]     Gauss weights on [0,1]   wa [N]  weights of the fast rule
+//   gq [Q]     Gauss points on [0,1]
+__host__ __device__ constexpr int tab_off_I(int, int) { return 0; }
+__host__ __device__ constexpr int tab_off_D(int N, int Q) { return Q * N; }
+__host__ __device__ constexpr int tab_off_IT(int N, int Q) { return 2 * Q * N; }
+__host__ __device__ constexpr int tab_off_DT(int N, int Q) { return 3 * Q * N; }
+__host__ __device__ constexpr int tab_off_Ia(int N, int Q) { return 4 * Q * N; }
+__host__ __device__ constexpr int tab_off_P(int N, int Q) { return 4 * Q * N + N * N; }
+__host__ __device__ constexpr int tab_off_PT(int N, int Q) { return 4 * Q * N + 2 * N * N; }
+__host__ __device__ constexpr int tab_off_IIT(int N, int Q) { return 4 * Q * N + 3 * N * N; }
+__host__ __device__ constexpr int tab_off_DDT(int N, int Q) { return 5 * Q * N + 3 * N * N; }
+__host__ __device__ constexpr int tab_off_IDT(int N, int Q) { return 6 * Q * N + 3 * N * N; }
+__host__ __device__ constexpr int tab_off_wq(int N, int Q) { return 7 * Q * N + 3 * N * N; }
+__host__ __device__ constexpr int tab_off_wa(int N, int Q) { return 7 * Q * N + 3 * N * N + Q; }
+__host__ __device__ constexpr int tab_off_gq(int N, int Q) { return 7 * Q * N + 3 * N * N + Q + N; }
+__host__ __device__ constexpr int tab_size(int N, int Q) { return 7 * Q * N + 3 * N * N + 2 * Q + N; }
+
+// Per-column terrain table (curved meshes).  For column (cx, cy) the bottom
+// height h is interpolated from its values at the column's (r+1)^2 GLL
+// nodes; with z = zeta + h (1 - zeta/H) the Jacobian only needs h and its
+// reference derivatives h1 = dh/dxi1, h2 = dh/dxi2:
+//   hq, h1q, h2q [Q*Q]  at (g_i, g_j), index i + Q j
+//   hx0, hx1     [Q]    h at xi1 = 0 / 1 along xi2 = g_j   (x faces)
+//   hy0, hy1     [Q]    h at xi2 = 0 / 1 along xi1 = g_i   (y faces)
+//   hqa          [N*N]  h at the fast-rule points (ga_i, ga_j)
+__host__ __device__ constexpr int col_off_hq(int, int) { return 0; }
+__host__ __device__ constexpr int col_off_h1q(int, int Q) { return Q * Q; }
+__host__ __device__ constexpr int col_off_h2q(int, int Q) { return 2 * Q * Q; }
+__host__ __device__ constexpr int col_off_hx(int, int Q, int s) { return 3 * Q * Q + s * Q; }
+__host__ __device__ constexpr int col_off_hy(int, int Q, int s) { return 3 * Q * Q + 2 * Q + s * Q; }
+__host__ __device__ constexpr int col_off_hqa(int, int Q) { return 3 * Q * Q + 4 * Q; }
+__host__ __device__ constexpr int col_size(int N, int Q) { return 3 * Q * Q + 4 * Q + N * N; }
+
+// Kernel parameters of the pressure operator.
+template <typename T>
+struct OpP {
+  int nx, ny, nz, bc_lat;  // bc_lat: 0 slip wall, 1 far field (transmissive)
+  T dx, dy, dz, H;         // cell sizes (dz of the uniform zeta grid) and Lz
+  T alpha;                 // a~_ll * dt
+  T gfac;                  // gamma / (gamma - 1)
+  T igm1;                  // 1 / (gamma - 1)
+  const T *tab;            // 1D tables of this degree
+  const T *col;            // per-column terrain tables (nullptr when flat)
+};
+
+// ---------------------------------------------------------------- context
+struct Buf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace dgx
+
+struct dgx_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+
+  // mesh
+  bool has_mesh = false;
+  dgx_mesh_desc mesh{};
+  int n = 0, q = 0;
+  long long ncell = 0, N = 0;
+  bool curved = false;
+  double *tab64 = nullptr;
+  float *tab32 = nullptr;
+  double *col64 = nullptr;
+  float *col32 = nullptr;
+
+  // background
+  bool has_bg = false;
+  dgx_background bg{};
+  double *rho_bar = nullptr, *p_bar = nullptr;
+
+  // coefficients of the current fixed-point iterate
+  bool has_coef = false;
+  double alpha = 0.0, gamma = 1.4;
+  double *rho64 = nullptr, *pk64 = nullptr;
+  float *rho32 = nullptr, *pk32 = nullptr;
+  double *diag64[3] = {nullptr, nullptr, nullptr};  // index DGX_PC_*: diagonal
+  double *dinv64[3] = {nullptr, nullptr, nullptr};  // inverse diagonal
+  float *dinv32[3] = {nullptr, nullptr, nullptr};
+
+  // operator scratch: V = A^-1 B p (3N)
+  double *V64 = nullptr;
+  float *V32 = nullptr;
+
+  // Krylov workspace (grown on demand)
+  double *kry64 = nullptr;
+  size_t kry64_elems = 0;
+  float *kry32 = nullptr;
+  size_t kry32_elems = 0;
+  double *red = nullptr;       // reduction partials
+  double *red_out = nullptr;   // reduced scalars (device)
+  double *host_red = nullptr;  // pinned host mirror
+  size_t red_elems = 0;
+
+  std::vector<void *> owned;  // everything cudaMalloc'd for the mesh
+};
+
+namespace dgx {
+
+int set_error(dgx_ctx *c, int code, const char *fmt, ...);
+// process-wide count of kernel launches made by the library
+void count_launch(int n = 1);
+long long launch_count();
+int check_cuda(dgx_ctx *c, cudaError_t e, const char *what);
+
+// operator kernels (dgx_operator.cu)
+template <typename T>
+int launch_grad(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s);
+template <typename T>
+int launch_div(dgx_ctx *c, const T *V, const T *p, const T *pk, T *y, cudaStream_t s);
+template <typename T>
+int launch_mass_inverse(dgx_ctx *c, const T *in, const T *rho, T *out, cudaStream_t s);
+int launch_diag(dgx_ctx *c, const double *rho, const double *pk, double *dh, double *die, cudaStream_t s);
+template <typename T>
+OpP<T> make_params(const dgx_ctx *c);
+
+// vector kernels (dgx_vector.cu)
+template <typename T>
+void vec_axpby(long long n, double a, const T *x, double b, T *y, cudaStream_t s);
+template <typename T>
+void vec_mul(long long n, const T *a, const T *x, T *y, cudaStream_t s);  // y = a .* x
+template <typename TO, typename TI>
+void vec_convert(long long n, const TI *x, TO *y, cudaStream_t s);
+void vec_inv(long long n, const double *d, double *dinv64, float *dinv32, cudaStream_t s);
+// h[i] = <V_i, w> for i < nv (V_i = V + i*ld), written to out (device doubles)
+template <typename T>
+void vec_mdot(long long n, int nv, const T *V, long long ld, const T *w, double *partial, double *out,
+              cudaStream_t s);
+// w -= sum_i h[i] V_i (h on device); optional: out_norm2 = <w,w> after update
+template <typename T>
+void vec_mupdate(long long n, int nv, const T *V, long long ld, const double *h, T *w, double *partial,
+                 double *out_norm2, cudaStream_t s);
+// y = x * (1 / sqrt(*nrm2)) with the scalar read on the device
+template <typename T>
+void vec_scale_by_inv_sqrt(long long n, const double *nrm2, const T *x, T *y, cudaStream_t s);
+// x += sum_i c[i] Z_i (c on host, passed by value array)
+template <typename T, typename TX>
+void vec_lincomb(long long n, int nv, const T *Z, long long ld, const double *c_dev, TX *x, cudaStream_t s);
+template <typename T>
+void vec_dot(long long n, const T *a, const T *b, double *partial, double *out, cudaStream_t s);
+int vec_partials();  // number of reduction blocks per vector pass
+
+}  // namespace dgx

@@ -1,0 +1,782 @@
+// Matrix-free pressure (Schur) operator of the IMEX-DG scheme, sm_103a.
+//
+// arXiv:2505.00384, Sec. 2: the fixed-point pressure equation
+//   D P + C A^-1 (F - B P) = G,   i.e. S P = (D - C A^-1 B) P,
+// with A the density-weighted velocity mass (Eq. for A^(l)), B the weak
+// pressure gradient, C the weak divergence of the enthalpy flux and D the
+// internal-energy mass.  Sec. 3.3: every integral uses Q = 2r+1 Gauss points
+// per direction; A^-1 = S^-T J^-1 S^-1 with r+1 Gauss points.
+//
+// Kernels (one hexahedral cell per CTA, sum factorisation in shared memory):
+//   k_grad  V = A^-1 B P   (volume weak gradient + central {p} face term +
+//                           fast inverse of the density-weighted mass)
+//   k_div   y = D P - C V  (volume weak divergence of kappa V + central face
+//                           flux + internal-energy mass), kappa = gamma p_k/(gamma-1)
+//   k_minv  out = A^-1 in  (the fast inverse alone)
+//   k_diag  Helmholtz and internal-energy diagonals of Sec. 3.1
+// Readings of the paper's open points (shared with the CPU oracle by
+// definition, not by code): central fluxes; p+ = p- on every boundary face;
+// zero normal flux of kappa V on slip walls, transmissive on far-field faces;
+// Gal-Chen terrain-following map z = zeta + h(x,y) (1 - zeta/H).
+#include <cstdio>
+
+#include "dgx_common.cuh"
+
+namespace dgx {
+namespace {
+
+// One sum-factorisation sweep along direction DIR of `nf` fields stored back
+// to back.  Input field shape (S0, S1, S2), x fastest, with S_DIR == MI; the
+// output replaces that extent by MO.  Field f uses the [MO][MI] row-major
+// matrix selected by bits 2f..2f+1 of `sel`.
+template <typename T, int DIR, int MO, int MI, int S0, int S1, int S2>
+__device__ __forceinline__ void sweep(int nf, unsigned sel, const T *M0, const T *M1, const T *M2,
+                                      const T *__restrict__ in, T *__restrict__ out) {
+  constexpr int O0 = DIR == 0 ? MO : S0;
+  constexpr int O1 = DIR == 1 ? MO : S1;
+  constexpr int O2 = DIR == 2 ? MO : S2;
+  constexpr int OT = O0 * O1 * O2;
+  constexpr int IT = S0 * S1 * S2;
+  const int total = nf * OT;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int f = idx / OT;
+    const int r = idx - f * OT;
+    const int i0 = r % O0;
+    const int i1 = (r / O0) % O1;
+    const int i2 = r / (O0 * O1);
+    const unsigned ms = (sel >> (2 * f)) & 3u;
+    const T *M = ms == 0 ? M0 : (ms == 1 ? M1 : M2);
+    const T *src = in + f * IT;
+    T acc = T(0);
+    if (DIR == 0) {
+      const T *row = M + i0 * MI;
+      const T *s = src + (i2 * S1 + i1) * S0;
+#pragma unroll
+      for (int m = 0; m < MI; ++m) acc += row[m] * s[m];
+    } else if (DIR == 1) {
+      const T *row = M + i1 * MI;
+      const T *s = src + i2 * S1 * S0 + i0;
+#pragma unroll
+      for (int m = 0; m < MI; ++m) acc += row[m] * s[m * S0];
+    } else {
+      const T *row = M + i2 * MI;
+      const T *s = src + i1 * S0 + i0;
+#pragma unroll
+      for (int m = 0; m < MI; ++m) acc += row[m] * s[m * S0 * S1];
+    }
+    out[idx] = acc;
+  }
+}
+
+// Node index of face-local point (t1, t2) on the face normal to direction k at
+// layer e (0 or N-1).  Tangential order: x face (xi2, xi3), y face (xi1, xi3),
+// z face (xi1, xi2).
+template <int N>
+__device__ __forceinline__ int face_node(int k, int e, int t1, int t2) {
+  return k == 0 ? e + N * (t1 + N * t2) : (k == 1 ? t1 + N * (e + N * t2) : t1 + N * (t2 + N * e));
+}
+
+struct CellPos {
+  long long cell;
+  int cx, cy, cz;
+};
+
+template <typename T>
+__device__ __forceinline__ CellPos cell_pos(const OpP<T> &P, long long cell) {
+  CellPos c;
+  c.cell = cell;
+  c.cx = (int)(cell % P.nx);
+  c.cy = (int)((cell / P.nx) % P.ny);
+  c.cz = (int)(cell / ((long long)P.nx * P.ny));
+  return c;
+}
+
+// Neighbour across face f = 2k+s, or -1 on the boundary.
+template <typename T>
+__device__ __forceinline__ long long neighbour(const OpP<T> &P, const CellPos &c, int f) {
+  const int k = f >> 1, s = f & 1;
+  int x = c.cx, y = c.cy, z = c.cz;
+  if (k == 0) {
+    x += s ? 1 : -1;
+    if (x < 0 || x >= P.nx) return -1;
+  } else if (k == 1) {
+    y += s ? 1 : -1;
+    if (y < 0 || y >= P.ny) return -1;
+  } else {
+    z += s ? 1 : -1;
+    if (z < 0 || z >= P.nz) return -1;
+  }
+  return x + (long long)P.nx * (y + (long long)P.ny * z);
+}
+
+template <typename T, int N, int Q>
+__device__ __forceinline__ void load_tables(const T *__restrict__ g, T *s) {
+  constexpr int TS = tab_size(N, Q);
+  for (int i = threadIdx.x; i < TS; i += blockDim.x) s[i] = g[i];
+}
+
+// Outward normal times area element of face f at face Gauss point (i, j)
+// (unweighted).  Curved z faces have all three components; x and y faces
+// stay planar (normal +-e_x, +-e_y) under the Gal-Chen map.
+template <typename T, int N, int Q, bool CURVED>
+__device__ __forceinline__ void face_normal(const OpP<T> &P, const T *colp, T zeta0, int f, int i, int j,
+                                            T nA[3]) {
+  const int k = f >> 1, s = f & 1;
+  const T sg = s ? T(1) : T(-1);
+  nA[0] = nA[1] = nA[2] = T(0);
+  if (k == 0) {
+    T z3 = P.dz;
+    if (CURVED) z3 = P.dz * (T(1) - colp[col_off_hx(N, Q, s) + i] / P.H);
+    nA[0] = sg * P.dy * z3;
+  } else if (k == 1) {
+    T z3 = P.dz;
+    if (CURVED) z3 = P.dz * (T(1) - colp[col_off_hy(N, Q, s) + i] / P.H);
+    nA[1] = sg * P.dx * z3;
+  } else {
+    nA[2] = sg * P.dx * P.dy;
+    if (CURVED) {
+      const T fac = T(1) - (zeta0 + T(s) * P.dz) / P.H;
+      nA[0] = -sg * P.dy * colp[col_off_h1q(N, Q) + i + Q * j] * fac;
+      nA[1] = -sg * P.dx * colp[col_off_h2q(N, Q) + i + Q * j] * fac;
+    }
+  }
+}
+
+// In-block fast inverse of the density-weighted mass for nf fields (N^3 each)
+// in `a` (result left in `a`); rq = rho at the fast-rule points.
+// A^-1 v = P^3 (J^-1 (P^T)^3 v), J_q = rho(x_q) w_q det J(x_q)   (Sec. 3.3).
+template <typename T, int N, int Q, bool CURVED>
+__device__ __forceinline__ void fast_inverse(const OpP<T> &P, const T *tab, const T *colp, const T *rq, int nf,
+                                             T *a, T *b) {
+  constexpr int N3 = N * N * N;
+  const T *PT = tab + tab_off_PT(N, Q);
+  const T *Pm = tab + tab_off_P(N, Q);
+  const T *wa = tab + tab_off_wa(N, Q);
+  sweep<T, 0, N, N, N, N, N>(nf, 0u, PT, PT, PT, a, b);
+  __syncthreads();
+  sweep<T, 1, N, N, N, N, N>(nf, 0u, PT, PT, PT, b, a);
+  __syncthreads();
+  sweep<T, 2, N, N, N, N, N>(nf, 0u, PT, PT, PT, a, b);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nf * N3; idx += blockDim.x) {
+    const int node = idx % N3;
+    const int i = node % N, j = (node / N) % N, k = node / (N * N);
+    T det = P.dx * P.dy * P.dz;
+    if (CURVED) det *= (T(1) - colp[col_off_hqa(N, Q) + i + N * j] / P.H);
+    b[idx] = b[idx] / (rq[node] * wa[i] * wa[j] * wa[k] * det);
+  }
+  __syncthreads();
+  sweep<T, 0, N, N, N, N, N>(nf, 0u, Pm, Pm, Pm, b, a);
+  __syncthreads();
+  sweep<T, 1, N, N, N, N, N>(nf, 0u, Pm, Pm, Pm, a, b);
+  __syncthreads();
+  sweep<T, 2, N, N, N, N, N>(nf, 0u, Pm, Pm, Pm, b, a);
+  __syncthreads();
+}
+
+// rho at the fast-rule points: Ia^3 rho.
+template <typename T, int N, int Q>
+__device__ __forceinline__ void rho_fast(const T *tab, const T *rho, T *t1, T *t2, T *rq) {
+  const T *Ia = tab + tab_off_Ia(N, Q);
+  sweep<T, 0, N, N, N, N, N>(1, 0u, Ia, Ia, Ia, rho, t1);
+  __syncthreads();
+  sweep<T, 1, N, N, N, N, N>(1, 0u, Ia, Ia, Ia, t1, t2);
+  __syncthreads();
+  sweep<T, 2, N, N, N, N, N>(1, 0u, Ia, Ia, Ia, t2, rq);
+  __syncthreads();
+}
+
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+
+// ------------------------------------------------------------------ k_grad
+template <int N, int Q, bool CURVED>
+struct GradL {
+  static constexpr int N2 = N * N, N3 = N * N * N, Q2 = Q * Q, Q3 = Q * Q * Q;
+  static constexpr int NFV = CURVED ? 5 : 3;   // volume flux fields f_{jd}
+  static constexpr int NFP = CURVED ? 10 : 6;  // (face, component) products
+  static constexpr int TAB = (tab_size(N, Q) + 1) & ~1;
+  static constexpr int oP = TAB, oRho = oP + N3, oRq = oRho + N3, oOut = oRq + N3;
+  static constexpr int oW = oOut + 3 * N3;
+  // R1, R2: interpolation temporaries and the fast-inverse ping buffer
+  static constexpr int szR1 = cmax(N2 * Q, 3 * N3), szR2 = cmax(N * Q2, N3);
+  static constexpr int oR1 = oW, oR2 = oR1 + szR1, oVol = oR2 + szR2;
+  static constexpr int szVol = NFV * Q3, szZ = NFV * Q2 * N, szY = NFV * Q * N2, szX = NFV * N3;
+  // Wy reuses Wv (dead after the z sweep), Wx reuses Wz (dead after the y sweep);
+  // the face stage reuses everything from oVol on (after the combine barrier).
+  static constexpr int oZ = oVol + szVol, oY = oVol, oX = oZ, oFace = oVol;
+  static constexpr int szFace = 6 * N2 + 6 * N * Q + 6 * Q2 + NFP * Q2 + NFP * N * Q + NFP * N2;
+  static_assert(szY <= szVol && szX <= szZ, "layout");
+  static constexpr int total = cmax(oZ + szZ, oFace + szFace);
+};
+
+template <typename T, int N, int Q, bool CURVED>
+__global__ void __launch_bounds__(256) k_grad(const OpP<T> P, const T *__restrict__ p, const T *__restrict__ rho,
+                                              T *__restrict__ V, long long Ntot) {
+  using L = GradL<N, Q, CURVED>;
+  constexpr int N2 = L::N2, N3 = L::N3, Q2 = L::Q2, Q3 = L::Q3, NFV = L::NFV, NFP = L::NFP;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *sm = reinterpret_cast<T *>(smraw);
+  T *tab = sm;
+  T *s_p = sm + L::oP, *s_rho = sm + L::oRho, *s_rq = sm + L::oRq, *s_out = sm + L::oOut;
+  T *R1 = sm + L::oR1, *R2 = sm + L::oR2, *Wv = sm + L::oVol, *Wz = sm + L::oZ, *Wy = sm + L::oY,
+    *Wx = sm + L::oX, *Wf = sm + L::oFace;
+
+  const long long cell = blockIdx.x;
+  const CellPos cp = cell_pos(P, cell);
+  const T *colp = CURVED ? P.col + (long long)(cp.cx + P.nx * cp.cy) * col_size(N, Q) : nullptr;
+  const T zeta0 = T(cp.cz) * P.dz;
+
+  load_tables<T, N, Q>(P.tab, tab);
+  for (int i = threadIdx.x; i < N3; i += blockDim.x) {
+    s_p[i] = p[cell * N3 + i];
+    s_rho[i] = rho[cell * N3 + i];
+  }
+  __syncthreads();
+  const T *I = tab + tab_off_I(N, Q), *IT = tab + tab_off_IT(N, Q), *DT = tab + tab_off_DT(N, Q);
+  const T *wq = tab + tab_off_wq(N, Q), *gq = tab + tab_off_gq(N, Q);
+
+  // p at the Q^3 Gauss points; rho at the fast-rule points
+  sweep<T, 0, Q, N, N, N, N>(1, 0u, I, I, I, s_p, R1);
+  __syncthreads();
+  sweep<T, 1, Q, N, Q, N, N>(1, 0u, I, I, I, R1, R2);
+  __syncthreads();
+  sweep<T, 2, Q, N, Q, Q, N>(1, 0u, I, I, I, R2, Wv);
+  __syncthreads();
+  rho_fast<T, N, Q>(tab, s_rho, R1, R2, s_rq);
+
+  // volume fluxes f_{jd} = -alpha w p adj(J)_{jd}  (weak gradient, Sec. 2)
+  for (int idx = threadIdx.x; idx < Q3; idx += blockDim.x) {
+    const int i = idx % Q, j = (idx / Q) % Q, k = idx / Q2;
+    const T c = -P.alpha * wq[i] * wq[j] * wq[k] * Wv[idx];
+    if (CURVED) {
+      const T h = colp[col_off_hq(N, Q) + i + Q * j];
+      const T h1 = colp[col_off_h1q(N, Q) + i + Q * j];
+      const T h2 = colp[col_off_h2q(N, Q) + i + Q * j];
+      const T fac = T(1) - (zeta0 + P.dz * gq[k]) / P.H;
+      const T z1 = h1 * fac, z2 = h2 * fac, z3 = P.dz * (T(1) - h / P.H);
+      Wv[0 * Q3 + idx] = c * P.dy * z3;   // j=0, d=0
+      Wv[1 * Q3 + idx] = -c * P.dy * z1;  // j=2, d=0
+      Wv[2 * Q3 + idx] = c * P.dx * z3;   // j=1, d=1
+      Wv[3 * Q3 + idx] = -c * P.dx * z2;  // j=2, d=1
+      Wv[4 * Q3 + idx] = c * P.dx * P.dy; // j=2, d=2
+    } else {
+      Wv[0 * Q3 + idx] = c * P.dy * P.dz;
+      Wv[1 * Q3 + idx] = c * P.dx * P.dz;
+      Wv[2 * Q3 + idx] = c * P.dx * P.dy;
+    }
+  }
+  __syncthreads();
+  // test with grad: z, y, x sweeps; D^T in the field's reference direction j
+  if (CURVED) {
+    sweep<T, 2, N, Q, Q, Q, Q>(NFV, (1u << 2) | (1u << 6) | (1u << 8), IT, DT, DT, Wv, Wz);
+    __syncthreads();
+    sweep<T, 1, N, Q, Q, Q, N>(NFV, (1u << 4), IT, DT, DT, Wz, Wy);
+    __syncthreads();
+    sweep<T, 0, N, Q, Q, N, N>(NFV, (1u << 0), IT, DT, DT, Wy, Wx);
+  } else {
+    sweep<T, 2, N, Q, Q, Q, Q>(NFV, (1u << 4), IT, DT, DT, Wv, Wz);
+    __syncthreads();
+    sweep<T, 1, N, Q, Q, Q, N>(NFV, (1u << 2), IT, DT, DT, Wz, Wy);
+    __syncthreads();
+    sweep<T, 0, N, Q, Q, N, N>(NFV, (1u << 0), IT, DT, DT, Wy, Wx);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 3 * N3; idx += blockDim.x) {
+    const int d = idx / N3, node = idx % N3;
+    T v;
+    if (CURVED) v = d == 0 ? Wx[node] + Wx[N3 + node] : (d == 1 ? Wx[2 * N3 + node] + Wx[3 * N3 + node] : Wx[4 * N3 + node]);
+    else v = Wx[d * N3 + node];
+    s_out[idx] = v;
+  }
+  __syncthreads();
+
+  // faces: alpha int p_hat psi n_d, p_hat = {p} inside, p- on the boundary
+  T *Fg = Wf, *F1 = Fg + 6 * N2, *F2 = F1 + 6 * N * Q, *Fp = F2 + 6 * Q2, *Fb1 = Fp + NFP * Q2, *Fb2 = Fb1 + NFP * N * Q;
+  for (int idx = threadIdx.x; idx < 6 * N2; idx += blockDim.x) {
+    const int f = idx / N2, t = idx % N2, t1 = t % N, t2 = t / N;
+    const int k = f >> 1, s = f & 1;
+    const T own = s_p[face_node<N>(k, s ? N - 1 : 0, t1, t2)];
+    const long long nb = neighbour(P, cp, f);
+    Fg[idx] = nb >= 0 ? T(0.5) * (own + p[nb * N3 + face_node<N>(k, s ? 0 : N - 1, t1, t2)]) : own;
+  }
+  __syncthreads();
+  sweep<T, 0, Q, N, N, N, 1>(6, 0u, I, I, I, Fg, F1);
+  __syncthreads();
+  sweep<T, 1, Q, N, Q, N, 1>(6, 0u, I, I, I, F1, F2);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < NFP * Q2; idx += blockDim.x) {
+    const int sl = idx / Q2, t = idx % Q2, i = t % Q, j = t / Q;
+    int f, d;
+    if (CURVED) {
+      f = sl < 4 ? sl : (sl < 7 ? 4 : 5);
+      d = sl < 4 ? (sl >> 1) : (sl < 7 ? sl - 4 : sl - 7);
+    } else {
+      f = sl;
+      d = sl >> 1;
+    }
+    T nA[3];
+    face_normal<T, N, Q, CURVED>(P, colp, zeta0, f, i, j, nA);
+    Fp[idx] = P.alpha * wq[i] * wq[j] * nA[d] * F2[f * Q2 + t];
+  }
+  __syncthreads();
+  sweep<T, 0, N, Q, Q, Q, 1>(NFP, 0u, IT, IT, IT, Fp, Fb1);
+  __syncthreads();
+  sweep<T, 1, N, Q, N, Q, 1>(NFP, 0u, IT, IT, IT, Fb1, Fb2);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 3 * N3; idx += blockDim.x) {
+    const int d = idx / N3, node = idx % N3;
+    const int a = node % N, b = (node / N) % N, c = node / N2;
+    T acc = s_out[idx];
+#pragma unroll
+    for (int sl = 0; sl < NFP; ++sl) {
+      int f, dd;
+      if (CURVED) {
+        f = sl < 4 ? sl : (sl < 7 ? 4 : 5);
+        dd = sl < 4 ? (sl >> 1) : (sl < 7 ? sl - 4 : sl - 7);
+      } else {
+        f = sl;
+        dd = sl >> 1;
+      }
+      if (dd != d) continue;
+      const int k = f >> 1, e = (f & 1) ? N - 1 : 0;
+      if (k == 0 && a == e) acc += Fb2[sl * N2 + b + N * c];
+      if (k == 1 && b == e) acc += Fb2[sl * N2 + a + N * c];
+      if (k == 2 && c == e) acc += Fb2[sl * N2 + a + N * b];
+    }
+    s_out[idx] = acc;
+  }
+  __syncthreads();
+
+  // V = A^-1 (B P), per component
+  fast_inverse<T, N, Q, CURVED>(P, tab, colp, s_rq, 3, s_out, R1);
+  for (int idx = threadIdx.x; idx < 3 * N3; idx += blockDim.x) {
+    const int d = idx / N3, node = idx % N3;
+    V[d * Ntot + cell * N3 + node] = s_out[idx];
+  }
+}
+
+// ------------------------------------------------------------------ k_div
+template <int N, int Q, bool CURVED>
+struct DivL {
+  static constexpr int N2 = N * N, N3 = N * N * N, Q2 = Q * Q, Q3 = Q * Q * Q;
+  static constexpr int NSL = CURVED ? 32 : 24;  // face trace slots
+  static constexpr int TAB = (tab_size(N, Q) + 1) & ~1;
+  static constexpr int oIn = TAB, oY = oIn + 5 * N3, oW = oY + N3;
+  // R1 (x sweep) and R3 (values at Q^3) share oW: R1 is dead when R3 is written.
+  // Wz reuses R2, Wy reuses R3; the face region starts at oW; Wx lies beyond all.
+  static constexpr int oR1 = oW, oR3 = oW, oR2 = oW + 5 * Q3, oZ = oR2, oYs = oW;
+  static constexpr int szFace = cmax(NSL * N2, NSL * Q2) + NSL * N * Q + 6 * (Q2 + N * Q + N2);
+  static constexpr int oFace = oW;
+  static constexpr int oX = oW + cmax(5 * Q3 + 5 * N * Q2, szFace);
+  static_assert(5 * N2 * Q <= 5 * Q3 && 4 * Q2 * N <= 5 * N * Q2 && 4 * Q * N2 <= 5 * Q3, "layout");
+  static constexpr int total = oX + 4 * N3;
+};
+
+// Face trace slot -> (face, side, field): field 0 = kappa, 1..3 = V_x,V_y,V_z.
+template <bool CURVED>
+__device__ __forceinline__ void div_slot(int sl, int &f, int &side, int &field) {
+  if (sl < 16) {
+    f = sl >> 2;
+    const int w = sl & 3;  // kappa-, Vk-, kappa+, Vk+
+    side = w >> 1;
+    field = (w & 1) ? 1 + (f >> 1) : 0;
+  } else if (CURVED) {
+    f = 4 + ((sl - 16) >> 3);
+    const int w = (sl - 16) & 7;  // kappa-, Vx-, Vy-, Vz-, kappa+, Vx+, Vy+, Vz+
+    side = w >> 2;
+    field = w & 3;
+  } else {
+    f = 4 + ((sl - 16) >> 2);
+    const int w = (sl - 16) & 3;
+    side = w >> 1;
+    field = (w & 1) ? 3 : 0;
+  }
+}
+
+template <bool CURVED>
+__device__ __forceinline__ int div_slot_base(int f) {
+  return f < 4 ? 4 * f : (CURVED ? 16 + 8 * (f - 4) : 16 + 4 * (f - 4));
+}
+
+template <typename T, int N, int Q, bool CURVED>
+__global__ void __launch_bounds__(256) k_div(const OpP<T> P, const T *__restrict__ V, const T *__restrict__ p,
+                                             const T *__restrict__ pk, T *__restrict__ y, long long Ntot) {
+  using L = DivL<N, Q, CURVED>;
+  constexpr int N2 = L::N2, N3 = L::N3, Q2 = L::Q2, Q3 = L::Q3, NSL = L::NSL;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *sm = reinterpret_cast<T *>(smraw);
+  T *tab = sm;
+  T *s_in = sm + L::oIn, *s_y = sm + L::oY;
+  T *R1 = sm + L::oR1, *R2 = sm + L::oR2, *R3 = sm + L::oR3, *Wz = sm + L::oZ, *Wy = sm + L::oYs, *Wx = sm + L::oX;
+  // gather (Fg) and second interpolation (F2) share a region: Fg is dead when F2 is written
+  T *Fg = sm + L::oFace, *F2 = Fg, *F1 = Fg + cmax(NSL * N2, NSL * Q2), *Ff = F1 + NSL * N * Q, *Fb1 = Ff + 6 * Q2,
+    *Fb2 = Fb1 + 6 * N * Q;
+
+  const long long cell = blockIdx.x;
+  const CellPos cp = cell_pos(P, cell);
+  const T *colp = CURVED ? P.col + (long long)(cp.cx + P.nx * cp.cy) * col_size(N, Q) : nullptr;
+  const T zeta0 = T(cp.cz) * P.dz;
+
+  load_tables<T, N, Q>(P.tab, tab);
+  for (int i = threadIdx.x; i < N3; i += blockDim.x) {
+    s_in[0 * N3 + i] = V[0 * Ntot + cell * N3 + i];
+    s_in[1 * N3 + i] = V[1 * Ntot + cell * N3 + i];
+    s_in[2 * N3 + i] = V[2 * Ntot + cell * N3 + i];
+    s_in[3 * N3 + i] = pk[cell * N3 + i];
+    s_in[4 * N3 + i] = p[cell * N3 + i];
+  }
+  __syncthreads();
+  const T *I = tab + tab_off_I(N, Q), *IT = tab + tab_off_IT(N, Q), *DT = tab + tab_off_DT(N, Q);
+  const T *wq = tab + tab_off_wq(N, Q), *gq = tab + tab_off_gq(N, Q);
+
+  sweep<T, 0, Q, N, N, N, N>(5, 0u, I, I, I, s_in, R1);
+  __syncthreads();
+  sweep<T, 1, Q, N, Q, N, N>(5, 0u, I, I, I, R1, R2);
+  __syncthreads();
+  sweep<T, 2, Q, N, Q, Q, N>(5, 0u, I, I, I, R2, R3);
+  __syncthreads();
+
+  // -C V volume part: + alpha int kappa V . grad psi  -> F_j = alpha kappa w sum_d adj_{jd} V_d
+  //  D P: w det J p / (gamma - 1)
+  for (int idx = threadIdx.x; idx < Q3; idx += blockDim.x) {
+    const int i = idx % Q, j = (idx / Q) % Q, k = idx / Q2;
+    const T w = wq[i] * wq[j] * wq[k];
+    const T v0 = R3[idx], v1 = R3[Q3 + idx], v2 = R3[2 * Q3 + idx], pkq = R3[3 * Q3 + idx], pq = R3[4 * Q3 + idx];
+    const T c = P.alpha * P.gfac * pkq * w;
+    if (CURVED) {
+      const T h = colp[col_off_hq(N, Q) + i + Q * j];
+      const T h1 = colp[col_off_h1q(N, Q) + i + Q * j];
+      const T h2 = colp[col_off_h2q(N, Q) + i + Q * j];
+      const T fac = T(1) - (zeta0 + P.dz * gq[k]) / P.H;
+      const T z1 = h1 * fac, z2 = h2 * fac, z3 = P.dz * (T(1) - h / P.H);
+      R3[idx] = c * P.dy * z3 * v0;
+      R3[Q3 + idx] = c * P.dx * z3 * v1;
+      R3[2 * Q3 + idx] = c * (P.dx * P.dy * v2 - P.dy * z1 * v0 - P.dx * z2 * v1);
+      R3[3 * Q3 + idx] = w * P.dx * P.dy * z3 * pq * P.igm1;
+    } else {
+      R3[idx] = c * P.dy * P.dz * v0;
+      R3[Q3 + idx] = c * P.dx * P.dz * v1;
+      R3[2 * Q3 + idx] = c * P.dx * P.dy * v2;
+      R3[3 * Q3 + idx] = w * P.dx * P.dy * P.dz * pq * P.igm1;
+    }
+  }
+  __syncthreads();
+  sweep<T, 2, N, Q, Q, Q, Q>(4, (1u << 4), IT, DT, DT, R3, Wz);
+  __syncthreads();
+  sweep<T, 1, N, Q, Q, Q, N>(4, (1u << 2), IT, DT, DT, Wz, Wy);
+  __syncthreads();
+  sweep<T, 0, N, Q, Q, N, N>(4, (1u << 0), IT, DT, DT, Wy, Wx);
+  __syncthreads();
+
+  // faces: - alpha int (kappa V)^ . n psi
+  for (int idx = threadIdx.x; idx < N3; idx += blockDim.x)
+    s_y[idx] = Wx[idx] + Wx[N3 + idx] + Wx[2 * N3 + idx] + Wx[3 * N3 + idx];
+  for (int idx = threadIdx.x; idx < NSL * N2; idx += blockDim.x) {
+    const int sl = idx / N2, t = idx % N2, t1 = t % N, t2 = t / N;
+    int f, side, field;
+    div_slot<CURVED>(sl, f, side, field);
+    const int k = f >> 1, s = f & 1;
+    const long long nb = neighbour(P, cp, f);
+    T v;
+    if (side == 0 || nb < 0) {
+      const int node = face_node<N>(k, s ? N - 1 : 0, t1, t2);
+      v = field == 0 ? P.gfac * s_in[3 * N3 + node] : s_in[(field - 1) * N3 + node];
+      // slip wall: no normal flux (all traces of this face set to zero)
+      if (nb < 0 && (k == 2 || P.bc_lat == 0)) v = T(0);
+    } else {
+      const long long node = nb * N3 + face_node<N>(k, s ? 0 : N - 1, t1, t2);
+      v = field == 0 ? P.gfac * pk[node] : V[(field - 1) * Ntot + node];
+    }
+    Fg[idx] = v;
+  }
+  __syncthreads();
+  sweep<T, 0, Q, N, N, N, 1>(NSL, 0u, I, I, I, Fg, F1);
+  __syncthreads();
+  sweep<T, 1, Q, N, Q, N, 1>(NSL, 0u, I, I, I, F1, F2);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 6 * Q2; idx += blockDim.x) {
+    const int f = idx / Q2, t = idx % Q2, i = t % Q, j = t / Q;
+    T nA[3];
+    face_normal<T, N, Q, CURVED>(P, colp, zeta0, f, i, j, nA);
+    const T *S = F2 + div_slot_base<CURVED>(f) * Q2 + t;
+    T flux;
+    if (f < 4 || !CURVED) {
+      const int k = f >> 1;
+      // slots: kappa-, V-, kappa+, V+
+      flux = T(0.5) * nA[k] * (S[0] * S[Q2] + S[2 * Q2] * S[3 * Q2]);
+    } else {
+      const T vm = S[Q2] * nA[0] + S[2 * Q2] * nA[1] + S[3 * Q2] * nA[2];
+      const T vp = S[5 * Q2] * nA[0] + S[6 * Q2] * nA[1] + S[7 * Q2] * nA[2];
+      flux = T(0.5) * (S[0] * vm + S[4 * Q2] * vp);
+    }
+    Ff[idx] = -P.alpha * wq[i] * wq[j] * flux;
+  }
+  __syncthreads();
+  sweep<T, 0, N, Q, Q, Q, 1>(6, 0u, IT, IT, IT, Ff, Fb1);
+  __syncthreads();
+  sweep<T, 1, N, Q, N, Q, 1>(6, 0u, IT, IT, IT, Fb1, Fb2);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < N3; idx += blockDim.x) {
+    const int a = idx % N, b = (idx / N) % N, c = idx / N2;
+    T acc = s_y[idx];
+    if (a == 0) acc += Fb2[0 * N2 + b + N * c];
+    if (a == N - 1) acc += Fb2[1 * N2 + b + N * c];
+    if (b == 0) acc += Fb2[2 * N2 + a + N * c];
+    if (b == N - 1) acc += Fb2[3 * N2 + a + N * c];
+    if (c == 0) acc += Fb2[4 * N2 + a + N * b];
+    if (c == N - 1) acc += Fb2[5 * N2 + a + N * b];
+    y[cell * N3 + idx] = acc;
+  }
+}
+
+// ------------------------------------------------------------------ k_minv
+template <int N, int Q>
+struct MinvL {
+  static constexpr int N3 = N * N * N;
+  static constexpr int TAB = (tab_size(N, Q) + 1) & ~1;
+  static constexpr int oRho = TAB, oRq = oRho + N3, oA = oRq + N3, oB = oA + 3 * N3, total = oB + 3 * N3;
+};
+
+template <typename T, int N, int Q, bool CURVED>
+__global__ void __launch_bounds__(128) k_minv(const OpP<T> P, const T *__restrict__ in, const T *__restrict__ rho,
+                                              T *__restrict__ out, long long Ntot) {
+  using L = MinvL<N, Q>;
+  constexpr int N3 = L::N3;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *sm = reinterpret_cast<T *>(smraw);
+  T *tab = sm, *s_rho = sm + L::oRho, *s_rq = sm + L::oRq, *A = sm + L::oA, *B = sm + L::oB;
+  const long long cell = blockIdx.x;
+  const CellPos cp = cell_pos(P, cell);
+  const T *colp = CURVED ? P.col + (long long)(cp.cx + P.nx * cp.cy) * col_size(N, Q) : nullptr;
+  load_tables<T, N, Q>(P.tab, tab);
+  for (int i = threadIdx.x; i < 3 * N3; i += blockDim.x) {
+    const int d = i / N3, node = i % N3;
+    A[i] = in[d * Ntot + cell * N3 + node];
+    if (d == 0) s_rho[node] = rho[cell * N3 + node];
+  }
+  __syncthreads();
+  rho_fast<T, N, Q>(tab, s_rho, B, B + N3, s_rq);
+  fast_inverse<T, N, Q, CURVED>(P, tab, colp, s_rq, 3, A, B);
+  for (int i = threadIdx.x; i < 3 * N3; i += blockDim.x) {
+    const int d = i / N3, node = i % N3;
+    out[d * Ntot + cell * N3 + node] = A[i];
+  }
+}
+
+// ------------------------------------------------------------------ k_diag
+template <int N, int Q, bool CURVED>
+struct DiagL {
+  static constexpr int N2 = N * N, N3 = N * N * N, Q2 = Q * Q, Q3 = Q * Q * Q;
+  static constexpr int NF = CURVED ? 6 : 4;
+  static constexpr int TAB = (tab_size(N, Q) + 1) & ~1;
+  // R3 (rho, p_k at Q^3) first; R1, R2 after it; the coefficient fields F reuse
+  // R1/R2 (dead after the z interpolation); Wy reuses F, Wx reuses Wz.
+  static constexpr int oIn = TAB, oR3 = oIn + 2 * N3, oR1 = oR3 + 2 * Q3, oR2 = oR1 + 2 * N2 * Q;
+  static constexpr int oF = oR1, oZ = oF + NF * Q3, oY = oF, oX = oZ;
+  static_assert(NF * Q * N2 <= NF * Q3 && NF * N3 <= NF * Q2 * N, "layout");
+  static constexpr int total = cmax(oR2 + 2 * N * Q2, oZ + NF * Q2 * N);
+};
+
+// Sec. 3.1: S~_ii = int psi_i^2/(gamma-1) + alpha^2 int h |grad psi_i|^2, h = gamma p_k/((gamma-1) rho)
+// |grad psi|^2 det J = sum_{j,j'} d_j psi d_j' psi (adj adj^T)_{jj'} / det J.
+template <int N, int Q, bool CURVED>
+__global__ void __launch_bounds__(256) k_diag(const OpP<double> P, const double *__restrict__ rho,
+                                              const double *__restrict__ pk, double *__restrict__ dh,
+                                              double *__restrict__ die) {
+  using T = double;
+  using L = DiagL<N, Q, CURVED>;
+  constexpr int N2 = L::N2, N3 = L::N3, Q2 = L::Q2, Q3 = L::Q3, NF = L::NF;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *sm = reinterpret_cast<T *>(smraw);
+  T *tab = sm, *s_in = sm + L::oIn, *R1 = sm + L::oR1, *R2 = sm + L::oR2, *R3 = sm + L::oR3, *F = sm + L::oF,
+    *Wz = sm + L::oZ, *Wy = sm + L::oY, *Wx = sm + L::oX;
+  const long long cell = blockIdx.x;
+  const CellPos cp = cell_pos(P, cell);
+  const T *colp = CURVED ? P.col + (long long)(cp.cx + P.nx * cp.cy) * col_size(N, Q) : nullptr;
+  const T zeta0 = T(cp.cz) * P.dz;
+  load_tables<T, N, Q>(P.tab, tab);
+  for (int i = threadIdx.x; i < N3; i += blockDim.x) {
+    s_in[i] = rho[cell * N3 + i];
+    s_in[N3 + i] = pk[cell * N3 + i];
+  }
+  __syncthreads();
+  const T *I = tab + tab_off_I(N, Q), *IIT = tab + tab_off_IIT(N, Q), *DDT = tab + tab_off_DDT(N, Q),
+          *IDT = tab + tab_off_IDT(N, Q), *wq = tab + tab_off_wq(N, Q), *gq = tab + tab_off_gq(N, Q);
+  sweep<T, 0, Q, N, N, N, N>(2, 0u, I, I, I, s_in, R1);
+  __syncthreads();
+  sweep<T, 1, Q, N, Q, N, N>(2, 0u, I, I, I, R1, R2);
+  __syncthreads();
+  sweep<T, 2, Q, N, Q, Q, N>(2, 0u, I, I, I, R2, R3);
+  __syncthreads();
+  const T a2 = P.alpha * P.alpha;
+  for (int idx = threadIdx.x; idx < Q3; idx += blockDim.x) {
+    const int i = idx % Q, j = (idx / Q) % Q, k = idx / Q2;
+    const T w = wq[i] * wq[j] * wq[k];
+    const T h = P.gfac * R3[Q3 + idx] / R3[idx];
+    T z1 = 0, z2 = 0, z3 = P.dz;
+    if (CURVED) {
+      const T hh = colp[col_off_hq(N, Q) + i + Q * j];
+      const T fac = T(1) - (zeta0 + P.dz * gq[k]) / P.H;
+      z1 = colp[col_off_h1q(N, Q) + i + Q * j] * fac;
+      z2 = colp[col_off_h2q(N, Q) + i + Q * j] * fac;
+      z3 = P.dz * (T(1) - hh / P.H);
+    }
+    const T det = P.dx * P.dy * z3;
+    const T A00 = P.dy * z3, A11 = P.dx * z3, A20 = -P.dy * z1, A21 = -P.dx * z2, A22 = P.dx * P.dy;
+    const T c = a2 * h * w / det;
+    F[0 * Q3 + idx] = w * det * P.igm1;
+    F[1 * Q3 + idx] = c * A00 * A00;
+    F[2 * Q3 + idx] = c * A11 * A11;
+    F[3 * Q3 + idx] = c * (A20 * A20 + A21 * A21 + A22 * A22);
+    if (CURVED) {
+      F[4 * Q3 + idx] = T(2) * c * A00 * A20;
+      F[5 * Q3 + idx] = T(2) * c * A11 * A21;
+    }
+  }
+  __syncthreads();
+  // matrices: 0 = (I o I)^T, 1 = (D o D)^T, 2 = (I o D)^T
+  const unsigned selz = (1u << 6) | (CURVED ? ((2u << 8) | (2u << 10)) : 0u);
+  const unsigned sely = (1u << 4) | (CURVED ? (2u << 10) : 0u);
+  const unsigned selx = (1u << 2) | (CURVED ? (2u << 8) : 0u);
+  sweep<T, 2, N, Q, Q, Q, Q>(NF, selz, IIT, DDT, IDT, F, Wz);
+  __syncthreads();
+  sweep<T, 1, N, Q, Q, Q, N>(NF, sely, IIT, DDT, IDT, Wz, Wy);
+  __syncthreads();
+  sweep<T, 0, N, Q, Q, N, N>(NF, selx, IIT, DDT, IDT, Wy, Wx);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < N3; idx += blockDim.x) {
+    T s = 0;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) s += Wx[f * N3 + idx];
+    dh[cell * N3 + idx] = s;
+    die[cell * N3 + idx] = Wx[idx];
+  }
+}
+
+template <typename Kern>
+int prep(dgx_ctx *c, Kern k, size_t smem) {
+  static_assert(sizeof(Kern) > 0, "");
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return check_cuda(c, e, "cudaFuncSetAttribute");
+}
+
+int threads_for(int N) { return N <= 3 ? 128 : 256; }
+
+template <typename T, int N, bool CURVED>
+int grad_impl(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s) {
+  constexpr int Q = 2 * N - 1;
+  const size_t smem = sizeof(T) * GradL<N, Q, CURVED>::total;
+  auto k = k_grad<T, N, Q, CURVED>;
+  if (int e = prep(c, k, smem)) return e;
+  count_launch();
+  k<<<(unsigned)c->ncell, threads_for(N), smem, s>>>(make_params<T>(c), p, rho, V, c->N);
+  return check_cuda(c, cudaGetLastError(), "k_grad launch");
+}
+
+template <typename T, int N, bool CURVED>
+int div_impl(dgx_ctx *c, const T *V, const T *p, const T *pk, T *y, cudaStream_t s) {
+  constexpr int Q = 2 * N - 1;
+  const size_t smem = sizeof(T) * DivL<N, Q, CURVED>::total;
+  auto k = k_div<T, N, Q, CURVED>;
+  if (int e = prep(c, k, smem)) return e;
+  count_launch();
+  k<<<(unsigned)c->ncell, threads_for(N), smem, s>>>(make_params<T>(c), V, p, pk, y, c->N);
+  return check_cuda(c, cudaGetLastError(), "k_div launch");
+}
+
+template <typename T, int N, bool CURVED>
+int minv_impl(dgx_ctx *c, const T *in, const T *rho, T *out, cudaStream_t s) {
+  constexpr int Q = 2 * N - 1;
+  const size_t smem = sizeof(T) * MinvL<N, Q>::total;
+  auto k = k_minv<T, N, Q, CURVED>;
+  if (int e = prep(c, k, smem)) return e;
+  count_launch();
+  k<<<(unsigned)c->ncell, 128, smem, s>>>(make_params<T>(c), in, rho, out, c->N);
+  return check_cuda(c, cudaGetLastError(), "k_minv launch");
+}
+
+template <int N, bool CURVED>
+int diag_impl(dgx_ctx *c, const double *rho, const double *pk, double *dh, double *die, cudaStream_t s) {
+  constexpr int Q = 2 * N - 1;
+  const size_t smem = sizeof(double) * DiagL<N, Q, CURVED>::total;
+  auto k = k_diag<N, Q, CURVED>;
+  if (int e = prep(c, k, smem)) return e;
+  count_launch();
+  k<<<(unsigned)c->ncell, threads_for(N), smem, s>>>(make_params<double>(c), rho, pk, dh, die);
+  return check_cuda(c, cudaGetLastError(), "k_diag launch");
+}
+
+#define DGX_DISPATCH(CALL)                                                         \
+  switch (c->n) {                                                                  \
+    case 2: return c->curved ? CALL(2, true) : CALL(2, false);                     \
+    case 3: return c->curved ? CALL(3, true) : CALL(3, false);                     \
+    case 4: return c->curved ? CALL(4, true) : CALL(4, false);                     \
+    case 5: return c->curved ? CALL(5, true) : CALL(5, false);                     \
+    case 6: return c->curved ? CALL(6, true) : CALL(6, false);                     \
+    case 7: return c->curved ? CALL(7, true) : CALL(7, false);                     \
+    default: return set_error(c, DGX_ERR_ARG, "unsupported degree %d", c->n - 1);  \
+  }
+
+}  // namespace
+
+template <typename T>
+OpP<T> make_params(const dgx_ctx *c) {
+  OpP<T> P;
+  P.nx = c->mesh.nx;
+  P.ny = c->mesh.ny;
+  P.nz = c->mesh.nz;
+  P.bc_lat = c->mesh.bc_lateral;
+  P.dx = (T)(c->mesh.Lx / c->mesh.nx);
+  P.dy = (T)(c->mesh.Ly / c->mesh.ny);
+  P.dz = (T)(c->mesh.Lz / c->mesh.nz);
+  P.H = (T)c->mesh.Lz;
+  P.alpha = (T)c->alpha;
+  P.gfac = (T)(c->gamma / (c->gamma - 1.0));
+  P.igm1 = (T)(1.0 / (c->gamma - 1.0));
+  if constexpr (sizeof(T) == 8) {
+    P.tab = reinterpret_cast<const T *>(c->tab64);
+    P.col = reinterpret_cast<const T *>(c->col64);
+  } else {
+    P.tab = reinterpret_cast<const T *>(c->tab32);
+    P.col = reinterpret_cast<const T *>(c->col32);
+  }
+  return P;
+}
+template OpP<double> make_params<double>(const dgx_ctx *);
+template OpP<float> make_params<float>(const dgx_ctx *);
+
+template <typename T>
+int launch_grad(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s) {
+#define CALL_GRAD(NN, CC) grad_impl<T, NN, CC>(c, p, rho, V, s)
+  DGX_DISPATCH(CALL_GRAD)
+#undef CALL_GRAD
+}
+
+template <typename T>
+int launch_div(dgx_ctx *c, const T *V, const T *p, const T *pk, T *y, cudaStream_t s) {
+#define CALL_DIV(NN, CC) div_impl<T, NN, CC>(c, V, p, pk, y, s)
+  DGX_DISPATCH(CALL_DIV)
+#undef CALL_DIV
+}
+
+template <typename T>
+int launch_mass_inverse(dgx_ctx *c, const T *in, const T *rho, T *out, cudaStream_t s) {
+#define CALL_MINV(NN, CC) minv_impl<T, NN, CC>(c, in, rho, out, s)
+  DGX_DISPATCH(CALL_MINV)
+#undef CALL_MINV
+}
+
+int launch_diag(dgx_ctx *c, const double *rho, const double *pk, double *dh, double *die, cudaStream_t s) {
+#define CALL_DIAG(NN, CC) diag_impl<NN, CC>(c, rho, pk, dh, die, s)
+  DGX_DISPATCH(CALL_DIAG)
+#undef CALL_DIAG
+}
+
+template int launch_grad<double>(dgx_ctx *, const double *, const double *, double *, cudaStream_t);
+template int launch_grad<float>(dgx_ctx *, const float *, const float *, float *, cudaStream_t);
+template int launch_div<double>(dgx_ctx *, const double *, const double *, const double *, double *, cudaStream_t);
+template int launch_div<float>(dgx_ctx *, const float *, const float *, const float *, float *, cudaStream_t);
+template int launch_mass_inverse<double>(dgx_ctx *, const double *, const double *, double *, cudaStream_t);
+template int launch_mass_inverse<float>(dgx_ctx *, const float *, const float *, float *, cudaStream_t);
+
+}  // namespace dgx

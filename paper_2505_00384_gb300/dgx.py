@@ -1,0 +1,219 @@
+"""Python binding of the dgx C ABI (``include/dgx.h``): argument marshalling only.
+
+Every function has the name of the C entry point it wraps and takes plain
+integers (device pointers, e.g. ``tensor.data_ptr()``) or ctypes structures.
+All arithmetic of the solver runs in the CUDA kernels of ``libdgx.so``; there
+is no CPU fallback: loading fails loudly if the library is missing.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdgx.so")
+
+DGX_OK = 0
+DGX_NOT_CONVERGED = 1
+DGX_FALLBACK_USED = 2
+DGX_ERR_ARG = -1
+DGX_ERR_OOM = -2
+DGX_ERR_CUDA = -3
+DGX_ERR_BREAKDOWN = -4
+DGX_ERR_DEVICE_TIMEOUT = -5
+DGX_ERR_STATE = -6
+
+DGX_F64, DGX_F32 = 0, 1
+DGX_PC_NONE, DGX_PC_HELMHOLTZ, DGX_PC_INTERNAL_ENERGY = 0, 1, 2
+DGX_SOLVER_FGMRES, DGX_SOLVER_CG, DGX_SOLVER_MIXED = 0, 1, 2
+
+
+class dgx_mesh_desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("degree", C.c_int), ("n_q", C.c_int),
+                ("terrain", C.c_int), ("bc_lateral", C.c_int), ("reserved", C.c_int),
+                ("Lx", C.c_double), ("Ly", C.c_double), ("Lz", C.c_double),
+                ("h_c", C.c_double), ("a_c", C.c_double), ("x_c", C.c_double), ("y_c", C.c_double)]
+
+
+class dgx_background(C.Structure):
+    _fields_ = [("kind", C.c_int), ("reserved", C.c_int), ("T", C.c_double), ("p0", C.c_double),
+                ("N_bv", C.c_double), ("R", C.c_double), ("gamma", C.c_double), ("g", C.c_double),
+                ("u_bar", C.c_double)]
+
+
+class dgx_solve_opts(C.Structure):
+    _fields_ = [("method", C.c_int), ("pc", C.c_int), ("restart", C.c_int), ("maxit", C.c_int),
+                ("tol", C.c_double), ("inner_restart", C.c_int), ("inner_maxit", C.c_int),
+                ("inner_tol", C.c_double), ("use_x0", C.c_int), ("reserved", C.c_int)]
+
+
+class dgx_solve_info(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("inner_iterations", C.c_int),
+                ("operator_f64", C.c_int), ("operator_f32", C.c_int), ("reserved", C.c_int),
+                ("relres", C.c_double), ("seconds", C.c_double)]
+
+
+# (name, restype, argtypes) of every entry point declared in include/dgx.h
+_P = C.c_void_p
+SIGNATURES = [
+    ("dgx_create", C.c_int, [C.POINTER(C.c_void_p), C.c_int, _P]),
+    ("dgx_destroy", None, [_P]),
+    ("dgx_last_error", C.c_char_p, [_P]),
+    ("dgx_mesh_build", C.c_int, [_P, C.POINTER(dgx_mesh_desc)]),
+    ("dgx_num_dofs", C.c_longlong, [_P]),
+    ("dgx_node_coords", C.c_int, [_P, _P]),
+    ("dgx_set_background", C.c_int, [_P, C.POINTER(dgx_background)]),
+    ("dgx_background_fields", C.c_int, [_P, _P, _P]),
+    ("dgx_set_coefficients", C.c_int, [_P, _P, _P, C.c_double, C.c_double]),
+    ("dgx_apply_operator", C.c_int, [_P, C.c_int, _P, _P]),
+    ("dgx_apply_grad", C.c_int, [_P, C.c_int, _P, _P]),
+    ("dgx_apply_div", C.c_int, [_P, C.c_int, _P, _P, _P]),
+    ("dgx_apply_mass_inverse", C.c_int, [_P, C.c_int, _P, _P]),
+    ("dgx_apply_preconditioner", C.c_int, [_P, C.c_int, C.c_int, _P, _P]),
+    ("dgx_preconditioner_diagonal", C.c_int, [_P, C.c_int, _P]),
+    ("dgx_solve_pressure", C.c_int, [_P, _P, _P, C.POINTER(dgx_solve_opts), C.POINTER(dgx_solve_info)]),
+    ("dgx_default_solve_opts", None, [C.POINTER(dgx_solve_opts)]),
+    ("dgx_operator_cost", C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("dgx_kernel_launches", C.c_longlong, []),
+]
+
+_lib = None
+
+
+def load(build_if_missing=True):
+    """Load libdgx.so (building it in-tree with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        from . import build as _b
+        _b.build()
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libdgx.so not found at %s: build it with __graft_entry__.build()" % LIB_PATH)
+    lib = C.CDLL(LIB_PATH)
+    for name, res, args in SIGNATURES:
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class DgxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("dgx error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _check(ctx, rc, allow=(DGX_OK,)):
+    if rc in allow:
+        return rc
+    msg = load().dgx_last_error(ctx).decode() if ctx else ""
+    raise DgxError(rc, msg)
+
+
+# ---------------------------------------------------------------- same-name wrappers
+def dgx_create(device=0, stream=0):
+    h = C.c_void_p()
+    rc = load().dgx_create(C.byref(h), int(device), C.c_void_p(int(stream) or None))
+    if rc != DGX_OK:
+        raise DgxError(rc, "dgx_create failed (device %d)" % device)
+    return h
+
+
+def dgx_destroy(ctx):
+    load().dgx_destroy(ctx)
+
+
+def dgx_last_error(ctx):
+    return load().dgx_last_error(ctx).decode()
+
+
+def dgx_mesh_build(ctx, desc):
+    return _check(ctx, load().dgx_mesh_build(ctx, C.byref(desc)))
+
+
+def dgx_num_dofs(ctx):
+    return int(load().dgx_num_dofs(ctx))
+
+
+def dgx_node_coords(ctx, X_ptr):
+    return _check(ctx, load().dgx_node_coords(ctx, C.c_void_p(X_ptr)))
+
+
+def dgx_set_background(ctx, bg):
+    return _check(ctx, load().dgx_set_background(ctx, C.byref(bg)))
+
+
+def dgx_background_fields(ctx, rho_ptr, p_ptr):
+    return _check(ctx, load().dgx_background_fields(ctx, C.c_void_p(rho_ptr), C.c_void_p(p_ptr)))
+
+
+def dgx_set_coefficients(ctx, rho_ptr, pk_ptr, a_dt, gamma=1.4):
+    return _check(ctx, load().dgx_set_coefficients(ctx, C.c_void_p(rho_ptr), C.c_void_p(pk_ptr), float(a_dt),
+                                                   float(gamma)))
+
+
+def dgx_apply_operator(ctx, prec, x_ptr, y_ptr):
+    return _check(ctx, load().dgx_apply_operator(ctx, prec, C.c_void_p(x_ptr), C.c_void_p(y_ptr)))
+
+
+def dgx_apply_grad(ctx, prec, p_ptr, V_ptr):
+    return _check(ctx, load().dgx_apply_grad(ctx, prec, C.c_void_p(p_ptr), C.c_void_p(V_ptr)))
+
+
+def dgx_apply_div(ctx, prec, V_ptr, p_ptr, y_ptr):
+    return _check(ctx, load().dgx_apply_div(ctx, prec, C.c_void_p(V_ptr), C.c_void_p(p_ptr), C.c_void_p(y_ptr)))
+
+
+def dgx_apply_mass_inverse(ctx, prec, in_ptr, out_ptr):
+    return _check(ctx, load().dgx_apply_mass_inverse(ctx, prec, C.c_void_p(in_ptr), C.c_void_p(out_ptr)))
+
+
+def dgx_apply_preconditioner(ctx, pc, prec, x_ptr, y_ptr):
+    return _check(ctx, load().dgx_apply_preconditioner(ctx, pc, prec, C.c_void_p(x_ptr), C.c_void_p(y_ptr)))
+
+
+def dgx_preconditioner_diagonal(ctx, pc, d_ptr):
+    return _check(ctx, load().dgx_preconditioner_diagonal(ctx, pc, C.c_void_p(d_ptr)))
+
+
+def dgx_default_solve_opts():
+    o = dgx_solve_opts()
+    load().dgx_default_solve_opts(C.byref(o))
+    return o
+
+
+def dgx_solve_pressure(ctx, b_ptr, x_ptr, opts=None):
+    """Returns (status, dgx_solve_info); raises DgxError on errors (< 0)."""
+    o = opts if opts is not None else dgx_default_solve_opts()
+    info = dgx_solve_info()
+    rc = load().dgx_solve_pressure(ctx, C.c_void_p(b_ptr), C.c_void_p(x_ptr), C.byref(o), C.byref(info))
+    _check(ctx, rc, allow=(DGX_OK, DGX_NOT_CONVERGED))
+    return rc, info
+
+
+def dgx_operator_cost(ctx):
+    """(flops of the gradient kernel, flops of the divergence kernel, HBM floor bytes in FP64)."""
+    f1, f2, b64 = C.c_double(), C.c_double(), C.c_double()
+    _check(ctx, load().dgx_operator_cost(ctx, C.byref(f1), C.byref(f2), C.byref(b64)))
+    return f1.value, f2.value, b64.value
+
+
+def dgx_kernel_launches():
+    return int(load().dgx_kernel_launches())
+
+
+def mesh_desc(nx, ny, nz, degree, Lx, Ly, Lz, terrain=0, h_c=0.0, a_c=1000.0, x_c=None, y_c=None, bc_lateral=0):
+    d = dgx_mesh_desc()
+    d.nx, d.ny, d.nz, d.degree, d.n_q = nx, ny, nz, degree, 0
+    d.terrain, d.bc_lateral = terrain, bc_lateral
+    d.Lx, d.Ly, d.Lz = Lx, Ly, Lz
+    d.h_c, d.a_c = h_c, a_c
+    d.x_c = Lx / 2 if x_c is None else x_c
+    d.y_c = Ly / 2 if y_c is None else y_c
+    return d
+
+
+def background(kind=0, T=250.0, p0=1e5, N_bv=0.01, R=287.0, gamma=1.4, g=9.81, u_bar=10.0):
+    b = dgx_background()
+    b.kind, b.T, b.p0, b.N_bv, b.R, b.gamma, b.g, b.u_bar = kind, T, p0, N_bv, R, gamma, g, u_bar
+    return b

@@ -1,0 +1,170 @@
+"""Parity of the CUDA pressure operator (through the C ABI) with the FP64 oracle.
+
+Bar (per result): FP64 operator action within 1e-12 of the oracle, measured
+as max |y_gpu - y_oracle| / max |y_oracle|; FP32 action within 2e-5 (FP32
+unit roundoff 6e-8 times the sum-factorisation depth and the conditioning
+of D - C A^-1 B).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2505_00384_gb300 import dgx
+from paper_2505_00384_gb300 import inputs
+
+from _util import GAMMA, Case, dev, host, rel_max_err
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 2e-5
+A_DT = 0.29289321881345254  # a~_22 dt of ARS(2,2,2) with dt = 1 s
+
+MESHES = [
+    dict(nx=1, ny=1, nz=1, r=1),
+    dict(nx=2, ny=1, nz=1, r=2),
+    dict(nx=3, ny=2, nz=2, r=2),
+    dict(nx=2, ny=3, nz=2, r=3, Lx=2000.0, Ly=3000.0, Lz=1500.0, terrain=1, hc=300.0, ac=700.0),
+    dict(nx=2, ny=2, nz=3, r=4, Lx=2000.0, Ly=2000.0, Lz=1500.0, terrain=2, hc=250.0, ac=600.0, bc_lateral=1),
+    dict(nx=3, ny=2, nz=1, r=5, Lx=3000.0, Ly=2000.0, Lz=800.0, terrain=1, hc=200.0, ac=900.0),
+    dict(nx=2, ny=1, nz=2, r=6, Lx=2000.0, Ly=1000.0, Lz=1000.0, terrain=1, hc=150.0, ac=500.0, bc_lateral=1),
+]
+
+
+def _ids(m):
+    return "%dx%dx%d_r%d_t%d_bc%d" % (m["nx"], m["ny"], m["nz"], m["r"], m.get("terrain", 0), m.get("bc_lateral", 0))
+
+
+@pytest.fixture(params=MESHES, ids=[_ids(m) for m in MESHES])
+def case(request):
+    c = Case(**request.param)
+    rho, pk = c.random_coefficients(seed=11)
+    c.set_coefficients(rho, pk, A_DT)
+    c.rho, c.pk = rho, pk
+    yield c
+    c.close()
+
+
+def test_node_coords(case):
+    import torch
+    X = torch.zeros(3 * case.N, dtype=torch.float64, device="cuda")
+    dgx.dgx_node_coords(case.ctx, X.data_ptr())
+    ref = case.coords()
+    assert np.abs(host(X).reshape(3, -1) - ref).max() <= 1e-9
+
+
+def test_preconditioner_diagonals(case):
+    import torch
+    for pc in (dgx.DGX_PC_HELMHOLTZ, dgx.DGX_PC_INTERNAL_ENERGY):
+        d = torch.zeros(case.N, dtype=torch.float64, device="cuda")
+        dgx.dgx_preconditioner_diagonal(case.ctx, pc, d.data_ptr())
+        ref = O.precond_diag(case.m, pc, A_DT, GAMMA, case.rho, case.pk)
+        assert rel_max_err(host(d), ref) <= TOL64
+    x = dev(inputs.random_field(case.N, 5))
+    y = torch.zeros_like(x)
+    dgx.dgx_apply_preconditioner(case.ctx, dgx.DGX_PC_HELMHOLTZ, dgx.DGX_F64, x.data_ptr(), y.data_ptr())
+    ref = host(x) / O.precond_diag(case.m, 1, A_DT, GAMMA, case.rho, case.pk)
+    assert rel_max_err(host(y), ref) <= TOL64
+
+
+def test_grad_and_mass_inverse(case):
+    import torch
+    p = inputs.random_field(case.N, 21, scale=100.0)
+    V = torch.zeros(3 * case.N, dtype=torch.float64, device="cuda")
+    dgx.dgx_apply_grad(case.ctx, dgx.DGX_F64, dev(p).data_ptr(), V.data_ptr())
+    ref = O.apply_Ainv(case.m, case.rho, O.apply_B(case.m, A_DT, p))
+    assert rel_max_err(host(V), ref) <= TOL64
+    w = inputs.random_field(3 * case.N, 22)
+    out = torch.zeros(3 * case.N, dtype=torch.float64, device="cuda")
+    dgx.dgx_apply_mass_inverse(case.ctx, dgx.DGX_F64, dev(w).data_ptr(), out.data_ptr())
+    assert rel_max_err(host(out), O.apply_Ainv(case.m, case.rho, w)) <= TOL64
+
+
+def test_div(case):
+    import torch
+    p = inputs.random_field(case.N, 31, scale=100.0)
+    V = inputs.random_field(3 * case.N, 32)
+    y = torch.zeros(case.N, dtype=torch.float64, device="cuda")
+    dgx.dgx_apply_div(case.ctx, dgx.DGX_F64, dev(V).data_ptr(), dev(p).data_ptr(), y.data_ptr())
+    ref = O.apply_D(case.m, GAMMA, p) - O.apply_C(case.m, A_DT, GAMMA, case.pk, V)
+    assert rel_max_err(host(y), ref) <= TOL64
+
+
+def test_operator_f64(case):
+    import torch
+    for seed in (41, 42):
+        p = inputs.random_field(case.N, seed, scale=100.0)
+        y = torch.zeros(case.N, dtype=torch.float64, device="cuda")
+        dgx.dgx_apply_operator(case.ctx, dgx.DGX_F64, dev(p).data_ptr(), y.data_ptr())
+        ref = O.apply_S(case.m, A_DT, GAMMA, case.rho, case.pk, p)
+        assert rel_max_err(host(y), ref) <= TOL64
+
+
+def test_operator_f32(case):
+    import torch
+    p = inputs.random_field(case.N, 51, scale=100.0)
+    y = torch.zeros(case.N, dtype=torch.float32, device="cuda")
+    dgx.dgx_apply_operator(case.ctx, dgx.DGX_F32, dev(p.astype(np.float32)).data_ptr(), y.data_ptr())
+    ref = O.apply_S(case.m, A_DT, GAMMA, case.rho, case.pk, p.astype(np.float32).astype(np.float64))
+    assert rel_max_err(host(y), ref) <= TOL32
+
+
+def test_operator_is_deterministic(case):
+    import torch
+    p = dev(inputs.random_field(case.N, 61))
+    y1 = torch.zeros_like(p)
+    y2 = torch.zeros_like(p)
+    dgx.dgx_apply_operator(case.ctx, dgx.DGX_F64, p.data_ptr(), y1.data_ptr())
+    dgx.dgx_apply_operator(case.ctx, dgx.DGX_F64, p.data_ptr(), y2.data_ptr())
+    assert np.array_equal(host(y1), host(y2))
+
+
+def test_errors_are_reported():
+    import torch
+    c = Case(2, 2, 2, 2)
+    x = torch.zeros(c.N, dtype=torch.float64, device="cuda")
+    with pytest.raises(dgx.DgxError) as e:  # no coefficients yet
+        dgx.dgx_apply_operator(c.ctx, dgx.DGX_F64, x.data_ptr(), x.data_ptr() + 8)
+    assert e.value.code == dgx.DGX_ERR_STATE
+    rho, pk = c.random_coefficients(3)
+    c.set_coefficients(rho, pk, A_DT)
+    with pytest.raises(dgx.DgxError) as e:  # aliasing input and output
+        dgx.dgx_apply_operator(c.ctx, dgx.DGX_F64, x.data_ptr(), x.data_ptr())
+    assert e.value.code == dgx.DGX_ERR_ARG
+    with pytest.raises(dgx.DgxError):
+        dgx.dgx_mesh_build(c.ctx, dgx.mesh_desc(2, 2, 2, 9, 1.0, 1.0, 1.0))  # degree too high
+    with pytest.raises(dgx.DgxError):
+        bad = dgx.mesh_desc(2, 2, 2, 2, 1000.0, 1000.0, 100.0, terrain=1, h_c=500.0, a_c=300.0)
+        dgx.dgx_mesh_build(c.ctx, bad)  # terrain above the model top
+    c.close()
+
+
+@pytest.mark.parametrize("terrain", [0, 1])
+def test_full_size_sampled(terrain):
+    """64 x 64 x 32 cells, r = 4 (16 384 000 DoFs), terrain-following hill,
+    far-field lateral faces: GPU apply over the whole mesh, compared on
+    sampled cells (corners, edges, the hill top, random) with the oracle's
+    cell-by-cell evaluation."""
+    import torch
+    c = Case(64, 64, 32, 4, Lx=60000.0, Ly=60000.0, Lz=20000.0, terrain=terrain, hc=400.0, ac=1000.0,
+             bc_lateral=1)
+    X = torch.zeros(3 * c.N, dtype=torch.float64, device="cuda")
+    dgx.dgx_node_coords(c.ctx, X.data_ptr())
+    z = host(X)[2 * c.N:]
+    rho = inputs.perturbed_profile(z, 1.2, 7314.0, 0.05, 71)
+    pk = inputs.perturbed_profile(z, 1e5, 7314.0, 0.05, 72)
+    c.set_coefficients(rho, pk, A_DT)
+    p = inputs.random_field(c.N, 73, scale=50.0)
+    y = torch.zeros(c.N, dtype=torch.float64, device="cuda")
+    dgx.dgx_apply_operator(c.ctx, dgx.DGX_F64, dev(p).data_ptr(), y.data_ptr())
+    yg = host(y)
+    nx, ny, nz = 64, 64, 32
+    cells = [0, nx - 1, nx * ny - 1, nx * ny * nz - 1, 32 + nx * 32, 32 + nx * (32 + ny * 0),
+             31 + nx * (31 + ny * 15)]
+    rng = np.random.default_rng(74)
+    cells += list(rng.integers(0, nx * ny * nz, 9))
+    ys = O.apply_S(c.m, A_DT, GAMMA, rho, pk, p, cells=cells)
+    n3 = 125
+    idx = np.concatenate([np.arange(cc * n3, (cc + 1) * n3) for cc in cells])
+    assert rel_max_err(yg[idx], ys[idx]) <= TOL64
+    c.close()
