@@ -71,12 +71,14 @@ def test_grad_and_mass_inverse(case):
     import torch
     p = inputs.random_field(case.N, 21, scale=100.0)
     V = torch.zeros(3 * case.N, dtype=torch.float64, device="cuda")
-    dgx.dgx_apply_grad(case.ctx, dgx.DGX_F64, dev(p).data_ptr(), V.data_ptr())
+    pd = dev(p)  # keep a reference: the library reads it asynchronously
+    dgx.dgx_apply_grad(case.ctx, dgx.DGX_F64, pd.data_ptr(), V.data_ptr())
     ref = O.apply_Ainv(case.m, case.rho, O.apply_B(case.m, A_DT, p))
     assert rel_max_err(host(V), ref) <= TOL64
     w = inputs.random_field(3 * case.N, 22)
     out = torch.zeros(3 * case.N, dtype=torch.float64, device="cuda")
-    dgx.dgx_apply_mass_inverse(case.ctx, dgx.DGX_F64, dev(w).data_ptr(), out.data_ptr())
+    wd = dev(w)
+    dgx.dgx_apply_mass_inverse(case.ctx, dgx.DGX_F64, wd.data_ptr(), out.data_ptr())
     assert rel_max_err(host(out), O.apply_Ainv(case.m, case.rho, w)) <= TOL64
 
 
@@ -85,7 +87,8 @@ def test_div(case):
     p = inputs.random_field(case.N, 31, scale=100.0)
     V = inputs.random_field(3 * case.N, 32)
     y = torch.zeros(case.N, dtype=torch.float64, device="cuda")
-    dgx.dgx_apply_div(case.ctx, dgx.DGX_F64, dev(V).data_ptr(), dev(p).data_ptr(), y.data_ptr())
+    Vd, pd = dev(V), dev(p)
+    dgx.dgx_apply_div(case.ctx, dgx.DGX_F64, Vd.data_ptr(), pd.data_ptr(), y.data_ptr())
     ref = O.apply_D(case.m, GAMMA, p) - O.apply_C(case.m, A_DT, GAMMA, case.pk, V)
     assert rel_max_err(host(y), ref) <= TOL64
 
@@ -95,7 +98,8 @@ def test_operator_f64(case):
     for seed in (41, 42):
         p = inputs.random_field(case.N, seed, scale=100.0)
         y = torch.zeros(case.N, dtype=torch.float64, device="cuda")
-        dgx.dgx_apply_operator(case.ctx, dgx.DGX_F64, dev(p).data_ptr(), y.data_ptr())
+        pd = dev(p)
+        dgx.dgx_apply_operator(case.ctx, dgx.DGX_F64, pd.data_ptr(), y.data_ptr())
         ref = O.apply_S(case.m, A_DT, GAMMA, case.rho, case.pk, p)
         assert rel_max_err(host(y), ref) <= TOL64
 
@@ -104,7 +108,8 @@ def test_operator_f32(case):
     import torch
     p = inputs.random_field(case.N, 51, scale=100.0)
     y = torch.zeros(case.N, dtype=torch.float32, device="cuda")
-    dgx.dgx_apply_operator(case.ctx, dgx.DGX_F32, dev(p.astype(np.float32)).data_ptr(), y.data_ptr())
+    pd = dev(p.astype(np.float32))
+    dgx.dgx_apply_operator(case.ctx, dgx.DGX_F32, pd.data_ptr(), y.data_ptr())
     ref = O.apply_S(case.m, A_DT, GAMMA, case.rho, case.pk, p.astype(np.float32).astype(np.float64))
     assert rel_max_err(host(y), ref) <= TOL32
 
@@ -156,7 +161,8 @@ def test_full_size_sampled(terrain):
     c.set_coefficients(rho, pk, A_DT)
     p = inputs.random_field(c.N, 73, scale=50.0)
     y = torch.zeros(c.N, dtype=torch.float64, device="cuda")
-    dgx.dgx_apply_operator(c.ctx, dgx.DGX_F64, dev(p).data_ptr(), y.data_ptr())
+    pd = dev(p)
+    dgx.dgx_apply_operator(c.ctx, dgx.DGX_F64, pd.data_ptr(), y.data_ptr())
     yg = host(y)
     nx, ny, nz = 64, 64, 32
     cells = [0, nx - 1, nx * ny - 1, nx * ny * nz - 1, 32 + nx * 32, 32 + nx * (32 + ny * 0),
