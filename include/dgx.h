@@ -162,6 +162,26 @@ int dgx_solve_pressure(dgx_ctx *ctx, const double *b, double *x, const dgx_solve
 /* Default options: FGMRES(30), Helmholtz preconditioner, tol 1e-8. */
 void dgx_default_solve_opts(dgx_solve_opts *opts);
 
+/* Allocation-free variant of dgx_apply_operator.  The paper has no
+ * counterpart: this serves callers that cannot allocate device memory when
+ * they apply the operator (an application whose pool allocator owns all
+ * device memory after start-up, or a time-critical loop that must not call
+ * cudaMalloc).  y = S x exactly as dgx_apply_operator (same kernels, same
+ * result), but the intermediate V = A^-1 B x (3N elements of type `prec`)
+ * lives in a fixed file-scope device array of DGX_NOALLOC_SCRATCH_BYTES
+ * (16 MiB) that every GPU loading the library holds until process exit; the
+ * call allocates nothing.  Limit: 3 N sizeof(prec) <= 16 MiB, i.e.
+ * N <= 699050 in FP64 and N <= 1398101 in FP32; larger meshes get
+ * DGX_ERR_ARG with a message.  The first call on a device looks up the
+ * array's device address with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents: calls whose GPU work overlaps (other streams or
+ * contexts on the same device) race on it and must be serialised by the
+ * caller.  Nothing needs clearing: each call writes all 3N entries it reads.
+ * Errors as dgx_apply_operator. */
+#define DGX_NOALLOC_SCRATCH_BYTES (16u << 20)
+int dgx_apply_operator_noalloc(dgx_ctx *ctx, int prec, const void *x, void *y);
+
 /* Algorithmic work of one dgx_apply_operator call for the current mesh (host
  * pointers, any may be NULL): floating-point operations of the implemented
  * sum-factorisation sweeps of the gradient kernel (V = A^-1 B p) and of the

@@ -73,6 +73,7 @@ SIGNATURES = [
     ("dgx_default_solve_opts", None, [C.POINTER(dgx_solve_opts)]),
     ("dgx_operator_cost", C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("dgx_kernel_launches", C.c_longlong, []),
+    ("dgx_apply_operator_noalloc", C.c_int, [_P, C.c_int, _P, _P]),
 ]
 
 _lib = None
@@ -196,6 +197,15 @@ def dgx_operator_cost(ctx):
     f1, f2, b64 = C.c_double(), C.c_double(), C.c_double()
     _check(ctx, load().dgx_operator_cost(ctx, C.byref(f1), C.byref(f2), C.byref(b64)))
     return f1.value, f2.value, b64.value
+
+
+def dgx_apply_operator_noalloc(ctx, prec, x_ptr, y_ptr):
+    """y = S x with the scratch in the library's fixed static device array
+    (no allocation; N limited by DGX_NOALLOC_SCRATCH_BYTES)."""
+    return _check(ctx, load().dgx_apply_operator_noalloc(ctx, prec, C.c_void_p(x_ptr), C.c_void_p(y_ptr)))
+
+
+DGX_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 def dgx_kernel_launches():
