@@ -204,3 +204,65 @@ def assemble(apply, n_in, n_out):
         Mx[:, j] = apply(e)
         e[j] = 0.0
     return Mx
+
+
+# ---------------------------------------------------------------- IMEX step
+class OrcBg(C.Structure):
+    """Mirror of ``orc_bg`` in orc_imex.c."""
+
+    _fields_ = [("kind", C.c_int), ("pad", C.c_int), ("T", C.c_double), ("p0", C.c_double), ("Nbv", C.c_double),
+                ("R", C.c_double), ("gamma", C.c_double), ("g", C.c_double), ("ubar", C.c_double)]
+
+
+def make_bg(kind=0, T=250.0, p0=1e5, Nbv=0.01, R=287.0, gamma=1.4, g=9.81, ubar=10.0):
+    b = OrcBg()
+    b.kind, b.T, b.p0, b.Nbv, b.R, b.gamma, b.g, b.ubar = kind, T, p0, Nbv, R, gamma, g, ubar
+    return b
+
+
+def background(m, bg):
+    N = ndofs(m)
+    rb, pb = np.zeros(N), np.zeros(N)
+    assert lib().orc_background(C.byref(m), C.byref(bg), _dp(rb), _dp(pb)) == 0
+    return rb, pb
+
+
+def explicit(m, bg, rho, u, rho_bar):
+    """Explicit tendencies (Erho, Em (3N), Ee) as dual vectors."""
+    N = ndofs(m)
+    Er, Em, Ee = np.zeros(N), np.zeros(3 * N), np.zeros(N)
+    c = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    assert lib().orc_explicit(C.byref(m), C.byref(bg), _dp(c(rho)), _dp(c(u)), _dp(c(rho_bar)), _dp(Er), _dp(Em),
+                              _dp(Ee)) == 0
+    return Er, Em, Ee
+
+
+def kinetic_mass(m, rho, u):
+    out = np.zeros(ndofs(m))
+    c = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    assert lib().orc_kinetic_mass(C.byref(m), _dp(c(rho)), _dp(c(u)), _dp(out)) == 0
+    return out
+
+
+def ars222():
+    """ARS(2,2,2) tableaux (explicit A, implicit At), gamma = 1 - 1/sqrt(2)."""
+    g = 1.0 - 1.0 / np.sqrt(2.0)
+    d = 1.0 - 1.0 / (2.0 * g)
+    A = np.array([[0, 0, 0], [g, 0, 0], [d, 1 - d, 0]], dtype=np.float64)
+    At = np.array([[0, 0, 0], [0, g, 0], [0, 1 - g, g]], dtype=np.float64)
+    return A, At
+
+
+def imex_step(m, bg, rho, u, p, dt, A=None, At=None, K=2, tol=1e-12):
+    """One IMEX step; returns (rho, u, p, status, Krylov iterations)."""
+    if A is None:
+        A, At = ars222()
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    At = np.ascontiguousarray(At, dtype=np.float64)
+    r = np.array(rho, dtype=np.float64)
+    v = np.array(u, dtype=np.float64)
+    q = np.array(p, dtype=np.float64)
+    its = C.c_int(0)
+    st = lib().orc_imex_step(C.byref(m), C.byref(bg), A.shape[0], _dp(A), _dp(At), C.c_double(dt), int(K),
+                             C.c_double(tol), _dp(r), _dp(v), _dp(q), C.byref(its))
+    return r, v, q, st, its.value

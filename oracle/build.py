@@ -16,7 +16,8 @@ def _stale():
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    return any(os.path.getmtime(os.path.join(HERE, s)) > t for s in SOURCES if os.path.exists(os.path.join(HERE, s)))
+    deps = SOURCES + ["orc_core.h"]
+    return any(os.path.getmtime(os.path.join(HERE, s)) > t for s in deps if os.path.exists(os.path.join(HERE, s)))
 
 
 def build(force=False):

@@ -1,0 +1,318 @@
+/*
+ * FP64 CPU oracle of the explicit fluxes and of one IMEX step of the
+ * compressible-Euler scheme (arXiv:2505.00384, Sec. 2: the IMEX-RK stage
+ * equations, the explicit sums m^(l) and e^(l), the pressure equation solved
+ * by fixed-point iterations, and the block system A U + B P = F,
+ * C U + D P = G).
+ *
+ * TEST INFRASTRUCTURE: the independent checker of the CUDA library; loaded
+ * only by the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark.  Plain definitions: fields evaluated at every quadrature point
+ * by summing over all basis functions, dense loops, no sum factorisation.
+ *
+ * Readings of what the paper leaves open (stated again where used):
+ *   - state (rho, u, p) nodal DG fields; rho E = p/(gamma-1) + rho |u|^2/2;
+ *   - perturbations p' = p - p_bar, rho' = rho - rho_bar against a hydrostatic
+ *     background; the pair -grad p + rho g becomes -grad p' + rho' g;
+ *   - explicit fluxes: continuity rho u, momentum rho u_d u, kinetic energy
+ *     rho k u, all with the local Lax-Friedrichs (Rusanov) flux with the
+ *     advective speed max(|u-.n|, |u+.n|); gravity work rho g.u explicit;
+ *   - implicit terms (tableau A~): pressure gradient with buoyancy rho' g in the
+ *     momentum equation, enthalpy flux in the energy equation (central fluxes,
+ *     the operators B and C of the pressure solve);
+ *   - boundaries: slip walls (mirror state) at bottom and top; lateral faces
+ *     slip walls or far field (ghost rho = rho_bar, u = (u_bar, 0, 0));
+ *   - the tableau must be stiffly accurate with an explicit first stage
+ *     (the new state is the last stage);
+ *   - K fixed-point iterations per implicit stage starting from the previous
+ *     stage, each one linear solve S p' = G' - C A^-1 F by FGMRES.
+ */
+#include "orc_core.h"
+
+/* defined in orc.c */
+int orc_apply_B(const orc_mesh *m, double alpha, const double *p, double *out);
+int orc_apply_A(const orc_mesh *m, const double *rho, const double *in, double *out);
+int orc_apply_Ainv(const orc_mesh *m, const double *rho, const double *in, double *out);
+int orc_apply_C(const orc_mesh *m, double alpha, double gamma, const double *pk, const double *V, double *out);
+int orc_apply_M(const orc_mesh *m, double scale, const double *f, double *out);
+int orc_precond_diag(const orc_mesh *m, int kind, double alpha, double gamma, const double *rho, const double *pk,
+                     double *dg);
+int orc_fgmres(const orc_mesh *m, double alpha, double gamma, const double *rho, const double *pk,
+               const double *dinv, const double *b, double *x, double tol, int restart, int maxit, int *its_out,
+               double *relres_out);
+
+typedef struct {
+  int kind;   /* 0 isothermal, 1 constant buoyancy frequency (Sec. 3) */
+  int pad;
+  double T, p0, Nbv, R, gamma, g, ubar;
+} orc_bg;
+
+static void bg_point(const orc_bg *b, double z, double *rho, double *p) {
+  if (b->kind == 0) {
+    *p = b->p0 * exp(-b->g * z / (b->R * b->T));
+    *rho = *p / (b->R * b->T);
+  } else {
+    /* Sec. 3: rho = rho_ref (p/p_ref)^(1/gamma) exp(-N^2 z / g), Gamma = (gamma-1)/gamma,
+     * p = p_ref {1 - (g^2/N^2) Gamma rho_ref/p_ref [1 - exp(-N^2 z/g)]}^(1/Gamma).
+     * Reading: the pressure formula as printed has g/N^2, which is not in
+     * hydrostatic balance (dp/dz = -rho instead of -rho g); g^2/N^2 is the
+     * balanced constant-buoyancy-frequency state the test case describes. */
+    double G = (b->gamma - 1.0) / b->gamma, rref = b->p0 / (b->R * b->T);
+    double e = exp(-b->Nbv * b->Nbv * z / b->g);
+    *p = b->p0 * pow(1.0 - b->g * b->g / (b->Nbv * b->Nbv) * G * rref / b->p0 * (1.0 - e), 1.0 / G);
+    *rho = rref * pow(*p / b->p0, 1.0 / b->gamma) * e;
+  }
+}
+
+/* Nodal background fields at the physical node heights. */
+int orc_background(const orc_mesh *m, const orc_bg *b, double *rho_bar, double *p_bar) {
+  tabs T;
+  if (tabs_init(&T, m)) return -1;
+  long nc = orc_num_cells(m);
+  int n3 = T.n3;
+#pragma omp parallel for schedule(static)
+  for (long c = 0; c < nc; ++c) {
+    double Xn[3 * ORC_MAXN * ORC_MAXN * ORC_MAXN];
+    cell_nodes(m, &T, c, Xn);
+    for (int i = 0; i < n3; ++i) bg_point(b, Xn[2 * n3 + i], &rho_bar[c * n3 + i], &p_bar[c * n3 + i]);
+  }
+  tabs_free(&T);
+  return 0;
+}
+
+/* Explicit tendencies of one state (dual vectors, tested against psi_i):
+ *   Erho_i = int rho u . grad psi_i - int_dK F^_rho psi_i
+ *   Em_{d,i} = int rho u_d u . grad psi_i - int_dK F^_{m_d} psi_i
+ *   Ee_i = int rho k u . grad psi_i - int_dK F^_k psi_i + int rho g.u psi_i
+ * F^ = (1/2)(q- u-.nA + q+ u+.nA) + (1/2) lambda |nA| (q- - q+),
+ * lambda = max(|u-.n|, |u+.n|) (local Lax-Friedrichs with the advective speed). */
+int orc_explicit(const orc_mesh *m, const orc_bg *b, const double *rho, const double *u, const double *rho_bar,
+                 double *Erho, double *Em, double *Ee) {
+  tabs T;
+  if (tabs_init(&T, m)) return -1;
+  long nc = orc_num_cells(m);
+  int n3 = T.n3;
+  long N = nc * n3;
+  const double *u0 = u, *u1 = u + N, *u2 = u + 2 * N;
+#pragma omp parallel
+  {
+    cgeo G;
+    cgeo_alloc(&G, &T);
+    double *loc = malloc(sizeof(double) * 5 * n3);
+#pragma omp for schedule(dynamic, 4)
+    for (long c = 0; c < nc; ++c) {
+      cell_geometry(m, &T, c, &G);
+      memset(loc, 0, sizeof(double) * 5 * n3);
+      const double *rc = rho + c * n3;
+      for (int qp = 0; qp < T.q3; ++qp) {
+        const double *ps = T.psi + (size_t)qp * n3, *dps = T.dpsi + (size_t)qp * 3 * n3;
+        const double *Ji = G.Ji + qp * 9;
+        double r = dotn(n3, rc, ps);
+        double v[3] = {dotn(n3, u0 + c * n3, ps), dotn(n3, u1 + c * n3, ps), dotn(n3, u2 + c * n3, ps)};
+        double k = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        double q[5] = {r, r * v[0], r * v[1], r * v[2], r * k};
+        double wd = G.wdet[qp];
+        for (int i = 0; i < n3; ++i) {
+          double ug = 0.0;
+          for (int d = 0; d < 3; ++d)
+            ug += v[d] * (dps[i] * Ji[d] + dps[n3 + i] * Ji[3 + d] + dps[2 * n3 + i] * Ji[6 + d]);
+          for (int f = 0; f < 5; ++f) loc[f * n3 + i] += wd * q[f] * ug;
+          loc[4 * n3 + i] += wd * (-b->g * r * v[2]) * ps[i];
+        }
+      }
+      for (int f = 0; f < 6; ++f) {
+        int kd = f / 2, s = f % 2;
+        long nb = neighbour(m, c, kd, s);
+        int bk = boundary_kind(m, kd);
+        const double *fps = T.fpsi[f], *fpsn = T.fpsi[2 * kd + (1 - s)];
+        for (int qp = 0; qp < T.q2; ++qp) {
+          const double *ps = fps + (size_t)qp * n3;
+          const double *nA = G.nA[f] + 3 * qp;
+          double an = sqrt(nA[0] * nA[0] + nA[1] * nA[1] + nA[2] * nA[2]);
+          double nh[3] = {nA[0] / an, nA[1] / an, nA[2] / an};
+          double rm = dotn(n3, rc, ps);
+          double vm[3] = {dotn(n3, u0 + c * n3, ps), dotn(n3, u1 + c * n3, ps), dotn(n3, u2 + c * n3, ps)};
+          double rp, vp[3];
+          if (nb >= 0) {
+            const double *pn = fpsn + (size_t)qp * n3;
+            rp = dotn(n3, rho + nb * n3, pn);
+            vp[0] = dotn(n3, u0 + nb * n3, pn);
+            vp[1] = dotn(n3, u1 + nb * n3, pn);
+            vp[2] = dotn(n3, u2 + nb * n3, pn);
+          } else if (bk == 0) { /* slip wall: mirror state */
+            double un = vm[0] * nh[0] + vm[1] * nh[1] + vm[2] * nh[2];
+            rp = rm;
+            for (int d = 0; d < 3; ++d) vp[d] = vm[d] - 2.0 * un * nh[d];
+          } else { /* far field: background density, uniform inflow */
+            rp = dotn(n3, rho_bar + c * n3, ps);
+            vp[0] = b->ubar; vp[1] = 0.0; vp[2] = 0.0;
+          }
+          double km = 0.5 * (vm[0] * vm[0] + vm[1] * vm[1] + vm[2] * vm[2]);
+          double kp = 0.5 * (vp[0] * vp[0] + vp[1] * vp[1] + vp[2] * vp[2]);
+          double qm[5] = {rm, rm * vm[0], rm * vm[1], rm * vm[2], rm * km};
+          double qpv[5] = {rp, rp * vp[0], rp * vp[1], rp * vp[2], rp * kp};
+          double unm = vm[0] * nA[0] + vm[1] * nA[1] + vm[2] * nA[2];
+          double unp = vp[0] * nA[0] + vp[1] * nA[1] + vp[2] * nA[2];
+          double lam = fmax(fabs(unm), fabs(unp)) / an;
+          for (int fl = 0; fl < 5; ++fl) {
+            double F = 0.5 * (qm[fl] * unm + qpv[fl] * unp) + 0.5 * lam * an * (qm[fl] - qpv[fl]);
+            for (int i = 0; i < n3; ++i) loc[fl * n3 + i] -= F * ps[i];
+          }
+        }
+      }
+      for (int i = 0; i < n3; ++i) {
+        Erho[c * n3 + i] = loc[i];
+        Em[c * n3 + i] = loc[n3 + i];
+        Em[N + c * n3 + i] = loc[2 * n3 + i];
+        Em[2 * N + c * n3 + i] = loc[3 * n3 + i];
+        Ee[c * n3 + i] = loc[4 * n3 + i];
+      }
+    }
+    free(loc);
+    cgeo_free(&G);
+  }
+  tabs_free(&T);
+  return 0;
+}
+
+/* out_i = int rho |u|^2/2 psi_i (consistent rule). */
+int orc_kinetic_mass(const orc_mesh *m, const double *rho, const double *u, double *out) {
+  tabs T;
+  if (tabs_init(&T, m)) return -1;
+  long nc = orc_num_cells(m);
+  int n3 = T.n3;
+  long N = nc * n3;
+#pragma omp parallel
+  {
+    cgeo G;
+    cgeo_alloc(&G, &T);
+#pragma omp for schedule(dynamic, 4)
+    for (long c = 0; c < nc; ++c) {
+      cell_geometry(m, &T, c, &G);
+      double *o = out + c * n3;
+      for (int i = 0; i < n3; ++i) o[i] = 0.0;
+      for (int qp = 0; qp < T.q3; ++qp) {
+        const double *ps = T.psi + (size_t)qp * n3;
+        double r = dotn(n3, rho + c * n3, ps);
+        double v0 = dotn(n3, u + c * n3, ps), v1 = dotn(n3, u + N + c * n3, ps), v2 = dotn(n3, u + 2 * N + c * n3, ps);
+        double f = 0.5 * r * (v0 * v0 + v1 * v1 + v2 * v2) * G.wdet[qp];
+        for (int i = 0; i < n3; ++i) o[i] += f * ps[i];
+      }
+    }
+    cgeo_free(&G);
+  }
+  tabs_free(&T);
+  return 0;
+}
+
+/* Implicit-type terms of one stage state (dual vectors, without the tableau
+ * weight): Im = -B_1 p' + int rho' g.phi, Ie = -C_1(kappa(p)) u, with B_1, C_1
+ * the weak gradient and divergence of the pressure solve at alpha = 1. */
+static void implicit_terms(const orc_mesh *m, const orc_bg *b, long N, const double *rho, const double *u,
+                           const double *p, const double *rho_bar, const double *p_bar, double *Im, double *Ie,
+                           double *tmp) {
+  for (long i = 0; i < N; ++i) tmp[i] = p[i] - p_bar[i];
+  orc_apply_B(m, 1.0, tmp, Im);
+  for (long i = 0; i < 3 * N; ++i) Im[i] = -Im[i];
+  for (long i = 0; i < N; ++i) tmp[i] = rho[i] - rho_bar[i];
+  orc_apply_M(m, -b->g, tmp, tmp + N); /* g.phi_z = -g */
+  for (long i = 0; i < N; ++i) Im[2 * N + i] += tmp[N + i];
+  orc_apply_C(m, 1.0, b->gamma, p, u, Ie);
+  for (long i = 0; i < N; ++i) Ie[i] = -Ie[i];
+}
+
+/* One IMEX step of the stage equations (Sec. 2) in place on (rho, u, p).
+ * A, At: s x s row-major tableaux (explicit, implicit); dt; K fixed-point
+ * iterations per implicit stage; each linear solve by FGMRES(30) with the
+ * Helmholtz preconditioner to relative tolerance `tol`.  Returns 0 or the
+ * first nonzero solver status; *total_its = Krylov iterations. */
+int orc_imex_step(const orc_mesh *m, const orc_bg *b, int s, const double *A, const double *At, double dt, int K,
+                  double tol, double *rho, double *u, double *p, int *total_its) {
+  long N = orc_num_cells(m) * (long)(m->r + 1) * (m->r + 1) * (m->r + 1);
+  double gm = b->gamma;
+  /* per-stage tendencies: Erho, Em(3), Ee, Im(3), Ie = 9 N each */
+  double *Ten = calloc((size_t)9 * N * s, sizeof(double));
+  double *rb = malloc(sizeof(double) * N), *pb = malloc(sizeof(double) * N);
+  double *rn = malloc(sizeof(double) * N), *un = malloc(sizeof(double) * 3 * N), *pn = malloc(sizeof(double) * N);
+  double *rl = malloc(sizeof(double) * N), *ul = malloc(sizeof(double) * 3 * N), *pl = malloc(sizeof(double) * N);
+  double *Fs = malloc(sizeof(double) * 3 * N), *Gs = malloc(sizeof(double) * N), *W = malloc(sizeof(double) * 3 * N);
+  double *rhs = malloc(sizeof(double) * N), *x = malloc(sizeof(double) * N), *t1 = malloc(sizeof(double) * 3 * N);
+  double *t2 = malloc(sizeof(double) * 3 * N), *dinv = malloc(sizeof(double) * N), *ones = malloc(sizeof(double) * N);
+  int status = 0, its_sum = 0;
+  orc_background(m, b, rb, pb);
+  memcpy(rn, rho, sizeof(double) * N);
+  memcpy(un, u, sizeof(double) * 3 * N);
+  memcpy(pn, p, sizeof(double) * N);
+  for (long i = 0; i < N; ++i) ones[i] = 1.0;
+  for (int l = 0; l < s; ++l) {
+    double *Erho = Ten + (size_t)9 * N * l, *Em = Erho + N, *Ee = Em + 3 * N, *Im = Ee + N, *Ie = Im + 3 * N;
+    if (l == 0) {
+      memcpy(rl, rn, sizeof(double) * N);
+      memcpy(ul, un, sizeof(double) * 3 * N);
+      memcpy(pl, pn, sizeof(double) * N);
+    } else {
+      double al = At[l * s + l] * dt;
+      /* rho^(l) = rho^n + M^-1 dt sum_m a_lm Erho^(m)   (fast mass, rho = 1) */
+      for (long i = 0; i < 3 * N; ++i) t1[i] = 0.0;
+      for (int mm = 0; mm < l; ++mm) {
+        const double *E = Ten + (size_t)9 * N * mm;
+        for (long i = 0; i < N; ++i) t1[i] += dt * A[l * s + mm] * E[i];
+      }
+      orc_apply_Ainv(m, ones, t1, t2);
+      for (long i = 0; i < N; ++i) rl[i] = rn[i] + t2[i];
+      /* F static: A(rho^n) u^n + dt sum (a Em + a~ Im) + al int rho'^(l) g.phi */
+      orc_apply_A(m, rn, un, Fs);
+      for (int mm = 0; mm < l; ++mm) {
+        const double *E = Ten + (size_t)9 * N * mm;
+        for (long i = 0; i < 3 * N; ++i) Fs[i] += dt * (A[l * s + mm] * E[N + i] + At[l * s + mm] * E[5 * N + i]);
+      }
+      for (long i = 0; i < N; ++i) t1[i] = rl[i] - rb[i];
+      orc_apply_M(m, -b->g * al, t1, t2);
+      for (long i = 0; i < N; ++i) Fs[2 * N + i] += t2[i];
+      /* G static: D p'^n + int rho^n k^n psi + dt sum (a Ee + a~ Ie) */
+      for (long i = 0; i < N; ++i) t1[i] = pn[i] - pb[i];
+      orc_apply_M(m, 1.0 / (gm - 1.0), t1, Gs);
+      orc_kinetic_mass(m, rn, un, t2);
+      for (long i = 0; i < N; ++i) Gs[i] += t2[i];
+      for (int mm = 0; mm < l; ++mm) {
+        const double *E = Ten + (size_t)9 * N * mm;
+        for (long i = 0; i < N; ++i) Gs[i] += dt * (A[l * s + mm] * E[4 * N + i] + At[l * s + mm] * E[8 * N + i]);
+      }
+      /* fixed point: start from the previous stage (ul, pl hold it) */
+      if (al > 0.0) {
+        for (int k = 0; k < K; ++k) {
+          orc_kinetic_mass(m, rl, ul, t2);
+          for (long i = 0; i < N; ++i) rhs[i] = Gs[i] - t2[i];
+          orc_apply_Ainv(m, rl, Fs, W);
+          orc_apply_C(m, al, gm, pl, W, t2);
+          for (long i = 0; i < N; ++i) rhs[i] -= t2[i];
+          orc_precond_diag(m, 1, al, gm, rl, pl, dinv);
+          for (long i = 0; i < N; ++i) { dinv[i] = 1.0 / dinv[i]; x[i] = pl[i] - pb[i]; }
+          int its = 0;
+          double rel = 0.0;
+          int st = orc_fgmres(m, al, gm, rl, pl, dinv, rhs, x, tol, 30, 2000, &its, &rel);
+          if (st && !status) status = st;
+          its_sum += its;
+          orc_apply_B(m, al, x, t1);
+          orc_apply_Ainv(m, rl, t1, t2);
+          for (long i = 0; i < 3 * N; ++i) ul[i] = W[i] - t2[i];
+          for (long i = 0; i < N; ++i) pl[i] = pb[i] + x[i];
+        }
+      } else {
+        /* stages after the first must be implicit (a~_ll > 0) */
+        status = status ? status : -3;
+      }
+    }
+    if (l < s - 1) {
+      orc_explicit(m, b, rl, ul, rb, Erho, Em, Ee);
+      implicit_terms(m, b, N, rl, ul, pl, rb, pb, Im, Ie, t1);
+    }
+  }
+  memcpy(rho, rl, sizeof(double) * N);
+  memcpy(u, ul, sizeof(double) * 3 * N);
+  memcpy(p, pl, sizeof(double) * N);
+  if (total_its) *total_its = its_sum;
+  free(Ten); free(rb); free(pb); free(rn); free(un); free(pn); free(rl); free(ul); free(pl);
+  free(Fs); free(Gs); free(W); free(rhs); free(x); free(t1); free(t2); free(dinv); free(ones);
+  return status;
+}
