@@ -80,7 +80,9 @@ typedef struct {
 } dgx_mesh_desc;
 
 /* Hydrostatic background (Sec. 3): kind 0 isothermal at T (p = p0 exp(-g z/(R T))),
- * kind 1 the constant-buoyancy-frequency state of Sec. 3 with N_bv, T = T_ref. */
+ * kind 1 the constant-buoyancy-frequency state of Sec. 3 with N_bv, T = T_ref
+ * (rho = rho_ref (p/p0)^(1/gamma) exp(-N^2 z/g), p from hydrostatic balance:
+ * p = p0 {1 - (g^2/N^2) Gamma rho_ref/p0 [1 - exp(-N^2 z/g)]}^(1/Gamma)). */
 typedef struct {
   int kind;
   int reserved;
@@ -184,8 +186,9 @@ int dgx_apply_operator_noalloc(dgx_ctx *ctx, int prec, const void *x, void *y);
 
 /* Algorithmic work of one dgx_apply_operator call for the current mesh (host
  * pointers, any may be NULL): floating-point operations of the implemented
- * sum-factorisation sweeps of the gradient kernel (V = A^-1 B p) and of the
- * divergence kernel (y = D p - C V), and the HBM floor of the whole
+ * (even-odd) sum-factorisation sweeps and pointwise work of the gradient
+ * kernel (V = A^-1 B p) and of the divergence kernel (y = D p - C V), and the
+ * HBM floor of the whole
  * application in bytes (p, rho, p_k read once, y written once: 32 bytes per
  * DoF in FP64). */
 int dgx_operator_cost(const dgx_ctx *ctx, double *flops_grad, double *flops_div, double *bytes_f64);

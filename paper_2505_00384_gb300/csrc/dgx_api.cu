@@ -215,6 +215,17 @@ bool make_tables(int r, Tables1D &T) {
   return true;
 }
 
+}  // namespace
+
+bool build_table_block(int r, std::vector<double> &tab) {
+  Tables1D T;
+  if (!make_tables(r, T)) return false;
+  tab = T.tab;
+  return true;
+}
+
+namespace {
+
 double terrain_h(const dgx_mesh_desc &m, double x, double y) {
   if (m.terrain == 0) return 0.0;
   const double s = 1.0 + ((x - m.x_c) * (x - m.x_c) + (y - m.y_c) * (y - m.y_c)) / (m.a_c * m.a_c);
@@ -267,7 +278,9 @@ __global__ void k_background(BgP b, long long N, const double *__restrict__ X, d
       const double G = (b.gamma - 1.0) / b.gamma;
       const double rref = b.p0 / (b.R * b.T);
       const double e = exp(-b.Nbv * b.Nbv * z / b.g);
-      pv = b.p0 * pow(1.0 - b.g / (b.Nbv * b.Nbv) * G * rref / b.p0 * (1.0 - e), 1.0 / G);
+      // g^2/N^2: the hydrostatically balanced form of the Sec. 3 state (the
+      // printed g/N^2 does not satisfy dp/dz = -rho g)
+      pv = b.p0 * pow(1.0 - b.g * b.g / (b.Nbv * b.Nbv) * G * rref / b.p0 * (1.0 - e), 1.0 / G);
       rv = rref * pow(pv / b.p0, 1.0 / b.gamma) * e;
     }
     p[i] = pv;
@@ -714,6 +727,7 @@ int dgx_mesh_build(dgx_ctx *c, const dgx_mesh_desc *d) {
   if (cudaSetDevice(c->device) != cudaSuccess) return set_error(c, DGX_ERR_CUDA, "cudaSetDevice");
   cudaStreamSynchronize(c->stream);
   free_mesh(c);
+  if (int e = ensure_const_tables(c)) return e;
   c->mesh = *d;
   c->mesh.n_q = 2 * r + 1;
   c->n = r + 1;
@@ -939,21 +953,30 @@ int dgx_solve_pressure(dgx_ctx *c, const double *b, double *x, const dgx_solve_o
   return inf.status;
 }
 
+// Floating-point operations of one even-odd sweep line (MO outputs from MI
+// inputs): e/d formation, the E and Od products (2 flops per multiply-add), the
+// middle column, and the final a +- b combinations.
+static double eo_line_flops(int MO, int MI) {
+  const int HO = (MO + 1) / 2, HI = MI / 2;
+  return 2.0 * HI + 4.0 * HO * HI + ((MI & 1) ? HO : 0) + 2.0 * HO - (MO & 1);
+}
+
 int dgx_operator_cost(const dgx_ctx *c, double *flops_grad, double *flops_div, double *b64) {
   if (!c || !c->has_mesh) return DGX_ERR_STATE;
-  const double N = c->n, Q = c->q;
-  const double N2 = N * N, N3 = N2 * N, Q2 = Q * Q, Q3 = Q2 * Q;
+  const int N = c->n, Q = c->q;
+  const double N2 = N * N, N3 = N2 * N, Q2 = (double)Q * Q, Q3 = Q2 * Q;
   const bool cv = c->curved;
-  // sum-factorisation sweep costs (2 flops per multiply-add)
-  const double fwd = 2 * N * (Q * N2 + Q2 * N + Q3);  // N^3 -> Q^3, one field
-  const double bwd = 2 * Q * (Q2 * N + Q * N2 + N3);  // Q^3 -> N^3, one field
-  const double fface = 2 * N * (Q * N + Q2);           // N^2 -> Q^2
-  const double bface = 2 * Q * (N * Q + N2);           // Q^2 -> N^2
-  const double fast = 2 * N * 3 * N3;                  // one N^3 -> N^3 tensor sweep triple
+  // sweeps of one field: N^3 -> Q^3 (x, y, z) and Q^3 -> N^3 (z, y, x), faces N^2 <-> Q^2, N^3 -> N^3
+  const double fwd = eo_line_flops(Q, N) * (N2 + Q * N + Q2);
+  const double bwd = eo_line_flops(N, Q) * (Q2 + Q * N + N2);
+  const double fface = eo_line_flops(Q, N) * (N + Q);
+  const double bface = eo_line_flops(N, Q) * (Q + N);
+  const double nn = 3.0 * eo_line_flops(N, N) * N2;  // three N^3 -> N^3 sweeps
   const int nfv = cv ? 5 : 3, nfp = cv ? 10 : 6, nsl = cv ? 32 : 24;
-  const double k1 = fwd + (cv ? 14 : 6) * Q3 + nfv * bwd + 6 * fface + nfp * (4 * Q2 + bface) + fast +
-                    3 * (2 * fast + 6 * N3);
-  const double k2 = 5 * fwd + (cv ? 22 : 14) * Q3 + 4 * bwd + nsl * fface + 6 * (10 * Q2) + 6 * bface;
+  // pointwise work per quadrature point (flux construction, geometry), per face point, per fast point
+  const double k1 = fwd + (cv ? 16 : 6) * Q3 + nfv * bwd + 6 * fface + nfp * (6 * Q2 + bface) + nn /* rho */ +
+                    3 * (2 * nn + 8 * N3) + (cv ? 6 : 2) * N2 * 3;
+  const double k2 = 5 * fwd + (cv ? 26 : 14) * Q3 + 4 * bwd + nsl * fface + 6 * (14 * Q2) + 6 * bface + 5 * N3;
   if (flops_grad) *flops_grad = k1 * c->ncell;
   if (flops_div) *flops_div = k2 * c->ncell;
   if (b64) *b64 = 32.0 * c->N;

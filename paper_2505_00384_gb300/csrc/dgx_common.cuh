@@ -43,6 +43,34 @@ __host__ __device__ constexpr int tab_off_wa(int N, int Q) { return 7 * Q * N + 
 __host__ __device__ constexpr int tab_off_gq(int N, int Q) { return 7 * Q * N + 3 * N * N + Q + N; }
 __host__ __device__ constexpr int tab_size(int N, int Q) { return 7 * Q * N + 3 * N * N + 2 * Q + N; }
 
+// Identifiers of the 1D matrices used by the sum-factorisation sweeps and
+// their even-odd (centro-symmetric) storage in constant memory, all degrees
+// back to back.  A matrix of R rows and C columns stores E[(R+1)/2][C/2],
+// Od[(R+1)/2][C/2] and, for odd C, the middle column Mc[(R+1)/2].
+enum MatId : int { M_I = 0, M_D, M_IT, M_DT, M_IA, M_P, M_PT, M_IIT, M_DDT, M_IDT, M_COUNT };
+__host__ __device__ constexpr int mat_rows(int id, int N) { return (id == M_I || id == M_D) ? 2 * N - 1 : N; }
+__host__ __device__ constexpr int mat_cols(int id, int N) {
+  return (id == M_I || id == M_D || id == M_IA || id == M_P || id == M_PT) ? N : 2 * N - 1;
+}
+__host__ __device__ constexpr int mat_parity(int id) { return (id == M_D || id == M_DT || id == M_IDT) ? -1 : 1; }
+__host__ __device__ constexpr int eo_size(int R, int C) { return 2 * ((R + 1) / 2) * (C / 2) + ((C & 1) ? (R + 1) / 2 : 0); }
+__host__ __device__ constexpr int eo_deg_size(int N) {
+  int s = 0;
+  for (int id = 0; id < M_COUNT; ++id) s += eo_size(mat_rows(id, N), mat_cols(id, N));
+  return s;
+}
+__host__ __device__ constexpr int eo_deg_base(int N) {
+  int s = 0;
+  for (int n = 2; n < N; ++n) s += eo_deg_size(n);
+  return s;
+}
+__host__ __device__ constexpr int eo_mat_off(int N, int id) {
+  int s = eo_deg_base(N);
+  for (int j = 0; j < id; ++j) s += eo_size(mat_rows(j, N), mat_cols(j, N));
+  return s;
+}
+constexpr int kEoTotal = eo_deg_base(kMaxDegree + 2);
+
 // Per-column terrain table (curved meshes).  For column (cx, cy) the bottom
 // height h is interpolated from its values at the column's (r+1)^2 GLL
 // nodes; with z = zeta + h (1 - zeta/H) the Jacobian only needs h and its
@@ -133,6 +161,12 @@ int set_error(dgx_ctx *c, int code, const char *fmt, ...);
 void count_launch(int n = 1);
 long long launch_count();
 int check_cuda(dgx_ctx *c, cudaError_t e, const char *what);
+
+// host 1D table block of degree r (layout above), dgx_api.cu
+bool build_table_block(int r, std::vector<double> &tab);
+// upload the even-odd matrices of all degrees to constant memory of the
+// context's device (once per device), dgx_operator.cu
+int ensure_const_tables(dgx_ctx *c);
 
 // operator kernels (dgx_operator.cu)
 template <typename T>

@@ -18,53 +18,100 @@
 // definition, not by code): central fluxes; p+ = p- on every boundary face;
 // zero normal flux of kappa V on slip walls, transmissive on far-field faces;
 // Gal-Chen terrain-following map z = zeta + h(x,y) (1 - zeta/H).
+#include <cmath>
 #include <cstdio>
+#include <mutex>
 
 #include "dgx_common.cuh"
 
 namespace dgx {
 namespace {
 
+// ------------------------------------------------------------- 1D matrices
+// The 1D matrices of every degree live in __constant__ memory in even-odd
+// form.  All of them are centro-symmetric, M[R-1-o][C-1-m] = s M[o][m] with
+// s = +1 (interpolation, mass-like) or -1 (derivative): the Gauss and
+// Gauss-Lobatto point sets are symmetric about 1/2.  Writing
+//   e_m = in[m] + in[C-1-m],  d_m = in[m] - in[C-1-m]   (m < C/2),
+//   a_o = sum_m E[o][m] e_m + Mc[o] in[mid],  b_o = sum_m Od[o][m] d_m,
+// with E = (M[o][m] + M[o][C-1-m])/2, Od = (M[o][m] - M[o][C-1-m])/2 and Mc the
+// middle column (odd C), gives out[o] = a_o + b_o and out[R-1-o] = s (a_o - b_o)
+// for o < (R+1)/2: half the multiply-adds of the plain product.  Unrolled with
+// compile-time indices, every coefficient is an FMA operand read straight from
+// the constant bank (no load instruction).
+__constant__ float c_eo32[kEoTotal];
+__constant__ double c_eo64[kEoTotal];
+
+template <typename T>
+__device__ __forceinline__ T ceo(int i);
+template <>
+__device__ __forceinline__ float ceo<float>(int i) { return c_eo32[i]; }
+template <>
+__device__ __forceinline__ double ceo<double>(int i) { return c_eo64[i]; }
+
+// One line of length MI (stride ss in `src`) -> MO outputs (stride ds in `dst`).
+template <typename T, int NN, int MAT, int MO, int MI>
+__device__ __forceinline__ void line_eo(const T *src, int ss, T *dst, int ds) {
+  constexpr int HO = (MO + 1) / 2, HI = MI / 2;
+  constexpr int base = eo_mat_off(NN, MAT);
+  constexpr bool odd_in = (MI & 1) != 0;
+  constexpr int par = mat_parity(MAT);
+  T e[HI > 0 ? HI : 1], d[HI > 0 ? HI : 1];
+#pragma unroll
+  for (int m = 0; m < HI; ++m) {
+    const T x = src[m * ss], y = src[(MI - 1 - m) * ss];
+    e[m] = x + y;
+    d[m] = x - y;
+  }
+  const T c = odd_in ? src[HI * ss] : T(0);
+#pragma unroll
+  for (int o = 0; o < HO; ++o) {
+    T a = odd_in ? ceo<T>(base + 2 * HO * HI + o) * c : T(0);
+    T b = T(0);
+#pragma unroll
+    for (int m = 0; m < HI; ++m) {
+      a += ceo<T>(base + o * HI + m) * e[m];
+      b += ceo<T>(base + HO * HI + o * HI + m) * d[m];
+    }
+    dst[o * ds] = a + b;
+    if (o != MO - 1 - o) dst[(MO - 1 - o) * ds] = par > 0 ? a - b : b - a;
+  }
+}
+
 // One sum-factorisation sweep along direction DIR of `nf` fields stored back
 // to back.  Input field shape (S0, S1, S2), x fastest, with S_DIR == MI; the
-// output replaces that extent by MO.  Field f uses the [MO][MI] row-major
-// matrix selected by bits 2f..2f+1 of `sel`.
-template <typename T, int DIR, int MO, int MI, int S0, int S1, int S2>
-__device__ __forceinline__ void sweep(int nf, unsigned sel, const T *M0, const T *M1, const T *M2,
-                                      const T *__restrict__ in, T *__restrict__ out) {
-  constexpr int O0 = DIR == 0 ? MO : S0;
-  constexpr int O1 = DIR == 1 ? MO : S1;
-  constexpr int O2 = DIR == 2 ? MO : S2;
-  constexpr int OT = O0 * O1 * O2;
-  constexpr int IT = S0 * S1 * S2;
-  const int total = nf * OT;
+// output replaces that extent by MO.  One thread per 1D line; field f uses the
+// matrix MAT0 / MAT1 / MAT2 selected by bits 2f..2f+1 of `sel`.
+template <typename T, int NN, int DIR, int MO, int MI, int S0, int S1, int S2, int MAT0, int MAT1, int MAT2>
+__device__ __forceinline__ void sweep(int nf, unsigned sel, const T *__restrict__ in, T *__restrict__ out) {
+  constexpr int L0 = DIR == 0 ? S1 : S0;  // faster non-DIR extent
+  constexpr int L1 = DIR == 2 ? S1 : S2;  // slower non-DIR extent
+  constexpr int NL = L0 * L1;
+  constexpr int IT = S0 * S1 * S2, OT = IT / MI * MO;
+  constexpr int O0 = DIR == 0 ? MO : S0, O1 = DIR == 1 ? MO : S1;
+  constexpr int ss = DIR == 0 ? 1 : (DIR == 1 ? S0 : S0 * S1);
+  constexpr int ds = DIR == 0 ? 1 : (DIR == 1 ? O0 : O0 * O1);
+  const int total = nf * NL;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int f = idx / OT;
-    const int r = idx - f * OT;
-    const int i0 = r % O0;
-    const int i1 = (r / O0) % O1;
-    const int i2 = r / (O0 * O1);
-    const unsigned ms = (sel >> (2 * f)) & 3u;
-    const T *M = ms == 0 ? M0 : (ms == 1 ? M1 : M2);
-    const T *src = in + f * IT;
-    T acc = T(0);
+    const int f = idx / NL, l = idx - f * NL;
+    const int l0 = l % L0, l1 = l / L0;
+    int io, oo;
     if (DIR == 0) {
-      const T *row = M + i0 * MI;
-      const T *s = src + (i2 * S1 + i1) * S0;
-#pragma unroll
-      for (int m = 0; m < MI; ++m) acc += row[m] * s[m];
+      io = (l1 * S1 + l0) * S0;
+      oo = (l1 * O1 + l0) * O0;
     } else if (DIR == 1) {
-      const T *row = M + i1 * MI;
-      const T *s = src + i2 * S1 * S0 + i0;
-#pragma unroll
-      for (int m = 0; m < MI; ++m) acc += row[m] * s[m * S0];
+      io = l0 + S0 * S1 * l1;
+      oo = l0 + O0 * O1 * l1;
     } else {
-      const T *row = M + i2 * MI;
-      const T *s = src + i1 * S0 + i0;
-#pragma unroll
-      for (int m = 0; m < MI; ++m) acc += row[m] * s[m * S0 * S1];
+      io = l0 + S0 * l1;
+      oo = l0 + O0 * l1;
     }
-    out[idx] = acc;
+    const T *src = in + f * IT + io;
+    T *dst = out + f * OT + oo;
+    const unsigned ms = (sel >> (2 * f)) & 3u;
+    if (ms == 0) line_eo<T, NN, MAT0, MO, MI>(src, ss, dst, ds);
+    else if (ms == 1) line_eo<T, NN, MAT1, MO, MI>(src, ss, dst, ds);
+    else line_eo<T, NN, MAT2, MO, MI>(src, ss, dst, ds);
   }
 }
 
@@ -152,11 +199,11 @@ __device__ __forceinline__ void fast_inverse(const OpP<T> &P, const T *tab, cons
   const T *PT = tab + tab_off_PT(N, Q);
   const T *Pm = tab + tab_off_P(N, Q);
   const T *wa = tab + tab_off_wa(N, Q);
-  sweep<T, 0, N, N, N, N, N>(nf, 0u, PT, PT, PT, a, b);
+  sweep<T, N, 0, N, N, N, N, N, M_PT, M_PT, M_PT>(nf, 0u, a, b);
   __syncthreads();
-  sweep<T, 1, N, N, N, N, N>(nf, 0u, PT, PT, PT, b, a);
+  sweep<T, N, 1, N, N, N, N, N, M_PT, M_PT, M_PT>(nf, 0u, b, a);
   __syncthreads();
-  sweep<T, 2, N, N, N, N, N>(nf, 0u, PT, PT, PT, a, b);
+  sweep<T, N, 2, N, N, N, N, N, M_PT, M_PT, M_PT>(nf, 0u, a, b);
   __syncthreads();
   for (int idx = threadIdx.x; idx < nf * N3; idx += blockDim.x) {
     const int node = idx % N3;
@@ -166,11 +213,11 @@ __device__ __forceinline__ void fast_inverse(const OpP<T> &P, const T *tab, cons
     b[idx] = b[idx] / (rq[node] * wa[i] * wa[j] * wa[k] * det);
   }
   __syncthreads();
-  sweep<T, 0, N, N, N, N, N>(nf, 0u, Pm, Pm, Pm, b, a);
+  sweep<T, N, 0, N, N, N, N, N, M_P, M_P, M_P>(nf, 0u, b, a);
   __syncthreads();
-  sweep<T, 1, N, N, N, N, N>(nf, 0u, Pm, Pm, Pm, a, b);
+  sweep<T, N, 1, N, N, N, N, N, M_P, M_P, M_P>(nf, 0u, a, b);
   __syncthreads();
-  sweep<T, 2, N, N, N, N, N>(nf, 0u, Pm, Pm, Pm, b, a);
+  sweep<T, N, 2, N, N, N, N, N, M_P, M_P, M_P>(nf, 0u, b, a);
   __syncthreads();
 }
 
@@ -178,11 +225,11 @@ __device__ __forceinline__ void fast_inverse(const OpP<T> &P, const T *tab, cons
 template <typename T, int N, int Q>
 __device__ __forceinline__ void rho_fast(const T *tab, const T *rho, T *t1, T *t2, T *rq) {
   const T *Ia = tab + tab_off_Ia(N, Q);
-  sweep<T, 0, N, N, N, N, N>(1, 0u, Ia, Ia, Ia, rho, t1);
+  sweep<T, N, 0, N, N, N, N, N, M_IA, M_IA, M_IA>(1, 0u, rho, t1);
   __syncthreads();
-  sweep<T, 1, N, N, N, N, N>(1, 0u, Ia, Ia, Ia, t1, t2);
+  sweep<T, N, 1, N, N, N, N, N, M_IA, M_IA, M_IA>(1, 0u, t1, t2);
   __syncthreads();
-  sweep<T, 2, N, N, N, N, N>(1, 0u, Ia, Ia, Ia, t2, rq);
+  sweep<T, N, 2, N, N, N, N, N, M_IA, M_IA, M_IA>(1, 0u, t2, rq);
   __syncthreads();
 }
 
@@ -209,8 +256,12 @@ struct GradL {
   static constexpr int total = cmax(oZ + szZ, oFace + szFace);
 };
 
+// FP64 at r <= 4: ask for <= 85 registers so that three 256-thread CTAs fit on an SM.
+template <typename T, int N>
+constexpr int min_ctas() { return (sizeof(T) == 8 && N <= 5) ? 3 : 1; }
+
 template <typename T, int N, int Q, bool CURVED>
-__global__ void __launch_bounds__(256) k_grad(const OpP<T> P, const T *__restrict__ p, const T *__restrict__ rho,
+__global__ void __launch_bounds__(256, min_ctas<T, N>()) k_grad(const OpP<T> P, const T *__restrict__ p, const T *__restrict__ rho,
                                               T *__restrict__ V, long long Ntot) {
   using L = GradL<N, Q, CURVED>;
   constexpr int N2 = L::N2, N3 = L::N3, Q2 = L::Q2, Q3 = L::Q3, NFV = L::NFV, NFP = L::NFP;
@@ -236,11 +287,11 @@ __global__ void __launch_bounds__(256) k_grad(const OpP<T> P, const T *__restric
   const T *wq = tab + tab_off_wq(N, Q), *gq = tab + tab_off_gq(N, Q);
 
   // p at the Q^3 Gauss points; rho at the fast-rule points
-  sweep<T, 0, Q, N, N, N, N>(1, 0u, I, I, I, s_p, R1);
+  sweep<T, N, 0, Q, N, N, N, N, M_I, M_I, M_I>(1, 0u, s_p, R1);
   __syncthreads();
-  sweep<T, 1, Q, N, Q, N, N>(1, 0u, I, I, I, R1, R2);
+  sweep<T, N, 1, Q, N, Q, N, N, M_I, M_I, M_I>(1, 0u, R1, R2);
   __syncthreads();
-  sweep<T, 2, Q, N, Q, Q, N>(1, 0u, I, I, I, R2, Wv);
+  sweep<T, N, 2, Q, N, Q, Q, N, M_I, M_I, M_I>(1, 0u, R2, Wv);
   __syncthreads();
   rho_fast<T, N, Q>(tab, s_rho, R1, R2, s_rq);
 
@@ -268,17 +319,17 @@ __global__ void __launch_bounds__(256) k_grad(const OpP<T> P, const T *__restric
   __syncthreads();
   // test with grad: z, y, x sweeps; D^T in the field's reference direction j
   if (CURVED) {
-    sweep<T, 2, N, Q, Q, Q, Q>(NFV, (1u << 2) | (1u << 6) | (1u << 8), IT, DT, DT, Wv, Wz);
+    sweep<T, N, 2, N, Q, Q, Q, Q, M_IT, M_DT, M_DT>(NFV, (1u << 2) | (1u << 6) | (1u << 8), Wv, Wz);
     __syncthreads();
-    sweep<T, 1, N, Q, Q, Q, N>(NFV, (1u << 4), IT, DT, DT, Wz, Wy);
+    sweep<T, N, 1, N, Q, Q, Q, N, M_IT, M_DT, M_DT>(NFV, (1u << 4), Wz, Wy);
     __syncthreads();
-    sweep<T, 0, N, Q, Q, N, N>(NFV, (1u << 0), IT, DT, DT, Wy, Wx);
+    sweep<T, N, 0, N, Q, Q, N, N, M_IT, M_DT, M_DT>(NFV, (1u << 0), Wy, Wx);
   } else {
-    sweep<T, 2, N, Q, Q, Q, Q>(NFV, (1u << 4), IT, DT, DT, Wv, Wz);
+    sweep<T, N, 2, N, Q, Q, Q, Q, M_IT, M_DT, M_DT>(NFV, (1u << 4), Wv, Wz);
     __syncthreads();
-    sweep<T, 1, N, Q, Q, Q, N>(NFV, (1u << 2), IT, DT, DT, Wz, Wy);
+    sweep<T, N, 1, N, Q, Q, Q, N, M_IT, M_DT, M_DT>(NFV, (1u << 2), Wz, Wy);
     __syncthreads();
-    sweep<T, 0, N, Q, Q, N, N>(NFV, (1u << 0), IT, DT, DT, Wy, Wx);
+    sweep<T, N, 0, N, Q, Q, N, N, M_IT, M_DT, M_DT>(NFV, (1u << 0), Wy, Wx);
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < 3 * N3; idx += blockDim.x) {
@@ -300,9 +351,9 @@ __global__ void __launch_bounds__(256) k_grad(const OpP<T> P, const T *__restric
     Fg[idx] = nb >= 0 ? T(0.5) * (own + p[nb * N3 + face_node<N>(k, s ? 0 : N - 1, t1, t2)]) : own;
   }
   __syncthreads();
-  sweep<T, 0, Q, N, N, N, 1>(6, 0u, I, I, I, Fg, F1);
+  sweep<T, N, 0, Q, N, N, N, 1, M_I, M_I, M_I>(6, 0u, Fg, F1);
   __syncthreads();
-  sweep<T, 1, Q, N, Q, N, 1>(6, 0u, I, I, I, F1, F2);
+  sweep<T, N, 1, Q, N, Q, N, 1, M_I, M_I, M_I>(6, 0u, F1, F2);
   __syncthreads();
   for (int idx = threadIdx.x; idx < NFP * Q2; idx += blockDim.x) {
     const int sl = idx / Q2, t = idx % Q2, i = t % Q, j = t / Q;
@@ -319,9 +370,9 @@ __global__ void __launch_bounds__(256) k_grad(const OpP<T> P, const T *__restric
     Fp[idx] = P.alpha * wq[i] * wq[j] * nA[d] * F2[f * Q2 + t];
   }
   __syncthreads();
-  sweep<T, 0, N, Q, Q, Q, 1>(NFP, 0u, IT, IT, IT, Fp, Fb1);
+  sweep<T, N, 0, N, Q, Q, Q, 1, M_IT, M_IT, M_IT>(NFP, 0u, Fp, Fb1);
   __syncthreads();
-  sweep<T, 1, N, Q, N, Q, 1>(NFP, 0u, IT, IT, IT, Fb1, Fb2);
+  sweep<T, N, 1, N, Q, N, Q, 1, M_IT, M_IT, M_IT>(NFP, 0u, Fb1, Fb2);
   __syncthreads();
   for (int idx = threadIdx.x; idx < 3 * N3; idx += blockDim.x) {
     const int d = idx / N3, node = idx % N3;
@@ -399,7 +450,7 @@ __device__ __forceinline__ int div_slot_base(int f) {
 }
 
 template <typename T, int N, int Q, bool CURVED>
-__global__ void __launch_bounds__(256) k_div(const OpP<T> P, const T *__restrict__ V, const T *__restrict__ p,
+__global__ void __launch_bounds__(256, min_ctas<T, N>()) k_div(const OpP<T> P, const T *__restrict__ V, const T *__restrict__ p,
                                              const T *__restrict__ pk, T *__restrict__ y, long long Ntot) {
   using L = DivL<N, Q, CURVED>;
   constexpr int N2 = L::N2, N3 = L::N3, Q2 = L::Q2, Q3 = L::Q3, NSL = L::NSL;
@@ -429,11 +480,11 @@ __global__ void __launch_bounds__(256) k_div(const OpP<T> P, const T *__restrict
   const T *I = tab + tab_off_I(N, Q), *IT = tab + tab_off_IT(N, Q), *DT = tab + tab_off_DT(N, Q);
   const T *wq = tab + tab_off_wq(N, Q), *gq = tab + tab_off_gq(N, Q);
 
-  sweep<T, 0, Q, N, N, N, N>(5, 0u, I, I, I, s_in, R1);
+  sweep<T, N, 0, Q, N, N, N, N, M_I, M_I, M_I>(5, 0u, s_in, R1);
   __syncthreads();
-  sweep<T, 1, Q, N, Q, N, N>(5, 0u, I, I, I, R1, R2);
+  sweep<T, N, 1, Q, N, Q, N, N, M_I, M_I, M_I>(5, 0u, R1, R2);
   __syncthreads();
-  sweep<T, 2, Q, N, Q, Q, N>(5, 0u, I, I, I, R2, R3);
+  sweep<T, N, 2, Q, N, Q, Q, N, M_I, M_I, M_I>(5, 0u, R2, R3);
   __syncthreads();
 
   // -C V volume part: + alpha int kappa V . grad psi  -> F_j = alpha kappa w sum_d adj_{jd} V_d
@@ -461,11 +512,11 @@ __global__ void __launch_bounds__(256) k_div(const OpP<T> P, const T *__restrict
     }
   }
   __syncthreads();
-  sweep<T, 2, N, Q, Q, Q, Q>(4, (1u << 4), IT, DT, DT, R3, Wz);
+  sweep<T, N, 2, N, Q, Q, Q, Q, M_IT, M_DT, M_DT>(4, (1u << 4), R3, Wz);
   __syncthreads();
-  sweep<T, 1, N, Q, Q, Q, N>(4, (1u << 2), IT, DT, DT, Wz, Wy);
+  sweep<T, N, 1, N, Q, Q, Q, N, M_IT, M_DT, M_DT>(4, (1u << 2), Wz, Wy);
   __syncthreads();
-  sweep<T, 0, N, Q, Q, N, N>(4, (1u << 0), IT, DT, DT, Wy, Wx);
+  sweep<T, N, 0, N, Q, Q, N, N, M_IT, M_DT, M_DT>(4, (1u << 0), Wy, Wx);
   __syncthreads();
 
   // faces: - alpha int (kappa V)^ . n psi
@@ -490,9 +541,9 @@ __global__ void __launch_bounds__(256) k_div(const OpP<T> P, const T *__restrict
     Fg[idx] = v;
   }
   __syncthreads();
-  sweep<T, 0, Q, N, N, N, 1>(NSL, 0u, I, I, I, Fg, F1);
+  sweep<T, N, 0, Q, N, N, N, 1, M_I, M_I, M_I>(NSL, 0u, Fg, F1);
   __syncthreads();
-  sweep<T, 1, Q, N, Q, N, 1>(NSL, 0u, I, I, I, F1, F2);
+  sweep<T, N, 1, Q, N, Q, N, 1, M_I, M_I, M_I>(NSL, 0u, F1, F2);
   __syncthreads();
   for (int idx = threadIdx.x; idx < 6 * Q2; idx += blockDim.x) {
     const int f = idx / Q2, t = idx % Q2, i = t % Q, j = t / Q;
@@ -512,9 +563,9 @@ __global__ void __launch_bounds__(256) k_div(const OpP<T> P, const T *__restrict
     Ff[idx] = -P.alpha * wq[i] * wq[j] * flux;
   }
   __syncthreads();
-  sweep<T, 0, N, Q, Q, Q, 1>(6, 0u, IT, IT, IT, Ff, Fb1);
+  sweep<T, N, 0, N, Q, Q, Q, 1, M_IT, M_IT, M_IT>(6, 0u, Ff, Fb1);
   __syncthreads();
-  sweep<T, 1, N, Q, N, Q, 1>(6, 0u, IT, IT, IT, Fb1, Fb2);
+  sweep<T, N, 1, N, Q, N, Q, 1, M_IT, M_IT, M_IT>(6, 0u, Fb1, Fb2);
   __syncthreads();
   for (int idx = threadIdx.x; idx < N3; idx += blockDim.x) {
     const int a = idx % N, b = (idx / N) % N, c = idx / N2;
@@ -602,11 +653,11 @@ __global__ void __launch_bounds__(256) k_diag(const OpP<double> P, const double 
   __syncthreads();
   const T *I = tab + tab_off_I(N, Q), *IIT = tab + tab_off_IIT(N, Q), *DDT = tab + tab_off_DDT(N, Q),
           *IDT = tab + tab_off_IDT(N, Q), *wq = tab + tab_off_wq(N, Q), *gq = tab + tab_off_gq(N, Q);
-  sweep<T, 0, Q, N, N, N, N>(2, 0u, I, I, I, s_in, R1);
+  sweep<T, N, 0, Q, N, N, N, N, M_I, M_I, M_I>(2, 0u, s_in, R1);
   __syncthreads();
-  sweep<T, 1, Q, N, Q, N, N>(2, 0u, I, I, I, R1, R2);
+  sweep<T, N, 1, Q, N, Q, N, N, M_I, M_I, M_I>(2, 0u, R1, R2);
   __syncthreads();
-  sweep<T, 2, Q, N, Q, Q, N>(2, 0u, I, I, I, R2, R3);
+  sweep<T, N, 2, Q, N, Q, Q, N, M_I, M_I, M_I>(2, 0u, R2, R3);
   __syncthreads();
   const T a2 = P.alpha * P.alpha;
   for (int idx = threadIdx.x; idx < Q3; idx += blockDim.x) {
@@ -638,11 +689,11 @@ __global__ void __launch_bounds__(256) k_diag(const OpP<double> P, const double 
   const unsigned selz = (1u << 6) | (CURVED ? ((2u << 8) | (2u << 10)) : 0u);
   const unsigned sely = (1u << 4) | (CURVED ? (2u << 10) : 0u);
   const unsigned selx = (1u << 2) | (CURVED ? (2u << 8) : 0u);
-  sweep<T, 2, N, Q, Q, Q, Q>(NF, selz, IIT, DDT, IDT, F, Wz);
+  sweep<T, N, 2, N, Q, Q, Q, Q, M_IIT, M_DDT, M_IDT>(NF, selz, F, Wz);
   __syncthreads();
-  sweep<T, 1, N, Q, Q, Q, N>(NF, sely, IIT, DDT, IDT, Wz, Wy);
+  sweep<T, N, 1, N, Q, Q, Q, N, M_IIT, M_DDT, M_IDT>(NF, sely, Wz, Wy);
   __syncthreads();
-  sweep<T, 0, N, Q, Q, N, N>(NF, selx, IIT, DDT, IDT, Wy, Wx);
+  sweep<T, N, 0, N, Q, Q, N, N, M_IIT, M_DDT, M_IDT>(NF, selx, Wy, Wx);
   __syncthreads();
   for (int idx = threadIdx.x; idx < N3; idx += blockDim.x) {
     T s = 0;
@@ -657,6 +708,8 @@ template <typename Kern>
 int prep(dgx_ctx *c, Kern k, size_t smem) {
   static_assert(sizeof(Kern) > 0, "");
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   return check_cuda(c, e, "cudaFuncSetAttribute");
 }
 
@@ -718,6 +771,51 @@ int diag_impl(dgx_ctx *c, const double *rho, const double *pk, double *dh, doubl
   }
 
 }  // namespace
+
+int ensure_const_tables(dgx_ctx *c) {
+  static std::mutex mu;
+  static bool done[64] = {};
+  if (c->device < 0 || c->device >= 64) return set_error(c, DGX_ERR_ARG, "device %d", c->device);
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[c->device]) return 0;
+  std::vector<double> eo(kEoTotal, 0.0);
+  for (int r = 1; r <= kMaxDegree; ++r) {
+    const int N = r + 1, Q = 2 * r + 1;
+    std::vector<double> tab;
+    if (!build_table_block(r, tab)) return set_error(c, DGX_ERR_ARG, "table construction failed (r=%d)", r);
+    const int off[M_COUNT] = {tab_off_I(N, Q),  tab_off_D(N, Q),  tab_off_IT(N, Q),  tab_off_DT(N, Q),
+                              tab_off_Ia(N, Q), tab_off_P(N, Q),  tab_off_PT(N, Q),  tab_off_IIT(N, Q),
+                              tab_off_DDT(N, Q), tab_off_IDT(N, Q)};
+    for (int id = 0; id < M_COUNT; ++id) {
+      const int R = mat_rows(id, N), C = mat_cols(id, N), HO = (R + 1) / 2, HI = C / 2;
+      const double *M = &tab[off[id]];
+      const double s = mat_parity(id);
+      double mx = 0.0, asym = 0.0;
+      for (int o = 0; o < R; ++o)
+        for (int m = 0; m < C; ++m) {
+          mx = std::fmax(mx, std::fabs(M[o * C + m]));
+          asym = std::fmax(asym, std::fabs(M[(R - 1 - o) * C + (C - 1 - m)] - s * M[o * C + m]));
+        }
+      if (asym > 1e-12 * mx)
+        return set_error(c, DGX_ERR_ARG, "1D matrix %d of degree %d is not centro-symmetric (%g)", id, r, asym / mx);
+      double *dst = &eo[eo_mat_off(N, id)];
+      for (int o = 0; o < HO; ++o) {
+        for (int m = 0; m < HI; ++m) {
+          dst[o * HI + m] = 0.5 * (M[o * C + m] + M[o * C + C - 1 - m]);
+          dst[HO * HI + o * HI + m] = 0.5 * (M[o * C + m] - M[o * C + C - 1 - m]);
+        }
+        if (C & 1) dst[2 * HO * HI + o] = M[o * C + HI];
+      }
+    }
+  }
+  std::vector<float> eo32(eo.begin(), eo.end());
+  if (int e = check_cuda(c, cudaMemcpyToSymbol(c_eo64, eo.data(), eo.size() * sizeof(double)), "constant tables"))
+    return e;
+  if (int e = check_cuda(c, cudaMemcpyToSymbol(c_eo32, eo32.data(), eo32.size() * sizeof(float)), "constant tables"))
+    return e;
+  done[c->device] = true;
+  return 0;
+}
 
 template <typename T>
 OpP<T> make_params(const dgx_ctx *c) {

@@ -1,9 +1,13 @@
 // Vector kernels of the Krylov solvers (Sec. 3.1: GMRES / CG with a Jacobi
 // preconditioner), sm_103a.  These are HBM-bound streams: one pass over the
-// operands, grid-stride loops, FP64 accumulation of every inner product
-// (also for FP32 vectors).  Reductions are deterministic: a fixed grid for a
-// given length, per-block partial sums, then a fixed-order tree over blocks.
+// operands, grid-stride loops.  FP64 vectors use FP64 throughout.  FP32
+// vectors (the inner solve of the mixed-precision preconditioner) use FP32
+// per-thread arithmetic -- FP64 runs at 1/64 of the FP32 rate on GB300 and
+// would make these streams ALU bound -- and FP64 for the block and grid
+// combination.  Reductions are deterministic: a fixed grid for a given
+// length, per-block partial sums, then a fixed-order tree over blocks.
 #include <atomic>
+#include <type_traits>
 
 #include "dgx_common.cuh"
 
@@ -71,17 +75,17 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_mdot(long long n, int nv, int i0, int cnt, const T *__restrict__ V,
                                                    long long ld, const T *__restrict__ w, double *__restrict__ partial) {
   __shared__ double sh[32];
-  double acc[kChunk];
+  T acc[kChunk];
 #pragma unroll
-  for (int c = 0; c < kChunk; ++c) acc[c] = 0.0;
+  for (int c = 0; c < kChunk; ++c) acc[c] = T(0);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double wi = (double)w[i];
+    const T wi = w[i];
 #pragma unroll
     for (int c = 0; c < kChunk; ++c)
-      if (c < cnt) acc[c] += (double)V[(long long)(i0 + c) * ld + i] * wi;
+      if (c < cnt) acc[c] += V[(long long)(i0 + c) * ld + i] * wi;
   }
   for (int c = 0; c < cnt; ++c) {
-    const double t = block_sum(acc[c], sh);
+    const double t = block_sum((double)acc[c], sh);
     if (threadIdx.x == 0) partial[(long long)blockIdx.x * nv + i0 + c] = t;
   }
 }
@@ -102,19 +106,18 @@ __global__ void __launch_bounds__(kThreads) k_mupdate(long long n, int nv, const
                                                       const double *__restrict__ h, T *__restrict__ w,
                                                       double *__restrict__ partial) {
   __shared__ double sh[32];
-  __shared__ double hs[128];
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = h[i];
+  __shared__ T hs[128];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = (T)h[i];
   __syncthreads();
-  double nrm = 0.0;
+  T nrm = T(0);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double v = (double)w[i];
-    for (int k = 0; k < nv; ++k) v -= hs[k] * (double)V[(long long)k * ld + i];
-    const T vt = (T)v;
-    w[i] = vt;
-    nrm += (double)vt * (double)vt;
+    T v = w[i];
+    for (int k = 0; k < nv; ++k) v -= hs[k] * V[(long long)k * ld + i];
+    w[i] = v;
+    nrm += v * v;
   }
   if (partial) {
-    const double t = block_sum(nrm, sh);
+    const double t = block_sum((double)nrm, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = t;
   }
 }
@@ -122,20 +125,22 @@ __global__ void __launch_bounds__(kThreads) k_mupdate(long long n, int nv, const
 template <typename T>
 __global__ void k_scale_inv_sqrt(long long n, const double *__restrict__ nrm2, const T *__restrict__ x,
                                  T *__restrict__ y) {
-  const double s = 1.0 / sqrt(*nrm2);
+  const T s = (T)(1.0 / sqrt(*nrm2));
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] = (T)((double)x[i] * s);
+    y[i] = x[i] * s;
 }
 
 template <typename T, typename TX>
 __global__ void __launch_bounds__(kThreads) k_lincomb(long long n, int nv, const T *__restrict__ Z, long long ld,
                                                       const double *__restrict__ c, TX *__restrict__ x) {
-  __shared__ double cs[128];
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) cs[i] = c[i];
+  // arithmetic in the wider of the two types
+  using A = typename std::conditional<(sizeof(T) > sizeof(TX)), T, TX>::type;
+  __shared__ A cs[128];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) cs[i] = (A)c[i];
   __syncthreads();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double v = (double)x[i];
-    for (int k = 0; k < nv; ++k) v += cs[k] * (double)Z[(long long)k * ld + i];
+    A v = (A)x[i];
+    for (int k = 0; k < nv; ++k) v += cs[k] * (A)Z[(long long)k * ld + i];
     x[i] = (TX)v;
   }
 }
