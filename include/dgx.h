@@ -63,9 +63,12 @@ typedef struct dgx_ctx dgx_ctx;
  * terrain-following in z (z = zeta + h(x,y) (1 - zeta/Lz), zeta uniform).
  * terrain: 0 flat; 1 bell h = h_c / (1 + ((x-x_c)^2 + (y-y_c)^2)/a_c^2);
  *          2 bell of Sec. 3, h = h_c [1 + ((x-x_c)^2 + (y-y_c)^2)/a_c^2]^(-3/2).
- * bc_lateral: 0 slip walls on the four lateral faces, 1 far field (the
- * explicit flux sees the background plus (u_bar,0,0); the pressure operator
- * is transmissive there).  Bottom and top are slip walls.
+ * bc_lateral: 0 slip walls on the four lateral faces; 1 far field (the
+ * explicit flux sees the background plus (u_bar,0,0); in the pressure operator
+ * the perturbation pressure takes its far-field value 0 in the B flux and the
+ * enthalpy flux is transmissive); 2 periodic in x and y (the terrain must
+ * match on opposite faces, e.g. a centred hill).  Bottom and top are slip
+ * walls.
  * n_q: Gauss points per direction of the consistent rule; 0 selects 2r+1
  * (Sec. 3.3), the only value the GPU kernels accept. */
 typedef struct {
@@ -163,6 +166,56 @@ int dgx_solve_pressure(dgx_ctx *ctx, const double *b, double *x, const dgx_solve
 
 /* Default options: FGMRES(30), Helmholtz preconditioner, tol 1e-8. */
 void dgx_default_solve_opts(dgx_solve_opts *opts);
+
+/* ---------------------------------------------------------------- IMEX step
+ * The IMEX Runge-Kutta stage equations of Sec. 2 (companion tableaux A, A~).
+ * State: rho (N), u (3N), p (N) nodal fields, total (not perturbation)
+ * values, FP64 device arrays.  Stage l: rho^(l) from the explicit continuity
+ * sums; momentum and energy coupled through the pressure (Helmholtz) equation,
+ * solved by K fixed-point iterations, each one linear solve S p' = G - C A^-1 F
+ * for p' = p - p_bar (background subtracted in FP64), then
+ * U = A^-1 (F - B p').  Explicit terms: advective fluxes of rho, rho u, rho k
+ * (local Lax-Friedrichs flux) and the gravity work rho g.u; implicit terms: the
+ * pressure gradient with buoyancy rho' g and the enthalpy flux.  Bottom and
+ * top slip walls; lateral faces per dgx_mesh_desc.bc_lateral (far field:
+ * background density and (u_bar, 0, 0)). */
+
+/* Tableaux (host, s x s row-major, 2 <= s <= 4): A strictly lower, A~ lower
+ * with an explicit first stage (A~ first row zero) and a~_ll > 0 for l > 1.
+ * The new state is the last stage (stiffly accurate pairs such as
+ * ARS(2,2,2)).  dt > 0; K fixed-point iterations per implicit stage. */
+int dgx_set_imex(dgx_ctx *ctx, int s, const double *A, const double *At, double dt, int K);
+
+/* Explicit tendencies of (rho, u) as dual vectors (tested against each basis
+ * function): Erho (N) = weak -div(rho u), Em (3N) = weak -div(rho u_d u),
+ * Ee (N) = weak -div(rho k u) + int rho g.u psi.  Needs the background. */
+int dgx_explicit_tendencies(dgx_ctx *ctx, const double *rho, const double *u, double *Erho, double *Em, double *Ee);
+/* out = A(rho) in (3N -> 3N): the fast density-weighted mass of Sec. 3.3 applied forward. */
+int dgx_apply_mass(dgx_ctx *ctx, const double *rho, const double *in, double *out);
+/* out_i = int rho |u|^2/2 psi_i (N), consistent rule. */
+int dgx_kinetic_mass(dgx_ctx *ctx, const double *rho, const double *u, double *out);
+
+typedef struct {
+  int steps;             /* steps completed                                              */
+  int solves;            /* pressure solves (stages x fixed-point iterations x steps)     */
+  int krylov_iterations; /* outer Krylov iterations, all solves                          */
+  int inner_iterations;  /* FP32 iterations (DGX_SOLVER_MIXED)                           */
+  int operator_f64;
+  int operator_f32;
+  int status;            /* DGX_OK, or DGX_NOT_CONVERGED if any solve stopped at maxit   */
+  int reserved;
+  double max_relres;     /* largest final relative residual of the solves                */
+  double seconds;        /* wall time of the call                                        */
+  double seconds_solve;  /* of which inside dgx_solve_pressure                           */
+} dgx_step_info;
+
+/* Advance (rho, u, p) in place by nsteps IMEX steps.  opts: the pressure
+ * solves (NULL: defaults; the initial guess is always the previous iterate).
+ * Needs mesh, background and tableau.  Returns after the last step; DGX_OK,
+ * DGX_NOT_CONVERGED or an error.  Workspace (9 N s + 27 N doubles) is owned by
+ * the context. */
+int dgx_imex_step(dgx_ctx *ctx, double *rho, double *u, double *p, int nsteps, const dgx_solve_opts *opts,
+                  dgx_step_info *info);
 
 /* Allocation-free variant of dgx_apply_operator.  The paper has no
  * counterpart: this serves callers that cannot allocate device memory when

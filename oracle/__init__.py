@@ -227,13 +227,21 @@ def background(m, bg):
     return rb, pb
 
 
-def explicit(m, bg, rho, u, rho_bar):
-    """Explicit tendencies (Erho, Em (3N), Ee) as dual vectors."""
+def explicit(m, bg, rho, u, rho_bar, cells=None):
+    """Explicit tendencies (Erho, Em (3N), Ee) as dual vectors; with ``cells``
+    only those cells are computed (the rest is NaN)."""
     N = ndofs(m)
     Er, Em, Ee = np.zeros(N), np.zeros(3 * N), np.zeros(N)
+    mask = None
+    if cells is not None:
+        for a in (Er, Em, Ee):
+            a[:] = np.nan
+        mk = np.zeros(m.nx * m.ny * m.nz, dtype=np.uint8)
+        mk[np.asarray(cells)] = 1
+        mask = mk.ctypes.data_as(C.c_void_p)
     c = lambda a: np.ascontiguousarray(a, dtype=np.float64)
-    assert lib().orc_explicit(C.byref(m), C.byref(bg), _dp(c(rho)), _dp(c(u)), _dp(c(rho_bar)), _dp(Er), _dp(Em),
-                              _dp(Ee)) == 0
+    assert lib().orc_explicit_masked(C.byref(m), C.byref(bg), _dp(c(rho)), _dp(c(u)), _dp(c(rho_bar)), mask,
+                                     _dp(Er), _dp(Em), _dp(Ee)) == 0
     return Er, Em, Ee
 
 

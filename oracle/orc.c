@@ -124,7 +124,10 @@ long orc_num_cells(const orc_mesh *m) { return (long)m->nx * m->ny * m->nz; }
 /* (B P) on one cell, 3 components [3][n3]:
  *   alpha [ - int_K p div(phi) + int_dK p_hat phi.n ]
  * Reading of the flux: p_hat = {p} = (p- + p+)/2 on interior faces,
- * p_hat = p- on every boundary face (p+ = p-). */
+ * p_hat = p- on slip walls (p+ = p-), and on far-field faces the far-field
+ * datum of the perturbation pressure, p_hat = 0, imposed weakly (the
+ * transmissive choice p+ = p- there makes the acoustic subsystem gain energy
+ * through the boundary). */
 static void cell_B(const orc_mesh *m, const tabs *T, const cgeo *G, long cell, double alpha,
                    const double *p, double *out) {
   int n3 = T->n3;
@@ -146,10 +149,12 @@ static void cell_B(const orc_mesh *m, const tabs *T, const cgeo *G, long cell, d
     int k = f / 2, s = f % 2;
     long nb = neighbour(m, cell, k, s);
     const double *fps = T->fpsi[f], *fpsn = T->fpsi[2 * k + (1 - s)];
+    int ff = nb < 0 && boundary_kind(m, k) == 1;
     for (int qp = 0; qp < T->q2; ++qp) {
       double pm = dotn(n3, pc, fps + (size_t)qp * n3);
       double ph = pm;
       if (nb >= 0) ph = 0.5 * (pm + dotn(n3, p + nb * n3, fpsn + (size_t)qp * n3));
+      if (ff) ph = 0.0; /* far field: the background pressure, p' = 0, imposed weakly */
       const double *nA = G->nA[f] + 3 * qp;
       for (int i = 0; i < n3; ++i) {
         double v = ph * fps[(size_t)qp * n3 + i];

@@ -22,7 +22,7 @@ typedef struct {
   int r;          /* polynomial degree                                         */
   int q;          /* Gauss points per direction of the consistent rule (2r+1)  */
   int terrain;    /* 0 flat, 1 bell h_c/(1+d^2/a_c^2), 2 bell with power -3/2  */
-  int bc_lateral; /* 0 slip wall, 1 far field on the four lateral faces        */
+  int bc_lateral; /* 0 slip wall, 1 far field, 2 periodic (lateral faces)      */
   int pad;
   double Lx, Ly, Lz;
   double hc, ac, xc, yc;
@@ -255,16 +255,21 @@ static void cell_geometry(const orc_mesh *m, const tabs *T, long cell, cgeo *G) 
   }
 }
 
-/* Neighbour across face (k, s); -1 on the domain boundary. */
+/* Neighbour across face (k, s); -1 on the domain boundary.  With periodic
+ * lateral boundaries (bc_lateral 2) the x and y directions wrap around. */
 static long neighbour(const orc_mesh *m, long cell, int k, int s) {
   long c[3] = {cell % m->nx, (cell / m->nx) % m->ny, cell / ((long)m->nx * m->ny)};
   long nn[3] = {m->nx, m->ny, m->nz};
   c[k] += s ? 1 : -1;
-  if (c[k] < 0 || c[k] >= nn[k]) return -1;
+  if (c[k] < 0 || c[k] >= nn[k]) {
+    if (k == 2 || m->bc_lateral != 2) return -1;
+    c[k] = (c[k] + nn[k]) % nn[k];
+  }
   return c[0] + m->nx * (c[1] + m->ny * c[2]);
 }
 
-/* Boundary kind of face direction k: 0 slip wall, 1 far field. */
+/* Boundary kind of face direction k: 0 slip wall, 1 far field (periodic
+ * lateral faces have neighbours and never reach this). */
 static int boundary_kind(const orc_mesh *m, int k) { return (k == 2) ? 0 : m->bc_lateral; }
 
 static double dotn(int n3, const double *f, const double *psi) {

@@ -86,8 +86,8 @@ int orc_background(const orc_mesh *m, const orc_bg *b, double *rho_bar, double *
  *   Ee_i = int rho k u . grad psi_i - int_dK F^_k psi_i + int rho g.u psi_i
  * F^ = (1/2)(q- u-.nA + q+ u+.nA) + (1/2) lambda |nA| (q- - q+),
  * lambda = max(|u-.n|, |u+.n|) (local Lax-Friedrichs with the advective speed). */
-int orc_explicit(const orc_mesh *m, const orc_bg *b, const double *rho, const double *u, const double *rho_bar,
-                 double *Erho, double *Em, double *Ee) {
+int orc_explicit_masked(const orc_mesh *m, const orc_bg *b, const double *rho, const double *u,
+                        const double *rho_bar, const unsigned char *mask, double *Erho, double *Em, double *Ee) {
   tabs T;
   if (tabs_init(&T, m)) return -1;
   long nc = orc_num_cells(m);
@@ -101,6 +101,7 @@ int orc_explicit(const orc_mesh *m, const orc_bg *b, const double *rho, const do
     double *loc = malloc(sizeof(double) * 5 * n3);
 #pragma omp for schedule(dynamic, 4)
     for (long c = 0; c < nc; ++c) {
+      if (mask && !mask[c]) continue;
       cell_geometry(m, &T, c, &G);
       memset(loc, 0, sizeof(double) * 5 * n3);
       const double *rc = rho + c * n3;
@@ -173,6 +174,11 @@ int orc_explicit(const orc_mesh *m, const orc_bg *b, const double *rho, const do
   }
   tabs_free(&T);
   return 0;
+}
+
+int orc_explicit(const orc_mesh *m, const orc_bg *b, const double *rho, const double *u, const double *rho_bar,
+                 double *Erho, double *Em, double *Ee) {
+  return orc_explicit_masked(m, b, rho, u, rho_bar, NULL, Erho, Em, Ee);
 }
 
 /* out_i = int rho |u|^2/2 psi_i (consistent rule). */

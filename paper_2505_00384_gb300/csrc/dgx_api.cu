@@ -316,6 +316,9 @@ void free_mesh(dgx_ctx *c) {
   c->V32 = nullptr;
   if (c->kry64) cudaFree(c->kry64);
   if (c->kry32) cudaFree(c->kry32);
+  if (c->imex_ws) cudaFree(c->imex_ws);
+  c->imex_ws = nullptr;
+  c->imex_ws_elems = 0;
   c->kry64 = nullptr;
   c->kry32 = nullptr;
   c->kry64_elems = c->kry32_elems = 0;
@@ -721,7 +724,18 @@ int dgx_mesh_build(dgx_ctx *c, const dgx_mesh_desc *d) {
     return set_error(c, DGX_ERR_ARG, "n_q must be 0 or 2r+1 = %d (consistent integration)", 2 * r + 1);
   if (d->terrain < 0 || d->terrain > 2) return set_error(c, DGX_ERR_ARG, "terrain kind %d", d->terrain);
   if (d->terrain > 0 && !(d->a_c > 0)) return set_error(c, DGX_ERR_ARG, "terrain half-width a_c must be > 0");
-  if (d->bc_lateral < 0 || d->bc_lateral > 1) return set_error(c, DGX_ERR_ARG, "bc_lateral %d", d->bc_lateral);
+  if (d->bc_lateral < 0 || d->bc_lateral > 2) return set_error(c, DGX_ERR_ARG, "bc_lateral %d", d->bc_lateral);
+  if (d->bc_lateral == 2 && d->terrain != 0) {
+    // periodic lateral boundaries need matching terrain on opposite faces
+    const int NS = 16;
+    for (int i = 0; i <= NS; ++i) {
+      const double y = d->Ly * i / NS, x = d->Lx * i / NS;
+      if (std::fabs(terrain_h(*d, 0.0, y) - terrain_h(*d, d->Lx, y)) > 1e-9 * (std::fabs(d->h_c) + 1.0) ||
+          std::fabs(terrain_h(*d, x, 0.0) - terrain_h(*d, x, d->Ly)) > 1e-9 * (std::fabs(d->h_c) + 1.0))
+        return set_error(c, DGX_ERR_ARG, "periodic lateral boundaries need terrain that matches on opposite faces "
+                                         "(centre the hill)");
+    }
+  }
   const long long ncell = (long long)d->nx * d->ny * d->nz;
   if (ncell > 2000000000LL) return set_error(c, DGX_ERR_ARG, "too many cells");
   if (cudaSetDevice(c->device) != cudaSuccess) return set_error(c, DGX_ERR_CUDA, "cudaSetDevice");

@@ -47,10 +47,10 @@ __host__ __device__ constexpr int tab_size(int N, int Q) { return 7 * Q * N + 3 
 // their even-odd (centro-symmetric) storage in constant memory, all degrees
 // back to back.  A matrix of R rows and C columns stores E[(R+1)/2][C/2],
 // Od[(R+1)/2][C/2] and, for odd C, the middle column Mc[(R+1)/2].
-enum MatId : int { M_I = 0, M_D, M_IT, M_DT, M_IA, M_P, M_PT, M_IIT, M_DDT, M_IDT, M_COUNT };
+enum MatId : int { M_I = 0, M_D, M_IT, M_DT, M_IA, M_P, M_PT, M_IIT, M_DDT, M_IDT, M_IAT, M_COUNT };
 __host__ __device__ constexpr int mat_rows(int id, int N) { return (id == M_I || id == M_D) ? 2 * N - 1 : N; }
 __host__ __device__ constexpr int mat_cols(int id, int N) {
-  return (id == M_I || id == M_D || id == M_IA || id == M_P || id == M_PT) ? N : 2 * N - 1;
+  return (id == M_I || id == M_D || id == M_IA || id == M_P || id == M_PT || id == M_IAT) ? N : 2 * N - 1;
 }
 __host__ __device__ constexpr int mat_parity(int id) { return (id == M_D || id == M_DT || id == M_IDT) ? -1 : 1; }
 __host__ __device__ constexpr int eo_size(int R, int C) { return 2 * ((R + 1) / 2) * (C / 2) + ((C & 1) ? (R + 1) / 2 : 0); }
@@ -151,6 +151,13 @@ struct dgx_ctx {
   double *host_red = nullptr;  // pinned host mirror
   size_t red_elems = 0;
 
+  // IMEX step: tableaux (s <= 4, row-major), time step, fixed-point iterations
+  bool has_imex = false;
+  int imex_s = 0, imex_K = 0;
+  double imex_A[16] = {}, imex_At[16] = {}, imex_dt = 0.0;
+  double *imex_ws = nullptr;
+  size_t imex_ws_elems = 0;
+
   std::vector<void *> owned;  // everything cudaMalloc'd for the mesh
 };
 
@@ -169,12 +176,21 @@ bool build_table_block(int r, std::vector<double> &tab);
 int ensure_const_tables(dgx_ctx *c);
 
 // operator kernels (dgx_operator.cu)
+// alpha < 0: use the context's a~_ll dt; inv = false: k_grad writes the dual B p
 template <typename T>
-int launch_grad(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s);
+int launch_grad(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s, bool inv = true, double alpha = -1.0);
 template <typename T>
-int launch_div(dgx_ctx *c, const T *V, const T *p, const T *pk, T *y, cudaStream_t s);
+int launch_div(dgx_ctx *c, const T *V, const T *p, const T *pk, T *y, cudaStream_t s, double alpha = -1.0);
 template <typename T>
-int launch_mass_inverse(dgx_ctx *c, const T *in, const T *rho, T *out, cudaStream_t s);
+int launch_mass_inverse(dgx_ctx *c, const T *in, const T *rho, T *out, cudaStream_t s, int nf = 3);
+// explicit part of the IMEX step (dgx_explicit.cu), FP64
+int launch_explicit(dgx_ctx *c, const double *rho, const double *u, const double *rho_bar, double *Er, double *Em,
+                    double *Ee, cudaStream_t s);
+// consistent mass of scale*f0 (mode 0) or scale*f0*|fv|^2/2 (mode 1)
+int launch_cmass(dgx_ctx *c, int mode, double scale, const double *f0, const double *fv, double *out,
+                 cudaStream_t s);
+// forward fast density-weighted mass A(rho) v, 3 components
+int launch_mass_fwd(dgx_ctx *c, const double *rho, const double *v, double *out, cudaStream_t s);
 int launch_diag(dgx_ctx *c, const double *rho, const double *pk, double *dh, double *die, cudaStream_t s);
 template <typename T>
 OpP<T> make_params(const dgx_ctx *c);

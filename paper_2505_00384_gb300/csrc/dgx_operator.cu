@@ -23,215 +23,10 @@
 #include <mutex>
 
 #include "dgx_common.cuh"
+#include "dgx_sweep.cuh"
 
 namespace dgx {
 namespace {
-
-// ------------------------------------------------------------- 1D matrices
-// The 1D matrices of every degree live in __constant__ memory in even-odd
-// form.  All of them are centro-symmetric, M[R-1-o][C-1-m] = s M[o][m] with
-// s = +1 (interpolation, mass-like) or -1 (derivative): the Gauss and
-// Gauss-Lobatto point sets are symmetric about 1/2.  Writing
-//   e_m = in[m] + in[C-1-m],  d_m = in[m] - in[C-1-m]   (m < C/2),
-//   a_o = sum_m E[o][m] e_m + Mc[o] in[mid],  b_o = sum_m Od[o][m] d_m,
-// with E = (M[o][m] + M[o][C-1-m])/2, Od = (M[o][m] - M[o][C-1-m])/2 and Mc the
-// middle column (odd C), gives out[o] = a_o + b_o and out[R-1-o] = s (a_o - b_o)
-// for o < (R+1)/2: half the multiply-adds of the plain product.  Unrolled with
-// compile-time indices, every coefficient is an FMA operand read straight from
-// the constant bank (no load instruction).
-__constant__ float c_eo32[kEoTotal];
-__constant__ double c_eo64[kEoTotal];
-
-template <typename T>
-__device__ __forceinline__ T ceo(int i);
-template <>
-__device__ __forceinline__ float ceo<float>(int i) { return c_eo32[i]; }
-template <>
-__device__ __forceinline__ double ceo<double>(int i) { return c_eo64[i]; }
-
-// One line of length MI (stride ss in `src`) -> MO outputs (stride ds in `dst`).
-template <typename T, int NN, int MAT, int MO, int MI>
-__device__ __forceinline__ void line_eo(const T *src, int ss, T *dst, int ds) {
-  constexpr int HO = (MO + 1) / 2, HI = MI / 2;
-  constexpr int base = eo_mat_off(NN, MAT);
-  constexpr bool odd_in = (MI & 1) != 0;
-  constexpr int par = mat_parity(MAT);
-  T e[HI > 0 ? HI : 1], d[HI > 0 ? HI : 1];
-#pragma unroll
-  for (int m = 0; m < HI; ++m) {
-    const T x = src[m * ss], y = src[(MI - 1 - m) * ss];
-    e[m] = x + y;
-    d[m] = x - y;
-  }
-  const T c = odd_in ? src[HI * ss] : T(0);
-#pragma unroll
-  for (int o = 0; o < HO; ++o) {
-    T a = odd_in ? ceo<T>(base + 2 * HO * HI + o) * c : T(0);
-    T b = T(0);
-#pragma unroll
-    for (int m = 0; m < HI; ++m) {
-      a += ceo<T>(base + o * HI + m) * e[m];
-      b += ceo<T>(base + HO * HI + o * HI + m) * d[m];
-    }
-    dst[o * ds] = a + b;
-    if (o != MO - 1 - o) dst[(MO - 1 - o) * ds] = par > 0 ? a - b : b - a;
-  }
-}
-
-// One sum-factorisation sweep along direction DIR of `nf` fields stored back
-// to back.  Input field shape (S0, S1, S2), x fastest, with S_DIR == MI; the
-// output replaces that extent by MO.  One thread per 1D line; field f uses the
-// matrix MAT0 / MAT1 / MAT2 selected by bits 2f..2f+1 of `sel`.
-template <typename T, int NN, int DIR, int MO, int MI, int S0, int S1, int S2, int MAT0, int MAT1, int MAT2>
-__device__ __forceinline__ void sweep(int nf, unsigned sel, const T *__restrict__ in, T *__restrict__ out) {
-  constexpr int L0 = DIR == 0 ? S1 : S0;  // faster non-DIR extent
-  constexpr int L1 = DIR == 2 ? S1 : S2;  // slower non-DIR extent
-  constexpr int NL = L0 * L1;
-  constexpr int IT = S0 * S1 * S2, OT = IT / MI * MO;
-  constexpr int O0 = DIR == 0 ? MO : S0, O1 = DIR == 1 ? MO : S1;
-  constexpr int ss = DIR == 0 ? 1 : (DIR == 1 ? S0 : S0 * S1);
-  constexpr int ds = DIR == 0 ? 1 : (DIR == 1 ? O0 : O0 * O1);
-  const int total = nf * NL;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int f = idx / NL, l = idx - f * NL;
-    const int l0 = l % L0, l1 = l / L0;
-    int io, oo;
-    if (DIR == 0) {
-      io = (l1 * S1 + l0) * S0;
-      oo = (l1 * O1 + l0) * O0;
-    } else if (DIR == 1) {
-      io = l0 + S0 * S1 * l1;
-      oo = l0 + O0 * O1 * l1;
-    } else {
-      io = l0 + S0 * l1;
-      oo = l0 + O0 * l1;
-    }
-    const T *src = in + f * IT + io;
-    T *dst = out + f * OT + oo;
-    const unsigned ms = (sel >> (2 * f)) & 3u;
-    if (ms == 0) line_eo<T, NN, MAT0, MO, MI>(src, ss, dst, ds);
-    else if (ms == 1) line_eo<T, NN, MAT1, MO, MI>(src, ss, dst, ds);
-    else line_eo<T, NN, MAT2, MO, MI>(src, ss, dst, ds);
-  }
-}
-
-// Node index of face-local point (t1, t2) on the face normal to direction k at
-// layer e (0 or N-1).  Tangential order: x face (xi2, xi3), y face (xi1, xi3),
-// z face (xi1, xi2).
-template <int N>
-__device__ __forceinline__ int face_node(int k, int e, int t1, int t2) {
-  return k == 0 ? e + N * (t1 + N * t2) : (k == 1 ? t1 + N * (e + N * t2) : t1 + N * (t2 + N * e));
-}
-
-struct CellPos {
-  long long cell;
-  int cx, cy, cz;
-};
-
-template <typename T>
-__device__ __forceinline__ CellPos cell_pos(const OpP<T> &P, long long cell) {
-  CellPos c;
-  c.cell = cell;
-  c.cx = (int)(cell % P.nx);
-  c.cy = (int)((cell / P.nx) % P.ny);
-  c.cz = (int)(cell / ((long long)P.nx * P.ny));
-  return c;
-}
-
-// Neighbour across face f = 2k+s, or -1 on the boundary.
-template <typename T>
-__device__ __forceinline__ long long neighbour(const OpP<T> &P, const CellPos &c, int f) {
-  const int k = f >> 1, s = f & 1;
-  int x = c.cx, y = c.cy, z = c.cz;
-  if (k == 0) {
-    x += s ? 1 : -1;
-    if (x < 0 || x >= P.nx) return -1;
-  } else if (k == 1) {
-    y += s ? 1 : -1;
-    if (y < 0 || y >= P.ny) return -1;
-  } else {
-    z += s ? 1 : -1;
-    if (z < 0 || z >= P.nz) return -1;
-  }
-  return x + (long long)P.nx * (y + (long long)P.ny * z);
-}
-
-template <typename T, int N, int Q>
-__device__ __forceinline__ void load_tables(const T *__restrict__ g, T *s) {
-  constexpr int TS = tab_size(N, Q);
-  for (int i = threadIdx.x; i < TS; i += blockDim.x) s[i] = g[i];
-}
-
-// Outward normal times area element of face f at face Gauss point (i, j)
-// (unweighted).  Curved z faces have all three components; x and y faces
-// stay planar (normal +-e_x, +-e_y) under the Gal-Chen map.
-template <typename T, int N, int Q, bool CURVED>
-__device__ __forceinline__ void face_normal(const OpP<T> &P, const T *colp, T zeta0, int f, int i, int j,
-                                            T nA[3]) {
-  const int k = f >> 1, s = f & 1;
-  const T sg = s ? T(1) : T(-1);
-  nA[0] = nA[1] = nA[2] = T(0);
-  if (k == 0) {
-    T z3 = P.dz;
-    if (CURVED) z3 = P.dz * (T(1) - colp[col_off_hx(N, Q, s) + i] / P.H);
-    nA[0] = sg * P.dy * z3;
-  } else if (k == 1) {
-    T z3 = P.dz;
-    if (CURVED) z3 = P.dz * (T(1) - colp[col_off_hy(N, Q, s) + i] / P.H);
-    nA[1] = sg * P.dx * z3;
-  } else {
-    nA[2] = sg * P.dx * P.dy;
-    if (CURVED) {
-      const T fac = T(1) - (zeta0 + T(s) * P.dz) / P.H;
-      nA[0] = -sg * P.dy * colp[col_off_h1q(N, Q) + i + Q * j] * fac;
-      nA[1] = -sg * P.dx * colp[col_off_h2q(N, Q) + i + Q * j] * fac;
-    }
-  }
-}
-
-// In-block fast inverse of the density-weighted mass for nf fields (N^3 each)
-// in `a` (result left in `a`); rq = rho at the fast-rule points.
-// A^-1 v = P^3 (J^-1 (P^T)^3 v), J_q = rho(x_q) w_q det J(x_q)   (Sec. 3.3).
-template <typename T, int N, int Q, bool CURVED>
-__device__ __forceinline__ void fast_inverse(const OpP<T> &P, const T *tab, const T *colp, const T *rq, int nf,
-                                             T *a, T *b) {
-  constexpr int N3 = N * N * N;
-  const T *PT = tab + tab_off_PT(N, Q);
-  const T *Pm = tab + tab_off_P(N, Q);
-  const T *wa = tab + tab_off_wa(N, Q);
-  sweep<T, N, 0, N, N, N, N, N, M_PT, M_PT, M_PT>(nf, 0u, a, b);
-  __syncthreads();
-  sweep<T, N, 1, N, N, N, N, N, M_PT, M_PT, M_PT>(nf, 0u, b, a);
-  __syncthreads();
-  sweep<T, N, 2, N, N, N, N, N, M_PT, M_PT, M_PT>(nf, 0u, a, b);
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < nf * N3; idx += blockDim.x) {
-    const int node = idx % N3;
-    const int i = node % N, j = (node / N) % N, k = node / (N * N);
-    T det = P.dx * P.dy * P.dz;
-    if (CURVED) det *= (T(1) - colp[col_off_hqa(N, Q) + i + N * j] / P.H);
-    b[idx] = b[idx] / (rq[node] * wa[i] * wa[j] * wa[k] * det);
-  }
-  __syncthreads();
-  sweep<T, N, 0, N, N, N, N, N, M_P, M_P, M_P>(nf, 0u, b, a);
-  __syncthreads();
-  sweep<T, N, 1, N, N, N, N, N, M_P, M_P, M_P>(nf, 0u, a, b);
-  __syncthreads();
-  sweep<T, N, 2, N, N, N, N, N, M_P, M_P, M_P>(nf, 0u, b, a);
-  __syncthreads();
-}
-
-// rho at the fast-rule points: Ia^3 rho.
-template <typename T, int N, int Q>
-__device__ __forceinline__ void rho_fast(const T *tab, const T *rho, T *t1, T *t2, T *rq) {
-  const T *Ia = tab + tab_off_Ia(N, Q);
-  sweep<T, N, 0, N, N, N, N, N, M_IA, M_IA, M_IA>(1, 0u, rho, t1);
-  __syncthreads();
-  sweep<T, N, 1, N, N, N, N, N, M_IA, M_IA, M_IA>(1, 0u, t1, t2);
-  __syncthreads();
-  sweep<T, N, 2, N, N, N, N, N, M_IA, M_IA, M_IA>(1, 0u, t2, rq);
-  __syncthreads();
-}
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
@@ -260,7 +55,8 @@ struct GradL {
 template <typename T, int N>
 constexpr int min_ctas() { return (sizeof(T) == 8 && N <= 5) ? 3 : 1; }
 
-template <typename T, int N, int Q, bool CURVED>
+// INV = true: V = A^-1 (B p); INV = false: the dual vector B p itself.
+template <typename T, int N, int Q, bool CURVED, bool INV = true>
 __global__ void __launch_bounds__(256, min_ctas<T, N>()) k_grad(const OpP<T> P, const T *__restrict__ p, const T *__restrict__ rho,
                                               T *__restrict__ V, long long Ntot) {
   using L = GradL<N, Q, CURVED>;
@@ -341,14 +137,18 @@ __global__ void __launch_bounds__(256, min_ctas<T, N>()) k_grad(const OpP<T> P, 
   }
   __syncthreads();
 
-  // faces: alpha int p_hat psi n_d, p_hat = {p} inside, p- on the boundary
+  // faces: alpha int p_hat psi n_d, p_hat = {p} inside, p- on slip walls, and
+  // the far-field datum p_hat = 0 (background pressure) on far-field faces
   T *Fg = Wf, *F1 = Fg + 6 * N2, *F2 = F1 + 6 * N * Q, *Fp = F2 + 6 * Q2, *Fb1 = Fp + NFP * Q2, *Fb2 = Fb1 + NFP * N * Q;
   for (int idx = threadIdx.x; idx < 6 * N2; idx += blockDim.x) {
     const int f = idx / N2, t = idx % N2, t1 = t % N, t2 = t / N;
     const int k = f >> 1, s = f & 1;
     const T own = s_p[face_node<N>(k, s ? N - 1 : 0, t1, t2)];
     const long long nb = neighbour(P, cp, f);
-    Fg[idx] = nb >= 0 ? T(0.5) * (own + p[nb * N3 + face_node<N>(k, s ? 0 : N - 1, t1, t2)]) : own;
+    T ph = own;
+    if (nb >= 0) ph = T(0.5) * (own + p[nb * N3 + face_node<N>(k, s ? 0 : N - 1, t1, t2)]);
+    else if (k < 2 && P.bc_lat == 1) ph = T(0);
+    Fg[idx] = ph;
   }
   __syncthreads();
   sweep<T, N, 0, Q, N, N, N, 1, M_I, M_I, M_I>(6, 0u, Fg, F1);
@@ -399,7 +199,7 @@ __global__ void __launch_bounds__(256, min_ctas<T, N>()) k_grad(const OpP<T> P, 
   __syncthreads();
 
   // V = A^-1 (B P), per component
-  fast_inverse<T, N, Q, CURVED>(P, tab, colp, s_rq, 3, s_out, R1);
+  if (INV) fast_inverse<T, N, Q, CURVED>(P, tab, colp, s_rq, 3, s_out, R1);
   for (int idx = threadIdx.x; idx < 3 * N3; idx += blockDim.x) {
     const int d = idx / N3, node = idx % N3;
     V[d * Ntot + cell * N3 + node] = s_out[idx];
@@ -590,7 +390,7 @@ struct MinvL {
 
 template <typename T, int N, int Q, bool CURVED>
 __global__ void __launch_bounds__(128) k_minv(const OpP<T> P, const T *__restrict__ in, const T *__restrict__ rho,
-                                              T *__restrict__ out, long long Ntot) {
+                                              T *__restrict__ out, long long Ntot, int nf) {
   using L = MinvL<N, Q>;
   constexpr int N3 = L::N3;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -600,15 +400,15 @@ __global__ void __launch_bounds__(128) k_minv(const OpP<T> P, const T *__restric
   const CellPos cp = cell_pos(P, cell);
   const T *colp = CURVED ? P.col + (long long)(cp.cx + P.nx * cp.cy) * col_size(N, Q) : nullptr;
   load_tables<T, N, Q>(P.tab, tab);
-  for (int i = threadIdx.x; i < 3 * N3; i += blockDim.x) {
+  for (int i = threadIdx.x; i < nf * N3; i += blockDim.x) {
     const int d = i / N3, node = i % N3;
     A[i] = in[d * Ntot + cell * N3 + node];
     if (d == 0) s_rho[node] = rho[cell * N3 + node];
   }
   __syncthreads();
   rho_fast<T, N, Q>(tab, s_rho, B, B + N3, s_rq);
-  fast_inverse<T, N, Q, CURVED>(P, tab, colp, s_rq, 3, A, B);
-  for (int i = threadIdx.x; i < 3 * N3; i += blockDim.x) {
+  fast_inverse<T, N, Q, CURVED>(P, tab, colp, s_rq, nf, A, B);
+  for (int i = threadIdx.x; i < nf * N3; i += blockDim.x) {
     const int d = i / N3, node = i % N3;
     out[d * Ntot + cell * N3 + node] = A[i];
   }
@@ -716,35 +516,46 @@ int prep(dgx_ctx *c, Kern k, size_t smem) {
 int threads_for(int N) { return N <= 3 ? 128 : 256; }
 
 template <typename T, int N, bool CURVED>
-int grad_impl(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s) {
+int grad_impl(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s, bool inv, double alpha) {
   constexpr int Q = 2 * N - 1;
   const size_t smem = sizeof(T) * GradL<N, Q, CURVED>::total;
-  auto k = k_grad<T, N, Q, CURVED>;
-  if (int e = prep(c, k, smem)) return e;
-  count_launch();
-  k<<<(unsigned)c->ncell, threads_for(N), smem, s>>>(make_params<T>(c), p, rho, V, c->N);
+  OpP<T> P = make_params<T>(c);
+  if (alpha >= 0.0) P.alpha = (T)alpha;
+  if (inv) {
+    auto k = k_grad<T, N, Q, CURVED, true>;
+    if (int e = prep(c, k, smem)) return e;
+    count_launch();
+    k<<<(unsigned)c->ncell, threads_for(N), smem, s>>>(P, p, rho, V, c->N);
+  } else {
+    auto k = k_grad<T, N, Q, CURVED, false>;
+    if (int e = prep(c, k, smem)) return e;
+    count_launch();
+    k<<<(unsigned)c->ncell, threads_for(N), smem, s>>>(P, p, rho, V, c->N);
+  }
   return check_cuda(c, cudaGetLastError(), "k_grad launch");
 }
 
 template <typename T, int N, bool CURVED>
-int div_impl(dgx_ctx *c, const T *V, const T *p, const T *pk, T *y, cudaStream_t s) {
+int div_impl(dgx_ctx *c, const T *V, const T *p, const T *pk, T *y, cudaStream_t s, double alpha) {
   constexpr int Q = 2 * N - 1;
   const size_t smem = sizeof(T) * DivL<N, Q, CURVED>::total;
   auto k = k_div<T, N, Q, CURVED>;
   if (int e = prep(c, k, smem)) return e;
+  OpP<T> P = make_params<T>(c);
+  if (alpha >= 0.0) P.alpha = (T)alpha;
   count_launch();
-  k<<<(unsigned)c->ncell, threads_for(N), smem, s>>>(make_params<T>(c), V, p, pk, y, c->N);
+  k<<<(unsigned)c->ncell, threads_for(N), smem, s>>>(P, V, p, pk, y, c->N);
   return check_cuda(c, cudaGetLastError(), "k_div launch");
 }
 
 template <typename T, int N, bool CURVED>
-int minv_impl(dgx_ctx *c, const T *in, const T *rho, T *out, cudaStream_t s) {
+int minv_impl(dgx_ctx *c, const T *in, const T *rho, T *out, cudaStream_t s, int nf) {
   constexpr int Q = 2 * N - 1;
   const size_t smem = sizeof(T) * MinvL<N, Q>::total;
   auto k = k_minv<T, N, Q, CURVED>;
   if (int e = prep(c, k, smem)) return e;
   count_launch();
-  k<<<(unsigned)c->ncell, 128, smem, s>>>(make_params<T>(c), in, rho, out, c->N);
+  k<<<(unsigned)c->ncell, 128, smem, s>>>(make_params<T>(c), in, rho, out, c->N, nf);
   return check_cuda(c, cudaGetLastError(), "k_minv launch");
 }
 
@@ -772,50 +583,7 @@ int diag_impl(dgx_ctx *c, const double *rho, const double *pk, double *dh, doubl
 
 }  // namespace
 
-int ensure_const_tables(dgx_ctx *c) {
-  static std::mutex mu;
-  static bool done[64] = {};
-  if (c->device < 0 || c->device >= 64) return set_error(c, DGX_ERR_ARG, "device %d", c->device);
-  std::lock_guard<std::mutex> lk(mu);
-  if (done[c->device]) return 0;
-  std::vector<double> eo(kEoTotal, 0.0);
-  for (int r = 1; r <= kMaxDegree; ++r) {
-    const int N = r + 1, Q = 2 * r + 1;
-    std::vector<double> tab;
-    if (!build_table_block(r, tab)) return set_error(c, DGX_ERR_ARG, "table construction failed (r=%d)", r);
-    const int off[M_COUNT] = {tab_off_I(N, Q),  tab_off_D(N, Q),  tab_off_IT(N, Q),  tab_off_DT(N, Q),
-                              tab_off_Ia(N, Q), tab_off_P(N, Q),  tab_off_PT(N, Q),  tab_off_IIT(N, Q),
-                              tab_off_DDT(N, Q), tab_off_IDT(N, Q)};
-    for (int id = 0; id < M_COUNT; ++id) {
-      const int R = mat_rows(id, N), C = mat_cols(id, N), HO = (R + 1) / 2, HI = C / 2;
-      const double *M = &tab[off[id]];
-      const double s = mat_parity(id);
-      double mx = 0.0, asym = 0.0;
-      for (int o = 0; o < R; ++o)
-        for (int m = 0; m < C; ++m) {
-          mx = std::fmax(mx, std::fabs(M[o * C + m]));
-          asym = std::fmax(asym, std::fabs(M[(R - 1 - o) * C + (C - 1 - m)] - s * M[o * C + m]));
-        }
-      if (asym > 1e-12 * mx)
-        return set_error(c, DGX_ERR_ARG, "1D matrix %d of degree %d is not centro-symmetric (%g)", id, r, asym / mx);
-      double *dst = &eo[eo_mat_off(N, id)];
-      for (int o = 0; o < HO; ++o) {
-        for (int m = 0; m < HI; ++m) {
-          dst[o * HI + m] = 0.5 * (M[o * C + m] + M[o * C + C - 1 - m]);
-          dst[HO * HI + o * HI + m] = 0.5 * (M[o * C + m] - M[o * C + C - 1 - m]);
-        }
-        if (C & 1) dst[2 * HO * HI + o] = M[o * C + HI];
-      }
-    }
-  }
-  std::vector<float> eo32(eo.begin(), eo.end());
-  if (int e = check_cuda(c, cudaMemcpyToSymbol(c_eo64, eo.data(), eo.size() * sizeof(double)), "constant tables"))
-    return e;
-  if (int e = check_cuda(c, cudaMemcpyToSymbol(c_eo32, eo32.data(), eo32.size() * sizeof(float)), "constant tables"))
-    return e;
-  done[c->device] = true;
-  return 0;
-}
+int ensure_const_tables(dgx_ctx *c) { return upload_const_tables(c); }
 
 template <typename T>
 OpP<T> make_params(const dgx_ctx *c) {
@@ -844,22 +612,22 @@ template OpP<double> make_params<double>(const dgx_ctx *);
 template OpP<float> make_params<float>(const dgx_ctx *);
 
 template <typename T>
-int launch_grad(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s) {
-#define CALL_GRAD(NN, CC) grad_impl<T, NN, CC>(c, p, rho, V, s)
+int launch_grad(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s, bool inv, double alpha) {
+#define CALL_GRAD(NN, CC) grad_impl<T, NN, CC>(c, p, rho, V, s, inv, alpha)
   DGX_DISPATCH(CALL_GRAD)
 #undef CALL_GRAD
 }
 
 template <typename T>
-int launch_div(dgx_ctx *c, const T *V, const T *p, const T *pk, T *y, cudaStream_t s) {
-#define CALL_DIV(NN, CC) div_impl<T, NN, CC>(c, V, p, pk, y, s)
+int launch_div(dgx_ctx *c, const T *V, const T *p, const T *pk, T *y, cudaStream_t s, double alpha) {
+#define CALL_DIV(NN, CC) div_impl<T, NN, CC>(c, V, p, pk, y, s, alpha)
   DGX_DISPATCH(CALL_DIV)
 #undef CALL_DIV
 }
 
 template <typename T>
-int launch_mass_inverse(dgx_ctx *c, const T *in, const T *rho, T *out, cudaStream_t s) {
-#define CALL_MINV(NN, CC) minv_impl<T, NN, CC>(c, in, rho, out, s)
+int launch_mass_inverse(dgx_ctx *c, const T *in, const T *rho, T *out, cudaStream_t s, int nf) {
+#define CALL_MINV(NN, CC) minv_impl<T, NN, CC>(c, in, rho, out, s, nf)
   DGX_DISPATCH(CALL_MINV)
 #undef CALL_MINV
 }
@@ -870,11 +638,12 @@ int launch_diag(dgx_ctx *c, const double *rho, const double *pk, double *dh, dou
 #undef CALL_DIAG
 }
 
-template int launch_grad<double>(dgx_ctx *, const double *, const double *, double *, cudaStream_t);
-template int launch_grad<float>(dgx_ctx *, const float *, const float *, float *, cudaStream_t);
-template int launch_div<double>(dgx_ctx *, const double *, const double *, const double *, double *, cudaStream_t);
-template int launch_div<float>(dgx_ctx *, const float *, const float *, const float *, float *, cudaStream_t);
-template int launch_mass_inverse<double>(dgx_ctx *, const double *, const double *, double *, cudaStream_t);
-template int launch_mass_inverse<float>(dgx_ctx *, const float *, const float *, float *, cudaStream_t);
+template int launch_grad<double>(dgx_ctx *, const double *, const double *, double *, cudaStream_t, bool, double);
+template int launch_grad<float>(dgx_ctx *, const float *, const float *, float *, cudaStream_t, bool, double);
+template int launch_div<double>(dgx_ctx *, const double *, const double *, const double *, double *, cudaStream_t,
+                                double);
+template int launch_div<float>(dgx_ctx *, const float *, const float *, const float *, float *, cudaStream_t, double);
+template int launch_mass_inverse<double>(dgx_ctx *, const double *, const double *, double *, cudaStream_t, int);
+template int launch_mass_inverse<float>(dgx_ctx *, const float *, const float *, float *, cudaStream_t, int);
 
 }  // namespace dgx

@@ -45,6 +45,13 @@ class dgx_solve_opts(C.Structure):
                 ("inner_tol", C.c_double), ("use_x0", C.c_int), ("reserved", C.c_int)]
 
 
+class dgx_step_info(C.Structure):
+    _fields_ = [("steps", C.c_int), ("solves", C.c_int), ("krylov_iterations", C.c_int),
+                ("inner_iterations", C.c_int), ("operator_f64", C.c_int), ("operator_f32", C.c_int),
+                ("status", C.c_int), ("reserved", C.c_int), ("max_relres", C.c_double), ("seconds", C.c_double),
+                ("seconds_solve", C.c_double)]
+
+
 class dgx_solve_info(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("inner_iterations", C.c_int),
                 ("operator_f64", C.c_int), ("operator_f32", C.c_int), ("reserved", C.c_int),
@@ -74,6 +81,11 @@ SIGNATURES = [
     ("dgx_operator_cost", C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("dgx_kernel_launches", C.c_longlong, []),
     ("dgx_apply_operator_noalloc", C.c_int, [_P, C.c_int, _P, _P]),
+    ("dgx_set_imex", C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int]),
+    ("dgx_explicit_tendencies", C.c_int, [_P, _P, _P, _P, _P, _P]),
+    ("dgx_apply_mass", C.c_int, [_P, _P, _P, _P]),
+    ("dgx_kinetic_mass", C.c_int, [_P, _P, _P, _P]),
+    ("dgx_imex_step", C.c_int, [_P, _P, _P, _P, C.c_int, C.POINTER(dgx_solve_opts), C.POINTER(dgx_step_info)]),
 ]
 
 _lib = None
@@ -206,6 +218,49 @@ def dgx_apply_operator_noalloc(ctx, prec, x_ptr, y_ptr):
 
 
 DGX_NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def dgx_set_imex(ctx, A, At, dt, K=2):
+    """A, At: host (s, s) float64 arrays (numpy)."""
+    import numpy as np
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    At = np.ascontiguousarray(At, dtype=np.float64)
+    s = A.shape[0]
+    return _check(ctx, load().dgx_set_imex(ctx, s, A.ctypes.data_as(C.c_void_p), At.ctypes.data_as(C.c_void_p),
+                                           float(dt), int(K)))
+
+
+def dgx_explicit_tendencies(ctx, rho_ptr, u_ptr, Erho_ptr, Em_ptr, Ee_ptr):
+    return _check(ctx, load().dgx_explicit_tendencies(ctx, C.c_void_p(rho_ptr), C.c_void_p(u_ptr),
+                                                      C.c_void_p(Erho_ptr), C.c_void_p(Em_ptr), C.c_void_p(Ee_ptr)))
+
+
+def dgx_apply_mass(ctx, rho_ptr, in_ptr, out_ptr):
+    return _check(ctx, load().dgx_apply_mass(ctx, C.c_void_p(rho_ptr), C.c_void_p(in_ptr), C.c_void_p(out_ptr)))
+
+
+def dgx_kinetic_mass(ctx, rho_ptr, u_ptr, out_ptr):
+    return _check(ctx, load().dgx_kinetic_mass(ctx, C.c_void_p(rho_ptr), C.c_void_p(u_ptr), C.c_void_p(out_ptr)))
+
+
+def dgx_imex_step(ctx, rho_ptr, u_ptr, p_ptr, nsteps=1, opts=None):
+    """Returns (status, dgx_step_info); raises DgxError on errors (< 0)."""
+    o = opts if opts is not None else dgx_default_solve_opts()
+    info = dgx_step_info()
+    rc = load().dgx_imex_step(ctx, C.c_void_p(rho_ptr), C.c_void_p(u_ptr), C.c_void_p(p_ptr), int(nsteps),
+                              C.byref(o), C.byref(info))
+    _check(ctx, rc, allow=(DGX_OK, DGX_NOT_CONVERGED))
+    return rc, info
+
+
+def ars222():
+    """ARS(2,2,2) companion tableaux (A explicit, At implicit), gamma = 1 - 1/sqrt(2)."""
+    import numpy as np
+    g = 1.0 - 1.0 / np.sqrt(2.0)
+    d = 1.0 - 1.0 / (2.0 * g)
+    A = np.array([[0, 0, 0], [g, 0, 0], [d, 1 - d, 0]], dtype=np.float64)
+    At = np.array([[0, 0, 0], [0, g, 0], [0, 1 - g, g]], dtype=np.float64)
+    return A, At
 
 
 def dgx_kernel_launches():

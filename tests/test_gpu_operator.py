@@ -28,6 +28,8 @@ MESHES = [
     dict(nx=2, ny=2, nz=3, r=4, Lx=2000.0, Ly=2000.0, Lz=1500.0, terrain=2, hc=250.0, ac=600.0, bc_lateral=1),
     dict(nx=3, ny=2, nz=1, r=5, Lx=3000.0, Ly=2000.0, Lz=800.0, terrain=1, hc=200.0, ac=900.0),
     dict(nx=2, ny=1, nz=2, r=6, Lx=2000.0, Ly=1000.0, Lz=1000.0, terrain=1, hc=150.0, ac=500.0, bc_lateral=1),
+    dict(nx=3, ny=2, nz=2, r=3, Lx=3000.0, Ly=2000.0, Lz=1500.0, terrain=1, hc=200.0, ac=800.0, bc_lateral=2),
+    dict(nx=1, ny=1, nz=2, r=2, Lx=1000.0, Ly=1000.0, Lz=1000.0, bc_lateral=2),
 ]
 
 

@@ -207,3 +207,35 @@ def test_imex_second_order_in_time():
         e.append(np.abs(p - pref).max())
     order = np.log2(e[0] / e[1])
     assert order >= 1.8, (e, order)
+
+
+def test_periodic_uniform_wind_is_steady():
+    """Flat periodic domain, hydrostatic background and a uniform horizontal
+    wind: an exact steady state; the explicit tendencies vanish and an IMEX
+    step leaves the state unchanged to roundoff."""
+    bg = O.make_bg(g=G, ubar=10.0)
+    m = O.make_mesh(3, 2, 3, 3, Lx=3000.0, Ly=2000.0, Lz=1500.0, bc_lateral=2)
+    N = O.ndofs(m)
+    rb, pb = O.background(m, bg)
+    u = np.concatenate([np.full(N, 10.0), np.full(N, -4.0), np.zeros(N)])
+    Er, Em, Ee = O.explicit(m, bg, rb, u, rb)
+    rng = np.random.default_rng(3)
+    sc = np.abs(O.explicit(m, bg, rb * (1 + 0.01 * rng.random(N)), u, rb)[0]).max()
+    assert np.abs(Er).max() <= 1e-12 * sc and np.abs(Em).max() <= 1e-12 * sc * 10 and np.abs(Ee).max() <= 1e-12 * sc * 60
+    r, u2, p, st, _ = O.imex_step(m, bg, rb, u, pb, 1.0)
+    assert st == 0
+    assert np.abs(r - rb).max() <= 1e-12 * rb.max()
+    assert np.abs(u2 - u).max() <= 1e-10 * 10.0
+    assert np.abs(p - pb).max() <= 1e-10 * pb.max()
+
+
+def test_periodic_mass_conservation():
+    bg = O.make_bg(g=G, ubar=10.0)
+    m = O.make_mesh(3, 2, 2, 2, Lx=3000.0, Ly=2000.0, Lz=1500.0, terrain=1, hc=200.0, ac=800.0, bc_lateral=2)
+    N = O.ndofs(m)
+    rb, pb = O.background(m, bg)
+    u = np.concatenate([np.full(N, 10.0), np.zeros(N), np.zeros(N)])
+    ones = np.ones(N)
+    mass = lambda r: O.apply_A(m, ones, np.concatenate([r, 0 * r, 0 * r]))[:N].sum()
+    r, _, _, st, _ = O.imex_step(m, bg, rb, u, pb, 1.0)
+    assert st == 0 and abs(mass(r) - mass(rb)) <= 1e-13 * mass(rb) and np.abs(r - rb).max() > 0

@@ -416,3 +416,21 @@ def test_sampled_apply_matches_full():
     n3 = 27
     for c in cells:
         assert np.array_equal(ys[c * n3:(c + 1) * n3], y[c * n3:(c + 1) * n3])
+
+
+@pytest.mark.parametrize("geo", [dict(terrain=0), dict(terrain=1, hc=300.0, ac=700.0)])
+def test_periodic_lateral_boundaries(geo):
+    """Periodic x, y (centred hill) and slip walls top and bottom: no boundary
+    flux remains, so S is symmetric positive definite for uniform
+    coefficients and S 1 = D 1, 1^T S = 1^T D for random coefficients."""
+    m = O.make_mesh(3, 2, 2, 2, Lx=3000.0, Ly=2000.0, Lz=1500.0, bc_lateral=2, **geo)
+    N = O.ndofs(m)
+    S = O.assemble(lambda v: O.apply_S(m, ALPHA, GAMMA, np.full(N, 1.1), np.full(N, 9e4), v), N, N)
+    assert np.abs(S - S.T).max() <= 1e-13 * np.abs(S).max()
+    assert np.linalg.eigvalsh(0.5 * (S + S.T)).min() > 0
+    rng = np.random.default_rng(9)
+    rho, pk = 1.2 * (1 + 0.2 * rng.random(N)), 1e5 * (1 + 0.2 * rng.random(N))
+    D1 = O.apply_D(m, GAMMA, np.ones(N))
+    assert np.abs(O.apply_S(m, ALPHA, GAMMA, rho, pk, np.ones(N)) - D1).max() <= 1e-13 * np.abs(D1).max()
+    S = O.assemble(lambda v: O.apply_S(m, ALPHA, GAMMA, rho, pk, v), N, N)
+    assert np.abs(S.sum(axis=0) - D1).max() <= 1e-12 * np.abs(D1).max()
