@@ -250,6 +250,43 @@ int dgx_operator_cost(const dgx_ctx *ctx, double *flops_grad, double *flops_div,
  * contexts); a diagnostic counter for benchmarks. */
 long long dgx_kernel_launches(void);
 
+/* ---------------------------------------------------------------- ensembles
+ * Several independent meshes (sizes, degrees, terrain) whose pressure
+ * systems S_m p_m = b_m (Sec. 2, Sec. 3.1) are solved together.  Vectors are
+ * the members' DoF blocks concatenated in member order (member m starts at
+ * dgx_ensemble_offset(e, m)); all arrays are device FP64 unless stated.
+ * The operator of all members of one degree runs as one kernel pair; the
+ * solver is FP64 iterative refinement around an FP32 GMRES(inner_maxit)
+ * cycle with the Helmholtz Jacobi preconditioner, every cycle of all members
+ * being one CUDA-graph launch (per-member Hessenberg and Givens rotations on
+ * the device); threads per CTA are chosen per degree group by a timing
+ * autotuner before the graph is captured. */
+typedef struct dgx_ensemble dgx_ensemble;
+int dgx_ensemble_create(dgx_ensemble **e, int device, void *cuda_stream, int n_members, const dgx_mesh_desc *descs);
+void dgx_ensemble_destroy(dgx_ensemble *e);
+const char *dgx_ensemble_last_error(const dgx_ensemble *e);
+/* DoFs of member m (m = -1: total) and offset of member m in the concatenated vectors. */
+long long dgx_ensemble_num_dofs(const dgx_ensemble *e, int m);
+long long dgx_ensemble_offset(const dgx_ensemble *e, int m);
+/* The member's own context (owned by the ensemble; for set-up calls such as
+ * dgx_set_background / dgx_node_coords on that member). */
+int dgx_ensemble_member(dgx_ensemble *e, int m, dgx_ctx **ctx);
+/* Concatenated rho^(l), p_k of all members; same a~_ll dt and gamma for all. */
+int dgx_ensemble_set_coefficients(dgx_ensemble *e, const double *rho_all, const double *p_k_all, double a_dt,
+                                  double gamma);
+/* y = S x for every member (prec: DGX_F64 or DGX_F32). */
+int dgx_ensemble_apply_operator(dgx_ensemble *e, int prec, const void *x_all, void *y_all);
+/* Choose threads per CTA of the multi-mesh operator per degree group (also done by the first solve). */
+int dgx_ensemble_autotune(dgx_ensemble *e);
+/* The autotuner's choice for degree group g (host outputs, any may be NULL). */
+int dgx_ensemble_tuning(const dgx_ensemble *e, int g, int *degree, int *members, int *threads64, int *threads32);
+/* Solve all members to ||b_m - S_m x_m|| <= tol ||b_m|| (FP64).  opts: tol, maxit
+ * (refinement sweeps), inner_maxit (FP32 GMRES cycle length, <= 64), inner_tol,
+ * use_x0.  info: array of n_members entries (host).  Returns DGX_OK,
+ * DGX_NOT_CONVERGED or an error. */
+int dgx_ensemble_solve(dgx_ensemble *e, const double *b_all, double *x_all, const dgx_solve_opts *opts,
+                       dgx_solve_info *info);
+
 #ifdef __cplusplus
 }
 #endif

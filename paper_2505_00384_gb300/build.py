@@ -50,8 +50,14 @@ def build(force=False, verbose=False, extra_flags=()):
     nv = nvcc()
     srcs = _sources()
 
+    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    newest_header = max([os.path.getmtime(h) for h in headers] + [0.0])
+
     def compile_one(src):
         obj = os.path.join(OBJ, os.path.basename(src) + ".o")
+        if (not force and not extra_flags and os.path.exists(obj)
+                and os.path.getmtime(obj) > max(os.path.getmtime(src), newest_header)):
+            return obj
         cmd = [nv] + ARCH + FLAGS + list(extra_flags) + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

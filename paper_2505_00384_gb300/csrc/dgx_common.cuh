@@ -99,6 +99,16 @@ struct OpP {
   const T *col;            // per-column terrain tables (nullptr when flat)
 };
 
+// One member of a multi-mesh (ensemble) launch: its operator parameters, its
+// coefficient copies and V scratch, and its place in the concatenated vectors.
+template <typename T>
+struct EnsMember {
+  OpP<T> P;
+  const T *rho, *pk;
+  T *V;
+  long long cell_off, dof_off, N;
+};
+
 // ---------------------------------------------------------------- context
 struct Buf {
   void *p = nullptr;
@@ -183,6 +193,11 @@ template <typename T>
 int launch_div(dgx_ctx *c, const T *V, const T *p, const T *pk, T *y, cudaStream_t s, double alpha = -1.0);
 template <typename T>
 int launch_mass_inverse(dgx_ctx *c, const T *in, const T *rho, T *out, cudaStream_t s, int nf = 3);
+// multi-mesh operator y = S x for members of one degree (N = r+1) and terrain kind;
+// `mem` is a device array of nmem members with consecutive cell ranges totalling ncell_total
+template <typename T>
+int launch_operator_multi(dgx_ctx *c0, int n, bool curved, const EnsMember<T> *mem, int nmem, long long ncell_total,
+                          const T *x_all, T *y_all, cudaStream_t s, int threads);
 // explicit part of the IMEX step (dgx_explicit.cu), FP64
 int launch_explicit(dgx_ctx *c, const double *rho, const double *u, const double *rho_bar, double *Er, double *Em,
                     double *Ee, cudaStream_t s);

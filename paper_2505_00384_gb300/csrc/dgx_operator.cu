@@ -21,6 +21,8 @@
 #include <cmath>
 #include <cstdio>
 #include <mutex>
+#include <set>
+#include <utility>
 
 #include "dgx_common.cuh"
 #include "dgx_sweep.cuh"
@@ -56,19 +58,17 @@ template <typename T, int N>
 constexpr int min_ctas() { return (sizeof(T) == 8 && N <= 5) ? 3 : 1; }
 
 // INV = true: V = A^-1 (B p); INV = false: the dual vector B p itself.
-template <typename T, int N, int Q, bool CURVED, bool INV = true>
-__global__ void __launch_bounds__(256, min_ctas<T, N>()) k_grad(const OpP<T> P, const T *__restrict__ p, const T *__restrict__ rho,
-                                              T *__restrict__ V, long long Ntot) {
+// One cell per CTA; `sm` is the CTA's dynamic shared memory (GradL layout).
+template <typename T, int N, int Q, bool CURVED, bool INV>
+__device__ __forceinline__ void grad_body(const OpP<T> &P, const long long cell, const T *__restrict__ p,
+                                          const T *__restrict__ rho, T *__restrict__ V, long long Ntot, T *sm) {
   using L = GradL<N, Q, CURVED>;
   constexpr int N2 = L::N2, N3 = L::N3, Q2 = L::Q2, Q3 = L::Q3, NFV = L::NFV, NFP = L::NFP;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T *sm = reinterpret_cast<T *>(smraw);
   T *tab = sm;
   T *s_p = sm + L::oP, *s_rho = sm + L::oRho, *s_rq = sm + L::oRq, *s_out = sm + L::oOut;
   T *R1 = sm + L::oR1, *R2 = sm + L::oR2, *Wv = sm + L::oVol, *Wz = sm + L::oZ, *Wy = sm + L::oY,
     *Wx = sm + L::oX, *Wf = sm + L::oFace;
 
-  const long long cell = blockIdx.x;
   const CellPos cp = cell_pos(P, cell);
   const T *colp = CURVED ? P.col + (long long)(cp.cx + P.nx * cp.cy) * col_size(N, Q) : nullptr;
   const T zeta0 = T(cp.cz) * P.dz;
@@ -206,6 +206,34 @@ __global__ void __launch_bounds__(256, min_ctas<T, N>()) k_grad(const OpP<T> P, 
   }
 }
 
+template <typename T, int N, int Q, bool CURVED, bool INV = true>
+__global__ void __launch_bounds__(256, min_ctas<T, N>()) k_grad(const OpP<T> P, const T *__restrict__ p,
+                                                                const T *__restrict__ rho, T *__restrict__ V,
+                                                                long long Ntot) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  grad_body<T, N, Q, CURVED, INV>(P, blockIdx.x, p, rho, V, Ntot, reinterpret_cast<T *>(smraw));
+}
+
+// Several meshes of the same degree in one launch: CTA b belongs to the member
+// whose cell range [cell_off, cell_off + ncell) holds b; vectors are the
+// members' DoF blocks concatenated (member m starts at dof_off).
+template <typename T>
+__device__ __forceinline__ int member_of(const EnsMember<T> *mem, int nmem, long long b) {
+  int m = 0;
+  while (m + 1 < nmem && mem[m + 1].cell_off <= b) ++m;
+  return m;
+}
+
+template <typename T, int N, int Q, bool CURVED>
+__global__ void __launch_bounds__(256, min_ctas<T, N>()) k_grad_multi(const EnsMember<T> *__restrict__ mem, int nmem,
+                                                                      const T *__restrict__ p_all) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int m = member_of(mem, nmem, blockIdx.x);
+  const EnsMember<T> M = mem[m];
+  grad_body<T, N, Q, CURVED, true>(M.P, blockIdx.x - M.cell_off, p_all + M.dof_off, M.rho, M.V, M.N,
+                                   reinterpret_cast<T *>(smraw));
+}
+
 // ------------------------------------------------------------------ k_div
 template <int N, int Q, bool CURVED>
 struct DivL {
@@ -250,12 +278,11 @@ __device__ __forceinline__ int div_slot_base(int f) {
 }
 
 template <typename T, int N, int Q, bool CURVED>
-__global__ void __launch_bounds__(256, min_ctas<T, N>()) k_div(const OpP<T> P, const T *__restrict__ V, const T *__restrict__ p,
-                                             const T *__restrict__ pk, T *__restrict__ y, long long Ntot) {
+__device__ __forceinline__ void div_body(const OpP<T> &P, const long long cell, const T *__restrict__ V,
+                                         const T *__restrict__ p, const T *__restrict__ pk, T *__restrict__ y,
+                                         long long Ntot, T *sm) {
   using L = DivL<N, Q, CURVED>;
   constexpr int N2 = L::N2, N3 = L::N3, Q2 = L::Q2, Q3 = L::Q3, NSL = L::NSL;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T *sm = reinterpret_cast<T *>(smraw);
   T *tab = sm;
   T *s_in = sm + L::oIn, *s_y = sm + L::oY;
   T *R1 = sm + L::oR1, *R2 = sm + L::oR2, *R3 = sm + L::oR3, *Wz = sm + L::oZ, *Wy = sm + L::oYs, *Wx = sm + L::oX;
@@ -263,7 +290,6 @@ __global__ void __launch_bounds__(256, min_ctas<T, N>()) k_div(const OpP<T> P, c
   T *Fg = sm + L::oFace, *F2 = Fg, *F1 = Fg + cmax(NSL * N2, NSL * Q2), *Ff = F1 + NSL * N * Q, *Fb1 = Ff + 6 * Q2,
     *Fb2 = Fb1 + 6 * N * Q;
 
-  const long long cell = blockIdx.x;
   const CellPos cp = cell_pos(P, cell);
   const T *colp = CURVED ? P.col + (long long)(cp.cx + P.nx * cp.cy) * col_size(N, Q) : nullptr;
   const T zeta0 = T(cp.cz) * P.dz;
@@ -378,6 +404,24 @@ __global__ void __launch_bounds__(256, min_ctas<T, N>()) k_div(const OpP<T> P, c
     if (c == N - 1) acc += Fb2[5 * N2 + a + N * b];
     y[cell * N3 + idx] = acc;
   }
+}
+
+template <typename T, int N, int Q, bool CURVED>
+__global__ void __launch_bounds__(256, min_ctas<T, N>()) k_div(const OpP<T> P, const T *__restrict__ V,
+                                                               const T *__restrict__ p, const T *__restrict__ pk,
+                                                               T *__restrict__ y, long long Ntot) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  div_body<T, N, Q, CURVED>(P, blockIdx.x, V, p, pk, y, Ntot, reinterpret_cast<T *>(smraw));
+}
+
+template <typename T, int N, int Q, bool CURVED>
+__global__ void __launch_bounds__(256, min_ctas<T, N>()) k_div_multi(const EnsMember<T> *__restrict__ mem, int nmem,
+                                                                     const T *__restrict__ p_all, T *__restrict__ y_all) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int m = member_of(mem, nmem, blockIdx.x);
+  const EnsMember<T> M = mem[m];
+  div_body<T, N, Q, CURVED>(M.P, blockIdx.x - M.cell_off, M.V, p_all + M.dof_off, M.pk, y_all + M.dof_off, M.N,
+                            reinterpret_cast<T *>(smraw));
 }
 
 // ------------------------------------------------------------------ k_minv
@@ -504,12 +548,25 @@ __global__ void __launch_bounds__(256) k_diag(const OpP<double> P, const double 
   }
 }
 
+// Kernel attributes (dynamic shared memory above 48 KB, maximum carveout), set
+// once per kernel and device, so that later launches -- also inside CUDA-graph
+// capture -- make no attribute calls.
 template <typename Kern>
 int prep(dgx_ctx *c, Kern k, size_t smem) {
-  static_assert(sizeof(Kern) > 0, "");
+  static std::mutex mu;
+  static std::set<std::pair<int, const void *>> done;  // (device, kernel)
+  const std::pair<int, const void *> key(c->device, reinterpret_cast<const void *>(k));
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(key)) return 0;
+  }
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(mu);
+    done.insert(key);
+  }
   return check_cuda(c, e, "cudaFuncSetAttribute");
 }
 
@@ -568,6 +625,21 @@ int diag_impl(dgx_ctx *c, const double *rho, const double *pk, double *dh, doubl
   count_launch();
   k<<<(unsigned)c->ncell, threads_for(N), smem, s>>>(make_params<double>(c), rho, pk, dh, die);
   return check_cuda(c, cudaGetLastError(), "k_diag launch");
+}
+
+template <typename T, int N, bool CURVED>
+int opmulti_impl(dgx_ctx *c, const EnsMember<T> *mem, int nmem, long long ncell, const T *x, T *y, cudaStream_t s,
+                 int threads) {
+  constexpr int Q = 2 * N - 1;
+  const size_t sg = sizeof(T) * GradL<N, Q, CURVED>::total, sd = sizeof(T) * DivL<N, Q, CURVED>::total;
+  auto kg = k_grad_multi<T, N, Q, CURVED>;
+  auto kd = k_div_multi<T, N, Q, CURVED>;
+  if (int e = prep(c, kg, sg)) return e;
+  if (int e = prep(c, kd, sd)) return e;
+  count_launch(2);
+  kg<<<(unsigned)ncell, threads, sg, s>>>(mem, nmem, x);
+  kd<<<(unsigned)ncell, threads, sd, s>>>(mem, nmem, x, y);
+  return check_cuda(c, cudaGetLastError(), "multi-mesh operator launch");
 }
 
 #define DGX_DISPATCH(CALL)                                                         \
@@ -637,6 +709,25 @@ int launch_diag(dgx_ctx *c, const double *rho, const double *pk, double *dh, dou
   DGX_DISPATCH(CALL_DIAG)
 #undef CALL_DIAG
 }
+
+template <typename T>
+int launch_operator_multi(dgx_ctx *c, int n, bool curved, const EnsMember<T> *mem, int nmem, long long ncell,
+                          const T *x, T *y, cudaStream_t s, int threads) {
+  if (threads < 32 || threads > 256 || threads % 32) return set_error(c, DGX_ERR_ARG, "threads %d", threads);
+  switch (n) {
+    case 2: return curved ? opmulti_impl<T, 2, true>(c, mem, nmem, ncell, x, y, s, threads) : opmulti_impl<T, 2, false>(c, mem, nmem, ncell, x, y, s, threads);
+    case 3: return curved ? opmulti_impl<T, 3, true>(c, mem, nmem, ncell, x, y, s, threads) : opmulti_impl<T, 3, false>(c, mem, nmem, ncell, x, y, s, threads);
+    case 4: return curved ? opmulti_impl<T, 4, true>(c, mem, nmem, ncell, x, y, s, threads) : opmulti_impl<T, 4, false>(c, mem, nmem, ncell, x, y, s, threads);
+    case 5: return curved ? opmulti_impl<T, 5, true>(c, mem, nmem, ncell, x, y, s, threads) : opmulti_impl<T, 5, false>(c, mem, nmem, ncell, x, y, s, threads);
+    case 6: return curved ? opmulti_impl<T, 6, true>(c, mem, nmem, ncell, x, y, s, threads) : opmulti_impl<T, 6, false>(c, mem, nmem, ncell, x, y, s, threads);
+    case 7: return curved ? opmulti_impl<T, 7, true>(c, mem, nmem, ncell, x, y, s, threads) : opmulti_impl<T, 7, false>(c, mem, nmem, ncell, x, y, s, threads);
+    default: return set_error(c, DGX_ERR_ARG, "unsupported degree %d", n - 1);
+  }
+}
+template int launch_operator_multi<double>(dgx_ctx *, int, bool, const EnsMember<double> *, int, long long,
+                                           const double *, double *, cudaStream_t, int);
+template int launch_operator_multi<float>(dgx_ctx *, int, bool, const EnsMember<float> *, int, long long,
+                                          const float *, float *, cudaStream_t, int);
 
 template int launch_grad<double>(dgx_ctx *, const double *, const double *, double *, cudaStream_t, bool, double);
 template int launch_grad<float>(dgx_ctx *, const float *, const float *, float *, cudaStream_t, bool, double);

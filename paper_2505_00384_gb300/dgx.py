@@ -86,6 +86,18 @@ SIGNATURES = [
     ("dgx_apply_mass", C.c_int, [_P, _P, _P, _P]),
     ("dgx_kinetic_mass", C.c_int, [_P, _P, _P, _P]),
     ("dgx_imex_step", C.c_int, [_P, _P, _P, _P, C.c_int, C.POINTER(dgx_solve_opts), C.POINTER(dgx_step_info)]),
+    ("dgx_ensemble_create", C.c_int, [C.POINTER(C.c_void_p), C.c_int, _P, C.c_int, C.POINTER(dgx_mesh_desc)]),
+    ("dgx_ensemble_destroy", None, [_P]),
+    ("dgx_ensemble_last_error", C.c_char_p, [_P]),
+    ("dgx_ensemble_num_dofs", C.c_longlong, [_P, C.c_int]),
+    ("dgx_ensemble_offset", C.c_longlong, [_P, C.c_int]),
+    ("dgx_ensemble_member", C.c_int, [_P, C.c_int, C.POINTER(C.c_void_p)]),
+    ("dgx_ensemble_set_coefficients", C.c_int, [_P, _P, _P, C.c_double, C.c_double]),
+    ("dgx_ensemble_apply_operator", C.c_int, [_P, C.c_int, _P, _P]),
+    ("dgx_ensemble_autotune", C.c_int, [_P]),
+    ("dgx_ensemble_tuning", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                      C.POINTER(C.c_int)]),
+    ("dgx_ensemble_solve", C.c_int, [_P, _P, _P, C.POINTER(dgx_solve_opts), C.POINTER(dgx_solve_info)]),
 ]
 
 _lib = None
@@ -251,6 +263,71 @@ def dgx_imex_step(ctx, rho_ptr, u_ptr, p_ptr, nsteps=1, opts=None):
                               C.byref(o), C.byref(info))
     _check(ctx, rc, allow=(DGX_OK, DGX_NOT_CONVERGED))
     return rc, info
+
+
+def _echeck(e, rc, allow=(DGX_OK,)):
+    if rc in allow:
+        return rc
+    raise DgxError(rc, load().dgx_ensemble_last_error(e).decode() if e else "")
+
+
+def dgx_ensemble_create(device, stream, descs):
+    """descs: list of dgx_mesh_desc.  Returns the ensemble handle."""
+    arr = (dgx_mesh_desc * len(descs))(*descs)
+    h = C.c_void_p()
+    rc = load().dgx_ensemble_create(C.byref(h), int(device), C.c_void_p(int(stream) or None), len(descs), arr)
+    if rc != DGX_OK:
+        msg = load().dgx_ensemble_last_error(h).decode() if h else ""
+        if h:
+            load().dgx_ensemble_destroy(h)
+        raise DgxError(rc, "dgx_ensemble_create: " + msg)
+    return h
+
+
+def dgx_ensemble_destroy(e):
+    load().dgx_ensemble_destroy(e)
+
+
+def dgx_ensemble_num_dofs(e, m=-1):
+    return int(load().dgx_ensemble_num_dofs(e, m))
+
+
+def dgx_ensemble_offset(e, m):
+    return int(load().dgx_ensemble_offset(e, m))
+
+
+def dgx_ensemble_member(e, m):
+    h = C.c_void_p()
+    _echeck(e, load().dgx_ensemble_member(e, m, C.byref(h)))
+    return h
+
+
+def dgx_ensemble_set_coefficients(e, rho_ptr, pk_ptr, a_dt, gamma=1.4):
+    return _echeck(e, load().dgx_ensemble_set_coefficients(e, C.c_void_p(rho_ptr), C.c_void_p(pk_ptr), float(a_dt),
+                                                           float(gamma)))
+
+
+def dgx_ensemble_apply_operator(e, prec, x_ptr, y_ptr):
+    return _echeck(e, load().dgx_ensemble_apply_operator(e, prec, C.c_void_p(x_ptr), C.c_void_p(y_ptr)))
+
+
+def dgx_ensemble_autotune(e):
+    return _echeck(e, load().dgx_ensemble_autotune(e))
+
+
+def dgx_ensemble_tuning(e, g):
+    v = [C.c_int() for _ in range(4)]
+    _echeck(e, load().dgx_ensemble_tuning(e, g, *[C.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def dgx_ensemble_solve(e, b_ptr, x_ptr, n_members, opts=None):
+    """Returns (status, [dgx_solve_info per member])."""
+    o = opts if opts is not None else dgx_default_solve_opts()
+    infos = (dgx_solve_info * n_members)()
+    rc = load().dgx_ensemble_solve(e, C.c_void_p(b_ptr), C.c_void_p(x_ptr), C.byref(o), infos)
+    _echeck(e, rc, allow=(DGX_OK, DGX_NOT_CONVERGED))
+    return rc, list(infos)
 
 
 def ars222():
