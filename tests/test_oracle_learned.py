@@ -1,0 +1,109 @@
+"""Pins of the learned-preconditioner oracle (oracle/learned.py).
+
+The convolution is checked against its definition written as explicit loops
+(independent of the vectorised form), against special cases (a centred delta
+kernel is the identity, an off-centre delta is a shift with zero fill), the
+backward pass against central finite differences of the loss, and the
+DoF-to-grid map against the physical node coordinates.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.learned as NL
+
+
+def _conv_loops(x, W, b):
+    Ci, Z, Y, X = x.shape
+    Co = W.shape[0]
+    y = np.zeros((Co, Z, Y, X))
+    for o in range(Co):
+        for z in range(Z):
+            for yy in range(Y):
+                for xx in range(X):
+                    s = b[o]
+                    for i in range(Ci):
+                        for dz in (-1, 0, 1):
+                            for dy in (-1, 0, 1):
+                                for dx in (-1, 0, 1):
+                                    zz, y2, x2 = z + dz, yy + dy, xx + dx
+                                    if 0 <= zz < Z and 0 <= y2 < Y and 0 <= x2 < X:
+                                        s += W[o, i, dz + 1, dy + 1, dx + 1] * x[i, zz, y2, x2]
+                    y[o, z, yy, xx] = s
+    return y
+
+
+def test_conv_matches_loop_definition():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((2, 3, 4, 5))
+    W = rng.standard_normal((3, 2, 3, 3, 3))
+    b = rng.standard_normal(3)
+    assert np.abs(NL.conv3d(x, W, b) - _conv_loops(x, W, b)).max() <= 1e-12
+
+
+def test_conv_delta_kernels():
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((1, 4, 5, 6))
+    W = np.zeros((1, 1, 3, 3, 3))
+    W[0, 0, 1, 1, 1] = 1.0
+    assert np.array_equal(NL.conv3d(x, W, np.zeros(1)), x)
+    W = np.zeros((1, 1, 3, 3, 3))
+    W[0, 0, 1, 1, 2] = 1.0  # y[x] = in[x+1]
+    y = NL.conv3d(x, W, np.zeros(1))
+    assert np.array_equal(y[..., :-1], x[..., 1:]) and np.all(y[..., -1] == 0)
+
+
+def test_backward_matches_finite_differences():
+    rng = np.random.default_rng(3)
+    shape = (3, 4, 5)
+    params = [(0.3 * rng.standard_normal((4, 2, 3, 3, 3)), 0.1 * rng.standard_normal(4)),
+              (0.3 * rng.standard_normal((3, 4, 3, 3, 3)), 0.1 * rng.standard_normal(3)),
+              (0.3 * rng.standard_normal((1, 3, 3, 3, 3)), 0.1 * rng.standard_normal(1))]
+    B = 2
+    feats = rng.standard_normal((B, 2) + shape)
+    j = rng.standard_normal((B,) + shape)
+    x = rng.standard_normal((B,) + shape)
+    s = np.array([0.7, 1.3])
+    L, grads = NL.loss_and_grad(params, feats, j, s, x)
+    h = 1e-6
+    for li, (W, b) in enumerate(params):
+        for idx in [(0, 0, 1, 1, 1), (1, 1, 0, 2, 1), (0, 1, 2, 0, 0)]:
+            if any(k >= d for k, d in zip(idx, W.shape)):
+                continue
+            Wp = [(w.copy(), bb.copy()) for w, bb in params]
+            Wm = [(w.copy(), bb.copy()) for w, bb in params]
+            Wp[li][0][idx] += h
+            Wm[li][0][idx] -= h
+            fd = (NL.loss_and_grad(Wp, feats, j, s, x)[0] - NL.loss_and_grad(Wm, feats, j, s, x)[0]) / (2 * h)
+            assert abs(fd - grads[li][0][idx]) <= 1e-6 * max(1.0, abs(fd)), (li, idx, fd, grads[li][0][idx])
+        Bp = [(w.copy(), bb.copy()) for w, bb in params]
+        Bm = [(w.copy(), bb.copy()) for w, bb in params]
+        Bp[li][1][0] += h
+        Bm[li][1][0] -= h
+        fd = (NL.loss_and_grad(Bp, feats, j, s, x)[0] - NL.loss_and_grad(Bm, feats, j, s, x)[0]) / (2 * h)
+        assert abs(fd - grads[li][1][0]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_grid_map_follows_the_mesh():
+    """Along each grid axis the physical node coordinate is non-decreasing
+    (nodes shared by neighbouring cells appear twice), and the map is a
+    permutation."""
+    m = O.make_mesh(3, 2, 2, 2, Lx=3000.0, Ly=2000.0, Lz=1500.0)
+    perm = NL.dof_to_grid_index(3, 2, 2, 2)
+    assert np.array_equal(np.sort(perm), np.arange(O.ndofs(m)))
+    X = O.node_coords(m)
+    shape = (2 * 3, 2 * 3, 3 * 3)
+    gx = NL.to_grid(X[0], shape, perm)
+    gy = NL.to_grid(X[1], shape, perm)
+    gz = NL.to_grid(X[2], shape, perm)
+    assert np.all(np.diff(gx, axis=2) >= 0) and np.all(np.diff(gy, axis=1) >= 0) and np.all(np.diff(gz, axis=0) >= 0)
+    v = np.random.default_rng(4).standard_normal(O.ndofs(m))
+    assert np.array_equal(NL.to_dof(NL.to_grid(v, shape, perm), perm), v)
+
+
+def test_bf16_rounding():
+    # bf16 keeps 7 fraction bits: ties go to the even neighbour.
+    a = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1.0 + 2 ** -9, 3.14159, -2.5e-3])
+    r = NL.bf16_round(a)
+    assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.015625 and r[3] == 1.0
+    assert np.all(np.abs(r - a) <= np.abs(a) * 2 ** -8)
