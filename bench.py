@@ -54,8 +54,10 @@ def parse():
     ap.add_argument("--mesh", default=None, help="NXxNYxNZ cells at the same cell size as the 64x64x32 workload")
     ap.add_argument("--profile", action="store_true",
                     help="only the warm-up and timed steps (for profiler launch lists); no side measurements")
-    ap.add_argument("--workload", default="hill", choices=["hill", "ensemble"],
-                    help="hill: one IMEX step of the 64x64x32 hill (default); ensemble: 16-member batched solve")
+    ap.add_argument("--workload", default="hill", choices=["hill", "ensemble", "learned"],
+                    help="hill: one IMEX step of the 64x64x32 hill (default); ensemble: 16-member batched solve; "
+                         "learned: pressure solves of held-out hill systems with the trained network")
+    ap.add_argument("--epochs", type=int, default=30, help="learned workload: training epochs")
     ap.add_argument("--members", type=int, default=16, help="ensemble members (first k of the 16)")
     return ap.parse_args()
 
@@ -213,6 +215,173 @@ ENSEMBLE = [(32, 32, 32), (40, 40, 32), (48, 48, 32), (48, 48, 40), (56, 56, 32)
             (96, 96, 48), (32, 64, 32)]
 
 
+def run_learned(args):
+    """Learned preconditioner: 400 pressure systems recorded along IMEX
+    trajectories over 16 seeded hills (h_c ~ U[200, 800] m, 25 steps each, the
+    last solve of every step) on the 4 x 4 x 4-cell degree-2 box of 1 km
+    (1728 DoFs, periodic lateral faces); 14 hills train a 9-layer 32-channel
+    network (198 977 parameters) on the GPU, the 50 systems of the other two
+    are solved to 1e-8 from x = 0 with FP64 FGMRES(30) + Helmholtz Jacobi
+    (plain), the same with the learned preconditioner, and the mixed-precision
+    solver.  One step = the 50 held-out solves with the learned
+    preconditioner; L2 is flushed before every timed solve."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_2505_00384_gb300 import dgx, inputs
+    from paper_2505_00384_gb300 import learned as LP
+    torch.cuda.set_device(0)
+    dgx.load()
+    stream = torch.cuda.current_stream()
+    ctx = dgx.dgx_create(0, stream.cuda_stream)
+    layers, channels = 9, 32
+    dgx.dgx_learned_create(ctx, layers, channels, inputs.DEFAULT_SEED)
+    nparams = dgx.dgx_learned_num_params(ctx)
+    nh, steps, test_hills = 16, 25, (14, 15)
+    heights = LP.hill_heights(nh)
+    t0 = time.time()
+    held = LP.collect(ctx, heights, steps=steps, record_stride=4, pairs=8, pair_stride=3, test_hills=test_hills,
+                      random_per_record=1)
+    t_collect = time.time() - t0
+    ntr, nte = dgx.dgx_learned_num_samples(ctx)
+    o = dgx.dgx_default_train_opts()
+    o.epochs = args.epochs
+    tinfo = dgx.dgx_learned_train(ctx, o)
+    N = dgx.dgx_num_dofs(ctx)
+    f64 = torch.float64
+
+    def sopts(method, pc, restart):
+        so = dgx.dgx_default_solve_opts()
+        so.method, so.pc, so.restart, so.tol, so.maxit = method, pc, restart, 1e-8, 3000
+        so.inner_maxit, so.inner_tol = 30, 1e-5
+        return so
+
+    solvers = {"learned": sopts(dgx.DGX_SOLVER_FGMRES, dgx.DGX_PC_LEARNED, 30),
+               "plain_fp64": sopts(dgx.DGX_SOLVER_FGMRES, dgx.DGX_PC_HELMHOLTZ, 30),
+               "mixed": sopts(dgx.DGX_SOLVER_MIXED, dgx.DGX_PC_HELMHOLTZ, 20)}
+    systems = [(hi, rec) for hi in sorted(held) for rec in held[hi]]
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    x = torch.zeros(N, dtype=f64, device="cuda")
+    cur = [None]
+
+    def solve(name, hi, rec, timed):
+        if cur[0] != hi:
+            LP.setup_hill(ctx, heights[hi])
+            cur[0] = hi
+        rho, pk, b, _, a_dt, gamma = LP.split_record(rec, N)
+        dgx.dgx_set_coefficients(ctx, rho.data_ptr(), pk.data_ptr(), a_dt, gamma)
+        x.zero_()
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, si = dgx.dgx_solve_pressure(ctx, b.data_ptr(), x.data_ptr(), solvers[name])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if st not in (dgx.DGX_OK, dgx.DGX_FALLBACK_USED) or si.relres > 1e-8:
+            raise RuntimeError("%s solve did not converge (relres %g)" % (name, si.relres))
+        return e0.elapsed_time(e1) / 1e3, si
+
+    for _ in range(max(args.warmup, 3)):
+        for name in solvers:
+            solve(name, *systems[0], False)
+    res = {k: [] for k in solvers}
+    launches0 = dgx.dgx_kernel_launches()
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            for hi, rec in systems:
+                res["learned"].append(solve("learned", hi, rec, True))
+    launches = (dgx.dgx_kernel_launches() - launches0) / args.steps
+    for name in ("plain_fp64", "mixed"):
+        for hi, rec in systems:
+            res[name].append(solve(name, hi, rec, True))
+
+    def summary(rs):
+        return {"s_per_solve": float(np.mean([t for t, _ in rs])),
+                "iterations": float(np.mean([si.iterations for _, si in rs])),
+                "max_relres": float(max(si.relres for _, si in rs)),
+                "fallbacks": int(sum(si.fallback for _, si in rs))}
+
+    stats = {k: summary(v) for k, v in res.items()}
+    # e2e: host coefficients and right-hand side in, host solution out, per system
+    hosts = [(hi, [t.cpu().pin_memory() for t in LP.split_record(rec, N)[:3]], LP.split_record(rec, N)[4:])
+             for hi, rec in systems]
+    dev_in = [torch.empty(N, dtype=f64, device="cuda") for _ in range(3)]
+    xh = torch.empty(N, dtype=f64).pin_memory()
+    te = []
+    for hi, (rh, pkh, bh), (a_dt, gamma) in hosts:
+        if cur[0] != hi:
+            LP.setup_hill(ctx, heights[hi])
+            cur[0] = hi
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for d, h in zip(dev_in, (rh, pkh, bh)):
+            d.copy_(h, non_blocking=True)
+        dgx.dgx_set_coefficients(ctx, dev_in[0].data_ptr(), dev_in[1].data_ptr(), a_dt, gamma)
+        x.zero_()
+        dgx.dgx_solve_pressure(ctx, dev_in[2].data_ptr(), x.data_ptr(), solvers["learned"])
+        xh.copy_(x, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        te.append(e0.elapsed_time(e1) / 1e3)
+    # roofline of the learned apply (graph of the network's kernels): FP32 FMA work
+    conv_flops = 2.0 * 27 * N * sum(ci * co for ci, co in
+                                     zip([5] + [channels] * (layers - 1), [channels] * (layers - 1) + [1]))
+    v = torch.from_numpy(inputs.normal(inputs.DEFAULT_SEED + 9, N)).cuda()
+    z = torch.zeros_like(v)
+    dgx.dgx_learned_apply(ctx, dgx.DGX_F64, v.data_ptr(), z.data_ptr())
+    dgx.dgx_learned_apply(ctx, dgx.DGX_F64, v.data_ptr(), z.data_ptr())
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(200):
+        dgx.dgx_learned_apply(ctx, dgx.DGX_F64, v.data_ptr(), z.data_ptr())
+    a1.record(stream)
+    torch.cuda.synchronize()
+    t_apply = a0.elapsed_time(a1) / 1e3 / 200
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # FMA lanes x 2 flops x max SM clock
+    # CPU baseline: the oracle's plain FGMRES on one held-out system
+    cpu = None
+    if not args.no_cpu_baseline:
+        hi, rec = systems[0]
+        rho, pk, b, _, a_dt, gamma = (t if isinstance(t, float) else t.cpu().numpy() for t in LP.split_record(rec, N))
+        L = LP.BOX["L"]
+        m = O.make_mesh(4, 4, 4, 2, Lx=L, Ly=L, Lz=L, terrain=1, hc=float(heights[hi]), ac=LP.BOX["a_c"],
+                        xc=L / 2, yc=L / 2, bc_lateral=2)
+        tc = time.time()
+        _, st, its, rel = O.solve(m, a_dt, gamma, rho, pk, b, tol=1e-8, restart=30, maxit=3000)
+        cpu = {"value": time.time() - tc, "unit": "s/solve", "cores": O.max_threads(), "kind": "oracle",
+               "sample": "1 held-out system, FP64 FGMRES(30) + Helmholtz Jacobi to 1e-8 (%d iterations)" % its}
+    lv = stats["learned"]["s_per_solve"]
+    line = {"metric": "pressure solve s/solve @1e-8 rel residual (learned preconditioner, held-out hills)",
+            "value": lv, "unit": "s/solve", "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": lv * len(systems) * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (network f32, bf16 weights)", "data": "synthetic",
+            "config": {"workload": "learned_box_4x4x4_r2_1728_dofs_16_hills", "systems_recorded": 400,
+                       "train_hills": nh - len(test_hills), "held_out_systems": len(systems),
+                       "network": "%d conv3d layers, %d channels, %d params" % (layers, channels, nparams),
+                       "l2": "flushed before every timed solve"},
+            "solvers": stats,
+            "speedup_vs_plain_fp64": stats["plain_fp64"]["s_per_solve"] / lv,
+            "iterations_ratio_vs_plain": stats["learned"]["iterations"] / stats["plain_fp64"]["iterations"],
+            "training": {"samples_train": ntr, "samples_test": nte, "epochs": args.epochs, "steps": tinfo.steps,
+                         "seconds": tinfo.seconds, "collect_seconds": t_collect,
+                         "loss_train": [tinfo.loss_train0, tinfo.loss_train],
+                         "loss_test": [tinfo.loss_test0, tinfo.loss_test]},
+            "e2e": {"value": float(np.mean(te)), "unit": "s/solve", "h2d_bytes_per_step": 3 * N * 8 * len(systems),
+                    "d2h_bytes_per_step": N * 8 * len(systems)},
+            "gpu_launches": launches,
+            "roofline": {"bound": "alu", "kernel": "learned apply (k_conv graph)", "achieved": conv_flops / t_apply / 1e12,
+                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": conv_flops / t_apply / 1e12 / fp32_peak,
+                         "traffic": None, "apply_us": t_apply * 1e6},
+            "cpu_baseline": cpu, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    dgx.dgx_destroy(ctx)
+    return 0
+
+
 def run_ensemble(args):
     """16 members (meshes 32^3 .. 96x96x48, degrees 3 + i mod 3, seeded hill
     heights 200-800 m and widths 0.5-2 km, 60 x 60 x 20 km, periodic lateral
@@ -332,6 +501,8 @@ def main():
         return run_reference(args, work)
     if args.workload == "ensemble":
         return run_ensemble(args)
+    if args.workload == "learned":
+        return run_learned(args)
 
     import torch
     from paper_2505_00384_gb300 import dgx

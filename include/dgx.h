@@ -50,6 +50,12 @@ extern "C" {
 #define DGX_PC_NONE 0
 #define DGX_PC_HELMHOLTZ 1       /* inverse diagonal of S~ (Helmholtz preconditioner)        */
 #define DGX_PC_INTERNAL_ENERGY 2 /* inverse diagonal of D (internal-energy preconditioner)  */
+#define DGX_PC_LEARNED 3         /* Helmholtz Jacobi guess plus a learned correction
+                                    (dgx_learned_*); DGX_SOLVER_FGMRES only.  The FP64
+                                    residual judges it: a cycle that does not halve the
+                                    residual, or a non-finite direction, switches the
+                                    rest of the solve to DGX_PC_HELMHOLTZ and the call
+                                    returns DGX_FALLBACK_USED                           */
 
 /* Krylov methods (Sec. 3.1: GMRES for the non-symmetric Schur system, CG
  * for the symmetric positive definite case). */
@@ -102,16 +108,17 @@ typedef struct {
   int inner_maxit;   /* DGX_SOLVER_MIXED: FP32 iterations per outer iteration            */
   double inner_tol;  /* DGX_SOLVER_MIXED: relative tolerance of the FP32 inner solve      */
   int use_x0;        /* 1: x holds the initial guess; 0: start from zero                  */
-  int reserved;
+  int learned_per_cycle; /* DGX_PC_LEARNED: directions per FGMRES cycle that use the network
+                            (the first ones; the rest use the Helmholtz Jacobi); 0 = all      */
 } dgx_solve_opts;
 
 typedef struct {
-  int status;          /* DGX_OK or DGX_NOT_CONVERGED                                    */
+  int status;          /* DGX_OK, DGX_NOT_CONVERGED or DGX_FALLBACK_USED                  */
   int iterations;      /* outer (FP64) Krylov iterations                                 */
   int inner_iterations;/* FP32 iterations (DGX_SOLVER_MIXED)                             */
   int operator_f64;    /* FP64 operator applications                                     */
   int operator_f32;    /* FP32 operator applications                                     */
-  int reserved;
+  int fallback;        /* DGX_PC_LEARNED: 1 if the solve switched to the Helmholtz Jacobi */
   double relres;       /* final true relative residual in FP64                            */
   double seconds;      /* wall time of the call                                          */
 } dgx_solve_info;
@@ -216,6 +223,88 @@ typedef struct {
  * the context. */
 int dgx_imex_step(dgx_ctx *ctx, double *rho, double *u, double *p, int nsteps, const dgx_solve_opts *opts,
                   dgx_step_info *info);
+
+/* Recorder of the pressure systems dgx_imex_step solves.  From this call on,
+ * every `stride`-th solve (the stride-th, 2 stride-th, ...; counting all
+ * stages and fixed-point iterations) appends one record of 4 N + 2 doubles to
+ * `store` (device, caller-owned, capacity records): rho^(l), p_k (the
+ * coefficients of dgx_set_coefficients), the right-hand side b, the solution
+ * x (p' of Sec. 2 after the solve), then a~_ll dt and gamma.  Recording stops
+ * when `capacity` records are written; store = NULL or capacity = 0 turns it
+ * off.  dgx_imex_recorded gives the number written so far. */
+int dgx_imex_record(dgx_ctx *ctx, double *store, int capacity, int stride);
+int dgx_imex_recorded(const dgx_ctx *ctx);
+
+/* ------------------------------------------------------- learned preconditioner
+ * The paper preconditions the Schur system with a Jacobi diagonal (Sec. 3.1);
+ * this extension adds a learned correction that flexible GMRES accepts as a
+ * variable preconditioner:  z = M(v) = j + s c,  j = D_H^-1 v (the Helmholtz
+ * Jacobi guess of the current coefficients), s = sqrt(mean(j^2)), and c the
+ * output of a network of `layers` 3x3x3 convolutions (zero padding, ReLU
+ * between layers, `channels` hidden channels) applied to the cell-DoF tensor:
+ * the N nodal values laid out as a grid of (nz n) x (ny n) x (nx n) points,
+ * n = r+1, each cell's n^3 nodes in their own block (grid index
+ * gx + X (gy + Y gz), X = nx n, Y = ny n).  Input channels, per grid point:
+ *   0  j / s                         1  log(d_i / mean(d)), d the Helmholtz diagonal
+ *   2  p_k / mean(p_k) - 1           3  rho / mean(rho) - 1
+ *   4  h(x, y) / Lz (terrain height at the node's column)
+ * Weights are stored in bfloat16 (FP32 master copies for training), biases
+ * in FP32; every convolution accumulates in FP32.  Parameter vector layout
+ * (FP32): for each layer, W[co][ci][kz][ky][kx] then b[co].
+ * Training pairs (v, e) with S e = v are stored in normalised form: the five
+ * channels and the target t = e / s; the loss of a batch of B pairs is
+ *   L = (1/B) sum_b || ch0_b + c_b - t_b ||^2 / || t_b ||^2
+ * (equal to ||M(v) - e||^2 / ||e||^2 per pair), minimised by Adam.  The
+ * network and the samples survive dgx_mesh_build while the grid extents
+ * X, Y, Z stay the same (another terrain, say); other extents drop the
+ * samples.  All arrays device unless stated. */
+typedef struct {
+  int epochs;              /* passes over the training samples                     */
+  int batch;               /* pairs per Adam step (1..256)                          */
+  double lr, lr_final;     /* learning rate, cosine-decayed from lr to lr_final    */
+  double beta1, beta2, eps;/* Adam                                                 */
+  unsigned long long seed; /* shuffling of the training samples                    */
+  int shuffle;             /* 0: samples in insertion order                        */
+  int reserved;
+} dgx_train_opts;
+
+typedef struct {
+  int steps;               /* Adam steps taken                                     */
+  int train_samples, test_samples, reserved;
+  double loss_train0, loss_test0; /* before training (mean over the samples)       */
+  double loss_train, loss_test;   /* after training                                */
+  double seconds;
+} dgx_train_info;
+
+/* Create (or replace) the network: 2 <= layers <= 16, channels a multiple of
+ * 8 in 8..64; He-normal weights from `seed` (splitmix64 + Box-Muller), the
+ * last layer zero so that M starts as the Jacobi preconditioner. */
+int dgx_learned_create(dgx_ctx *ctx, int layers, int channels, unsigned long long seed);
+long long dgx_learned_num_params(const dgx_ctx *ctx);
+/* FP32 parameter vector (host), layout above; set rounds weights to bfloat16
+ * for use and keeps the FP32 values as master copies; resets Adam. */
+int dgx_learned_get_params(dgx_ctx *ctx, float *host_params);
+int dgx_learned_set_params(dgx_ctx *ctx, const float *host_params);
+/* z = M(v) for the current coefficients (prec DGX_F64 or DGX_F32). */
+int dgx_learned_apply(dgx_ctx *ctx, int prec, const void *v, void *z);
+/* Add training pairs from one pressure system: sets the coefficients
+ * (as dgx_set_coefficients), stores (b, x) and then, from restarted FGMRES
+ * cycles of `stride` Jacobi iterations from x = 0, the pairs (r_k, x - x_k)
+ * (residual and error of the k-th cycle) while ||r_k|| >= 1e-6 ||b||, up to
+ * `pairs` pairs in all.  x must solve S x = b to ~1e-10.  test != 0 keeps the
+ * pairs out of training (held out for dgx_train_info.loss_test). */
+int dgx_learned_add_system(dgx_ctx *ctx, const double *rho, const double *pk, double a_dt, double gamma,
+                           const double *b, const double *x, int pairs, int stride, int test);
+int dgx_learned_num_samples(const dgx_ctx *ctx, int *train, int *test);
+/* Sample i (insertion order) as 6 G floats (host): channels 0..4 then t. */
+int dgx_learned_sample(dgx_ctx *ctx, int i, float *host_out);
+int dgx_learned_clear_samples(dgx_ctx *ctx);
+/* Mean loss over samples first..first+count-1 (one batch, count <= 256) and
+ * its gradient w.r.t. the parameter vector (host FP32, may be NULL); no update. */
+int dgx_learned_loss(dgx_ctx *ctx, int first, int count, double *loss, float *grad_host);
+/* Train on the non-test samples with Adam; fills info (may be NULL). */
+int dgx_learned_train(dgx_ctx *ctx, const dgx_train_opts *opts, dgx_train_info *info);
+void dgx_default_train_opts(dgx_train_opts *opts);
 
 /* Allocation-free variant of dgx_apply_operator.  The paper has no
  * counterpart: this serves callers that cannot allocate device memory when

@@ -119,3 +119,54 @@ def bf16_round(a):
     rnd = ((u >> 16) & 1) + 0x7FFF
     u = ((u + rnd) >> 16) << 16
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def features(v, d, rho, pk, h_over_H, perm, shape):
+    """Input channels (5, Z, Y, X) of the network and the scale s for the
+    vector v: j = v / d (Helmholtz Jacobi guess), s = rms(j) (1 if j = 0);
+    channels j / s, log(d / mean d), p_k / mean p_k - 1, rho / mean rho - 1,
+    and the terrain height over the domain height."""
+    v, d = np.asarray(v, float), np.asarray(d, float)
+    j = v / d
+    s = float(np.sqrt(np.mean(j * j)))
+    s = s if s > 0.0 else 1.0
+    chans = [j / s, np.log(d / d.mean()), pk / np.mean(pk) - 1.0, rho / np.mean(rho) - 1.0,
+             np.asarray(h_over_H, float)]
+    return np.stack([to_grid(c, shape, perm) for c in chans]), s
+
+
+def apply_preconditioner(params, v, d, rho, pk, h_over_H, perm, shape):
+    """z = D^-1 v + s c(features(v)) in DoF order."""
+    f, s = features(v, d, rho, pk, h_over_H, perm, shape)
+    c, _ = forward(params, f)
+    return np.asarray(v, float) / d + s * to_dof(c[0], perm)
+
+
+def adam_step(theta, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015, Algorithm 1) at step t >= 1; returns
+    the new (theta, m, v)."""
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    mh = m / (1.0 - b1 ** t)
+    vh = v / (1.0 - b2 ** t)
+    return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def unpack(p, layers, channels, cin=5):
+    """Split a flat parameter vector (per layer W[co][ci][3][3][3] then b[co])
+    into [(W, b)]."""
+    out, o = [], 0
+    for l in range(layers):
+        ci = cin if l == 0 else channels
+        co = 1 if l == layers - 1 else channels
+        W = np.asarray(p[o:o + co * ci * 27], float).reshape(co, ci, 3, 3, 3)
+        o += co * ci * 27
+        b = np.asarray(p[o:o + co], float)
+        o += co
+        out.append((W, b))
+    assert o == len(p)
+    return out
+
+
+def pack(params):
+    return np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in params])

@@ -323,6 +323,9 @@ void free_mesh(dgx_ctx *c) {
   c->kry32 = nullptr;
   c->kry64_elems = c->kry32_elems = 0;
   c->has_mesh = c->has_coef = c->has_bg = false;
+  c->rec_store = nullptr;
+  c->rec_cap = c->rec_count = c->rec_seen = 0;
+  learned_mesh_changed(c);
 }
 
 template <typename T>
@@ -529,8 +532,12 @@ int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dg
     if (int e = grow<float>(c, (size_t)(mi + 4) * N)) return e;
   }
   double *Vb = c->kry64, *Zb = Vb + (size_t)(m + 1) * N, *w = Zb + (size_t)m * N;
-  const double *dinv = o.pc == DGX_PC_NONE ? nullptr : c->dinv64[o.pc];
-  const float *dinv32 = o.pc == DGX_PC_NONE ? nullptr : c->dinv32[o.pc];
+  // the learned preconditioner falls back to the Helmholtz Jacobi diagonal
+  const int pcd = o.pc == DGX_PC_LEARNED ? DGX_PC_HELMHOLTZ : o.pc;
+  const double *dinv = o.pc == DGX_PC_NONE ? nullptr : c->dinv64[pcd];
+  const float *dinv32 = o.pc == DGX_PC_NONE ? nullptr : c->dinv32[pcd];
+  bool use_learned = o.pc == DGX_PC_LEARNED;
+  double prev_beta = INFINITY;
   // FP32 right-hand side / solution of the inner solve, after the inner basis (V, w, u)
   float *io32 = mixed ? c->kry32 + (size_t)(std::max(1, std::min(o.inner_maxit, 64)) + 3) * N : nullptr;
   if (mixed && !dinv32) return set_error(c, DGX_ERR_ARG, "mixed solver needs a Jacobi preconditioner");
@@ -556,9 +563,16 @@ int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dg
     info.relres = beta / bn;
     if (std::isnan(beta)) return set_error(c, DGX_ERR_BREAKDOWN, "NaN residual");
     if (info.relres <= o.tol) {
-      info.status = DGX_OK;
+      info.status = info.fallback ? DGX_FALLBACK_USED : DGX_OK;
       break;
     }
+    // the FP64 residual judges the learned preconditioner: a cycle that did
+    // not at least halve it hands the solve to the Jacobi preconditioner
+    if (use_learned && !(beta < 0.5 * prev_beta)) {
+      use_learned = false;
+      info.fallback = 1;
+    }
+    prev_beta = beta;
     if (its >= o.maxit) {
       info.status = DGX_NOT_CONVERGED;
       break;
@@ -567,9 +581,14 @@ int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dg
     std::fill(H.g.begin(), H.g.end(), 0.0);
     H.g[0] = beta;
     int jj = 0;
+    bool failed = false;  // learned cycle produced a non-finite direction
     for (int j = 0; j < m; ++j) {
       double *vj = Vb + (size_t)j * N, *zj = Zb + (size_t)j * N;
-      if (mixed) {
+      if (use_learned && (o.learned_per_cycle <= 0 || j < o.learned_per_cycle)) {
+        if ((err = learned_apply<double>(c, vj, zj))) return err;
+      } else if (use_learned) {
+        vec_mul<double>(N, dinv, vj, zj, c->stream);
+      } else if (mixed) {
         // z_j ~= S^-1 v_j by FP32 GMRES on the FP32 operator and diagonal
         vec_convert<float, double>(N, vj, io32, c->stream);
         int iits = 0;
@@ -586,6 +605,11 @@ int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dg
       ++info.operator_f64;
       const double hn = arnoldi<double>(c, N, j, Vb, w, H, &err);
       if (err) return err;
+      if (use_learned && !std::isfinite(hn)) {
+        failed = true;
+        ++its;
+        break;
+      }
       if (std::isnan(hn)) return set_error(c, DGX_ERR_BREAKDOWN, "NaN in Arnoldi");
       const double res = H.add_column(j);
       ++its;
@@ -594,7 +618,20 @@ int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dg
       vec_scale_by_inv_sqrt<double>(N, c->red_out + 128, w, Vb + (size_t)(j + 1) * N, c->stream);
       if (res <= o.tol * bn || its >= o.maxit) break;
     }
-    H.solve(jj);
+    if (!failed) {
+      H.solve(jj);
+      for (int k = 0; k < jj; ++k)
+        if (!std::isfinite(H.y[k])) failed = use_learned;
+    }
+    if (failed) {  // discard the cycle, restart from the same x with Jacobi
+      use_learned = false;
+      info.fallback = 1;
+      if (its >= o.maxit) {
+        info.status = DGX_NOT_CONVERGED;
+        break;
+      }
+      continue;
+    }
     for (int k = 0; k < jj; ++k)
       if (std::isnan(H.y[k])) return set_error(c, DGX_ERR_BREAKDOWN, "NaN in least-squares solution");
     if ((err = check_cuda(c, cudaMemcpyAsync(c->red_out + 192, H.y.data(), jj * sizeof(double),
@@ -664,6 +701,24 @@ int cg64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dgx_so
 }
 
 }  // namespace
+
+void node_terrain_heights(const dgx_ctx *c, std::vector<double> &h) {
+  const int n = c->n;
+  std::vector<double> x, w;
+  gll_rule(n, x, w);
+  const dgx_mesh_desc &m = c->mesh;
+  const double dx = m.Lx / m.nx, dy = m.Ly / m.ny;
+  const long long n3 = (long long)n * n * n;
+  h.assign((size_t)c->N, 0.0);
+  for (long long i = 0; i < c->N; ++i) {
+    const long long cell = i / n3;
+    const int node = (int)(i % n3);
+    const int a = node % n, b = (node / n) % n;
+    const long long cx = cell % m.nx, cy = (cell / m.nx) % m.ny;
+    h[(size_t)i] = terrain_h(m, (cx + x[a]) * dx, (cy + x[b]) * dy);
+  }
+}
+
 }  // namespace dgx
 
 using namespace dgx;
@@ -692,6 +747,7 @@ void dgx_destroy(dgx_ctx *c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   free_mesh(c);
+  learned_free(c);
   if (c->red) cudaFree(c->red);
   if (c->red_out) cudaFree(c->red_out);
   if (c->host_red) cudaFreeHost(c->host_red);
@@ -876,6 +932,7 @@ int dgx_set_coefficients(dgx_ctx *c, const double *rho, const double *pk, double
   vec_convert<float, double>(N, pk, c->pk32, c->stream);
   c->alpha = a_dt;
   c->gamma = gamma;
+  ++c->coef_version;
   if (int e = launch_diag(c, c->rho64, c->pk64, c->diag64[DGX_PC_HELMHOLTZ], c->diag64[DGX_PC_INTERNAL_ENERGY],
                           c->stream))
     return e;
@@ -920,7 +977,8 @@ int dgx_apply_mass_inverse(dgx_ctx *c, int prec, const void *in, void *out) {
 int dgx_apply_preconditioner(dgx_ctx *c, int pc, int prec, const void *x, void *y) {
   if (int e = check_ready(c, true)) return e;
   if (!x || !y) return set_error(c, DGX_ERR_ARG, "null array");
-  if (pc < 0 || pc > 2) return set_error(c, DGX_ERR_ARG, "preconditioner %d", pc);
+  if (pc < 0 || pc > 3) return set_error(c, DGX_ERR_ARG, "preconditioner %d", pc);
+  if (pc == DGX_PC_LEARNED) return dgx_learned_apply(c, prec, x, y);
   const long long N = c->N;
   if (prec == DGX_F64) {
     if (pc == DGX_PC_NONE) cudaMemcpyAsync(y, x, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
@@ -948,7 +1006,9 @@ int dgx_solve_pressure(dgx_ctx *c, const double *b, double *x, const dgx_solve_o
   dgx_solve_opts o;
   if (opts) o = *opts;
   else dgx_default_solve_opts(&o);
-  if (o.pc < 0 || o.pc > 2) return set_error(c, DGX_ERR_ARG, "preconditioner %d", o.pc);
+  if (o.pc < 0 || o.pc > 3) return set_error(c, DGX_ERR_ARG, "preconditioner %d", o.pc);
+  if (o.pc == DGX_PC_LEARNED && (o.method != DGX_SOLVER_FGMRES || !learned_ready(c)))
+    return set_error(c, DGX_ERR_ARG, "the learned preconditioner needs DGX_SOLVER_FGMRES and dgx_learned_create");
   if (o.restart < 1 || o.restart > 64 || o.maxit < 0 || !(o.tol > 0))
     return set_error(c, DGX_ERR_ARG, "need 1 <= restart <= 64, maxit >= 0, tol > 0");
   if (o.method == DGX_SOLVER_MIXED && (o.inner_maxit < 1 || o.inner_maxit > 64 || !(o.inner_tol > 0)))

@@ -115,6 +115,8 @@ struct Buf {
   size_t bytes = 0;
 };
 
+struct Learned;  // learned preconditioner state (dgx_learned.cu)
+
 }  // namespace dgx
 
 struct dgx_ctx {
@@ -167,6 +169,14 @@ struct dgx_ctx {
   double imex_A[16] = {}, imex_At[16] = {}, imex_dt = 0.0;
   double *imex_ws = nullptr;
   size_t imex_ws_elems = 0;
+
+  // recorder of the pressure systems solved inside dgx_imex_step
+  double *rec_store = nullptr;
+  int rec_cap = 0, rec_stride = 1, rec_count = 0, rec_seen = 0;
+
+  // incremented by every dgx_set_coefficients (invalidates derived caches)
+  long long coef_version = 0;
+  dgx::Learned *learned = nullptr;
 
   std::vector<void *> owned;  // everything cudaMalloc'd for the mesh
 };
@@ -235,5 +245,15 @@ void vec_lincomb(long long n, int nv, const T *Z, long long ld, const double *c_
 template <typename T>
 void vec_dot(long long n, const T *a, const T *b, double *partial, double *out, cudaStream_t s);
 int vec_partials();  // number of reduction blocks per vector pass
+
+// learned preconditioner (dgx_learned.cu)
+void learned_free(dgx_ctx *c);          // release everything (dgx_destroy)
+void learned_mesh_changed(dgx_ctx *c);  // drop mesh-dependent buffers and samples (keeps the weights)
+bool learned_ready(const dgx_ctx *c);
+// z = M(v): Helmholtz Jacobi guess plus the network's correction, current coefficients
+template <typename T>
+int learned_apply(dgx_ctx *c, const T *v, T *z);
+// host: terrain height h(x, y) at every DoF of the mesh (dgx_api.cu)
+void node_terrain_heights(const dgx_ctx *c, std::vector<double> &h);
 
 }  // namespace dgx

@@ -201,6 +201,18 @@ int dgx_imex_step(dgx_ctx *c, double *rho, double *u, double *p, int nsteps, con
           solve_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - ts).count();
           if (rc < 0) return rc;
           if (rc == DGX_NOT_CONVERGED) inf.status = DGX_NOT_CONVERGED;
+          if (c->rec_store && c->rec_count < c->rec_cap && (++c->rec_seen % c->rec_stride) == 0) {
+            double *r = c->rec_store + (size_t)c->rec_count * (4 * N + 2);
+            const double sc[2] = {al, gm};
+            cudaMemcpyAsync(r, c->rho64, b1, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(r + N, c->pk64, b1, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(r + 2 * N, w.rhs, b1, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(r + 3 * N, w.x, b1, cudaMemcpyDeviceToDevice, st);
+            if ((e = check_cuda(c, cudaMemcpyAsync(r + 4 * N, sc, sizeof(sc), cudaMemcpyHostToDevice, st), "record")))
+              return e;
+            if ((e = check_cuda(c, cudaStreamSynchronize(st), "record"))) return e;
+            ++c->rec_count;
+          }
           inf.solves += 1;
           inf.krylov_iterations += si.iterations;
           inf.inner_iterations += si.inner_iterations;
@@ -236,5 +248,18 @@ int dgx_imex_step(dgx_ctx *c, double *rho, double *u, double *p, int nsteps, con
   if (info) *info = inf;
   return inf.status;
 }
+
+int dgx_imex_record(dgx_ctx *c, double *store, int capacity, int stride) {
+  if (!c) return DGX_ERR_ARG;
+  if (capacity < 0 || stride < 1) return set_error(c, DGX_ERR_ARG, "need capacity >= 0 and stride >= 1");
+  c->rec_store = capacity > 0 ? store : nullptr;
+  c->rec_cap = c->rec_store ? capacity : 0;
+  c->rec_stride = stride;
+  c->rec_count = 0;
+  c->rec_seen = 0;
+  return DGX_OK;
+}
+
+int dgx_imex_recorded(const dgx_ctx *c) { return c ? c->rec_count : -1; }
 
 }  // extern "C"

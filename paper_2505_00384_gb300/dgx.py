@@ -22,7 +22,7 @@ DGX_ERR_DEVICE_TIMEOUT = -5
 DGX_ERR_STATE = -6
 
 DGX_F64, DGX_F32 = 0, 1
-DGX_PC_NONE, DGX_PC_HELMHOLTZ, DGX_PC_INTERNAL_ENERGY = 0, 1, 2
+DGX_PC_NONE, DGX_PC_HELMHOLTZ, DGX_PC_INTERNAL_ENERGY, DGX_PC_LEARNED = 0, 1, 2, 3
 DGX_SOLVER_FGMRES, DGX_SOLVER_CG, DGX_SOLVER_MIXED = 0, 1, 2
 
 
@@ -42,7 +42,7 @@ class dgx_background(C.Structure):
 class dgx_solve_opts(C.Structure):
     _fields_ = [("method", C.c_int), ("pc", C.c_int), ("restart", C.c_int), ("maxit", C.c_int),
                 ("tol", C.c_double), ("inner_restart", C.c_int), ("inner_maxit", C.c_int),
-                ("inner_tol", C.c_double), ("use_x0", C.c_int), ("reserved", C.c_int)]
+                ("inner_tol", C.c_double), ("use_x0", C.c_int), ("learned_per_cycle", C.c_int)]
 
 
 class dgx_step_info(C.Structure):
@@ -54,8 +54,20 @@ class dgx_step_info(C.Structure):
 
 class dgx_solve_info(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("inner_iterations", C.c_int),
-                ("operator_f64", C.c_int), ("operator_f32", C.c_int), ("reserved", C.c_int),
+                ("operator_f64", C.c_int), ("operator_f32", C.c_int), ("fallback", C.c_int),
                 ("relres", C.c_double), ("seconds", C.c_double)]
+
+
+class dgx_train_opts(C.Structure):
+    _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_double), ("lr_final", C.c_double),
+                ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double), ("seed", C.c_ulonglong),
+                ("shuffle", C.c_int), ("reserved", C.c_int)]
+
+
+class dgx_train_info(C.Structure):
+    _fields_ = [("steps", C.c_int), ("train_samples", C.c_int), ("test_samples", C.c_int), ("reserved", C.c_int),
+                ("loss_train0", C.c_double), ("loss_test0", C.c_double), ("loss_train", C.c_double),
+                ("loss_test", C.c_double), ("seconds", C.c_double)]
 
 
 # (name, restype, argtypes) of every entry point declared in include/dgx.h
@@ -98,6 +110,20 @@ SIGNATURES = [
     ("dgx_ensemble_tuning", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                       C.POINTER(C.c_int)]),
     ("dgx_ensemble_solve", C.c_int, [_P, _P, _P, C.POINTER(dgx_solve_opts), C.POINTER(dgx_solve_info)]),
+    ("dgx_imex_record", C.c_int, [_P, _P, C.c_int, C.c_int]),
+    ("dgx_imex_recorded", C.c_int, [_P]),
+    ("dgx_learned_create", C.c_int, [_P, C.c_int, C.c_int, C.c_ulonglong]),
+    ("dgx_learned_num_params", C.c_longlong, [_P]),
+    ("dgx_learned_get_params", C.c_int, [_P, _P]),
+    ("dgx_learned_set_params", C.c_int, [_P, _P]),
+    ("dgx_learned_apply", C.c_int, [_P, C.c_int, _P, _P]),
+    ("dgx_learned_add_system", C.c_int, [_P, _P, _P, C.c_double, C.c_double, _P, _P, C.c_int, C.c_int, C.c_int]),
+    ("dgx_learned_num_samples", C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    ("dgx_learned_sample", C.c_int, [_P, C.c_int, _P]),
+    ("dgx_learned_clear_samples", C.c_int, [_P]),
+    ("dgx_learned_loss", C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_double), _P]),
+    ("dgx_learned_train", C.c_int, [_P, C.POINTER(dgx_train_opts), C.POINTER(dgx_train_info)]),
+    ("dgx_default_train_opts", None, [C.POINTER(dgx_train_opts)]),
 ]
 
 _lib = None
@@ -212,7 +238,7 @@ def dgx_solve_pressure(ctx, b_ptr, x_ptr, opts=None):
     o = opts if opts is not None else dgx_default_solve_opts()
     info = dgx_solve_info()
     rc = load().dgx_solve_pressure(ctx, C.c_void_p(b_ptr), C.c_void_p(x_ptr), C.byref(o), C.byref(info))
-    _check(ctx, rc, allow=(DGX_OK, DGX_NOT_CONVERGED))
+    _check(ctx, rc, allow=(DGX_OK, DGX_NOT_CONVERGED, DGX_FALLBACK_USED))
     return rc, info
 
 
@@ -263,6 +289,95 @@ def dgx_imex_step(ctx, rho_ptr, u_ptr, p_ptr, nsteps=1, opts=None):
                               C.byref(o), C.byref(info))
     _check(ctx, rc, allow=(DGX_OK, DGX_NOT_CONVERGED))
     return rc, info
+
+
+def dgx_imex_record(ctx, store_ptr, capacity, stride=1):
+    """Record every stride-th pressure system of dgx_imex_step into a device
+    buffer of capacity x (4 N + 2) float64: rho, p_k, b, x, a_dt, gamma."""
+    return _check(ctx, load().dgx_imex_record(ctx, C.c_void_p(store_ptr), int(capacity), int(stride)))
+
+
+def dgx_imex_recorded(ctx):
+    return load().dgx_imex_recorded(ctx)
+
+
+# ---------------------------------------------------------------- learned preconditioner
+DGX_LEARNED_CHANNELS = 5  # input channels; a stored sample holds these plus the target
+
+
+def dgx_learned_create(ctx, layers, channels, seed=20250501):
+    return _check(ctx, load().dgx_learned_create(ctx, int(layers), int(channels), C.c_ulonglong(seed)))
+
+
+def dgx_learned_num_params(ctx):
+    return load().dgx_learned_num_params(ctx)
+
+
+def dgx_learned_get_params(ctx):
+    """FP32 master parameters as a numpy array (host)."""
+    import numpy as np
+    out = np.empty(dgx_learned_num_params(ctx), dtype=np.float32)
+    _check(ctx, load().dgx_learned_get_params(ctx, out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def dgx_learned_set_params(ctx, params):
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.size != dgx_learned_num_params(ctx):
+        raise ValueError("expected %d parameters, got %d" % (dgx_learned_num_params(ctx), p.size))
+    return _check(ctx, load().dgx_learned_set_params(ctx, p.ctypes.data_as(C.c_void_p)))
+
+
+def dgx_learned_apply(ctx, prec, v_ptr, z_ptr):
+    return _check(ctx, load().dgx_learned_apply(ctx, prec, C.c_void_p(v_ptr), C.c_void_p(z_ptr)))
+
+
+def dgx_learned_add_system(ctx, rho_ptr, pk_ptr, a_dt, gamma, b_ptr, x_ptr, pairs=1, stride=4, test=False):
+    return _check(ctx, load().dgx_learned_add_system(ctx, C.c_void_p(rho_ptr), C.c_void_p(pk_ptr), float(a_dt),
+                                                     float(gamma), C.c_void_p(b_ptr), C.c_void_p(x_ptr), int(pairs),
+                                                     int(stride), int(bool(test))))
+
+
+def dgx_learned_num_samples(ctx):
+    tr, te = C.c_int(), C.c_int()
+    _check(ctx, load().dgx_learned_num_samples(ctx, C.byref(tr), C.byref(te)))
+    return tr.value, te.value
+
+
+def dgx_learned_sample(ctx, i, grid_points):
+    """Sample i as a (6, G) float32 numpy array: channels 0..4, then the target."""
+    import numpy as np
+    out = np.empty((DGX_LEARNED_CHANNELS + 1, grid_points), dtype=np.float32)
+    _check(ctx, load().dgx_learned_sample(ctx, int(i), out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def dgx_learned_clear_samples(ctx):
+    return _check(ctx, load().dgx_learned_clear_samples(ctx))
+
+
+def dgx_learned_loss(ctx, first, count, want_grad=True):
+    """(mean loss, gradient as float32 numpy array or None) over samples first..first+count-1."""
+    import numpy as np
+    loss = C.c_double()
+    g = np.empty(dgx_learned_num_params(ctx), dtype=np.float32) if want_grad else None
+    _check(ctx, load().dgx_learned_loss(ctx, int(first), int(count), C.byref(loss),
+                                        g.ctypes.data_as(C.c_void_p) if g is not None else None))
+    return loss.value, g
+
+
+def dgx_default_train_opts():
+    o = dgx_train_opts()
+    load().dgx_default_train_opts(C.byref(o))
+    return o
+
+
+def dgx_learned_train(ctx, opts=None):
+    o = opts if opts is not None else dgx_default_train_opts()
+    info = dgx_train_info()
+    _check(ctx, load().dgx_learned_train(ctx, C.byref(o), C.byref(info)))
+    return info
 
 
 def _echeck(e, rc, allow=(DGX_OK,)):

@@ -44,3 +44,6 @@ def test_structs_match_header_layout():
     assert ctypes.sizeof(dgx.dgx_background) == 2 * 4 + 7 * 8
     assert ctypes.sizeof(dgx.dgx_solve_opts) == 4 * 4 + 8 + 2 * 4 + 8 + 2 * 4
     assert ctypes.sizeof(dgx.dgx_solve_info) == 6 * 4 + 2 * 8
+    # 2 ints, 5 doubles, one 64-bit seed, 2 ints; 4 ints then 5 doubles
+    assert ctypes.sizeof(dgx.dgx_train_opts) == 2 * 4 + 5 * 8 + 8 + 2 * 4
+    assert ctypes.sizeof(dgx.dgx_train_info) == 4 * 4 + 5 * 8

@@ -107,3 +107,42 @@ def test_bf16_rounding():
     r = NL.bf16_round(a)
     assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.015625 and r[3] == 1.0
     assert np.all(np.abs(r - a) <= np.abs(a) * 2 ** -8)
+
+
+def test_features_normalisation():
+    """Channel 0 has unit rms and is invariant to positive scaling of v;
+    uniform coefficients give zero coefficient channels."""
+    rng = np.random.default_rng(5)
+    perm = NL.dof_to_grid_index(2, 2, 1, 1)
+    shape = (2, 4, 4)
+    n = perm.size
+    v = rng.standard_normal(n)
+    d = rng.uniform(1.0, 3.0, n)
+    f, s = NL.features(v, d, np.full(n, 1.2), np.full(n, 9e4), np.zeros(n), perm, shape)
+    assert abs(np.sqrt(np.mean(f[0] ** 2)) - 1.0) < 1e-14
+    assert np.all(f[2] == 0) and np.all(f[3] == 0)
+    f2, s2 = NL.features(7.5 * v, d, np.full(n, 1.2), np.full(n, 9e4), np.zeros(n), perm, shape)
+    assert np.allclose(f2[0], f[0], rtol=1e-14, atol=1e-14) and abs(s2 / s - 7.5) < 1e-13
+    # a zero network gives the Jacobi preconditioner
+    params = [(np.zeros((4, 5, 3, 3, 3)), np.zeros(4)), (np.zeros((1, 4, 3, 3, 3)), np.zeros(1))]
+    z = NL.apply_preconditioner(params, v, d, np.full(n, 1.2), np.full(n, 9e4), np.zeros(n), perm, shape)
+    assert np.allclose(z, v / d, rtol=1e-15, atol=0)
+
+
+def test_adam_closed_form():
+    """First Adam step: m_hat = g, v_hat = g^2, so theta moves by
+    -lr g / (|g| + eps); repeating the same gradient keeps that step."""
+    g = np.array([0.3, -2.0, 1e-3, 0.0])
+    th = np.array([1.0, 1.0, 1.0, 1.0])
+    t1, m, v = NL.adam_step(th, g, np.zeros(4), np.zeros(4), 1, lr=0.01)
+    assert np.allclose(t1 - th, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
+    t2, m, v = NL.adam_step(t1, g, m, v, 2, lr=0.01)
+    assert np.allclose(t2 - t1, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
+
+
+def test_pack_roundtrip():
+    rng = np.random.default_rng(6)
+    p = rng.standard_normal(5 * 8 * 27 + 8 + 8 * 8 * 27 + 8 + 8 * 27 + 1)
+    params = NL.unpack(p, 3, 8)
+    assert [W.shape for W, _ in params] == [(8, 5, 3, 3, 3), (8, 8, 3, 3, 3), (1, 8, 3, 3, 3)]
+    assert np.array_equal(NL.pack(params), p)
