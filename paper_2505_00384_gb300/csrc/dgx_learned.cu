@@ -32,7 +32,6 @@ constexpr int kCin = 5;                        // input channels
 constexpr int kTile = 4;                       // output tile edge
 constexpr int kHalo = kTile + 2;               // staged input tile edge
 constexpr int kHalo3 = kHalo * kHalo * kHalo;  // 216
-constexpr int kKS = 8;                         // input-channel splits of the forward kernel
 constexpr int kMaxBatch = 256;
 constexpr int kRedBlocks = 128;  // partial sums of the feature reductions
 
@@ -99,16 +98,16 @@ struct ConvArgs {
   long long mask_bs;
 };
 
-// y[co][p] = b[co] + sum_ci sum_k W[co][ci][k] x[ci][p + k - 1].  128 threads:
-// 16 rows of 4 points along x (a 4x4x4 tile) x kKS input-channel groups; each
-// thread keeps 4 points x COB output channels in registers and reuses the 6
-// staged inputs of its row for the three x taps.
-template <int COB>
-__global__ void __launch_bounds__(128) k_conv(ConvArgs a) {
+// y[co][p] = b[co] + sum_ci sum_k W[co][ci][k] x[ci][p + k - 1].  16 KS
+// threads: 16 rows of 4 points along x (a 4x4x4 tile) x KS input-channel
+// groups; each thread keeps 4 points x COB output channels in registers and
+// reuses the 6 staged inputs of its row for the three x taps.
+template <int COB, int KS>
+__global__ void __launch_bounds__(16 * KS) k_conv(ConvArgs a) {
   extern __shared__ __align__(16) float sm[];
   float *xs = sm;                     // [Ci][216]
   float *ws = xs + a.Ci * kHalo3;     // [Ci][27][COB]
-  float *red = ws + a.Ci * 27 * COB;  // [kKS][COB][64]
+  float *red = ws + a.Ci * 27 * COB;  // [KS][COB][64]
   const Grid3 &g = a.g;
   const int tile = blockIdx.x, co0 = blockIdx.y * COB, b = blockIdx.z;
   const int tx = tile % g.tx, ty = (tile / g.tx) % g.ty, tz = tile / (g.tx * g.ty);
@@ -136,7 +135,7 @@ __global__ void __launch_bounds__(128) k_conv(ConvArgs a) {
   for (int p = 0; p < 4; ++p)
 #pragma unroll
     for (int co = 0; co < COB; ++co) acc[p][co] = 0.f;
-  for (int ci = ks; ci < a.Ci; ci += kKS) {
+  for (int ci = ks; ci < a.Ci; ci += KS) {
 #pragma unroll
     for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
@@ -179,7 +178,7 @@ __global__ void __launch_bounds__(128) k_conv(ConvArgs a) {
     if (gx >= g.X || gy >= g.Y || gz >= g.Z) continue;
     float v = 0.f;
 #pragma unroll
-    for (int k = 0; k < kKS; ++k) v += red[(k * COB + co) * 64 + pt];
+    for (int k = 0; k < KS; ++k) v += red[(k * COB + co) * 64 + pt];
     const long long gi = gx + (long long)g.X * (gy + (long long)g.Y * gz);
     if (a.bias) v += a.bias[co0 + co];
     if (a.mask && !(a.mask[b * a.mask_bs + (co0 + co) * g.G + gi] > 0.f)) v = 0.f;
@@ -661,20 +660,23 @@ int features(dgx_ctx *c, const T *v, const double *e, float *dst, float *tn2_out
   return check_cuda(c, cudaGetLastError(), "learned features");
 }
 
-size_t conv_smem(int Ci, int cob) { return (size_t)(Ci * kHalo3 + Ci * 27 * cob + kKS * cob * 64) * sizeof(float); }
+size_t conv_smem(int Ci, int cob, int ks) { return (size_t)(Ci * kHalo3 + Ci * 27 * cob + ks * cob * 64) * sizeof(float); }
 
-template <int COB>
+template <int COB, int KS>
 int launch_conv_t(dgx_ctx *c, const ConvArgs &a, int B) {
-  if (int e = prep(c, (const void *)k_conv<COB>)) return e;
+  if (int e = prep(c, (const void *)k_conv<COB, KS>)) return e;
   count_launch();
-  k_conv<COB><<<dim3(a.g.tiles(), a.Co / COB, B), 128, conv_smem(a.Ci, COB), c->stream>>>(a);
+  k_conv<COB, KS><<<dim3(a.g.tiles(), a.Co / COB, B), 16 * KS, conv_smem(a.Ci, COB, KS), c->stream>>>(a);
   return check_cuda(c, cudaGetLastError(), "k_conv");
 }
 
-// Output channels per thread: 8 (hidden layers), 1 (the output layer).
+// Hidden layers: 8 output channels x 8 channel groups per CTA when the grid
+// of CTAs fills the GPU several times over (training batches), else 4 x 16
+// (more, shorter threads for single-sample inference); output layer 1 x 16.
 int launch_conv(dgx_ctx *c, const ConvArgs &a, int B) {
-  if (a.Co % 8 == 0) return launch_conv_t<8>(c, a, B);
-  return launch_conv_t<1>(c, a, B);
+  if (a.Co % 8 == 0 && (long long)a.g.tiles() * (a.Co / 8) * B >= 4 * 152) return launch_conv_t<8, 8>(c, a, B);
+  if (a.Co % 4 == 0) return launch_conv_t<4, 16>(c, a, B);
+  return launch_conv_t<1, 16>(c, a, B);
 }
 
 int wgrad_chunks(int items, int cogroups) {
