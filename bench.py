@@ -237,6 +237,21 @@ def run_learned(args):
     layers, channels = 9, 32
     dgx.dgx_learned_create(ctx, layers, channels, inputs.DEFAULT_SEED)
     nparams = dgx.dgx_learned_num_params(ctx)
+    if args.profile:
+        # for profiler launch lists: --warmup + --steps applies of the (untrained)
+        # network on the 500 m hill box with the background as coefficients
+        N = LP.setup_hill(ctx, 500.0)
+        rho = torch.zeros(N, dtype=torch.float64, device="cuda")
+        pk = torch.zeros_like(rho)
+        dgx.dgx_background_fields(ctx, rho.data_ptr(), pk.data_ptr())
+        dgx.dgx_set_coefficients(ctx, rho.data_ptr(), pk.data_ptr(), A_LL, 1.4)
+        v = torch.from_numpy(inputs.normal(inputs.DEFAULT_SEED + 9, N)).cuda()
+        z = torch.zeros_like(v)
+        for _ in range(args.warmup + args.steps):
+            dgx.dgx_learned_apply(ctx, dgx.DGX_F64, v.data_ptr(), z.data_ptr())
+        torch.cuda.synchronize()
+        dgx.dgx_destroy(ctx)
+        return 0
     nh, steps, test_hills = 16, 25, (14, 15)
     heights = LP.hill_heights(nh)
     t0 = time.time()
