@@ -142,7 +142,26 @@ __global__ void __launch_bounds__(kT) k_seg_mdot(const long long *off, const lon
   float acc[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) acc[c] = 0.f;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  long long done = 0;
+  if constexpr (sizeof(T) == 4) {
+    // 16-byte loads when the member's segment starts on a 16-byte boundary
+    if (((o | ld) & 3) == 0) {
+      const long long n4 = n / 4;
+      const float4 *w4 = reinterpret_cast<const float4 *>(w + o);
+      for (long long i = tid; i < n4; i += stride) {
+        const float4 wi = w4[i];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          if (c < cnt) {
+            const float4 a = reinterpret_cast<const float4 *>(V + (long long)(i0 + c) * ld + o)[i];
+            acc[c] += a.x * wi.x + a.y * wi.y + a.z * wi.z + a.w * wi.w;
+          }
+      }
+      done = n4 * 4;
+    }
+  }
+  for (long long i = done + tid; i < n; i += stride) {
     const float wi = (float)w[o + i];
 #pragma unroll
     for (int c = 0; c < 8; ++c)
@@ -177,7 +196,26 @@ __global__ void __launch_bounds__(kT) k_seg_mupdate(const long long *off, const 
   __syncthreads();
   const long long o = off[m], n = len[m];
   float acc = 0.f;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  long long done = 0;
+  if (((o | ld) & 3) == 0) {  // 16-byte loads and stores
+    const long long n4 = n / 4;
+    float4 *w4 = reinterpret_cast<float4 *>(w + o);
+    for (long long i = tid; i < n4; i += stride) {
+      float4 v = w4[i];
+      for (int k = 0; k < nv; ++k) {
+        const float4 a = reinterpret_cast<const float4 *>(V + (long long)k * ld + o)[i];
+        v.x -= hs[k] * a.x;
+        v.y -= hs[k] * a.y;
+        v.z -= hs[k] * a.z;
+        v.w -= hs[k] * a.w;
+      }
+      w4[i] = v;
+      acc += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
+    }
+    done = n4 * 4;
+  }
+  for (long long i = done + tid; i < n; i += stride) {
     float v = w[o + i];
     for (int k = 0; k < nv; ++k) v -= hs[k] * V[(long long)k * ld + o + i];
     w[o + i] = v;

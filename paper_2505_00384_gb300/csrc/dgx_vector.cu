@@ -7,6 +7,7 @@
 // combination.  Reductions are deterministic: a fixed grid for a given
 // length, per-block partial sums, then a fixed-order tree over blocks.
 #include <atomic>
+#include <cstdint>
 #include <type_traits>
 
 #include "dgx_common.cuh"
@@ -70,15 +71,49 @@ __global__ void k_inv(long long n, const double *__restrict__ d, double *__restr
   }
 }
 
-// partial[blk * nv + i] = sum over this block's share of V_i . w, i in [i0, i0 + cnt)
+// 16-byte vector of T
 template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static constexpr int W = 4;
+  __device__ static float dot(const float4 &a, const float4 &b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static constexpr int W = 2;
+  __device__ static double dot(const double2 &a, const double2 &b) { return a.x * b.x + a.y * b.y; }
+};
+
+// partial[blk * nv + i] = sum over this block's share of V_i . w, i in [i0, i0 + cnt).
+// VEC: 16-byte loads (V_i and w 16-byte aligned, ld a multiple of the vector
+// width), the n % W tail by the first threads.
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(kThreads) k_mdot(long long n, int nv, int i0, int cnt, const T *__restrict__ V,
                                                    long long ld, const T *__restrict__ w, double *__restrict__ partial) {
   __shared__ double sh[32];
   T acc[kChunk];
 #pragma unroll
   for (int c = 0; c < kChunk; ++c) acc[c] = T(0);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  long long done = 0;
+  if (VEC) {
+    using V16 = Vec16<T>;
+    using VT = typename V16::type;
+    constexpr int W = V16::W;
+    const long long nw = n / W;
+    const VT *w4 = reinterpret_cast<const VT *>(w);
+    for (long long i = tid; i < nw; i += stride) {
+      const VT wi = w4[i];
+#pragma unroll
+      for (int c = 0; c < kChunk; ++c)
+        if (c < cnt) acc[c] += V16::dot(reinterpret_cast<const VT *>(V + (long long)(i0 + c) * ld)[i], wi);
+    }
+    done = nw * W;
+  }
+  for (long long i = done + tid; i < n; i += stride) {
     const T wi = w[i];
 #pragma unroll
     for (int c = 0; c < kChunk; ++c)
@@ -101,7 +136,7 @@ __global__ void __launch_bounds__(kThreads) k_reduce(int nb, int nv, const doubl
 }
 
 // w -= sum_i h[i] V_i ; partial norm^2 of the updated w (if partial != null)
-template <typename T>
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(kThreads) k_mupdate(long long n, int nv, const T *__restrict__ V, long long ld,
                                                       const double *__restrict__ h, T *__restrict__ w,
                                                       double *__restrict__ partial) {
@@ -110,7 +145,30 @@ __global__ void __launch_bounds__(kThreads) k_mupdate(long long n, int nv, const
   for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = (T)h[i];
   __syncthreads();
   T nrm = T(0);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  long long done = 0;
+  if (VEC) {
+    using V16 = Vec16<T>;
+    using VT = typename V16::type;
+    constexpr int W = V16::W;
+    const long long nw = n / W;
+    VT *w4 = reinterpret_cast<VT *>(w);
+    for (long long i = tid; i < nw; i += stride) {
+      VT v = w4[i];
+      T *vv = reinterpret_cast<T *>(&v);
+      for (int k = 0; k < nv; ++k) {
+        const VT a = reinterpret_cast<const VT *>(V + (long long)k * ld)[i];
+        const T *aa = reinterpret_cast<const T *>(&a);
+#pragma unroll
+        for (int q = 0; q < W; ++q) vv[q] -= hs[k] * aa[q];
+      }
+      w4[i] = v;
+#pragma unroll
+      for (int q = 0; q < W; ++q) nrm += vv[q] * vv[q];
+    }
+    done = nw * W;
+  }
+  for (long long i = done + tid; i < n; i += stride) {
     T v = w[i];
     for (int k = 0; k < nv; ++k) v -= hs[k] * V[(long long)k * ld + i];
     w[i] = v;
@@ -169,14 +227,23 @@ void vec_inv(long long n, const double *d, double *dinv64, float *dinv32, cudaSt
   k_inv<<<nblocks(n), kThreads, 0, s>>>(n, d, dinv64, dinv32);
 }
 
+// 16-byte loads when every vector starts on a 16-byte boundary
+template <typename T>
+bool vec16_ok(const void *a, const void *b, long long ld) {
+  constexpr int W = 16 / sizeof(T);
+  return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) == 0 && (ld % W) == 0;
+}
+
 template <typename T>
 void vec_mdot(long long n, int nv, const T *V, long long ld, const T *w, double *partial, double *out,
               cudaStream_t s) {
   const int nb = nblocks(n);
+  const bool vec = vec16_ok<T>(V, w, nv > 1 ? ld : 0);
   for (int i0 = 0; i0 < nv; i0 += kChunk) {
     const int cnt = nv - i0 < kChunk ? nv - i0 : kChunk;
     count_launch();
-    k_mdot<T><<<nb, kThreads, 0, s>>>(n, nv, i0, cnt, V, ld, w, partial);
+    if (vec) k_mdot<T, true><<<nb, kThreads, 0, s>>>(n, nv, i0, cnt, V, ld, w, partial);
+    else k_mdot<T, false><<<nb, kThreads, 0, s>>>(n, nv, i0, cnt, V, ld, w, partial);
   }
   count_launch();
   k_reduce<<<nv, kThreads, 0, s>>>(nb, nv, partial, out);
@@ -187,7 +254,10 @@ void vec_mupdate(long long n, int nv, const T *V, long long ld, const double *h,
                  double *out_norm2, cudaStream_t s) {
   const int nb = nblocks(n);
   count_launch(out_norm2 ? 2 : 1);
-  k_mupdate<T><<<nb, kThreads, 0, s>>>(n, nv, V, ld, h, w, out_norm2 ? partial : nullptr);
+  if (vec16_ok<T>(V, w, nv > 1 ? ld : 0))
+    k_mupdate<T, true><<<nb, kThreads, 0, s>>>(n, nv, V, ld, h, w, out_norm2 ? partial : nullptr);
+  else
+    k_mupdate<T, false><<<nb, kThreads, 0, s>>>(n, nv, V, ld, h, w, out_norm2 ? partial : nullptr);
   if (out_norm2) k_reduce<<<1, kThreads, 0, s>>>(nb, 1, partial, out_norm2);
 }
 
