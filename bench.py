@@ -733,7 +733,9 @@ def main():
                   "k_grad_f32_ms": t_grad32 * 1e3, "k_div_f32_ms": t_div32 * 1e3, "k_explicit_ms": t_expl * 1e3,
                   "flops_per_apply": fl_grad + fl_div, "hbm_floor_bytes_f64": bytes64,
                   "f64_tflops": (fl_grad + fl_div) / t_app64 / 1e12, "f32_tflops": (fl_grad + fl_div) / t_app32 / 1e12,
-                  "fp64_peak_measured_tflops": peak64},
+                  "fp64_peak_measured_tflops": peak64,
+                  "threads_per_cta_autotuned": {"f64": dgx.dgx_operator_threads(ctx, dgx.DGX_F64),
+                                                "f32": dgx.dgx_operator_threads(ctx, dgx.DGX_F32)}},
     }
     print(json.dumps(line), flush=True)
     dgx.dgx_destroy(ctx)

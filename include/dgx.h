@@ -335,6 +335,13 @@ int dgx_apply_operator_noalloc(dgx_ctx *ctx, int prec, const void *x, void *y);
  * DoF in FP64). */
 int dgx_operator_cost(const dgx_ctx *ctx, double *flops_grad, double *flops_div, double *bytes_f64);
 
+/* Threads per CTA of the operator kernels (k_grad, k_div) for prec on this
+ * context's mesh: a timing autotuner picks 128, 192 or 256 before the first
+ * application on meshes of 2048 cells or more (outside stream capture); the
+ * result of the operator does not depend on it.  0 before the first
+ * application (and on smaller meshes: the degree's default). */
+int dgx_operator_threads(const dgx_ctx *ctx, int prec);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * contexts); a diagnostic counter for benchmarks. */
 long long dgx_kernel_launches(void);

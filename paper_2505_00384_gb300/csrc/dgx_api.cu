@@ -322,6 +322,8 @@ void free_mesh(dgx_ctx *c) {
   c->kry64 = nullptr;
   c->kry32 = nullptr;
   c->kry64_elems = c->kry32_elems = 0;
+  c->op_threads[0] = c->op_threads[1] = 0;
+  c->op_tuned[0] = c->op_tuned[1] = false;
   c->has_mesh = c->has_coef = c->has_bg = false;
   c->rec_store = nullptr;
   c->rec_cap = c->rec_count = c->rec_seen = 0;
@@ -363,9 +365,58 @@ NodeP node_params(const dgx_ctx *c, const Tables1D *T = nullptr) {
   return p;
 }
 
+template <typename T>
+int apply_S(dgx_ctx *c, const T *x, T *y);
+
+// Timing autotuner of the threads per CTA of k_grad / k_div (128, 192, 256)
+// for this mesh and precision, run once before the first application on
+// meshes of at least 2048 cells (outside stream capture).  The operator's
+// result does not depend on the choice (each line of a sweep is computed by
+// one thread whatever the CTA size).
+template <typename T>
+int tune_operator(dgx_ctx *c) {
+  const int ix = sizeof(T) == 8 ? 0 : 1;
+  if (c->op_tuned[ix]) return 0;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 0;
+  c->op_tuned[ix] = true;
+  if (c->ncell < 2048) return 0;
+  const size_t bytes = (size_t)c->N * sizeof(T);
+  void *buf = nullptr;
+  if (int e = check_cuda(c, cudaMalloc(&buf, 2 * bytes), "cudaMalloc (autotune)")) return e;
+  T *x = reinterpret_cast<T *>(buf), *y = x + c->N;
+  cudaMemsetAsync(x, 0, bytes, c->stream);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_t = 0, err = 0;
+  for (int t : {128, 192, 256}) {
+    c->op_threads[ix] = t;
+    if ((err = apply_S<T>(c, x, y))) break;
+    cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < 2 && !err; ++r) err = apply_S<T>(c, x, y);
+    cudaEventRecord(e1, c->stream);
+    if (err || (err = check_cuda(c, cudaEventSynchronize(e1), "autotune"))) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_t = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  c->op_threads[ix] = err ? 0 : best_t;
+  return err;
+}
+
 // y = S x through the context's V scratch buffer
 template <typename T>
 int apply_S(dgx_ctx *c, const T *x, T *y) {
+  if (!c->op_tuned[sizeof(T) == 8 ? 0 : 1])
+    if (int e = tune_operator<T>(c)) return e;
   T *V;
   const T *rho, *pk;
   if constexpr (sizeof(T) == 8) {
@@ -1033,6 +1084,11 @@ int dgx_solve_pressure(dgx_ctx *c, const double *b, double *x, const dgx_solve_o
 static double eo_line_flops(int MO, int MI) {
   const int HO = (MO + 1) / 2, HI = MI / 2;
   return 2.0 * HI + 4.0 * HO * HI + ((MI & 1) ? HO : 0) + 2.0 * HO - (MO & 1);
+}
+
+int dgx_operator_threads(const dgx_ctx *c, int prec) {
+  if (!c || (prec != DGX_F64 && prec != DGX_F32)) return -1;
+  return c->op_threads[prec == DGX_F64 ? 0 : 1];
 }
 
 int dgx_operator_cost(const dgx_ctx *c, double *flops_grad, double *flops_div, double *b64) {

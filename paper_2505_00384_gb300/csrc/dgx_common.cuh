@@ -153,6 +153,11 @@ struct dgx_ctx {
   double *V64 = nullptr;
   float *V32 = nullptr;
 
+  // threads per CTA of k_grad / k_div chosen by the timing autotuner per
+  // precision ([0] FP64, [1] FP32; 0 = the default of the degree)
+  int op_threads[2] = {0, 0};
+  bool op_tuned[2] = {false, false};
+
   // Krylov workspace (grown on demand)
   double *kry64 = nullptr;
   size_t kry64_elems = 0;

@@ -572,6 +572,12 @@ int prep(dgx_ctx *c, Kern k, size_t smem) {
 
 int threads_for(int N) { return N <= 3 ? 128 : 256; }
 
+template <typename T>
+int op_threads(const dgx_ctx *c, int N) {
+  const int t = c->op_threads[sizeof(T) == 8 ? 0 : 1];
+  return t > 0 ? t : threads_for(N);
+}
+
 template <typename T, int N, bool CURVED>
 int grad_impl(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s, bool inv, double alpha) {
   constexpr int Q = 2 * N - 1;
@@ -582,12 +588,12 @@ int grad_impl(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s, bool i
     auto k = k_grad<T, N, Q, CURVED, true>;
     if (int e = prep(c, k, smem)) return e;
     count_launch();
-    k<<<(unsigned)c->ncell, threads_for(N), smem, s>>>(P, p, rho, V, c->N);
+    k<<<(unsigned)c->ncell, op_threads<T>(c, N), smem, s>>>(P, p, rho, V, c->N);
   } else {
     auto k = k_grad<T, N, Q, CURVED, false>;
     if (int e = prep(c, k, smem)) return e;
     count_launch();
-    k<<<(unsigned)c->ncell, threads_for(N), smem, s>>>(P, p, rho, V, c->N);
+    k<<<(unsigned)c->ncell, op_threads<T>(c, N), smem, s>>>(P, p, rho, V, c->N);
   }
   return check_cuda(c, cudaGetLastError(), "k_grad launch");
 }
@@ -601,7 +607,7 @@ int div_impl(dgx_ctx *c, const T *V, const T *p, const T *pk, T *y, cudaStream_t
   OpP<T> P = make_params<T>(c);
   if (alpha >= 0.0) P.alpha = (T)alpha;
   count_launch();
-  k<<<(unsigned)c->ncell, threads_for(N), smem, s>>>(P, V, p, pk, y, c->N);
+  k<<<(unsigned)c->ncell, op_threads<T>(c, N), smem, s>>>(P, V, p, pk, y, c->N);
   return check_cuda(c, cudaGetLastError(), "k_div launch");
 }
 

@@ -92,6 +92,7 @@ SIGNATURES = [
     ("dgx_default_solve_opts", None, [C.POINTER(dgx_solve_opts)]),
     ("dgx_operator_cost", C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("dgx_kernel_launches", C.c_longlong, []),
+    ("dgx_operator_threads", C.c_int, [_P, C.c_int]),
     ("dgx_apply_operator_noalloc", C.c_int, [_P, C.c_int, _P, _P]),
     ("dgx_set_imex", C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int]),
     ("dgx_explicit_tendencies", C.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -453,6 +454,11 @@ def ars222():
     A = np.array([[0, 0, 0], [g, 0, 0], [d, 1 - d, 0]], dtype=np.float64)
     At = np.array([[0, 0, 0], [0, g, 0], [0, 1 - g, g]], dtype=np.float64)
     return A, At
+
+
+def dgx_operator_threads(ctx, prec):
+    """Threads per CTA of the operator kernels chosen by the autotuner (0 = default)."""
+    return load().dgx_operator_threads(ctx, prec)
 
 
 def dgx_kernel_launches():
