@@ -40,6 +40,11 @@ A_LL = 1.0 - 1.0 / 2.0 ** 0.5
 # terms, counted as half applications); used only to scale the oracle's sampled cost to a step.
 PLAIN_STEP_APPLIES = 140
 STEP_EXTRA_HALF_APPLIES = 12
+# DRAM bytes per DoF of one launch of the FP64 operator kernels, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the 48x48x24 r=4 hill mesh
+# (6 912 000 DoFs, inputs larger than L2); one launch reads each cell's data once,
+# so the traffic scales with the DoFs.  Valid for the kernels as captured.
+DRAM_BYTES_PER_DOF_F64 = {"k_div<double>": 333.5e6 / 6912000, "k_grad<double>": 242.7e6 / 6912000}
 
 
 def parse():
@@ -694,9 +699,11 @@ def main():
                             else ("k_grad<double>", t_grad64, fl_grad))
         peak, peak_src = peak64, "measured cuBLAS DGEMM (torch.matmul float64 4096^3) on this GPU"
     achieved = fl_k / t_k / 1e12
+    traffic = DRAM_BYTES_PER_DOF_F64[kname] * N if kname in DRAM_BYTES_PER_DOF_F64 else None
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_src, "flops_per_launch": fl_k,
-                "launch_s": t_k, "step_share_estimate_s": share}
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_source": "ncu DRAM bytes per DoF on the 48x48x24 r=4 mesh, scaled by DoFs" if traffic else None,
+                "peak_source": peak_src, "flops_per_launch": fl_k, "launch_s": t_k, "step_share_estimate_s": share}
 
     cpu = None
     if not args.no_cpu_baseline and ws == 1:

@@ -96,6 +96,30 @@ def test_features_target_and_apply():
     c.close()
 
 
+def test_training_pairs_satisfy_the_operator():
+    """Every stored pair (v, e) of a system satisfies S e = v: in normalised
+    form S t = D_H ch0 (t = e/s, ch0 = D_H^-1 v / s), checked with the oracle's
+    operator; the first pair is (b, x), the others the residual / error of
+    restarted Jacobi FGMRES cycles."""
+    c = _case(4, 4, 4, 2)
+    dgx.dgx_learned_create(c.ctx, 3, 8, SEED)
+    b = inputs.random_field(c.N, SEED + 7)
+    x = O.solve(c.m, A_DT, GAMMA, c.rho, c.pk, b, tol=1e-12, maxit=3000)[0]
+    bd, xd = dev(b), dev(x)
+    dgx.dgx_learned_add_system(c.ctx, c._rho.data_ptr(), c._pk.data_ptr(), A_DT, GAMMA, bd.data_ptr(),
+                               xd.data_ptr(), pairs=5, stride=3)
+    ntr, nte = dgx.dgx_learned_num_samples(c.ctx)
+    assert nte == 0 and 3 <= ntr <= 5
+    for k in range(ntr):
+        smp = dgx.dgx_learned_sample(c.ctx, k, c.N).astype(np.float64)
+        ch0 = NL.to_dof(smp[0].reshape(c.shape), c.perm)
+        t = NL.to_dof(smp[5].reshape(c.shape), c.perm)
+        r = c.d * ch0
+        St = O.apply_S(c.m, A_DT, GAMMA, c.rho, c.pk, t)
+        assert np.linalg.norm(St - r) <= 1e-3 * np.linalg.norm(r), k
+    c.close()
+
+
 def test_zero_network_is_jacobi():
     c = _case()
     dgx.dgx_learned_create(c.ctx, 3, 8, SEED)  # last layer starts at zero
