@@ -68,7 +68,11 @@ __device__ __forceinline__ void line_eo(const T *src, int ss, T *dst, int ds) {
 // One sum-factorisation sweep along direction DIR of `nf` fields stored back
 // to back.  Input field shape (S0, S1, S2), x fastest, with S_DIR == MI; the
 // output replaces that extent by MO.  One thread per 1D line; field f uses the
-// matrix MAT0 / MAT1 / MAT2 selected by bits 2f..2f+1 of `sel`.
+// matrix MAT0 / MAT1 / MAT2 selected by bits 2f..2f+1 of `sel`.  The lines are
+// dealt out with the fields grouped by matrix (a permutation packed 4 bits per
+// field, nf <= 16), so that the threads of a warp take the same branch except
+// at the two group boundaries; each line's arithmetic does not depend on
+// which thread computes it.
 template <typename T, int NN, int DIR, int MO, int MI, int S0, int S1, int S2, int MAT0, int MAT1, int MAT2>
 __device__ __forceinline__ void sweep(int nf, unsigned sel, const T *__restrict__ in, T *__restrict__ out) {
   constexpr int L0 = DIR == 0 ? S1 : S0;  // faster non-DIR extent
@@ -79,8 +83,20 @@ __device__ __forceinline__ void sweep(int nf, unsigned sel, const T *__restrict_
   constexpr int ss = DIR == 0 ? 1 : (DIR == 1 ? S0 : S0 * S1);
   constexpr int ds = DIR == 0 ? 1 : (DIR == 1 ? O0 : O0 * O1);
   const int total = nf * NL;
+  unsigned long long perm = 0;  // grouped position g -> field, 4 bits each
+  int c0 = nf, c01 = nf;        // ends of the MAT0 and MAT1 groups
+  if (sel) {
+    int k = 0;
+    for (int m = 0; m < 3; ++m) {
+      for (int f = 0; f < nf; ++f)
+        if (((sel >> (2 * f)) & 3u) == (unsigned)m) perm |= (unsigned long long)f << (4 * k++);
+      if (m == 0) c0 = k;
+      if (m == 1) c01 = k;
+    }
+  }
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int f = idx / NL, l = idx - f * NL;
+    const int g = idx / NL, l = idx - g * NL;
+    const int f = sel ? (int)((perm >> (4 * g)) & 15u) : g;
     const int l0 = l % L0, l1 = l / L0;
     int io, oo;
     if (DIR == 0) {
@@ -95,10 +111,16 @@ __device__ __forceinline__ void sweep(int nf, unsigned sel, const T *__restrict_
     }
     const T *src = in + f * IT + io;
     T *dst = out + f * OT + oo;
-    const unsigned ms = (sel >> (2 * f)) & 3u;
-    if (ms == 0) line_eo<T, NN, MAT0, MO, MI>(src, ss, dst, ds);
-    else if (ms == 1) line_eo<T, NN, MAT1, MO, MI>(src, ss, dst, ds);
-    else line_eo<T, NN, MAT2, MO, MI>(src, ss, dst, ds);
+    if constexpr (MAT0 == MAT1 && MAT1 == MAT2) {  // one matrix: one copy of the line code
+      line_eo<T, NN, MAT0, MO, MI>(src, ss, dst, ds);
+    } else if constexpr (MAT1 == MAT2) {
+      if (g < c0) line_eo<T, NN, MAT0, MO, MI>(src, ss, dst, ds);
+      else line_eo<T, NN, MAT1, MO, MI>(src, ss, dst, ds);
+    } else {
+      if (g < c0) line_eo<T, NN, MAT0, MO, MI>(src, ss, dst, ds);
+      else if (g < c01) line_eo<T, NN, MAT1, MO, MI>(src, ss, dst, ds);
+      else line_eo<T, NN, MAT2, MO, MI>(src, ss, dst, ds);
+    }
   }
 }
 
