@@ -59,9 +59,10 @@ def parse():
     ap.add_argument("--mesh", default=None, help="NXxNYxNZ cells at the same cell size as the 64x64x32 workload")
     ap.add_argument("--profile", action="store_true",
                     help="only the warm-up and timed steps (for profiler launch lists); no side measurements")
-    ap.add_argument("--workload", default="hill", choices=["hill", "ensemble", "learned"],
+    ap.add_argument("--workload", default="hill", choices=["hill", "ensemble", "learned", "mixed"],
                     help="hill: one IMEX step of the 64x64x32 hill (default); ensemble: 16-member batched solve; "
-                         "learned: pressure solves of held-out hill systems with the trained network")
+                         "learned: pressure solves of held-out hill systems with the trained network; "
+                         "mixed: mixed-precision solves on the 4x4x4 box at degrees 2, 3, 5 against the oracle")
     ap.add_argument("--epochs", type=int, default=30, help="learned workload: training epochs")
     ap.add_argument("--members", type=int, default=16, help="ensemble members (first k of the 16)")
     return ap.parse_args()
@@ -218,6 +219,147 @@ def run_reference(args, work):
 ENSEMBLE = [(32, 32, 32), (40, 40, 32), (48, 48, 32), (48, 48, 40), (56, 56, 32), (64, 64, 32), (64, 64, 40),
             (64, 64, 48), (72, 72, 36), (80, 80, 40), (80, 80, 48), (88, 88, 44), (96, 96, 32), (96, 96, 40),
             (96, 96, 48), (32, 64, 32)]
+
+
+def run_mixed(args):
+    """Mixed precision on the 4 x 4 x 4-cell (1 km)^3 box with slip walls at
+    degrees 2, 3 and 5 (1728, 4096, 13 824 DoFs): isothermal 250 K background as
+    rho^(l) and p_k, a~_ll dt = 1 - 1/sqrt(2), right-hand side = Gaussian bump
+    (sigma 200 m, box centre) + N(0, 1e-3^2) noise.  FP32 GMRES(30) inside FP64
+    FGMRES(20) against plain FP64 FGMRES(30), both to 1e-8 from zero, each
+    solution's error against the oracle's FP64 solution (to 1e-12); then one
+    IMEX step with mixed solves on the degree-2 box with a centred 400 m hill
+    (periodic lateral faces, background + 10 m/s wind + a pressure bump)
+    against the oracle's step, error per field.  One step = the three mixed
+    solves; L2 is flushed before every timed solve."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_2505_00384_gb300 import dgx, inputs
+    from paper_2505_00384_gb300 import learned as LP
+    torch.cuda.set_device(0)
+    dgx.load()
+    stream = torch.cuda.current_stream()
+    ctx = dgx.dgx_create(0, stream.cuda_stream)
+    f64 = torch.float64
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+
+    def sopts(method, restart):
+        so = dgx.dgx_default_solve_opts()
+        so.method, so.pc, so.restart, so.tol, so.maxit = method, dgx.DGX_PC_HELMHOLTZ, restart, 1e-8, 3000
+        so.inner_maxit, so.inner_tol = 30, 1e-5
+        return so
+
+    solvers = {"mixed": sopts(dgx.DGX_SOLVER_MIXED, 20), "plain_fp64": sopts(dgx.DGX_SOLVER_FGMRES, 30)}
+    degrees, ts_mixed, launches, cpu = [], [], 0, None
+    for r in (2, 3, 5):
+        dgx.dgx_mesh_build(ctx, dgx.mesh_desc(4, 4, 4, r, 1000.0, 1000.0, 1000.0))
+        N = dgx.dgx_num_dofs(ctx)
+        dgx.dgx_set_background(ctx, dgx.background(kind=0, T=250.0, u_bar=0.0))
+        rho = torch.zeros(N, dtype=f64, device="cuda")
+        pk = torch.zeros_like(rho)
+        dgx.dgx_background_fields(ctx, rho.data_ptr(), pk.data_ptr())
+        dgx.dgx_set_coefficients(ctx, rho.data_ptr(), pk.data_ptr(), A_LL, 1.4)
+        X = torch.zeros(3 * N, dtype=f64, device="cuda")
+        dgx.dgx_node_coords(ctx, X.data_ptr())
+        Xh = X.cpu().numpy().reshape(3, N)
+        b = inputs.gaussian_bump_rhs(Xh, [500.0, 500.0, 500.0], 200.0, 1e-3, inputs.DEFAULT_SEED)
+        m = O.make_mesh(4, 4, 4, r)
+        if r == 2 and not args.no_cpu_baseline:
+            tc = time.time()
+            _, _, its_o, _ = O.solve(m, A_LL, 1.4, rho.cpu().numpy(), pk.cpu().numpy(), b, tol=1e-8, maxit=3000)
+            t_oracle = time.time() - tc
+        xo = O.solve(m, A_LL, 1.4, rho.cpu().numpy(), pk.cpu().numpy(), b, tol=1e-12, maxit=6000)[0]
+        if r == 2 and not args.no_cpu_baseline:
+            cpu = {"value": t_oracle, "unit": "s/solve", "cores": O.max_threads(), "kind": "oracle",
+                   "sample": "degree-2 box, FP64 FGMRES(30) + Helmholtz Jacobi to 1e-8 (%d iterations)" % its_o}
+        bd = torch.from_numpy(b).cuda()
+        x = torch.zeros_like(bd)
+        row = {"degree": r, "dofs": N}
+        for name, so in solvers.items():
+            for _ in range(max(args.warmup, 3)):
+                x.zero_()
+                dgx.dgx_solve_pressure(ctx, bd.data_ptr(), x.data_ptr(), so)
+            ts = []
+            for _ in range(args.steps):
+                x.zero_()
+                flush.zero_()
+                torch.cuda.synchronize()
+                l0 = dgx.dgx_kernel_launches()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st, si = dgx.dgx_solve_pressure(ctx, bd.data_ptr(), x.data_ptr(), so)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if name == "mixed":
+                    launches += dgx.dgx_kernel_launches() - l0
+                if st != dgx.DGX_OK:
+                    raise RuntimeError("%s solve at degree %d did not converge" % (name, r))
+                ts.append(e0.elapsed_time(e1) / 1e3)
+            xh = x.cpu().numpy()
+            row[name] = {"s_per_solve": statistics.median(ts), "iterations": si.iterations,
+                         "inner_iterations": si.inner_iterations, "relres": si.relres,
+                         "max_rel_err_vs_oracle": float(np.abs(xh - xo).max() / np.abs(xo).max()),
+                         "l2_rel_err_vs_oracle": float(np.linalg.norm(xh - xo) / np.linalg.norm(xo))}
+            if name == "mixed":
+                ts_mixed.append(statistics.median(ts))
+        degrees.append(row)
+    # e2e at degree 5 (the last mesh): host right-hand side in, host solution out
+    bh = bd.cpu().pin_memory()
+    xhost = torch.empty_like(bh).pin_memory()
+    te = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bd.copy_(bh, non_blocking=True)
+        x.zero_()
+        dgx.dgx_solve_pressure(ctx, bd.data_ptr(), x.data_ptr(), solvers["mixed"])
+        xhost.copy_(x, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        te.append(e0.elapsed_time(e1) / 1e3)
+    # one IMEX step with mixed solves against the oracle's step, error per field
+    N = LP.setup_hill(ctx, 400.0)
+    L = LP.BOX["L"]
+    m = O.make_mesh(4, 4, 4, 2, Lx=L, Ly=L, Lz=L, terrain=1, hc=400.0, ac=LP.BOX["a_c"], xc=L / 2, yc=L / 2,
+                    bc_lateral=2)
+    obg = O.make_bg(kind=0, T=250.0, ubar=LP.BOX["u_bar"])
+    rb, pb = O.background(m, obg)
+    Xo = O.node_coords(m)
+    bump = np.exp(-((Xo[0] - 500.0) ** 2 + (Xo[1] - 500.0) ** 2 + (Xo[2] - 500.0) ** 2) / (2 * 150.0 ** 2))
+    r0, p0 = rb.copy(), pb + 100.0 * bump
+    u0 = np.concatenate([np.full(N, LP.BOX["u_bar"]), np.zeros(N), np.zeros(N)])
+    rd, ud, pd = (torch.from_numpy(a.copy()).cuda() for a in (r0, u0, p0))
+    so = sopts(dgx.DGX_SOLVER_MIXED, 20)
+    st, sinfo = dgx.dgx_imex_step(ctx, rd.data_ptr(), ud.data_ptr(), pd.data_ptr(), 1, so)
+    ro, uo, po, sto, _ = O.imex_step(m, obg, r0, u0, p0, LP.BOX["dt"], K=LP.BOX["K"], tol=1e-11)
+    rg, ug, pg = rd.cpu().numpy(), ud.cpu().numpy(), pd.cpu().numpy()
+
+    def rel(a, b, ref):
+        return float(np.abs(a - b).max() / max(np.abs(ref).max(), 1e-300))
+
+    fields = {"rho'": rel(rg, ro, ro - rb), "u": rel(ug[:N], uo[:N], uo[:N]), "v": rel(ug[N:2 * N], uo[N:2 * N], uo),
+              "w": rel(ug[2 * N:], uo[2 * N:], uo), "p'": rel(pg, po, po - pb)}
+    v = ts_mixed[0]
+    line = {"metric": "mixed-precision pressure solve s/solve @1e-8 rel residual (4x4x4 box, degree 2)",
+            "value": v, "unit": "s/solve", "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": sum(ts_mixed) * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": "mixed_box_4x4x4_degrees_2_3_5", "step": "mixed solves at degrees 2, 3, 5",
+                       "l2": "flushed before every timed solve"},
+            "degrees": degrees,
+            "imex_step_vs_oracle": {"mesh": "4x4x4 r=2 box, 400 m hill, periodic", "status": st,
+                                    "solves": sinfo.solves, "max_rel_err_per_field": fields},
+            "e2e": {"value": statistics.median(te), "unit": "s/solve (degree 5)", "h2d_bytes_per_step": bd.numel() * 8,
+                    "d2h_bytes_per_step": bd.numel() * 8},
+            "gpu_launches": launches / args.steps,
+            "roofline": None, "roofline_note": "latency-bound meshes of 1728-13824 DoFs: see the hill workload",
+            "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    dgx.dgx_destroy(ctx)
+    return 0
 
 
 def run_learned(args):
@@ -523,6 +665,8 @@ def main():
         return run_ensemble(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "mixed":
+        return run_mixed(args)
 
     import torch
     from paper_2505_00384_gb300 import dgx
