@@ -572,17 +572,21 @@ int inner_gmres32(dgx_ctx *c, const float *v, float *z, const float *dinv, int m
 }
 
 // Flexible GMRES(m) in FP64 (Saad), right preconditioned.  pc_kind selects
-// the Jacobi diagonal; mixed = FP32 GMRES preconditioner.
+// the Jacobi diagonal; mixed = FP32 GMRES preconditioner.  The residual that
+// starts a solve is b - S x0 (b itself when x0 = 0); the residual after a
+// cycle is r0 - sum_j y_j (S z_j) with the FP64 products S z_j of that cycle
+// kept aside: b - S x of the updated x by linearity of S, without a further
+// application.
 int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dgx_solve_info &info) {
   const long long N = c->N;
   const int m = std::max(1, std::min(o.restart, 64));
   const bool mixed = o.method == DGX_SOLVER_MIXED;
-  if (int e = grow<double>(c, (size_t)(2 * m + 3) * N)) return e;
+  if (int e = grow<double>(c, (size_t)(3 * m + 3) * N)) return e;
   if (mixed) {
     const int mi = std::max(1, std::min(o.inner_maxit, 64));
     if (int e = grow<float>(c, (size_t)(mi + 4) * N)) return e;
   }
-  double *Vb = c->kry64, *Zb = Vb + (size_t)(m + 1) * N, *w = Zb + (size_t)m * N;
+  double *Vb = c->kry64, *Zb = Vb + (size_t)(m + 1) * N, *w = Zb + (size_t)m * N, *SZ = w + N;
   // the learned preconditioner falls back to the Helmholtz Jacobi diagonal
   const int pcd = o.pc == DGX_PC_LEARNED ? DGX_PC_HELMHOLTZ : o.pc;
   const double *dinv = o.pc == DGX_PC_NONE ? nullptr : c->dinv64[pcd];
@@ -605,10 +609,18 @@ int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dg
   }
   Hess H(m);
   int its = 0;
+  bool have_r = false;  // w holds b - S x
+  if (!o.use_x0) {
+    cudaMemcpyAsync(w, b, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    have_r = true;
+  }
   for (;;) {
-    if ((err = apply_S<double>(c, x, w))) return err;
-    ++info.operator_f64;
-    vec_axpby<double>(N, 1.0, b, -1.0, w, c->stream);  // w = b - S x
+    if (!have_r) {
+      if ((err = apply_S<double>(c, x, w))) return err;
+      ++info.operator_f64;
+      vec_axpby<double>(N, 1.0, b, -1.0, w, c->stream);  // w = b - S x
+    }
+    have_r = false;
     const double beta = dev_norm(c, N, w, &err);
     if (err) return err;
     info.relres = beta / bn;
@@ -654,6 +666,7 @@ int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dg
       }
       if ((err = apply_S<double>(c, zj, w))) return err;
       ++info.operator_f64;
+      cudaMemcpyAsync(SZ + (size_t)j * N, w, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
       const double hn = arnoldi<double>(c, N, j, Vb, w, H, &err);
       if (err) return err;
       if (use_learned && !std::isfinite(hn)) {
@@ -688,6 +701,11 @@ int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dg
     if ((err = check_cuda(c, cudaMemcpyAsync(c->red_out + 192, H.y.data(), jj * sizeof(double),
                                              cudaMemcpyHostToDevice, c->stream), "memcpy"))) return err;
     vec_lincomb<double, double>(N, jj, Zb, N, c->red_out + 192, x, c->stream);
+    // residual of the updated x: beta V_0 - sum_j y_j (S z_j)
+    cudaMemcpyAsync(w, Vb, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    vec_axpby<double>(N, 0.0, Vb, beta, w, c->stream);
+    vec_mupdate<double>(N, jj, SZ, N, c->red_out + 192, w, c->red, nullptr, c->stream);
+    have_r = true;
     if ((err = check_cuda(c, cudaStreamSynchronize(c->stream), "sync"))) return err;
   }
   info.iterations = its;
