@@ -38,7 +38,7 @@ A_LL = 1.0 - 1.0 / 2.0 ** 0.5
 # FP64 operator applications of one IMEX step of this workload with plain FP64 FGMRES(30) solves to 1e-8
 # (four solves), and the other operator-type kernel calls of a step (velocity recovery, -C A^-1 F, stage
 # terms, counted as half applications); used only to scale the oracle's sampled cost to a step.
-PLAIN_STEP_APPLIES = 140
+PLAIN_STEP_APPLIES = 138
 STEP_EXTRA_HALF_APPLIES = 12
 # DRAM bytes per DoF of one launch of the FP64 operator kernels, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the 48x48x24 r=4 hill mesh
@@ -698,10 +698,12 @@ def main():
     rho, u, p = rho0.clone(), u0.clone(), p0.clone()
 
     def opts(method):
+        # inner FP32 GMRES(25) to 3e-6: the fastest of a sweep of (inner_maxit, inner_tol) on this
+        # workload; the outer FP64 FGMRES tolerance 1e-8 is the method's and does not change
         o = dgx.dgx_default_solve_opts()
         o.method, o.pc, o.tol, o.maxit = method, dgx.DGX_PC_HELMHOLTZ, 1e-8, 2000
         o.restart = 20 if method == dgx.DGX_SOLVER_MIXED else 30
-        o.inner_maxit, o.inner_tol = 30, 1e-5
+        o.inner_maxit, o.inner_tol = 25, 3e-6
         return o
 
     o_mixed, o_plain = opts(dgx.DGX_SOLVER_MIXED), opts(dgx.DGX_SOLVER_FGMRES)
@@ -864,7 +866,7 @@ def main():
                    "mesh": "%dx%dx%d cells, r=%d, N=%d per field" % (work["nx"], work["ny"], work["nz"], work["r"], N),
                    "terrain": "bell h_c=400 m a_c=1 km centred, Gal-Chen", "background": "isothermal 250 K",
                    "boundaries": "periodic lateral, slip walls bottom/top", "initial": "background + 10 m/s wind",
-                   "step": "dgx_imex_step: ARS(2,2,2), 2 fixed-point its, 4 mixed FGMRES(20)/FP32 GMRES(30) "
+                   "step": "dgx_imex_step: ARS(2,2,2), 2 fixed-point its, 4 mixed FGMRES(20)/FP32 GMRES(25) "
                            "solves to 1e-8",
                    "l2": "state and Krylov bases larger than L2 (no flush needed)", "parallelism": "replicas"},
         "e2e": {"value": t_e2e / (args.steps * ws), "unit": "s/step", "h2d_bytes_per_step": io_bytes,

@@ -310,7 +310,7 @@ void free_mesh(dgx_ctx *c) {
   c->rho32 = c->pk32 = nullptr;
   for (int i = 0; i < 3; ++i) {
     c->diag64[i] = c->dinv64[i] = nullptr;
-    c->dinv32[i] = nullptr;
+    c->diag32[i] = c->dinv32[i] = nullptr;
   }
   c->V64 = nullptr;
   c->V32 = nullptr;
@@ -593,6 +593,8 @@ int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dg
   const float *dinv32 = o.pc == DGX_PC_NONE ? nullptr : c->dinv32[pcd];
   bool use_learned = o.pc == DGX_PC_LEARNED;
   double prev_beta = INFINITY;
+  if (o.pc != DGX_PC_NONE)  // FP32 diagonal alone for the mixed solver's inner GMRES
+    if (int e = ensure_diag(c, !mixed || use_learned)) return e;
   // FP32 right-hand side / solution of the inner solve, after the inner basis (V, w, u)
   float *io32 = mixed ? c->kry32 + (size_t)(std::max(1, std::min(o.inner_maxit, 64)) + 3) * N : nullptr;
   if (mixed && !dinv32) return set_error(c, DGX_ERR_ARG, "mixed solver needs a Jacobi preconditioner");
@@ -718,6 +720,8 @@ int cg64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dgx_so
   if (int e = grow<double>(c, (size_t)4 * N)) return e;
   double *r = c->kry64, *z = r + N, *p = z + N, *q = p + N;
   const double *dinv = o.pc == DGX_PC_NONE ? nullptr : c->dinv64[o.pc];
+  if (o.pc != DGX_PC_NONE)
+    if (int e = ensure_diag(c, true)) return e;
   int err = 0;
   double bn = dev_norm(c, N, b, &err);
   if (err) return err;
@@ -770,6 +774,25 @@ int cg64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dgx_so
 }
 
 }  // namespace
+
+int ensure_diag(dgx_ctx *c, bool f64) {
+  if (f64 ? c->diag64_ok : c->diag32_ok) return 0;
+  const long long N = c->N;
+  if (f64) {
+    if (int e = launch_diag<double>(c, c->rho64, c->pk64, c->diag64[DGX_PC_HELMHOLTZ],
+                                    c->diag64[DGX_PC_INTERNAL_ENERGY], c->stream))
+      return e;
+    for (int k = 1; k < 3; ++k) vec_inv(N, c->diag64[k], c->dinv64[k], c->dinv32[k], c->stream);
+    c->diag64_ok = c->diag32_ok = true;
+  } else {
+    if (int e = launch_diag<float>(c, c->rho32, c->pk32, c->diag32[DGX_PC_HELMHOLTZ],
+                                   c->diag32[DGX_PC_INTERNAL_ENERGY], c->stream))
+      return e;
+    for (int k = 1; k < 3; ++k) vec_inv32(N, c->diag32[k], c->dinv32[k], c->stream);
+    c->diag32_ok = true;
+  }
+  return check_cuda(c, cudaGetLastError(), "Jacobi diagonal");
+}
 
 void node_terrain_heights(const dgx_ctx *c, std::vector<double> &h) {
   const int n = c->n;
@@ -944,7 +967,8 @@ int dgx_mesh_build(dgx_ctx *c, const dgx_mesh_desc *d) {
       (e = dalloc(c, &c->pk64, Nn)) || (e = dalloc(c, &c->rho32, Nn)) || (e = dalloc(c, &c->pk32, Nn)))
     return e;
   for (int k = 1; k < 3; ++k)
-    if ((e = dalloc(c, &c->diag64[k], Nn)) || (e = dalloc(c, &c->dinv64[k], Nn)) || (e = dalloc(c, &c->dinv32[k], Nn)))
+    if ((e = dalloc(c, &c->diag64[k], Nn)) || (e = dalloc(c, &c->dinv64[k], Nn)) || (e = dalloc(c, &c->dinv32[k], Nn)) ||
+        (e = dalloc(c, &c->diag32[k], Nn)))
       return e;
   if ((e = check_cuda(c, cudaDeviceSynchronize(), "mesh upload"))) return e;
   c->has_mesh = true;
@@ -1002,10 +1026,7 @@ int dgx_set_coefficients(dgx_ctx *c, const double *rho, const double *pk, double
   c->alpha = a_dt;
   c->gamma = gamma;
   ++c->coef_version;
-  if (int e = launch_diag(c, c->rho64, c->pk64, c->diag64[DGX_PC_HELMHOLTZ], c->diag64[DGX_PC_INTERNAL_ENERGY],
-                          c->stream))
-    return e;
-  for (int k = 1; k < 3; ++k) vec_inv(N, c->diag64[k], c->dinv64[k], c->dinv32[k], c->stream);
+  c->diag64_ok = c->diag32_ok = false;  // the Jacobi diagonals follow on first use (ensure_diag)
   if (int e = check_cuda(c, cudaGetLastError(), "set_coefficients")) return e;
   c->has_coef = true;
   return DGX_OK;
@@ -1048,6 +1069,8 @@ int dgx_apply_preconditioner(dgx_ctx *c, int pc, int prec, const void *x, void *
   if (!x || !y) return set_error(c, DGX_ERR_ARG, "null array");
   if (pc < 0 || pc > 3) return set_error(c, DGX_ERR_ARG, "preconditioner %d", pc);
   if (pc == DGX_PC_LEARNED) return dgx_learned_apply(c, prec, x, y);
+  if (pc != DGX_PC_NONE)
+    if (int e = ensure_diag(c, prec == DGX_F64)) return e;
   const long long N = c->N;
   if (prec == DGX_F64) {
     if (pc == DGX_PC_NONE) cudaMemcpyAsync(y, x, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
@@ -1065,6 +1088,7 @@ int dgx_preconditioner_diagonal(dgx_ctx *c, int pc, double *d) {
   if (int e = check_ready(c, true)) return e;
   if (pc != DGX_PC_HELMHOLTZ && pc != DGX_PC_INTERNAL_ENERGY) return set_error(c, DGX_ERR_ARG, "pc %d", pc);
   if (!d) return set_error(c, DGX_ERR_ARG, "null array");
+  if (int e = ensure_diag(c, true)) return e;
   cudaMemcpyAsync(d, c->diag64[pc], c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   return check_cuda(c, cudaGetLastError(), "diagonal copy");
 }

@@ -147,7 +147,9 @@ struct dgx_ctx {
   float *rho32 = nullptr, *pk32 = nullptr;
   double *diag64[3] = {nullptr, nullptr, nullptr};  // index DGX_PC_*: diagonal
   double *dinv64[3] = {nullptr, nullptr, nullptr};  // inverse diagonal
+  float *diag32[3] = {nullptr, nullptr, nullptr};
   float *dinv32[3] = {nullptr, nullptr, nullptr};
+  bool diag64_ok = false, diag32_ok = false;         // valid for the current coefficients
 
   // operator scratch: V = A^-1 B p (3N)
   double *V64 = nullptr;
@@ -221,7 +223,13 @@ int launch_cmass(dgx_ctx *c, int mode, double scale, const double *f0, const dou
                  cudaStream_t s);
 // forward fast density-weighted mass A(rho) v, 3 components
 int launch_mass_fwd(dgx_ctx *c, const double *rho, const double *v, double *out, cudaStream_t s);
-int launch_diag(dgx_ctx *c, const double *rho, const double *pk, double *dh, double *die, cudaStream_t s);
+// Helmholtz (dh) and internal-energy (die) diagonals of Sec. 3.1 in precision T
+template <typename T>
+int launch_diag(dgx_ctx *c, const T *rho, const T *pk, T *dh, T *die, cudaStream_t s);
+// Jacobi diagonals of the current coefficients, computed on first use:
+// FP64 (diag64, dinv64, and dinv32 rounded from them) or, when only FP32 is
+// needed (the mixed solver's inner GMRES), the FP32 diagonal kernel (dinv32).
+int ensure_diag(dgx_ctx *c, bool f64);
 template <typename T>
 OpP<T> make_params(const dgx_ctx *c);
 
@@ -233,6 +241,7 @@ void vec_mul(long long n, const T *a, const T *x, T *y, cudaStream_t s);  // y =
 template <typename TO, typename TI>
 void vec_convert(long long n, const TI *x, TO *y, cudaStream_t s);
 void vec_inv(long long n, const double *d, double *dinv64, float *dinv32, cudaStream_t s);
+void vec_inv32(long long n, const float *d, float *dinv, cudaStream_t s);
 // h[i] = <V_i, w> for i < nv (V_i = V + i*ld), written to out (device doubles)
 template <typename T>
 void vec_mdot(long long n, int nv, const T *V, long long ld, const T *w, double *partial, double *out,

@@ -602,6 +602,8 @@ int dgx_ensemble_set_coefficients(dgx_ensemble *e, const double *rho_all, const 
     dgx_ctx *c = e->mem[m];
     if (int r = dgx_set_coefficients(c, rho_all + e->off[m], pk_all + e->off[m], a_dt, gamma))
       return eset(e, r, "member %d: %s", m, c->err.c_str());
+    if (int r = ensure_diag(c, false))  // the FP32 cycles use the FP32 Helmholtz diagonal
+      return eset(e, r, "member %d: %s", m, c->err.c_str());
     cudaMemcpyAsync(e->dinv32 + e->off[m], c->dinv32[DGX_PC_HELMHOLTZ], c->N * sizeof(float),
                     cudaMemcpyDeviceToDevice, e->stream);
   }

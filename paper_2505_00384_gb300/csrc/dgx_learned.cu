@@ -629,6 +629,7 @@ int ensure_grid(dgx_ctx *c) {
 // Coefficient channels of the live feature buffer for the current coefficients.
 int ensure_coef_features(dgx_ctx *c) {
   Learned *m = c->learned;
+  if (int e = ensure_diag(c, true)) return e;  // the Helmholtz diagonal in FP64
   if (m->live_version == c->coef_version) return 0;
   const long long G = m->g.G;
   vec_dot<double>(G, c->diag64[DGX_PC_HELMHOLTZ], m->ones, c->red, m->scal + 0, c->stream);

@@ -474,11 +474,9 @@ struct DiagL {
 
 // Sec. 3.1: S~_ii = int psi_i^2/(gamma-1) + alpha^2 int h |grad psi_i|^2, h = gamma p_k/((gamma-1) rho)
 // |grad psi|^2 det J = sum_{j,j'} d_j psi d_j' psi (adj adj^T)_{jj'} / det J.
-template <int N, int Q, bool CURVED>
-__global__ void __launch_bounds__(256) k_diag(const OpP<double> P, const double *__restrict__ rho,
-                                              const double *__restrict__ pk, double *__restrict__ dh,
-                                              double *__restrict__ die) {
-  using T = double;
+template <typename T, int N, int Q, bool CURVED>
+__global__ void __launch_bounds__(256) k_diag(const OpP<T> P, const T *__restrict__ rho, const T *__restrict__ pk,
+                                              T *__restrict__ dh, T *__restrict__ die) {
   using L = DiagL<N, Q, CURVED>;
   constexpr int N2 = L::N2, N3 = L::N3, Q2 = L::Q2, Q3 = L::Q3, NF = L::NF;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -622,14 +620,14 @@ int minv_impl(dgx_ctx *c, const T *in, const T *rho, T *out, cudaStream_t s, int
   return check_cuda(c, cudaGetLastError(), "k_minv launch");
 }
 
-template <int N, bool CURVED>
-int diag_impl(dgx_ctx *c, const double *rho, const double *pk, double *dh, double *die, cudaStream_t s) {
+template <typename T, int N, bool CURVED>
+int diag_impl(dgx_ctx *c, const T *rho, const T *pk, T *dh, T *die, cudaStream_t s) {
   constexpr int Q = 2 * N - 1;
-  const size_t smem = sizeof(double) * DiagL<N, Q, CURVED>::total;
-  auto k = k_diag<N, Q, CURVED>;
+  const size_t smem = sizeof(T) * DiagL<N, Q, CURVED>::total;
+  auto k = k_diag<T, N, Q, CURVED>;
   if (int e = prep(c, k, smem)) return e;
   count_launch();
-  k<<<(unsigned)c->ncell, threads_for(N), smem, s>>>(make_params<double>(c), rho, pk, dh, die);
+  k<<<(unsigned)c->ncell, threads_for(N), smem, s>>>(make_params<T>(c), rho, pk, dh, die);
   return check_cuda(c, cudaGetLastError(), "k_diag launch");
 }
 
@@ -710,11 +708,14 @@ int launch_mass_inverse(dgx_ctx *c, const T *in, const T *rho, T *out, cudaStrea
 #undef CALL_MINV
 }
 
-int launch_diag(dgx_ctx *c, const double *rho, const double *pk, double *dh, double *die, cudaStream_t s) {
-#define CALL_DIAG(NN, CC) diag_impl<NN, CC>(c, rho, pk, dh, die, s)
+template <typename T>
+int launch_diag(dgx_ctx *c, const T *rho, const T *pk, T *dh, T *die, cudaStream_t s) {
+#define CALL_DIAG(NN, CC) diag_impl<T, NN, CC>(c, rho, pk, dh, die, s)
   DGX_DISPATCH(CALL_DIAG)
 #undef CALL_DIAG
 }
+template int launch_diag<double>(dgx_ctx *, const double *, const double *, double *, double *, cudaStream_t);
+template int launch_diag<float>(dgx_ctx *, const float *, const float *, float *, float *, cudaStream_t);
 
 template <typename T>
 int launch_operator_multi(dgx_ctx *c, int n, bool curved, const EnsMember<T> *mem, int nmem, long long ncell,

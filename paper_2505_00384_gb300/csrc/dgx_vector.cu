@@ -63,6 +63,11 @@ __global__ void k_convert(long long n, const TI *__restrict__ x, TO *__restrict_
     y[i] = (TO)x[i];
 }
 
+__global__ void k_inv32(long long n, const float *__restrict__ d, float *__restrict__ di) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    di[i] = 1.0f / d[i];
+}
+
 __global__ void k_inv(long long n, const double *__restrict__ d, double *__restrict__ di64, float *__restrict__ di32) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double v = 1.0 / d[i];
@@ -221,6 +226,10 @@ template <typename TO, typename TI>
 void vec_convert(long long n, const TI *x, TO *y, cudaStream_t s) {
   count_launch();
   k_convert<TO, TI><<<nblocks(n), kThreads, 0, s>>>(n, x, y);
+}
+void vec_inv32(long long n, const float *d, float *dinv, cudaStream_t s) {
+  count_launch();
+  k_inv32<<<nblocks(n), kThreads, 0, s>>>(n, d, dinv);
 }
 void vec_inv(long long n, const double *d, double *dinv64, float *dinv32, cudaStream_t s) {
   count_launch();

@@ -69,6 +69,19 @@ def test_preconditioner_diagonals(case):
     assert rel_max_err(host(y), ref) <= TOL64
 
 
+def test_fp32_preconditioner_diagonals(case):
+    """Before any FP64 use, an FP32 preconditioner application computes the
+    diagonals with the FP32 kernel (the mixed solver's inner GMRES): both
+    Jacobi preconditioners against the oracle's diagonals to FP32 accuracy."""
+    import torch
+    x = dev(inputs.random_field(case.N, 6)).float()
+    for pc in (dgx.DGX_PC_HELMHOLTZ, dgx.DGX_PC_INTERNAL_ENERGY):
+        y = torch.zeros_like(x)
+        dgx.dgx_apply_preconditioner(case.ctx, pc, dgx.DGX_F32, x.data_ptr(), y.data_ptr())
+        ref = host(x).astype(np.float64) / O.precond_diag(case.m, pc, A_DT, GAMMA, case.rho, case.pk)
+        assert rel_max_err(host(y), ref) <= TOL32
+
+
 def test_grad_and_mass_inverse(case):
     import torch
     p = inputs.random_field(case.N, 21, scale=100.0)
