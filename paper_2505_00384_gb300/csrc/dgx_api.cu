@@ -576,17 +576,22 @@ int inner_gmres32(dgx_ctx *c, const float *v, float *z, const float *dinv, int m
 // starts a solve is b - S x0 (b itself when x0 = 0); the residual after a
 // cycle is r0 - sum_j y_j (S z_j) with the FP64 products S z_j of that cycle
 // kept aside: b - S x of the updated x by linearity of S, without a further
-// application.
-int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dgx_solve_info &info) {
+// application.  With Vx (3N), the solver also returns A^-1 B x of its
+// solution, kept the same way from the A^-1 B intermediates of its FP64
+// applications (the velocity recovery of the IMEX step needs it).
+int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dgx_solve_info &info,
+             double *Vx = nullptr) {
   const long long N = c->N;
   const int m = std::max(1, std::min(o.restart, 64));
   const bool mixed = o.method == DGX_SOLVER_MIXED;
-  if (int e = grow<double>(c, (size_t)(3 * m + 3) * N)) return e;
+  if (int e = grow<double>(c, (size_t)(3 * m + 3) * N + (Vx ? (size_t)3 * m * N : 0))) return e;
   if (mixed) {
     const int mi = std::max(1, std::min(o.inner_maxit, 64));
     if (int e = grow<float>(c, (size_t)(mi + 4) * N)) return e;
   }
   double *Vb = c->kry64, *Zb = Vb + (size_t)(m + 1) * N, *w = Zb + (size_t)m * N, *SZ = w + N;
+  double *VZ = SZ + (size_t)m * N;  // A^-1 B z_j of the cycle (3N each), with Vx
+  const size_t b3 = (size_t)3 * N * sizeof(double);
   // the learned preconditioner falls back to the Helmholtz Jacobi diagonal
   const int pcd = o.pc == DGX_PC_LEARNED ? DGX_PC_HELMHOLTZ : o.pc;
   const double *dinv = o.pc == DGX_PC_NONE ? nullptr : c->dinv64[pcd];
@@ -614,12 +619,14 @@ int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dg
   bool have_r = false;  // w holds b - S x
   if (!o.use_x0) {
     cudaMemcpyAsync(w, b, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    if (Vx) cudaMemsetAsync(Vx, 0, b3, c->stream);
     have_r = true;
   }
   for (;;) {
     if (!have_r) {
       if ((err = apply_S<double>(c, x, w))) return err;
       ++info.operator_f64;
+      if (Vx) cudaMemcpyAsync(Vx, c->V64, b3, cudaMemcpyDeviceToDevice, c->stream);
       vec_axpby<double>(N, 1.0, b, -1.0, w, c->stream);  // w = b - S x
     }
     have_r = false;
@@ -669,6 +676,7 @@ int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dg
       if ((err = apply_S<double>(c, zj, w))) return err;
       ++info.operator_f64;
       cudaMemcpyAsync(SZ + (size_t)j * N, w, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+      if (Vx) cudaMemcpyAsync(VZ + (size_t)3 * j * N, c->V64, b3, cudaMemcpyDeviceToDevice, c->stream);
       const double hn = arnoldi<double>(c, N, j, Vb, w, H, &err);
       if (err) return err;
       if (use_learned && !std::isfinite(hn)) {
@@ -703,6 +711,7 @@ int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dg
     if ((err = check_cuda(c, cudaMemcpyAsync(c->red_out + 192, H.y.data(), jj * sizeof(double),
                                              cudaMemcpyHostToDevice, c->stream), "memcpy"))) return err;
     vec_lincomb<double, double>(N, jj, Zb, N, c->red_out + 192, x, c->stream);
+    if (Vx) vec_lincomb<double, double>(3 * N, jj, VZ, 3 * N, c->red_out + 192, Vx, c->stream);
     // residual of the updated x: beta V_0 - sum_j y_j (S z_j)
     cudaMemcpyAsync(w, Vb, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
     vec_axpby<double>(N, 0.0, Vb, beta, w, c->stream);
@@ -809,6 +818,45 @@ void node_terrain_heights(const dgx_ctx *c, std::vector<double> &h) {
     const long long cx = cell % m.nx, cy = (cell / m.nx) % m.ny;
     h[(size_t)i] = terrain_h(m, (cx + x[a]) * dx, (cy + x[b]) * dy);
   }
+}
+
+}  // namespace dgx
+
+namespace dgx {
+
+// dgx_solve_pressure that, with Vx != nullptr, also returns A^-1 B x (3N) of
+// the solution: kept by the FGMRES methods, one k_grad after CG.
+int solve_pressure_vx(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts *opts,
+                           dgx_solve_info *info, double *Vx) {
+  if (int e = check_ready(c, true)) return e;
+  if (!b || !x || b == x) return set_error(c, DGX_ERR_ARG, "b, x must be distinct non-null arrays");
+  dgx_solve_opts o;
+  if (opts) o = *opts;
+  else dgx_default_solve_opts(&o);
+  if (o.pc < 0 || o.pc > 3) return set_error(c, DGX_ERR_ARG, "preconditioner %d", o.pc);
+  if (o.pc == DGX_PC_LEARNED && (o.method != DGX_SOLVER_FGMRES || !learned_ready(c)))
+    return set_error(c, DGX_ERR_ARG, "the learned preconditioner needs DGX_SOLVER_FGMRES and dgx_learned_create");
+  if (o.restart < 1 || o.restart > 64 || o.maxit < 0 || !(o.tol > 0))
+    return set_error(c, DGX_ERR_ARG, "need 1 <= restart <= 64, maxit >= 0, tol > 0");
+  if (o.method == DGX_SOLVER_MIXED && (o.inner_maxit < 1 || o.inner_maxit > 64 || !(o.inner_tol > 0)))
+    return set_error(c, DGX_ERR_ARG, "need 1 <= inner_maxit <= 64 and inner_tol > 0");
+  dgx_solve_info inf;
+  std::memset(&inf, 0, sizeof(inf));
+  Clock clk;
+  int e;
+  if (o.method == DGX_SOLVER_FGMRES || o.method == DGX_SOLVER_MIXED) {
+    e = fgmres64(c, b, x, o, inf, Vx);
+  } else if (o.method == DGX_SOLVER_CG) {
+    e = cg64(c, b, x, o, inf);
+    if (!e && Vx) e = launch_grad<double>(c, x, c->rho64, Vx, c->stream);
+  } else {
+    return set_error(c, DGX_ERR_ARG, "solver %d", o.method);
+  }
+  if (!e) e = check_cuda(c, cudaStreamSynchronize(c->stream), "solve sync");
+  inf.seconds = clk.s();
+  if (info) *info = inf;
+  if (e) return e;
+  return inf.status;
 }
 
 }  // namespace dgx
@@ -1094,30 +1142,7 @@ int dgx_preconditioner_diagonal(dgx_ctx *c, int pc, double *d) {
 }
 
 int dgx_solve_pressure(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts *opts, dgx_solve_info *info) {
-  if (int e = check_ready(c, true)) return e;
-  if (!b || !x || b == x) return set_error(c, DGX_ERR_ARG, "b, x must be distinct non-null arrays");
-  dgx_solve_opts o;
-  if (opts) o = *opts;
-  else dgx_default_solve_opts(&o);
-  if (o.pc < 0 || o.pc > 3) return set_error(c, DGX_ERR_ARG, "preconditioner %d", o.pc);
-  if (o.pc == DGX_PC_LEARNED && (o.method != DGX_SOLVER_FGMRES || !learned_ready(c)))
-    return set_error(c, DGX_ERR_ARG, "the learned preconditioner needs DGX_SOLVER_FGMRES and dgx_learned_create");
-  if (o.restart < 1 || o.restart > 64 || o.maxit < 0 || !(o.tol > 0))
-    return set_error(c, DGX_ERR_ARG, "need 1 <= restart <= 64, maxit >= 0, tol > 0");
-  if (o.method == DGX_SOLVER_MIXED && (o.inner_maxit < 1 || o.inner_maxit > 64 || !(o.inner_tol > 0)))
-    return set_error(c, DGX_ERR_ARG, "need 1 <= inner_maxit <= 64 and inner_tol > 0");
-  dgx_solve_info inf;
-  std::memset(&inf, 0, sizeof(inf));
-  Clock clk;
-  int e;
-  if (o.method == DGX_SOLVER_FGMRES || o.method == DGX_SOLVER_MIXED) e = fgmres64(c, b, x, o, inf);
-  else if (o.method == DGX_SOLVER_CG) e = cg64(c, b, x, o, inf);
-  else return set_error(c, DGX_ERR_ARG, "solver %d", o.method);
-  if (!e) e = check_cuda(c, cudaStreamSynchronize(c->stream), "solve sync");
-  inf.seconds = clk.s();
-  if (info) *info = inf;
-  if (e) return e;
-  return inf.status;
+  return solve_pressure_vx(c, b, x, opts, info, nullptr);
 }
 
 // Floating-point operations of one even-odd sweep line (MO outputs from MI

@@ -260,6 +260,10 @@ template <typename T>
 void vec_dot(long long n, const T *a, const T *b, double *partial, double *out, cudaStream_t s);
 int vec_partials();  // number of reduction blocks per vector pass
 
+// dgx_solve_pressure that also returns Vx = A^-1 B x (3N) of the solution (dgx_api.cu)
+int solve_pressure_vx(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts *opts, dgx_solve_info *info,
+                      double *Vx);
+
 // learned preconditioner (dgx_learned.cu)
 void learned_free(dgx_ctx *c);          // release everything (dgx_destroy)
 void learned_mesh_changed(dgx_ctx *c);  // drop mesh-dependent buffers and samples (keeps the weights)

@@ -197,7 +197,7 @@ int dgx_imex_step(dgx_ctx *c, double *rho, double *u, double *p, int nsteps, con
           vec_axpby<double>(N, -1.0, c->p_bar, 1.0, w.x, st);  // initial guess p'^(l,k)
           dgx_solve_info si;
           const auto ts = std::chrono::steady_clock::now();
-          const int rc = dgx_solve_pressure(c, w.rhs, w.x, &o, &si);
+          const int rc = solve_pressure_vx(c, w.rhs, w.x, &o, &si, w.t1);  // t1 = A^-1 B of the solution
           solve_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - ts).count();
           if (rc < 0) return rc;
           if (rc == DGX_NOT_CONVERGED) inf.status = DGX_NOT_CONVERGED;
@@ -219,7 +219,6 @@ int dgx_imex_step(dgx_ctx *c, double *rho, double *u, double *p, int nsteps, con
           inf.operator_f64 += si.operator_f64;
           inf.operator_f32 += si.operator_f32;
           inf.max_relres = std::fmax(inf.max_relres, si.relres);
-          if ((e = launch_grad<double>(c, w.x, c->rho64, w.t1, st))) return e;  // A^-1 B p'
           if ((e = cp(w.ul, w.W, b3))) return e;
           vec_axpby<double>(3 * N, -1.0, w.t1, 1.0, w.ul, st);
           if ((e = cp(w.pl, c->p_bar, b1))) return e;
