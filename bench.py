@@ -65,12 +65,14 @@ def parse():
                          "mixed: mixed-precision solves on the 4x4x4 box at degrees 2, 3, 5 against the oracle")
     ap.add_argument("--epochs", type=int, default=30, help="learned workload: training epochs")
     ap.add_argument("--members", type=int, default=16, help="ensemble members (first k of the 16)")
+    ap.add_argument("--inner-maxit", type=int, default=None, help="override the FP32 GMRES cycle length")
+    ap.add_argument("--inner-tol", type=float, default=None, help="override the FP32 GMRES tolerance")
     return ap.parse_args()
 
 
 def dist_env():
-    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
-            int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_2505_00384_gb300 import replicas
+    return replicas.env()
 
 
 class ClockSampler:
@@ -591,6 +593,10 @@ def run_ensemble(args):
     dgx.dgx_ensemble_autotune(e)
     o = dgx.dgx_default_solve_opts()
     o.tol, o.maxit, o.inner_maxit, o.inner_tol = 1e-8, 50, 30, 1e-5
+    if args.inner_maxit:
+        o.inner_maxit = args.inner_maxit
+    if args.inner_tol:
+        o.inner_tol = args.inner_tol
     x = torch.zeros_like(b)
     for _ in range(args.warmup):
         x.zero_()
@@ -671,13 +677,10 @@ def main():
     import torch
     from paper_2505_00384_gb300 import dgx
 
+    from paper_2505_00384_gb300 import replicas
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
-    pg = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-        pg = dist
+    pg = replicas.init("nccl")
     dgx.load()
     stream = torch.cuda.current_stream()
     ctx = dgx.dgx_create(local, stream.cuda_stream)
@@ -733,11 +736,8 @@ def main():
         torch.cuda.synchronize()
     launches = dgx.dgx_kernel_launches() - launches0
     t_dev = e0.elapsed_time(e1) / 1e3
-    if pg:
-        tt = torch.tensor([t_dev], dtype=f64, device="cuda")
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t_dev = float(tt.item())
-        pg.barrier()
+    t_dev = replicas.max_over_ranks(pg, t_dev, "cuda")
+    replicas.barrier(pg)
     step_infos = list(infos)
     finite = bool(torch.isfinite(p).all() and torch.isfinite(u).all())
     if args.profile:
@@ -782,10 +782,7 @@ def main():
     e3.record(stream)
     torch.cuda.synchronize()
     t_e2e = e2.elapsed_time(e3) / 1e3
-    if pg:
-        tt = torch.tensor([t_e2e], dtype=f64, device="cuda")
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e = replicas.max_over_ranks(pg, t_e2e, "cuda")
     io_bytes = sum(t.numel() * t.element_size() for t in h_state)
     del d_state
 
