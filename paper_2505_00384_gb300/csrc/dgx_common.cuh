@@ -90,7 +90,7 @@ __host__ __device__ constexpr int col_size(int N, int Q) { return 3 * Q * Q + 4 
 // Kernel parameters of the pressure operator.
 template <typename T>
 struct OpP {
-  int nx, ny, nz, bc_lat;  // bc_lat: 0 slip wall, 1 far field (transmissive)
+  int nx, ny, nz, bc_lat;  // lateral faces: 0 slip wall, 1 far field, 2 periodic
   T dx, dy, dz, H;         // cell sizes (dz of the uniform zeta grid) and Lz
   T alpha;                 // a~_ll * dt
   T gfac;                  // gamma / (gamma - 1)

@@ -15,8 +15,9 @@
 //   k_minv  out = A^-1 in  (the fast inverse alone)
 //   k_diag  Helmholtz and internal-energy diagonals of Sec. 3.1
 // Readings of the paper's open points (shared with the CPU oracle by
-// definition, not by code): central fluxes; p+ = p- on every boundary face;
-// zero normal flux of kappa V on slip walls, transmissive on far-field faces;
+// definition, not by code): central fluxes (also across periodic faces);
+// p_hat = p- on slip walls and 0 (the background) on far-field faces; zero
+// normal flux of kappa V on slip walls, transmissive on far-field faces;
 // Gal-Chen terrain-following map z = zeta + h(x,y) (1 - zeta/H).
 #include <cmath>
 #include <cstdio>
