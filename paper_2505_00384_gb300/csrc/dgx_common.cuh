@@ -92,6 +92,7 @@ template <typename T>
 struct OpP {
   int nx, ny, nz, bc_lat;  // lateral faces: 0 slip wall, 1 far field, 2 periodic
   T dx, dy, dz, H;         // cell sizes (dz of the uniform zeta grid) and Lz
+  T invH;                  // 1 / Lz (the map's factor 1 - zeta/H without a division per point)
   T alpha;                 // a~_ll * dt
   T gfac;                  // gamma / (gamma - 1)
   T igm1;                  // 1 / (gamma - 1)

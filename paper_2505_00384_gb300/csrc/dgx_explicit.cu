@@ -86,10 +86,10 @@ __global__ void __launch_bounds__(256) k_explicit(const ExP X, const double *__r
       T z1 = 0, z2 = 0, z3 = P.dz;
       if (CURVED) {
         const T h = colp[col_off_hq(N, Q) + i + Q * j];
-        const T fac = T(1) - (zeta0 + P.dz * gq[k]) / P.H;
+        const T fac = T(1) - (zeta0 + P.dz * gq[k]) * P.invH;
         z1 = colp[col_off_h1q(N, Q) + i + Q * j] * fac;
         z2 = colp[col_off_h2q(N, Q) + i + Q * j] * fac;
-        z3 = P.dz * (T(1) - h / P.H);
+        z3 = P.dz * (T(1) - h * P.invH);
       }
       if (c < 5) {
         const T q = c == 0 ? r : (c == 1 ? r * v0 : (c == 2 ? r * v1 : (c == 3 ? r * v2 : T(0.5) * r * (v0 * v0 + v1 * v1 + v2 * v2))));
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(256) k_cmass(const OpP<double> P, double scale
   for (int idx = threadIdx.x; idx < Q3; idx += blockDim.x) {
     const int i = idx % Q, j = (idx / Q) % Q;
     T det = P.dx * P.dy * P.dz;
-    if (CURVED) det *= T(1) - colp[col_off_hq(N, Q) + i + Q * j] / P.H;
+    if (CURVED) det *= T(1) - colp[col_off_hq(N, Q) + i + Q * j] * P.invH;
     const int k = idx / Q2;
     T v = R3[idx];
     if (MODE == 1) v *= T(0.5) * (R3[Q3 + idx] * R3[Q3 + idx] + R3[2 * Q3 + idx] * R3[2 * Q3 + idx] +
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(128) k_mass_fwd(const OpP<double> P, const dou
     const int node = idx % N3;
     const int i = node % N, j = (node / N) % N, k = node / (N * N);
     T det = P.dx * P.dy * P.dz;
-    if (CURVED) det *= T(1) - colp[col_off_hqa(N, Q) + i + N * j] / P.H;
+    if (CURVED) det *= T(1) - colp[col_off_hqa(N, Q) + i + N * j] * P.invH;
     B[idx] *= B[3 * N3 + node] * wa[i] * wa[j] * wa[k] * det;
   }
   __syncthreads();

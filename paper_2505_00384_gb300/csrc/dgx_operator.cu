@@ -100,8 +100,8 @@ __device__ __forceinline__ void grad_body(const OpP<T> &P, const long long cell,
       const T h = colp[col_off_hq(N, Q) + i + Q * j];
       const T h1 = colp[col_off_h1q(N, Q) + i + Q * j];
       const T h2 = colp[col_off_h2q(N, Q) + i + Q * j];
-      const T fac = T(1) - (zeta0 + P.dz * gq[k]) / P.H;
-      const T z1 = h1 * fac, z2 = h2 * fac, z3 = P.dz * (T(1) - h / P.H);
+      const T fac = T(1) - (zeta0 + P.dz * gq[k]) * P.invH;
+      const T z1 = h1 * fac, z2 = h2 * fac, z3 = P.dz * (T(1) - h * P.invH);
       Wv[0 * Q3 + idx] = c * P.dy * z3;   // j=0, d=0
       Wv[1 * Q3 + idx] = -c * P.dy * z1;  // j=2, d=0
       Wv[2 * Q3 + idx] = c * P.dx * z3;   // j=1, d=1
@@ -325,8 +325,8 @@ __device__ __forceinline__ void div_body(const OpP<T> &P, const long long cell, 
       const T h = colp[col_off_hq(N, Q) + i + Q * j];
       const T h1 = colp[col_off_h1q(N, Q) + i + Q * j];
       const T h2 = colp[col_off_h2q(N, Q) + i + Q * j];
-      const T fac = T(1) - (zeta0 + P.dz * gq[k]) / P.H;
-      const T z1 = h1 * fac, z2 = h2 * fac, z3 = P.dz * (T(1) - h / P.H);
+      const T fac = T(1) - (zeta0 + P.dz * gq[k]) * P.invH;
+      const T z1 = h1 * fac, z2 = h2 * fac, z3 = P.dz * (T(1) - h * P.invH);
       R3[idx] = c * P.dy * z3 * v0;
       R3[Q3 + idx] = c * P.dx * z3 * v1;
       R3[2 * Q3 + idx] = c * (P.dx * P.dy * v2 - P.dy * z1 * v0 - P.dx * z2 * v1);
@@ -510,10 +510,10 @@ __global__ void __launch_bounds__(256) k_diag(const OpP<T> P, const T *__restric
     T z1 = 0, z2 = 0, z3 = P.dz;
     if (CURVED) {
       const T hh = colp[col_off_hq(N, Q) + i + Q * j];
-      const T fac = T(1) - (zeta0 + P.dz * gq[k]) / P.H;
+      const T fac = T(1) - (zeta0 + P.dz * gq[k]) * P.invH;
       z1 = colp[col_off_h1q(N, Q) + i + Q * j] * fac;
       z2 = colp[col_off_h2q(N, Q) + i + Q * j] * fac;
-      z3 = P.dz * (T(1) - hh / P.H);
+      z3 = P.dz * (T(1) - hh * P.invH);
     }
     const T det = P.dx * P.dy * z3;
     const T A00 = P.dy * z3, A11 = P.dx * z3, A20 = -P.dy * z1, A21 = -P.dx * z2, A22 = P.dx * P.dy;
@@ -673,6 +673,7 @@ OpP<T> make_params(const dgx_ctx *c) {
   P.dy = (T)(c->mesh.Ly / c->mesh.ny);
   P.dz = (T)(c->mesh.Lz / c->mesh.nz);
   P.H = (T)c->mesh.Lz;
+  P.invH = (T)(1.0 / c->mesh.Lz);
   P.alpha = (T)c->alpha;
   P.gfac = (T)(c->gamma / (c->gamma - 1.0));
   P.igm1 = (T)(1.0 / (c->gamma - 1.0));

@@ -189,16 +189,16 @@ __device__ __forceinline__ void face_normal(const OpP<T> &P, const T *colp, T ze
   nA[0] = nA[1] = nA[2] = T(0);
   if (k == 0) {
     T z3 = P.dz;
-    if (CURVED) z3 = P.dz * (T(1) - colp[col_off_hx(N, Q, s) + i] / P.H);
+    if (CURVED) z3 = P.dz * (T(1) - colp[col_off_hx(N, Q, s) + i] * P.invH);
     nA[0] = sg * P.dy * z3;
   } else if (k == 1) {
     T z3 = P.dz;
-    if (CURVED) z3 = P.dz * (T(1) - colp[col_off_hy(N, Q, s) + i] / P.H);
+    if (CURVED) z3 = P.dz * (T(1) - colp[col_off_hy(N, Q, s) + i] * P.invH);
     nA[1] = sg * P.dx * z3;
   } else {
     nA[2] = sg * P.dx * P.dy;
     if (CURVED) {
-      const T fac = T(1) - (zeta0 + T(s) * P.dz) / P.H;
+      const T fac = T(1) - (zeta0 + T(s) * P.dz) * P.invH;
       nA[0] = -sg * P.dy * colp[col_off_h1q(N, Q) + i + Q * j] * fac;
       nA[1] = -sg * P.dx * colp[col_off_h2q(N, Q) + i + Q * j] * fac;
     }
@@ -225,7 +225,7 @@ __device__ __forceinline__ void fast_inverse(const OpP<T> &P, const T *tab, cons
     const int node = idx % N3;
     const int i = node % N, j = (node / N) % N, k = node / (N * N);
     T det = P.dx * P.dy * P.dz;
-    if (CURVED) det *= (T(1) - colp[col_off_hqa(N, Q) + i + N * j] / P.H);
+    if (CURVED) det *= (T(1) - colp[col_off_hqa(N, Q) + i + N * j] * P.invH);
     b[idx] = b[idx] / (rq[node] * wa[i] * wa[j] * wa[k] * det);
   }
   __syncthreads();
