@@ -150,11 +150,10 @@ __global__ void __launch_bounds__(256) k_explicit(const ExP X, const double *__r
       const int i = idx % Q, j = idx / Q;
       T nA[3];
       face_normal<T, N, Q, CURVED>(P, colp, zeta0, f, i, j, nA);
-      const T an = sqrt(nA[0] * nA[0] + nA[1] * nA[1] + nA[2] * nA[2]);
       const T rm = F2[idx], vm0 = F2[Q2 + idx], vm1 = F2[2 * Q2 + idx], vm2 = F2[3 * Q2 + idx];
       T rp = F2[4 * Q2 + idx], vp0 = F2[5 * Q2 + idx], vp1 = F2[6 * Q2 + idx], vp2 = F2[7 * Q2 + idx];
-      if (wall) {
-        const T un = (vm0 * nA[0] + vm1 * nA[1] + vm2 * nA[2]) / (an * an);
+      if (wall) {  // mirror state: u+ = u- - 2 (u-.n) n with n = nA / |nA|
+        const T un = (vm0 * nA[0] + vm1 * nA[1] + vm2 * nA[2]) / (nA[0] * nA[0] + nA[1] * nA[1] + nA[2] * nA[2]);
         rp = rm;
         vp0 = vm0 - T(2) * un * nA[0];
         vp1 = vm1 - T(2) * un * nA[1];

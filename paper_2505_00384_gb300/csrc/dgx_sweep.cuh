@@ -221,12 +221,12 @@ __device__ __forceinline__ void fast_inverse(const OpP<T> &P, const T *tab, cons
   __syncthreads();
   sweep<T, N, 2, N, N, N, N, N, M_PT, M_PT, M_PT>(nf, 0u, a, b);
   __syncthreads();
-  for (int idx = threadIdx.x; idx < nf * N3; idx += blockDim.x) {
-    const int node = idx % N3;
+  for (int node = threadIdx.x; node < N3; node += blockDim.x) {  // one division per node, all fields
     const int i = node % N, j = (node / N) % N, k = node / (N * N);
     T det = P.dx * P.dy * P.dz;
     if (CURVED) det *= (T(1) - colp[col_off_hqa(N, Q) + i + N * j] * P.invH);
-    b[idx] = b[idx] / (rq[node] * wa[i] * wa[j] * wa[k] * det);
+    const T inv = T(1) / (rq[node] * wa[i] * wa[j] * wa[k] * det);
+    for (int f = 0; f < nf; ++f) b[f * N3 + node] *= inv;
   }
   __syncthreads();
   sweep<T, N, 0, N, N, N, N, N, M_P, M_P, M_P>(nf, 0u, b, a);
