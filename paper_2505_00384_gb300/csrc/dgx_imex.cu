@@ -184,13 +184,14 @@ int dgx_imex_step(dgx_ctx *c, double *rho, double *u, double *p, int nsteps, con
           if (c->imex_At[l * s + m] != 0.0)
             vec_axpby<double>(N, dt * c->imex_At[l * s + m], Erm + 8 * N, 1.0, w.Gs, st);
         }
+        // W = A(rho^(l))^-1 F: the same for every fixed-point iteration of the stage
+        if ((e = launch_mass_inverse<double>(c, w.Fs, w.rl, w.W, st, 3))) return e;
         // fixed-point iterations from the previous stage (ul, pl)
         for (int k = 0; k < K; ++k) {
           if ((e = dgx_set_coefficients(c, w.rl, w.pl, al, gm))) return e;
           if ((e = launch_cmass(c, 1, 1.0, w.rl, w.ul, w.t2, st))) return e;
           if ((e = cp(w.rhs, w.Gs, b1))) return e;
           vec_axpby<double>(N, -1.0, w.t2, 1.0, w.rhs, st);
-          if ((e = launch_mass_inverse<double>(c, w.Fs, w.rl, w.W, st, 3))) return e;
           if ((e = launch_div<double>(c, w.W, w.zeros, c->pk64, w.t2, st))) return e;  // -C A^-1 F
           vec_axpby<double>(N, 1.0, w.t2, 1.0, w.rhs, st);
           if ((e = cp(w.x, w.pl, b1))) return e;
