@@ -1000,6 +1000,20 @@ int dgx_mesh_build(dgx_ctx *c, const dgx_mesh_desc *d) {
               for (int a = 0; a < N; ++a) h += la[i * N + a] * la[j * N + b] * hn[a + N * b];
             cp[col_off_hqa(N, Q) + i + N * j] = h;
           }
+        {
+          const double dz = d->Lz / d->nz, invH = 1.0 / d->Lz;
+          for (int j = 0; j < Q; ++j)
+            for (int i = 0; i < Q; ++i) {
+              const int t = i + Q * j;
+              const double w = T.gw[i] * T.gw[j], e = 1.0 - cp[col_off_hq(N, Q) + t] * invH;
+              cp[col_off_w(N, Q, 0) + t] = w * dy * dz * e;
+              cp[col_off_w(N, Q, 1) + t] = w * dx * dz * e;
+              cp[col_off_w(N, Q, 2) + t] = w * dx * dy;
+              cp[col_off_w(N, Q, 3) + t] = -w * dy * cp[col_off_h1q(N, Q) + t];
+              cp[col_off_w(N, Q, 4) + t] = -w * dx * cp[col_off_h2q(N, Q) + t];
+              cp[col_off_w(N, Q, 5) + t] = w * dx * dy * dz * e;
+            }
+        }
       }
     // each column must keep positive cell heights: h < Lz at every point
     for (long long i = 0; i < ncol; ++i)

@@ -85,7 +85,14 @@ __host__ __device__ constexpr int col_off_h2q(int, int Q) { return 2 * Q * Q; }
 __host__ __device__ constexpr int col_off_hx(int, int Q, int s) { return 3 * Q * Q + s * Q; }
 __host__ __device__ constexpr int col_off_hy(int, int Q, int s) { return 3 * Q * Q + 2 * Q + s * Q; }
 __host__ __device__ constexpr int col_off_hqa(int, int Q) { return 3 * Q * Q + 4 * Q; }
-__host__ __device__ constexpr int col_size(int N, int Q) { return 3 * Q * Q + 4 * Q + N * N; }
+// Weighted metric products of the column at (g_i, g_j), w_ij = wq_i wq_j, e = 1 - h/H:
+//   wA = w_ij dy dz e,  wB = w_ij dx dz e,  wC = w_ij dx dy,
+//   wE = -w_ij dy h1,   wF = -w_ij dx h2,   wG = w_ij dx dy dz e   [Q*Q each]
+// so that at layer point k, with wk = wq_k and wf = wq_k (1 - zeta_k/H), the
+// quadrature weight times the five nonzeros of adj(J) are wk wA, wk wB, wk wC,
+// wf wE, wf wF and the weight times det J is wk wG.
+__host__ __device__ constexpr int col_off_w(int N, int Q, int t) { return 3 * Q * Q + 4 * Q + N * N + t * Q * Q; }
+__host__ __device__ constexpr int col_size(int N, int Q) { return 9 * Q * Q + 4 * Q + N * N; }
 
 // Kernel parameters of the pressure operator.
 template <typename T>

@@ -95,19 +95,17 @@ __device__ __forceinline__ void grad_body(const OpP<T> &P, const long long cell,
   // volume fluxes f_{jd} = -alpha w p adj(J)_{jd}  (weak gradient, Sec. 2)
   for (int idx = threadIdx.x; idx < Q3; idx += blockDim.x) {
     const int i = idx % Q, j = (idx / Q) % Q, k = idx / Q2;
-    const T c = -P.alpha * wq[i] * wq[j] * wq[k] * Wv[idx];
-    if (CURVED) {
-      const T h = colp[col_off_hq(N, Q) + i + Q * j];
-      const T h1 = colp[col_off_h1q(N, Q) + i + Q * j];
-      const T h2 = colp[col_off_h2q(N, Q) + i + Q * j];
-      const T fac = T(1) - (zeta0 + P.dz * gq[k]) * P.invH;
-      const T z1 = h1 * fac, z2 = h2 * fac, z3 = P.dz * (T(1) - h * P.invH);
-      Wv[0 * Q3 + idx] = c * P.dy * z3;   // j=0, d=0
-      Wv[1 * Q3 + idx] = -c * P.dy * z1;  // j=2, d=0
-      Wv[2 * Q3 + idx] = c * P.dx * z3;   // j=1, d=1
-      Wv[3 * Q3 + idx] = -c * P.dx * z2;  // j=2, d=1
-      Wv[4 * Q3 + idx] = c * P.dx * P.dy; // j=2, d=2
+    if (CURVED) {  // weighted metric products from the column table
+      const int t = i + Q * j;
+      const T a = -P.alpha * Wv[idx];
+      const T aw = a * wq[k], af = aw * (T(1) - (zeta0 + P.dz * gq[k]) * P.invH);
+      Wv[0 * Q3 + idx] = aw * colp[col_off_w(N, Q, 0) + t];  // j=0, d=0
+      Wv[1 * Q3 + idx] = af * colp[col_off_w(N, Q, 3) + t];  // j=2, d=0
+      Wv[2 * Q3 + idx] = aw * colp[col_off_w(N, Q, 1) + t];  // j=1, d=1
+      Wv[3 * Q3 + idx] = af * colp[col_off_w(N, Q, 4) + t];  // j=2, d=1
+      Wv[4 * Q3 + idx] = aw * colp[col_off_w(N, Q, 2) + t];  // j=2, d=2
     } else {
+      const T c = -P.alpha * wq[i] * wq[j] * wq[k] * Wv[idx];
       Wv[0 * Q3 + idx] = c * P.dy * P.dz;
       Wv[1 * Q3 + idx] = c * P.dx * P.dz;
       Wv[2 * Q3 + idx] = c * P.dx * P.dy;
@@ -318,20 +316,19 @@ __device__ __forceinline__ void div_body(const OpP<T> &P, const long long cell, 
   //  D P: w det J p / (gamma - 1)
   for (int idx = threadIdx.x; idx < Q3; idx += blockDim.x) {
     const int i = idx % Q, j = (idx / Q) % Q, k = idx / Q2;
-    const T w = wq[i] * wq[j] * wq[k];
     const T v0 = R3[idx], v1 = R3[Q3 + idx], v2 = R3[2 * Q3 + idx], pkq = R3[3 * Q3 + idx], pq = R3[4 * Q3 + idx];
-    const T c = P.alpha * P.gfac * pkq * w;
-    if (CURVED) {
-      const T h = colp[col_off_hq(N, Q) + i + Q * j];
-      const T h1 = colp[col_off_h1q(N, Q) + i + Q * j];
-      const T h2 = colp[col_off_h2q(N, Q) + i + Q * j];
-      const T fac = T(1) - (zeta0 + P.dz * gq[k]) * P.invH;
-      const T z1 = h1 * fac, z2 = h2 * fac, z3 = P.dz * (T(1) - h * P.invH);
-      R3[idx] = c * P.dy * z3 * v0;
-      R3[Q3 + idx] = c * P.dx * z3 * v1;
-      R3[2 * Q3 + idx] = c * (P.dx * P.dy * v2 - P.dy * z1 * v0 - P.dx * z2 * v1);
-      R3[3 * Q3 + idx] = w * P.dx * P.dy * z3 * pq * P.igm1;
+    if (CURVED) {  // weighted metric products from the column table
+      const int t = i + Q * j;
+      const T c0 = P.alpha * P.gfac * pkq;
+      const T ck = c0 * wq[k], cf = ck * (T(1) - (zeta0 + P.dz * gq[k]) * P.invH);
+      R3[idx] = ck * colp[col_off_w(N, Q, 0) + t] * v0;
+      R3[Q3 + idx] = ck * colp[col_off_w(N, Q, 1) + t] * v1;
+      R3[2 * Q3 + idx] = ck * colp[col_off_w(N, Q, 2) + t] * v2 +
+                         cf * (colp[col_off_w(N, Q, 3) + t] * v0 + colp[col_off_w(N, Q, 4) + t] * v1);
+      R3[3 * Q3 + idx] = (wq[k] * P.igm1) * colp[col_off_w(N, Q, 5) + t] * pq;
     } else {
+      const T w = wq[i] * wq[j] * wq[k];
+      const T c = P.alpha * P.gfac * pkq * w;
       R3[idx] = c * P.dy * P.dz * v0;
       R3[Q3 + idx] = c * P.dx * P.dz * v1;
       R3[2 * Q3 + idx] = c * P.dx * P.dy * v2;
