@@ -32,7 +32,8 @@ struct ExL {
   static constexpr int oVQ = oR2 + 4 * N * Q2;       // rho, u0, u1, u2 at the Q^3 points
   static constexpr int oFL = oVQ + 4 * Q3;           // three flux fields of one quantity
   static constexpr int oWx = oFL + 3 * Q3;           // x sweep output (3 fields)
-  static constexpr int oEnd = oWx + 3 * N3;
+  static constexpr int oU = oWx + 3 * N3;            // w adj(J) u (contravariant velocity times weight)
+  static constexpr int oEnd = oU + 3 * Q3;
   // faces reuse everything from oR1 on (volume finished)
   static constexpr int szFace = 8 * cmax2(N2, Q2) + 8 * N * Q + 5 * Q2 + 5 * N * Q + 5 * N2;
   static constexpr int total = cmax2(oEnd, oR1 + szFace);
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(256) k_explicit(const ExP X, const double *__r
   extern __shared__ __align__(16) unsigned char smraw[];
   T *sm = reinterpret_cast<T *>(smraw);
   T *tab = sm, *s_in = sm + L::oIn, *s_out = sm + L::oOut, *R1 = sm + L::oR1, *R2 = sm + L::oR2, *VQ = sm + L::oVQ,
-    *FL = sm + L::oFL, *Wx = sm + L::oWx;
+    *FL = sm + L::oFL, *Wx = sm + L::oWx, *U = sm + L::oU;
   T *Wy = R1, *Wz = R2;
   const long long cell = blockIdx.x;
   const CellPos cp = cell_pos(P, cell);
@@ -77,27 +78,38 @@ __global__ void __launch_bounds__(256) k_explicit(const ExP X, const double *__r
   sweep<T, N, 2, Q, N, Q, Q, N, M_I, M_I, M_I>(4, 0u, R2, VQ);
   __syncthreads();
 
-  // volume: int q_c u . grad psi = sum_j D_j^T (q_c w sum_d adj_{jd} u_d); pass 5 = gravity work
+  // volume: int q_c u . grad psi = sum_j D_j^T (q_c U_j), U_j = w sum_d adj_{jd} u_d the same for
+  // every quantity q_c (weighted metric products from the column table); pass 5 = gravity work
+  for (int idx = threadIdx.x; idx < Q3; idx += blockDim.x) {
+    const int i = idx % Q, j = (idx / Q) % Q, k = idx / Q2;
+    const T v0 = VQ[Q3 + idx], v1 = VQ[2 * Q3 + idx], v2 = VQ[3 * Q3 + idx];
+    if (CURVED) {
+      const int t = i + Q * j;
+      const T wk = wq[k], wf = wk * (T(1) - (zeta0 + P.dz * gq[k]) * P.invH);
+      U[idx] = wk * colp[col_off_w(N, Q, 0) + t] * v0;
+      U[Q3 + idx] = wk * colp[col_off_w(N, Q, 1) + t] * v1;
+      U[2 * Q3 + idx] =
+          wk * colp[col_off_w(N, Q, 2) + t] * v2 + wf * (colp[col_off_w(N, Q, 3) + t] * v0 + colp[col_off_w(N, Q, 4) + t] * v1);
+    } else {
+      const T w = wq[i] * wq[j] * wq[k];
+      U[idx] = w * P.dy * P.dz * v0;
+      U[Q3 + idx] = w * P.dx * P.dz * v1;
+      U[2 * Q3 + idx] = w * P.dx * P.dy * v2;
+    }
+  }
+  __syncthreads();
   for (int c = 0; c < 6; ++c) {
     for (int idx = threadIdx.x; idx < Q3; idx += blockDim.x) {
-      const int i = idx % Q, j = (idx / Q) % Q, k = idx / Q2;
-      const T w = wq[i] * wq[j] * wq[k];
       const T r = VQ[idx], v0 = VQ[Q3 + idx], v1 = VQ[2 * Q3 + idx], v2 = VQ[3 * Q3 + idx];
-      T z1 = 0, z2 = 0, z3 = P.dz;
-      if (CURVED) {
-        const T h = colp[col_off_hq(N, Q) + i + Q * j];
-        const T fac = T(1) - (zeta0 + P.dz * gq[k]) * P.invH;
-        z1 = colp[col_off_h1q(N, Q) + i + Q * j] * fac;
-        z2 = colp[col_off_h2q(N, Q) + i + Q * j] * fac;
-        z3 = P.dz * (T(1) - h * P.invH);
-      }
       if (c < 5) {
         const T q = c == 0 ? r : (c == 1 ? r * v0 : (c == 2 ? r * v1 : (c == 3 ? r * v2 : T(0.5) * r * (v0 * v0 + v1 * v1 + v2 * v2))));
-        FL[idx] = q * w * P.dy * z3 * v0;
-        FL[Q3 + idx] = q * w * P.dx * z3 * v1;
-        FL[2 * Q3 + idx] = q * w * (P.dx * P.dy * v2 - P.dy * z1 * v0 - P.dx * z2 * v1);
+        FL[idx] = q * U[idx];
+        FL[Q3 + idx] = q * U[Q3 + idx];
+        FL[2 * Q3 + idx] = q * U[2 * Q3 + idx];
       } else {
-        FL[idx] = -X.g * r * v2 * w * P.dx * P.dy * z3;
+        const int i = idx % Q, j = (idx / Q) % Q, k = idx / Q2;
+        const T wdet = CURVED ? wq[k] * colp[col_off_w(N, Q, 5) + i + Q * j] : wq[i] * wq[j] * wq[k] * P.dx * P.dy * P.dz;
+        FL[idx] = -X.g * r * v2 * wdet;
       }
     }
     __syncthreads();
