@@ -56,6 +56,8 @@ __global__ void __launch_bounds__(256) k_explicit(const ExP X, const double *__r
   T *Wy = R1, *Wz = R2;
   const long long cell = blockIdx.x;
   const CellPos cp = cell_pos(P, cell);
+  __shared__ long long s_nb[6];  // the six face neighbours (-1: boundary), read after the first barrier
+  if (threadIdx.x < 6) s_nb[threadIdx.x] = neighbour(P, cp, threadIdx.x);
   const T *colp = CURVED ? P.col + (long long)(cp.cx + P.nx * cp.cy) * col_size(N, Q) : nullptr;
   const T zeta0 = T(cp.cz) * P.dz;
 
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(256) k_explicit(const ExP X, const double *__r
     *Fb2 = Fb1 + 5 * N * Q;
   for (int f = 0; f < 6; ++f) {
     const int kd = f >> 1, s = f & 1;
-    const long long nb = neighbour(P, cp, f);
+    const long long nb = s_nb[f];
     const bool wall = nb < 0 && (kd == 2 || P.bc_lat == 0);
     const bool far = nb < 0 && !wall;
     for (int idx = threadIdx.x; idx < 8 * N2; idx += blockDim.x) {

@@ -71,6 +71,8 @@ __device__ __forceinline__ void grad_body(const OpP<T> &P, const long long cell,
     *Wx = sm + L::oX, *Wf = sm + L::oFace;
 
   const CellPos cp = cell_pos(P, cell);
+  __shared__ long long s_nb[6];  // the six face neighbours (-1: boundary), read after the first barrier
+  if (threadIdx.x < 6) s_nb[threadIdx.x] = neighbour(P, cp, threadIdx.x);
   const T *colp = CURVED ? P.col + (long long)(cp.cx + P.nx * cp.cy) * col_size(N, Q) : nullptr;
   const T zeta0 = T(cp.cz) * P.dz;
 
@@ -143,7 +145,7 @@ __device__ __forceinline__ void grad_body(const OpP<T> &P, const long long cell,
     const int f = idx / N2, t = idx % N2, t1 = t % N, t2 = t / N;
     const int k = f >> 1, s = f & 1;
     const T own = s_p[face_node<N>(k, s ? N - 1 : 0, t1, t2)];
-    const long long nb = neighbour(P, cp, f);
+    const long long nb = s_nb[f];
     T ph = own;
     if (nb >= 0) ph = T(0.5) * (own + p[nb * N3 + face_node<N>(k, s ? 0 : N - 1, t1, t2)]);
     else if (k < 2 && P.bc_lat == 1) ph = T(0);
@@ -290,6 +292,8 @@ __device__ __forceinline__ void div_body(const OpP<T> &P, const long long cell, 
     *Fb2 = Fb1 + 6 * N * Q;
 
   const CellPos cp = cell_pos(P, cell);
+  __shared__ long long s_nb[6];  // the six face neighbours (-1: boundary), read after the first barrier
+  if (threadIdx.x < 6) s_nb[threadIdx.x] = neighbour(P, cp, threadIdx.x);
   const T *colp = CURVED ? P.col + (long long)(cp.cx + P.nx * cp.cy) * col_size(N, Q) : nullptr;
   const T zeta0 = T(cp.cz) * P.dz;
 
@@ -351,7 +355,7 @@ __device__ __forceinline__ void div_body(const OpP<T> &P, const long long cell, 
     int f, side, field;
     div_slot<CURVED>(sl, f, side, field);
     const int k = f >> 1, s = f & 1;
-    const long long nb = neighbour(P, cp, f);
+    const long long nb = s_nb[f];
     T v;
     if (side == 0 || nb < 0) {
       const int node = face_node<N>(k, s ? N - 1 : 0, t1, t2);
