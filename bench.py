@@ -63,7 +63,7 @@ def parse():
                     help="hill: one IMEX step of the 64x64x32 hill (default); ensemble: 16-member batched solve; "
                          "learned: pressure solves of held-out hill systems with the trained network; "
                          "mixed: mixed-precision solves on the 4x4x4 box at degrees 2, 3, 5 against the oracle")
-    ap.add_argument("--epochs", type=int, default=30, help="learned workload: training epochs")
+    ap.add_argument("--epochs", type=int, default=100, help="learned workload: training epochs (batch 32)")
     ap.add_argument("--members", type=int, default=16, help="ensemble members (first k of the 16)")
     ap.add_argument("--inner-maxit", type=int, default=None, help="override the FP32 GMRES cycle length")
     ap.add_argument("--inner-tol", type=float, default=None, help="override the FP32 GMRES tolerance")
@@ -409,7 +409,7 @@ def run_learned(args):
     t_collect = time.time() - t0
     ntr, nte = dgx.dgx_learned_num_samples(ctx)
     o = dgx.dgx_default_train_opts()
-    o.epochs = args.epochs
+    o.epochs, o.batch = args.epochs, 32  # from a sweep of epochs, batch and rate on this workload
     tinfo = dgx.dgx_learned_train(ctx, o)
     N = dgx.dgx_num_dofs(ctx)
     f64 = torch.float64
