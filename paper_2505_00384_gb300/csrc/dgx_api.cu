@@ -312,6 +312,10 @@ void free_mesh(dgx_ctx *c) {
     c->diag64[i] = c->dinv64[i] = nullptr;
     c->diag32[i] = c->dinv32[i] = nullptr;
   }
+  {
+    c->kq64 = nullptr;
+    c->kq64_version = -1;
+  }
   c->V64 = nullptr;
   c->V32 = nullptr;
   if (c->kry64) cudaFree(c->kry64);
@@ -1089,6 +1093,12 @@ int dgx_set_coefficients(dgx_ctx *c, const double *rho, const double *pk, double
   c->gamma = gamma;
   ++c->coef_version;
   c->diag64_ok = c->diag32_ok = false;  // the Jacobi diagonals follow on first use (ensure_diag)
+  if (c->use_kappa) {  // kappa at the Gauss points for the FP64 k_div
+    if (!c->kq64)
+      if (int e = dalloc(c, &c->kq64, (size_t)c->ncell * c->q * c->q * c->q)) return e;
+    if (int e = launch_kappa<double>(c, c->pk64, c->kq64, c->stream)) return e;
+    c->kq64_version = c->coef_version;
+  }
   if (int e = check_cuda(c, cudaGetLastError(), "set_coefficients")) return e;
   c->has_coef = true;
   return DGX_OK;

@@ -158,6 +158,10 @@ struct dgx_ctx {
   float *diag32[3] = {nullptr, nullptr, nullptr};
   float *dinv32[3] = {nullptr, nullptr, nullptr};
   bool diag64_ok = false, diag32_ok = false;         // valid for the current coefficients
+  // alpha gamma/(gamma-1) p_k at the Q^3 Gauss points (FP64 k_div), with the coefficient version it holds
+  double *kq64 = nullptr;
+  long long kq64_version = -1;
+  bool use_kappa = true;  // ensembles' member contexts (multi-mesh kernels) do without
 
   // operator scratch: V = A^-1 B p (3N)
   double *V64 = nullptr;
@@ -231,6 +235,9 @@ int launch_cmass(dgx_ctx *c, int mode, double scale, const double *f0, const dou
                  cudaStream_t s);
 // forward fast density-weighted mass A(rho) v, 3 components
 int launch_mass_fwd(dgx_ctx *c, const double *rho, const double *v, double *out, cudaStream_t s);
+// kq = alpha gamma/(gamma-1) p_k at the Gauss points of every cell (Q^3 per cell)
+template <typename T>
+int launch_kappa(dgx_ctx *c, const T *pk, T *kq, cudaStream_t s);
 // Helmholtz (dh) and internal-energy (die) diagonals of Sec. 3.1 in precision T
 template <typename T>
 int launch_diag(dgx_ctx *c, const T *rho, const T *pk, T *dh, T *die, cudaStream_t s);

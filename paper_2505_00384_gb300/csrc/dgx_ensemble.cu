@@ -513,6 +513,7 @@ int dgx_ensemble_create(dgx_ensemble **out, int device, void *stream, int n, con
     dgx_ctx *c = nullptr;
     int r = dgx_create(&c, device, e->stream);
     if (r) return fail(eset(e, r, "member %d: context creation failed", m));
+    c->use_kappa = false;  // the multi-mesh kernels interpolate p_k themselves
     e->mem.push_back(c);
     r = dgx_mesh_build(c, &descs[m]);
     if (r) return fail(eset(e, r, "member %d: %s", m, c->err.c_str()));

@@ -281,7 +281,7 @@ __device__ __forceinline__ int div_slot_base(int f) {
 template <typename T, int N, int Q, bool CURVED>
 __device__ __forceinline__ void div_body(const OpP<T> &P, const long long cell, const T *__restrict__ V,
                                          const T *__restrict__ p, const T *__restrict__ pk, T *__restrict__ y,
-                                         long long Ntot, T *sm) {
+                                         long long Ntot, T *sm, const T *__restrict__ kq = nullptr) {
   using L = DivL<N, Q, CURVED>;
   constexpr int N2 = L::N2, N3 = L::N3, Q2 = L::Q2, Q3 = L::Q3, NSL = L::NSL;
   T *tab = sm;
@@ -298,32 +298,37 @@ __device__ __forceinline__ void div_body(const OpP<T> &P, const long long cell, 
   const T zeta0 = T(cp.cz) * P.dz;
 
   load_tables<T, N, Q>(P.tab, tab);
+  // with kq (alpha gamma/(gamma-1) p_k at the Q^3 points of this coefficient set)
+  // the p_k interpolation is skipped: fields V0, V1, V2, p, p_k instead of V0, V1, V2, p_k, p
+  const bool pre = kq != nullptr;
+  const int ip = pre ? 3 : 4, ik = pre ? 4 : 3;
   for (int i = threadIdx.x; i < N3; i += blockDim.x) {
     s_in[0 * N3 + i] = V[0 * Ntot + cell * N3 + i];
     s_in[1 * N3 + i] = V[1 * Ntot + cell * N3 + i];
     s_in[2 * N3 + i] = V[2 * Ntot + cell * N3 + i];
-    s_in[3 * N3 + i] = pk[cell * N3 + i];
-    s_in[4 * N3 + i] = p[cell * N3 + i];
+    s_in[ik * N3 + i] = pk[cell * N3 + i];
+    s_in[ip * N3 + i] = p[cell * N3 + i];
   }
   __syncthreads();
   const T *I = tab + tab_off_I(N, Q), *IT = tab + tab_off_IT(N, Q), *DT = tab + tab_off_DT(N, Q);
   const T *wq = tab + tab_off_wq(N, Q), *gq = tab + tab_off_gq(N, Q);
 
-  sweep<T, N, 0, Q, N, N, N, N, M_I, M_I, M_I>(5, 0u, s_in, R1);
+  const int nfi = pre ? 4 : 5;
+  sweep<T, N, 0, Q, N, N, N, N, M_I, M_I, M_I>(nfi, 0u, s_in, R1);
   __syncthreads();
-  sweep<T, N, 1, Q, N, Q, N, N, M_I, M_I, M_I>(5, 0u, R1, R2);
+  sweep<T, N, 1, Q, N, Q, N, N, M_I, M_I, M_I>(nfi, 0u, R1, R2);
   __syncthreads();
-  sweep<T, N, 2, Q, N, Q, Q, N, M_I, M_I, M_I>(5, 0u, R2, R3);
+  sweep<T, N, 2, Q, N, Q, Q, N, M_I, M_I, M_I>(nfi, 0u, R2, R3);
   __syncthreads();
 
   // -C V volume part: + alpha int kappa V . grad psi  -> F_j = alpha kappa w sum_d adj_{jd} V_d
   //  D P: w det J p / (gamma - 1)
   for (int idx = threadIdx.x; idx < Q3; idx += blockDim.x) {
     const int i = idx % Q, j = (idx / Q) % Q, k = idx / Q2;
-    const T v0 = R3[idx], v1 = R3[Q3 + idx], v2 = R3[2 * Q3 + idx], pkq = R3[3 * Q3 + idx], pq = R3[4 * Q3 + idx];
+    const T v0 = R3[idx], v1 = R3[Q3 + idx], v2 = R3[2 * Q3 + idx], pq = R3[ip * Q3 + idx];
+    const T c0 = pre ? kq[cell * Q3 + idx] : P.alpha * P.gfac * R3[3 * Q3 + idx];
     if (CURVED) {  // weighted metric products from the column table
       const int t = i + Q * j;
-      const T c0 = P.alpha * P.gfac * pkq;
       const T ck = c0 * wq[k], cf = ck * (T(1) - (zeta0 + P.dz * gq[k]) * P.invH);
       R3[idx] = ck * colp[col_off_w(N, Q, 0) + t] * v0;
       R3[Q3 + idx] = ck * colp[col_off_w(N, Q, 1) + t] * v1;
@@ -332,7 +337,7 @@ __device__ __forceinline__ void div_body(const OpP<T> &P, const long long cell, 
       R3[3 * Q3 + idx] = (wq[k] * P.igm1) * colp[col_off_w(N, Q, 5) + t] * pq;
     } else {
       const T w = wq[i] * wq[j] * wq[k];
-      const T c = P.alpha * P.gfac * pkq * w;
+      const T c = c0 * w;
       R3[idx] = c * P.dy * P.dz * v0;
       R3[Q3 + idx] = c * P.dx * P.dz * v1;
       R3[2 * Q3 + idx] = c * P.dx * P.dy * v2;
@@ -359,7 +364,7 @@ __device__ __forceinline__ void div_body(const OpP<T> &P, const long long cell, 
     T v;
     if (side == 0 || nb < 0) {
       const int node = face_node<N>(k, s ? N - 1 : 0, t1, t2);
-      v = field == 0 ? P.gfac * s_in[3 * N3 + node] : s_in[(field - 1) * N3 + node];
+      v = field == 0 ? P.gfac * s_in[ik * N3 + node] : s_in[(field - 1) * N3 + node];
       // slip wall: no normal flux (all traces of this face set to zero)
       if (nb < 0 && (k == 2 || P.bc_lat == 0)) v = T(0);
     } else {
@@ -411,9 +416,32 @@ __device__ __forceinline__ void div_body(const OpP<T> &P, const long long cell, 
 template <typename T, int N, int Q, bool CURVED>
 __global__ void __launch_bounds__(256, min_ctas<T, N>()) k_div(const OpP<T> P, const T *__restrict__ V,
                                                                const T *__restrict__ p, const T *__restrict__ pk,
-                                                               T *__restrict__ y, long long Ntot) {
+                                                               T *__restrict__ y, long long Ntot,
+                                                               const T *__restrict__ kq) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  div_body<T, N, Q, CURVED>(P, blockIdx.x, V, p, pk, y, Ntot, reinterpret_cast<T *>(smraw));
+  div_body<T, N, Q, CURVED>(P, blockIdx.x, V, p, pk, y, Ntot, reinterpret_cast<T *>(smraw), kq);
+}
+
+// kq = alpha gamma/(gamma-1) p_k at the Q^3 Gauss points of every cell (the
+// coefficient part of k_div's volume term, once per coefficient set)
+template <typename T, int N, int Q>
+__global__ void __launch_bounds__(128) k_kappa(const OpP<T> P, const T *__restrict__ pk, T *__restrict__ kq) {
+  constexpr int N2 = N * N, N3 = N * N * N, Q3 = Q * Q * Q;
+  constexpr int TAB = (tab_size(N, Q) + 1) & ~1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *sm = reinterpret_cast<T *>(smraw);
+  T *tab = sm, *s_in = sm + TAB, *R1 = s_in + N3, *R2 = R1 + N2 * Q, *R3 = R2 + N * Q * Q;
+  const long long cell = blockIdx.x;
+  load_tables<T, N, Q>(P.tab, tab);
+  for (int i = threadIdx.x; i < N3; i += blockDim.x) s_in[i] = pk[cell * N3 + i];
+  __syncthreads();
+  sweep<T, N, 0, Q, N, N, N, N, M_I, M_I, M_I>(1, 0u, s_in, R1);
+  __syncthreads();
+  sweep<T, N, 1, Q, N, Q, N, N, M_I, M_I, M_I>(1, 0u, R1, R2);
+  __syncthreads();
+  sweep<T, N, 2, Q, N, Q, Q, N, M_I, M_I, M_I>(1, 0u, R2, R3);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < Q3; idx += blockDim.x) kq[cell * Q3 + idx] = P.alpha * P.gfac * R3[idx];
 }
 
 template <typename T, int N, int Q, bool CURVED>
@@ -606,9 +634,25 @@ int div_impl(dgx_ctx *c, const T *V, const T *p, const T *pk, T *y, cudaStream_t
   if (int e = prep(c, k, smem)) return e;
   OpP<T> P = make_params<T>(c);
   if (alpha >= 0.0) P.alpha = (T)alpha;
+  // the precomputed kappa applies to the context's own p_k and alpha only, and
+  // to FP64 (FP32 interpolates p_k faster than it loads the Q^3 values)
+  const T *kq = nullptr;
+  if constexpr (sizeof(T) == 8)
+    if (alpha < 0.0 && pk == c->pk64 && c->kq64_version == c->coef_version) kq = reinterpret_cast<const T *>(c->kq64);
   count_launch();
-  k<<<(unsigned)c->ncell, op_threads<T>(c, N), smem, s>>>(P, V, p, pk, y, c->N);
+  k<<<(unsigned)c->ncell, op_threads<T>(c, N), smem, s>>>(P, V, p, pk, y, c->N, kq);
   return check_cuda(c, cudaGetLastError(), "k_div launch");
+}
+
+template <typename T, int N, bool CURVED>
+int kappa_impl(dgx_ctx *c, const T *pk, T *kq, cudaStream_t s) {
+  constexpr int Q = 2 * N - 1;
+  const size_t smem = sizeof(T) * (((tab_size(N, Q) + 1) & ~1) + N * N * N + N * N * Q + N * Q * Q + Q * Q * Q);
+  auto k = k_kappa<T, N, Q>;
+  if (int e = prep(c, k, smem)) return e;
+  count_launch();
+  k<<<(unsigned)c->ncell, 128, smem, s>>>(make_params<T>(c), pk, kq);
+  return check_cuda(c, cudaGetLastError(), "k_kappa launch");
 }
 
 template <typename T, int N, bool CURVED>
@@ -710,6 +754,14 @@ int launch_mass_inverse(dgx_ctx *c, const T *in, const T *rho, T *out, cudaStrea
   DGX_DISPATCH(CALL_MINV)
 #undef CALL_MINV
 }
+
+template <typename T>
+int launch_kappa(dgx_ctx *c, const T *pk, T *kq, cudaStream_t s) {
+#define CALL_KAPPA(NN, CC) kappa_impl<T, NN, CC>(c, pk, kq, s)
+  DGX_DISPATCH(CALL_KAPPA)
+#undef CALL_KAPPA
+}
+template int launch_kappa<double>(dgx_ctx *, const double *, double *, cudaStream_t);
 
 template <typename T>
 int launch_diag(dgx_ctx *c, const T *rho, const T *pk, T *dh, T *die, cudaStream_t s) {
