@@ -43,8 +43,9 @@ STEP_EXTRA_HALF_APPLIES = 12
 # DRAM bytes per DoF of one launch of the FP64 operator kernels, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the 48x48x24 r=4 hill mesh
 # (6 912 000 DoFs, inputs larger than L2); one launch reads each cell's data once,
-# so the traffic scales with the DoFs.  Valid for the kernels as captured.
-DRAM_BYTES_PER_DOF_F64 = {"k_div<double>": 333.5e6 / 6912000, "k_grad<double>": 242.7e6 / 6912000}
+# so the traffic scales with the DoFs.  k_div as applied inside the solver (with the
+# per-coefficient-set kappa at the Gauss points).  Valid for the kernels as captured.
+DRAM_BYTES_PER_DOF_F64 = {"k_div<double>": 696.2e6 / 6912000, "k_grad<double>": 252.9e6 / 6912000}
 
 
 def parse():
