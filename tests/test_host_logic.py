@@ -1,0 +1,52 @@
+"""Host-side logic on CPU: seeded inputs, the learned workload's set-up
+helpers, and the benchmark's command line (no GPU, no library calls)."""
+import importlib.util
+import os
+
+import numpy as np
+
+from paper_2505_00384_gb300 import inputs
+from paper_2505_00384_gb300 import learned as LP
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_splitmix64_known_values():
+    """splitmix64 from seed 0: the first outputs of the published generator."""
+    z = inputs.splitmix64(0, 3)
+    assert [int(v) for v in z] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_normal_deviates_are_standard():
+    x = inputs.normal(inputs.DEFAULT_SEED, 200000)
+    assert abs(x.mean()) < 0.01 and abs(x.std() - 1.0) < 0.01
+    assert np.array_equal(x, inputs.normal(inputs.DEFAULT_SEED, 200000))
+
+
+def test_hill_heights_are_seeded_and_in_range():
+    h = LP.hill_heights(16)
+    assert h.shape == (16,) and h.min() >= 200.0 and h.max() <= 800.0
+    assert np.array_equal(h, LP.hill_heights(16)) and not np.array_equal(h, LP.hill_heights(16, seed=7))
+
+
+def test_box_mesh_description():
+    d = LP.box_mesh(450.0)
+    assert (d.nx, d.ny, d.nz, d.degree) == (4, 4, 4, 2)
+    assert d.terrain == 1 and d.bc_lateral == 2 and d.h_c == 450.0
+    assert d.x_c == d.y_c == 500.0 and d.Lx == d.Ly == d.Lz == 1000.0
+
+
+def test_bench_defaults():
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    import sys
+    argv = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        a = bench.parse()
+    finally:
+        sys.argv = argv
+    assert a.gpus == 1 and a.warmup >= 3 and a.workload == "hill" and a.impl == "ours"
+    w = bench.workload(a)
+    assert (w["nx"], w["ny"], w["nz"], w["r"]) == (64, 64, 32, 4) and w["bc_lateral"] == 2
