@@ -54,10 +54,6 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -90,7 +86,7 @@ struct ConvArgs {
   long long in_bs;    // sample stride of the input
   const int *bidx;    // batch slot -> sample of the input (nullptr: slot itself)
   int relu_in;        // input is a pre-activation: apply max(., 0) on load
-  const float *Wf;    // [Ci][27][Co]: the bfloat16 weights widened to FP32, Co fastest
+  const __nv_bfloat16 *W;  // [Ci][27][Co] bfloat16 weights, Co fastest (8-byte aligned rows of 4)
   const float *bias;  // [Co] or nullptr
   float *out;
   long long out_bs;
@@ -114,15 +110,20 @@ __global__ void __launch_bounds__(16 * KS) k_conv(ConvArgs a) {
   const int x0 = tx * kTile - 1, y0 = ty * kTile - 1, z0 = tz * kTile - 1;
   const long long sb = a.bidx ? a.bidx[b] : b;
   stage_halo_points(xs, a.in + sb * a.in_bs, g, a.Ci, x0, y0, z0);
+  // weights: bfloat16 from global, widened to FP32 into [Ci][27][COB] while the halo copies fly
   if constexpr (COB % 4 == 0) {
+#pragma unroll 4
     for (int i = threadIdx.x; i < a.Ci * 27 * (COB / 4); i += blockDim.x) {
       const int row = i / (COB / 4), part = i - row * (COB / 4);  // row = ci * 27 + k
-      cp_async16(ws + row * COB + part * 4, a.Wf + (long long)row * a.Co + co0 + part * 4);
+      const uint2 u = *reinterpret_cast<const uint2 *>(a.W + (long long)row * a.Co + co0 + part * 4);
+      const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
+      const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
+      *reinterpret_cast<float4 *>(ws + row * COB + part * 4) = make_float4(lo.x, lo.y, hi.x, hi.y);
     }
   } else {
     for (int i = threadIdx.x; i < a.Ci * 27 * COB; i += blockDim.x) {
       const int row = i / COB, co = i - row * COB;
-      cp_async4(ws + i, a.Wf + (long long)row * a.Co + co0 + co);
+      ws[i] = __bfloat162float(a.W[(long long)row * a.Co + co0 + co]);
     }
   }
   cp_async_wait_all();
@@ -275,8 +276,7 @@ struct AdamArgs {
   long long stride;  // per-chunk stride of the partials
   const float *part;
   float *grad, *master, *m, *v;  // layer slices (W then b)
-  __nv_bfloat16 *wbf;            // layer weights [Co][Ci][27]
-  float *wf, *wtf;               // widened copies: [Ci][27][Co], and [Co][27][Ci] with flipped taps
+  __nv_bfloat16 *wbf, *wtbf;     // layer weights [Ci][27][Co], and [Co][27][Ci] with flipped taps
   float lr, b1, b2, eps, c1, c2;  // c1 = 1/(1-b1^t), c2 = 1/(1-b2^t)
 };
 
@@ -298,25 +298,22 @@ __global__ void k_adam(AdamArgs a) {
     if (e < nW) {
       const int co = (int)(e / (a.Ci * 27)), ci = (int)((e / 27) % a.Ci), k = (int)(e % 27);
       const __nv_bfloat16 hb = __float2bfloat16_rn(th);
-      const float hf = __bfloat162float(hb);
-      a.wbf[e] = hb;
-      a.wf[((long long)ci * 27 + k) * a.Co + co] = hf;
-      a.wtf[((long long)co * 27 + 26 - k) * a.Ci + ci] = hf;
+      a.wbf[((long long)ci * 27 + k) * a.Co + co] = hb;
+      a.wtbf[((long long)co * 27 + 26 - k) * a.Ci + ci] = hb;
     }
   }
 }
 
-// bfloat16 weights of a layer from its FP32 master copy, and their widened
-// copies in the layouts the convolution kernels stage.
-__global__ void k_round_weights(int Ci, int Co, const float *master, __nv_bfloat16 *wbf, float *wf, float *wtf) {
+// bfloat16 weights of a layer from its FP32 master copy ([co][ci][k] ->
+// [ci][k][co]), and the transposed copy with flipped taps ([co][26-k][ci]) used
+// by the backward-data convolution: the layouts the convolution kernel stages.
+__global__ void k_round_weights(int Ci, int Co, const float *master, __nv_bfloat16 *wbf, __nv_bfloat16 *wtbf) {
   const long long nW = (long long)Co * Ci * 27;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nW; e += (long long)gridDim.x * blockDim.x) {
     const int co = (int)(e / (Ci * 27)), ci = (int)((e / 27) % Ci), k = (int)(e % 27);
     const __nv_bfloat16 hb = __float2bfloat16_rn(master[e]);
-    const float hf = __bfloat162float(hb);
-    wbf[e] = hb;
-    wf[((long long)ci * 27 + k) * Co + co] = hf;
-    wtf[((long long)co * 27 + 26 - k) * Ci + ci] = hf;
+    wbf[((long long)ci * 27 + k) * Co + co] = hb;
+    wtbf[((long long)co * 27 + 26 - k) * Ci + ci] = hb;
   }
 }
 
@@ -483,11 +480,11 @@ struct Learned {
   // network
   int L = 0, C = 0;
   std::vector<int> ci, co;
-  std::vector<long long> poff, woff, foff;  // layer offsets: parameters, bf16 weights, widened copies
-  long long P = 0, nW = 0, nWf = 0;
+  std::vector<long long> poff, woff;  // layer offsets: parameter vector, bf16 weights
+  long long P = 0, nW = 0;
   float *master = nullptr, *am = nullptr, *av = nullptr, *grad = nullptr;
   __nv_bfloat16 *wbf = nullptr;
-  float *wf = nullptr, *wtf = nullptr;
+  __nv_bfloat16 *wtbf = nullptr;
   // CUDA graphs of the apply, per (v, z, type); replayed on a private stream
   struct GraphRec {
     cudaGraphExec_t exec;
@@ -560,10 +557,10 @@ void free_graphs(Learned *m) {
 
 void free_net(Learned *m) {
   free_graphs(m);
-  for (void *p : {(void *)m->master, (void *)m->am, (void *)m->av, (void *)m->grad, (void *)m->wbf, (void *)m->wf,
-                  (void *)m->wtf})
+  for (void *p : {(void *)m->master, (void *)m->am, (void *)m->av, (void *)m->grad, (void *)m->wbf, (void *)m->wtbf})
     if (p) cudaFree(p);
-  m->master = m->am = m->av = m->grad = m->wf = m->wtf = nullptr;
+  m->master = m->am = m->av = m->grad = nullptr;
+  m->wtbf = nullptr;
   m->wbf = nullptr;
   if (m->gev0) cudaEventDestroy(m->gev0);
   if (m->gev1) cudaEventDestroy(m->gev1);
@@ -731,7 +728,7 @@ int net_forward1(dgx_ctx *c, const float *src, float **out) {
     a.in_bs = in_bs;
     a.bidx = nullptr;
     a.relu_in = l > 0;
-    a.Wf = m->wf + m->foff[l];
+    a.W = m->wbf + m->woff[l];
     a.bias = m->master + m->poff[l] + (long long)a.Co * a.Ci * 27;
     a.out = dst;
     a.out_bs = (long long)a.Co * G;
@@ -790,7 +787,7 @@ int batch_forward_loss(dgx_ctx *c, const int *bidx, int B) {
       a.in_bs = (long long)m->co[l - 1] * G;
       a.relu_in = 1;
     }
-    a.Wf = m->wf + m->foff[l];
+    a.W = m->wbf + m->woff[l];
     a.bias = m->master + m->poff[l] + (long long)a.Co * a.Ci * 27;
     a.out = act_of(m, l, B);
     a.out_bs = (long long)a.Co * G;
@@ -839,7 +836,7 @@ int batch_backward(dgx_ctx *c, const int *bidx, int B, bool update, float lr, fl
       a.in = gcur;
       a.in_bs = (long long)m->co[l] * G;
       a.relu_in = 0;
-      a.Wf = m->wtf + m->foff[l];
+      a.W = m->wtbf + m->woff[l];
       a.bias = nullptr;
       a.out = gnext;
       a.out_bs = (long long)m->ci[l] * G;
@@ -859,8 +856,7 @@ int batch_backward(dgx_ctx *c, const int *bidx, int B, bool update, float lr, fl
     ad.m = m->am + m->poff[l];
     ad.v = m->av + m->poff[l];
     ad.wbf = m->wbf + m->woff[l];
-    ad.wf = m->wf + m->foff[l];
-    ad.wtf = m->wtf + m->foff[l];
+    ad.wtbf = m->wtbf + m->woff[l];
     ad.lr = lr;
     ad.b1 = b1;
     ad.b2 = b2;
@@ -1072,11 +1068,9 @@ int dgx_learned_create(dgx_ctx *c, int layers, int channels, unsigned long long 
     m->co.push_back(l == layers - 1 ? 1 : channels);
     m->poff.push_back(m->P);
     m->woff.push_back(m->nW);
-    m->foff.push_back(m->nWf);
     const long long nw = (long long)m->ci[l] * m->co[l] * 27;
     m->P += nw + m->co[l];
-    m->nW += nw;
-    m->nWf += (nw + 3) / 4 * 4;  // 16-byte aligned layers for the staging copies
+    m->nW += (nw + 3) / 4 * 4;  // layers start on 8-byte boundaries (rows of 4 bf16)
   }
   std::vector<float> p((size_t)m->P, 0.f);
   SplitMix rng{seed};
@@ -1087,8 +1081,8 @@ int dgx_learned_create(dgx_ctx *c, int layers, int channels, unsigned long long 
   }
   int e;
   if ((e = dmalloc(c, &m->master, m->P)) || (e = dmalloc(c, &m->am, m->P)) || (e = dmalloc(c, &m->av, m->P)) ||
-      (e = dmalloc(c, &m->grad, m->P)) || (e = dmalloc(c, &m->wbf, m->nW)) || (e = dmalloc(c, &m->wf, m->nWf)) ||
-      (e = dmalloc(c, &m->wtf, m->nWf))) {
+      (e = dmalloc(c, &m->grad, m->P)) || (e = dmalloc(c, &m->wbf, m->nW)) ||
+      (e = dmalloc(c, &m->wtbf, m->nW))) {
     learned_free(c);
     return e;
   }
@@ -1110,7 +1104,7 @@ int dgx_learned_set_params(dgx_ctx *c, const float *host) {
   for (int l = 0; l < m->L; ++l) {
     count_launch();
     k_round_weights<<<blocks_for((long long)m->ci[l] * m->co[l] * 27), 256, 0, c->stream>>>(
-        m->ci[l], m->co[l], m->master + m->poff[l], m->wbf + m->woff[l], m->wf + m->foff[l], m->wtf + m->foff[l]);
+        m->ci[l], m->co[l], m->master + m->poff[l], m->wbf + m->woff[l], m->wtbf + m->woff[l]);
   }
   return check_cuda(c, cudaStreamSynchronize(c->stream), "set parameters");
 }
