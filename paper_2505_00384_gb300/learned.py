@@ -8,7 +8,7 @@ arithmetic step runs in ``libdgx.so``.
 Workload (small-box hill flow): a [0, L]^3 box of nx x ny x nz cells of
 degree r with periodic lateral faces and slip walls at bottom and top, a
 Gal-Chen bell hill h(x, y) = h_c / (1 + ((x - L/2)^2 + (y - L/2)^2) / a_c^2)
-centred in the box (Sec. 4 terrain test, scaled down), isothermal background
+centred in the box (the terrain test of Sec. 3, scaled down), isothermal background
 at 250 K, initial state background plus a uniform wind u_bar along x,
 ARS(2,2,2) steps of dt with K = 2 fixed-point iterations.
 """
