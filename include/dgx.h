@@ -119,7 +119,7 @@ typedef struct {
   int operator_f64;    /* FP64 operator applications                                     */
   int operator_f32;    /* FP32 operator applications                                     */
   int fallback;        /* DGX_PC_LEARNED: 1 if the solve switched to the Helmholtz Jacobi */
-  double relres;       /* final true relative residual in FP64                            */
+  double relres;       /* final relative residual ||b - S x|| / ||b|| in FP64 (see below)  */
   double seconds;      /* wall time of the call                                          */
 } dgx_solve_info;
 
@@ -146,8 +146,10 @@ int dgx_background_fields(dgx_ctx *ctx, double *rho_bar, double *p_bar);
 /* Coefficients of the Schur operator of one fixed-point iteration (Sec. 2):
  * rho_l = rho^(l) (nodal, N doubles), p_k = total pressure of the previous
  * fixed-point iterate (nodal, N doubles), a_dt = a~_ll * dt, gamma.  The
- * library copies both fields (FP64 and FP32 copies) and rebuilds the
- * Helmholtz and internal-energy diagonals (Sec. 3.1). */
+ * library copies both fields (FP64 and FP32 copies) and the coefficient
+ * factor a_dt gamma/(gamma-1) p_k at the Gauss points; the Helmholtz and
+ * internal-energy diagonals (Sec. 3.1) follow on first use (FP64, or FP32
+ * when only the mixed solver's FP32 inner solve needs them). */
 int dgx_set_coefficients(dgx_ctx *ctx, const double *rho_l, const double *p_k, double a_dt, double gamma);
 
 /* y = S x = D x - C A^-1 B x, the matrix-free Schur operator of the
@@ -166,8 +168,12 @@ int dgx_apply_preconditioner(dgx_ctx *ctx, int pc, int prec, const void *x, void
 int dgx_preconditioner_diagonal(dgx_ctx *ctx, int pc, double *d);
 
 /* Solve S x = b (Sec. 3.1) to ||b - S x|| <= tol ||b|| in FP64.  b, x:
- * device, N doubles.  Returns DGX_OK, DGX_NOT_CONVERGED (x holds the last
- * iterate) or an error (DGX_ERR_BREAKDOWN on a NaN or zero Krylov scalar). */
+ * device, N doubles.  FGMRES computes b - S x0 with an FP64 application when
+ * a solve starts (b itself when use_x0 = 0) and, after each restart cycle, as
+ * r0 - sum_j y_j (S z_j) from the FP64 products of that cycle (S is linear).
+ * Returns DGX_OK, DGX_NOT_CONVERGED (x holds the last iterate),
+ * DGX_FALLBACK_USED (DGX_PC_LEARNED only) or an error (DGX_ERR_BREAKDOWN on a
+ * NaN or zero Krylov scalar). */
 int dgx_solve_pressure(dgx_ctx *ctx, const double *b, double *x, const dgx_solve_opts *opts,
                        dgx_solve_info *info);
 
