@@ -108,8 +108,7 @@ typedef struct {
   int inner_maxit;   /* DGX_SOLVER_MIXED: FP32 iterations per outer iteration            */
   double inner_tol;  /* DGX_SOLVER_MIXED: relative tolerance of the FP32 inner solve      */
   int use_x0;        /* 1: x holds the initial guess; 0: start from zero                  */
-  int learned_per_cycle; /* DGX_PC_LEARNED: directions per FGMRES cycle that use the network
-                            (the first ones; the rest use the Helmholtz Jacobi); 0 = all      */
+  int reserved;
 } dgx_solve_opts;
 
 typedef struct {

@@ -660,10 +660,8 @@ int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dg
     bool failed = false;  // learned cycle produced a non-finite direction
     for (int j = 0; j < m; ++j) {
       double *vj = Vb + (size_t)j * N, *zj = Zb + (size_t)j * N;
-      if (use_learned && (o.learned_per_cycle <= 0 || j < o.learned_per_cycle)) {
+      if (use_learned) {
         if ((err = learned_apply<double>(c, vj, zj))) return err;
-      } else if (use_learned) {
-        vec_mul<double>(N, dinv, vj, zj, c->stream);
       } else if (mixed) {
         // z_j ~= S^-1 v_j by FP32 GMRES on the FP32 operator and diagonal
         vec_convert<float, double>(N, vj, io32, c->stream);

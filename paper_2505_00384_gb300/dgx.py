@@ -42,7 +42,7 @@ class dgx_background(C.Structure):
 class dgx_solve_opts(C.Structure):
     _fields_ = [("method", C.c_int), ("pc", C.c_int), ("restart", C.c_int), ("maxit", C.c_int),
                 ("tol", C.c_double), ("inner_restart", C.c_int), ("inner_maxit", C.c_int),
-                ("inner_tol", C.c_double), ("use_x0", C.c_int), ("learned_per_cycle", C.c_int)]
+                ("inner_tol", C.c_double), ("use_x0", C.c_int), ("reserved", C.c_int)]
 
 
 class dgx_step_info(C.Structure):
