@@ -234,10 +234,11 @@ def run_mixed(args):
     IMEX step with mixed solves on the degree-2 box with a centred 400 m hill
     (periodic lateral faces, background + 10 m/s wind + a pressure bump)
     against the oracle's step, error per field.  One step = the three mixed
-    solves; L2 is flushed before every timed solve."""
+    solves; L2 is flushed before every timed solve.  The oracle runs only in the
+    CPU-baseline leg (skipped with --no-cpu-baseline): its solves and step are
+    the timed baseline, and their results give the errors against the oracle."""
     import numpy as np
     import torch
-    import oracle as O
     from paper_2505_00384_gb300 import dgx, inputs
     from paper_2505_00384_gb300 import learned as LP
     torch.cuda.set_device(0)
@@ -255,6 +256,7 @@ def run_mixed(args):
 
     solvers = {"mixed": sopts(dgx.DGX_SOLVER_MIXED, 20), "plain_fp64": sopts(dgx.DGX_SOLVER_FGMRES, 30)}
     degrees, ts_mixed, launches, cpu = [], [], 0, None
+    systems, solutions = [], {}
     for r in (2, 3, 5):
         dgx.dgx_mesh_build(ctx, dgx.mesh_desc(4, 4, 4, r, 1000.0, 1000.0, 1000.0))
         N = dgx.dgx_num_dofs(ctx)
@@ -267,15 +269,7 @@ def run_mixed(args):
         dgx.dgx_node_coords(ctx, X.data_ptr())
         Xh = X.cpu().numpy().reshape(3, N)
         b = inputs.gaussian_bump_rhs(Xh, [500.0, 500.0, 500.0], 200.0, 1e-3, inputs.DEFAULT_SEED)
-        m = O.make_mesh(4, 4, 4, r)
-        if r == 2 and not args.no_cpu_baseline:
-            tc = time.time()
-            _, _, its_o, _ = O.solve(m, A_LL, 1.4, rho.cpu().numpy(), pk.cpu().numpy(), b, tol=1e-8, maxit=3000)
-            t_oracle = time.time() - tc
-        xo = O.solve(m, A_LL, 1.4, rho.cpu().numpy(), pk.cpu().numpy(), b, tol=1e-12, maxit=6000)[0]
-        if r == 2 and not args.no_cpu_baseline:
-            cpu = {"value": t_oracle, "unit": "s/solve", "cores": O.max_threads(), "kind": "oracle",
-                   "sample": "degree-2 box, FP64 FGMRES(30) + Helmholtz Jacobi to 1e-8 (%d iterations)" % its_o}
+        systems.append((r, rho.cpu().numpy(), pk.cpu().numpy(), b))
         bd = torch.from_numpy(b).cuda()
         x = torch.zeros_like(bd)
         row = {"degree": r, "dofs": N}
@@ -299,11 +293,9 @@ def run_mixed(args):
                 if st != dgx.DGX_OK:
                     raise RuntimeError("%s solve at degree %d did not converge" % (name, r))
                 ts.append(e0.elapsed_time(e1) / 1e3)
-            xh = x.cpu().numpy()
+            solutions[(r, name)] = x.cpu().numpy()
             row[name] = {"s_per_solve": statistics.median(ts), "iterations": si.iterations,
-                         "inner_iterations": si.inner_iterations, "relres": si.relres,
-                         "max_rel_err_vs_oracle": float(np.abs(xh - xo).max() / np.abs(xo).max()),
-                         "l2_rel_err_vs_oracle": float(np.linalg.norm(xh - xo) / np.linalg.norm(xo))}
+                         "inner_iterations": si.inner_iterations, "relres": si.relres}
             if name == "mixed":
                 ts_mixed.append(statistics.median(ts))
         degrees.append(row)
@@ -323,28 +315,52 @@ def run_mixed(args):
         e1.record(stream)
         torch.cuda.synchronize()
         te.append(e0.elapsed_time(e1) / 1e3)
-    # one IMEX step with mixed solves against the oracle's step, error per field
+    # one IMEX step with mixed solves on the hill box: background + wind + a 100 Pa bump
     N = LP.setup_hill(ctx, 400.0)
-    L = LP.BOX["L"]
-    m = O.make_mesh(4, 4, 4, 2, Lx=L, Ly=L, Lz=L, terrain=1, hc=400.0, ac=LP.BOX["a_c"], xc=L / 2, yc=L / 2,
-                    bc_lateral=2)
-    obg = O.make_bg(kind=0, T=250.0, ubar=LP.BOX["u_bar"])
-    rb, pb = O.background(m, obg)
-    Xo = O.node_coords(m)
-    bump = np.exp(-((Xo[0] - 500.0) ** 2 + (Xo[1] - 500.0) ** 2 + (Xo[2] - 500.0) ** 2) / (2 * 150.0 ** 2))
-    r0, p0 = rb.copy(), pb + 100.0 * bump
+    rbd = torch.zeros(N, dtype=f64, device="cuda")
+    pbd = torch.zeros_like(rbd)
+    dgx.dgx_background_fields(ctx, rbd.data_ptr(), pbd.data_ptr())
+    X = torch.zeros(3 * N, dtype=f64, device="cuda")
+    dgx.dgx_node_coords(ctx, X.data_ptr())
+    Xh = X.cpu().numpy().reshape(3, N)
+    bump = np.exp(-((Xh[0] - 500.0) ** 2 + (Xh[1] - 500.0) ** 2 + (Xh[2] - 500.0) ** 2) / (2 * 150.0 ** 2))
+    r0, p0 = rbd.cpu().numpy(), pbd.cpu().numpy() + 100.0 * bump
     u0 = np.concatenate([np.full(N, LP.BOX["u_bar"]), np.zeros(N), np.zeros(N)])
     rd, ud, pd = (torch.from_numpy(a.copy()).cuda() for a in (r0, u0, p0))
     so = sopts(dgx.DGX_SOLVER_MIXED, 20)
     st, sinfo = dgx.dgx_imex_step(ctx, rd.data_ptr(), ud.data_ptr(), pd.data_ptr(), 1, so)
-    ro, uo, po, sto, _ = O.imex_step(m, obg, r0, u0, p0, LP.BOX["dt"], K=LP.BOX["K"], tol=1e-11)
     rg, ug, pg = rd.cpu().numpy(), ud.cpu().numpy(), pd.cpu().numpy()
 
-    def rel(a, b, ref):
-        return float(np.abs(a - b).max() / max(np.abs(ref).max(), 1e-300))
+    # CPU-baseline leg: the oracle's solves and step (timed), and the errors against them
+    fields = None
+    if not args.no_cpu_baseline:
+        import oracle as O
+        for r, rho_h, pk_h, b in systems:
+            m = O.make_mesh(4, 4, 4, r)
+            if r == 2:
+                tc = time.time()
+                _, _, its_o, _ = O.solve(m, A_LL, 1.4, rho_h, pk_h, b, tol=1e-8, maxit=3000)
+                cpu = {"value": time.time() - tc, "unit": "s/solve", "cores": O.max_threads(), "kind": "oracle",
+                       "sample": "degree-2 box, FP64 FGMRES(30) + Helmholtz Jacobi to 1e-8 (%d iterations)" % its_o}
+            xo = O.solve(m, A_LL, 1.4, rho_h, pk_h, b, tol=1e-12, maxit=6000)[0]
+            row = next(d for d in degrees if d["degree"] == r)
+            for name in solvers:
+                xh = solutions[(r, name)]
+                row[name]["max_rel_err_vs_oracle"] = float(np.abs(xh - xo).max() / np.abs(xo).max())
+                row[name]["l2_rel_err_vs_oracle"] = float(np.linalg.norm(xh - xo) / np.linalg.norm(xo))
+        L = LP.BOX["L"]
+        m = O.make_mesh(4, 4, 4, 2, Lx=L, Ly=L, Lz=L, terrain=1, hc=400.0, ac=LP.BOX["a_c"], xc=L / 2, yc=L / 2,
+                        bc_lateral=2)
+        obg = O.make_bg(kind=0, T=250.0, ubar=LP.BOX["u_bar"])
+        rb, pb = O.background(m, obg)
+        ro, uo, po, sto, _ = O.imex_step(m, obg, r0, u0, p0, LP.BOX["dt"], K=LP.BOX["K"], tol=1e-11)
 
-    fields = {"rho'": rel(rg, ro, ro - rb), "u": rel(ug[:N], uo[:N], uo[:N]), "v": rel(ug[N:2 * N], uo[N:2 * N], uo),
-              "w": rel(ug[2 * N:], uo[2 * N:], uo), "p'": rel(pg, po, po - pb)}
+        def rel(a, b, ref):
+            return float(np.abs(a - b).max() / max(np.abs(ref).max(), 1e-300))
+
+        fields = {"rho'": rel(rg, ro, ro - rb), "u": rel(ug[:N], uo[:N], uo[:N]),
+                  "v": rel(ug[N:2 * N], uo[N:2 * N], uo), "w": rel(ug[2 * N:], uo[2 * N:], uo),
+                  "p'": rel(pg, po, po - pb)}
     v = ts_mixed[0]
     line = {"metric": "mixed-precision pressure solve s/solve @1e-8 rel residual (4x4x4 box, degree 2)",
             "value": v, "unit": "s/solve", "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
@@ -377,7 +393,6 @@ def run_learned(args):
     preconditioner; L2 is flushed before every timed solve."""
     import numpy as np
     import torch
-    import oracle as O
     from paper_2505_00384_gb300 import dgx, inputs
     from paper_2505_00384_gb300 import learned as LP
     torch.cuda.set_device(0)
@@ -510,6 +525,7 @@ def run_learned(args):
     # CPU baseline: the oracle's plain FGMRES on one held-out system
     cpu = None
     if not args.no_cpu_baseline:
+        import oracle as O
         hi, rec = systems[0]
         rho, pk, b, _, a_dt, gamma = (t if isinstance(t, float) else t.cpu().numpy() for t in LP.split_record(rec, N))
         L = LP.BOX["L"]
