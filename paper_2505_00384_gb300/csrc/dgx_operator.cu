@@ -508,7 +508,7 @@ template <typename T, int N, int Q, bool CURVED>
 __global__ void __launch_bounds__(256) k_diag(const OpP<T> P, const T *__restrict__ rho, const T *__restrict__ pk,
                                               T *__restrict__ dh, T *__restrict__ die) {
   using L = DiagL<N, Q, CURVED>;
-  constexpr int N2 = L::N2, N3 = L::N3, Q2 = L::Q2, Q3 = L::Q3, NF = L::NF;
+  constexpr int N3 = L::N3, Q2 = L::Q2, Q3 = L::Q3, NF = L::NF;
   extern __shared__ __align__(16) unsigned char smraw[];
   T *sm = reinterpret_cast<T *>(smraw);
   T *tab = sm, *s_in = sm + L::oIn, *R1 = sm + L::oR1, *R2 = sm + L::oR2, *R3 = sm + L::oR3, *F = sm + L::oF,
