@@ -146,3 +146,34 @@ def test_pack_roundtrip():
     params = NL.unpack(p, 3, 8)
     assert [W.shape for W, _ in params] == [(8, 5, 3, 3, 3), (8, 8, 3, 3, 3), (1, 8, 3, 3, 3)]
     assert np.array_equal(NL.pack(params), p)
+
+
+def test_network_matches_torch_autograd():
+    """Forward, loss and parameter gradients of the oracle network equal
+    PyTorch's conv3d (zero padding 1, cross-correlation) with autograd in FP64."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(8)
+    shape = (4, 3, 5)
+    params = [(0.3 * rng.standard_normal((4, 5, 3, 3, 3)), 0.1 * rng.standard_normal(4)),
+              (0.3 * rng.standard_normal((4, 4, 3, 3, 3)), 0.1 * rng.standard_normal(4)),
+              (0.3 * rng.standard_normal((1, 4, 3, 3, 3)), 0.1 * rng.standard_normal(1))]
+    B = 2
+    feats = rng.standard_normal((B, 5) + shape)
+    j = rng.standard_normal((B,) + shape)
+    x = rng.standard_normal((B,) + shape)
+    s = np.array([0.8, 1.7])
+    L, grads = NL.loss_and_grad(params, feats, j, s, x)
+    tp = [(torch.tensor(W, requires_grad=True), torch.tensor(b, requires_grad=True)) for W, b in params]
+    h = torch.tensor(feats)
+    for l, (W, b) in enumerate(tp):
+        h = torch.nn.functional.conv3d(h, W, b, padding=1)
+        if l + 1 < len(tp):
+            h = torch.relu(h)
+    c = h[:, 0]
+    e = torch.tensor(j) + torch.tensor(s)[:, None, None, None] * c - torch.tensor(x)
+    Lt = ((e ** 2).sum(dim=(1, 2, 3)) / (torch.tensor(x) ** 2).sum(dim=(1, 2, 3))).mean()
+    Lt.backward()
+    assert abs(float(Lt.detach()) - L) <= 1e-12 * L
+    for (gW, gb), (W, b) in zip(grads, tp):
+        assert np.abs(gW - W.grad.numpy()).max() <= 1e-11 * max(1.0, np.abs(gW).max())
+        assert np.abs(gb - b.grad.numpy()).max() <= 1e-11 * max(1.0, np.abs(gb).max())
