@@ -515,22 +515,41 @@ struct Hess {
 };
 
 // One Arnoldi step on the basis V (columns 0..j) with w = S z_j already in
-// `w`: classical Gram-Schmidt twice.  Fills H column j, normalises V_{j+1}.
-// Returns hn (the subdiagonal) or NaN on error (err set).
+// `w`: classical Gram-Schmidt twice, then v_{j+1} = w / |w| on the device.
+// arnoldi_launch enqueues the kernels and the copy of the 129 scalars to the
+// host; arnoldi_finish waits for that copy only and fills H column j (the
+// next direction may already be in flight behind it).  Returns hn (the
+// subdiagonal) or NaN on error (err set).
 template <typename T>
-double arnoldi(dgx_ctx *c, long long N, int j, T *V, T *w, Hess &H, int *err) {
+int arnoldi_launch(dgx_ctx *c, long long N, int j, T *V, T *w) {
   double *h1 = c->red_out, *h2 = c->red_out + 64, *nrm = c->red_out + 128;
   vec_mdot<T>(N, j + 1, V, N, w, c->red, h1, c->stream);
   vec_mupdate<T>(N, j + 1, V, N, h1, w, c->red, nullptr, c->stream);
   vec_mdot<T>(N, j + 1, V, N, w, c->red, h2, c->stream);
   vec_mupdate<T>(N, j + 1, V, N, h2, w, c->red, nrm, c->stream);
-  *err = fetch(c, 129);
+  if (!c->arn_ev)
+    if (int e = check_cuda(c, cudaEventCreateWithFlags(&c->arn_ev, cudaEventDisableTiming), "event")) return e;
+  if (int e = check_cuda(c, cudaMemcpyAsync(c->host_red, c->red_out, 129 * sizeof(double), cudaMemcpyDeviceToHost,
+                                            c->stream), "memcpy"))
+    return e;
+  if (int e = check_cuda(c, cudaEventRecord(c->arn_ev, c->stream), "event")) return e;
+  vec_scale_by_inv_sqrt<T>(N, nrm, w, V + (size_t)(j + 1) * N, c->stream);
+  return 0;
+}
+
+double arnoldi_finish(dgx_ctx *c, int j, Hess &H, int *err) {
+  *err = check_cuda(c, cudaEventSynchronize(c->arn_ev), "Arnoldi scalars");
   if (*err) return NAN;
   for (int i = 0; i <= j; ++i) H.h(i, j) = c->host_red[i] + c->host_red[64 + i];
   const double hn = std::sqrt(c->host_red[128]);
   H.h(j + 1, j) = hn;
   return hn;
 }
+
+// Meshes small enough that a Krylov iteration is bound by launch and host
+// latency: the next direction is computed while the host waits for the
+// Arnoldi scalars (one wasted operator application when a cycle stops).
+constexpr long long kPipelineDofs = 1LL << 20;
 
 // Inner FP32 GMRES (single cycle of up to `maxit` iterations, zero initial
 // guess, right Jacobi preconditioning): z32 ~= S32^-1 v32.
@@ -551,18 +570,27 @@ int inner_gmres32(dgx_ctx *c, const float *v, float *z, const float *dinv, int m
   vec_scale_by_inv_sqrt<float>(N, c->red_out, v, Vb, c->stream);
   H.g.assign(m + 1, 0.0);
   H.g[0] = beta;
-  int jj = 0;
+  int jj = 0, launched = -1;
+  const bool pipe = N <= kPipelineDofs;
   for (int j = 0; j < m; ++j) {
-    vec_mul<float>(N, dinv, Vb + (size_t)j * N, u, c->stream);
-    if ((err = apply_S<float>(c, u, w))) return err;
-    const double hn = arnoldi<float>(c, N, j, Vb, w, H, &err);
+    if (launched < j) {
+      vec_mul<float>(N, dinv, Vb + (size_t)j * N, u, c->stream);
+      if ((err = apply_S<float>(c, u, w))) return err;
+      launched = j;
+    }
+    if ((err = arnoldi_launch<float>(c, N, j, Vb, w))) return err;
+    if (pipe && j + 1 < m) {  // next direction while the host waits
+      vec_mul<float>(N, dinv, Vb + (size_t)(j + 1) * N, u, c->stream);
+      if ((err = apply_S<float>(c, u, w))) return err;
+      launched = j + 1;
+    }
+    const double hn = arnoldi_finish(c, j, H, &err);
     if (err) return err;
     if (std::isnan(hn)) return set_error(c, DGX_ERR_BREAKDOWN, "inner GMRES: NaN in Arnoldi");
     const double res = H.add_column(j);
     jj = j + 1;
     ++*its;
     if (hn <= 1e-300 || res <= tol * beta) break;
-    vec_scale_by_inv_sqrt<float>(N, c->red_out + 128, w, Vb + (size_t)(j + 1) * N, c->stream);
   }
   H.solve(jj);
   // z = dinv .* (V y)
@@ -656,17 +684,20 @@ int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dg
     vec_scale_by_inv_sqrt<double>(N, c->red_out, w, Vb, c->stream);
     std::fill(H.g.begin(), H.g.end(), 0.0);
     H.g[0] = beta;
-    int jj = 0;
+    int jj = 0, launched = -1;
     bool failed = false;  // learned cycle produced a non-finite direction
-    for (int j = 0; j < m; ++j) {
+    const bool pipe = !mixed && N <= kPipelineDofs;
+    // z_j = M v_j, w = S z_j (kept aside as S z_j, and A^-1 B z_j with Vx)
+    auto direction = [&](int j) -> int {
       double *vj = Vb + (size_t)j * N, *zj = Zb + (size_t)j * N;
+      int e2 = 0;
       if (use_learned) {
         if ((err = learned_apply<double>(c, vj, zj))) return err;
       } else if (mixed) {
         // z_j ~= S^-1 v_j by FP32 GMRES on the FP32 operator and diagonal
         vec_convert<float, double>(N, vj, io32, c->stream);
         int iits = 0;
-        if ((err = inner_gmres32(c, io32, io32, dinv32, o.inner_maxit, o.inner_tol, &iits))) return err;
+        if ((e2 = inner_gmres32(c, io32, io32, dinv32, o.inner_maxit, o.inner_tol, &iits))) return e2;
         info.inner_iterations += iits;
         info.operator_f32 += iits;
         vec_convert<double, float>(N, io32, zj, c->stream);
@@ -675,11 +706,23 @@ int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dg
       } else {
         cudaMemcpyAsync(zj, vj, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
       }
-      if ((err = apply_S<double>(c, zj, w))) return err;
+      if ((e2 = apply_S<double>(c, zj, w))) return e2;
       ++info.operator_f64;
       cudaMemcpyAsync(SZ + (size_t)j * N, w, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
       if (Vx) cudaMemcpyAsync(VZ + (size_t)3 * j * N, c->V64, b3, cudaMemcpyDeviceToDevice, c->stream);
-      const double hn = arnoldi<double>(c, N, j, Vb, w, H, &err);
+      return 0;
+    };
+    for (int j = 0; j < m; ++j) {
+      if (launched < j) {
+        if ((err = direction(j))) return err;
+        launched = j;
+      }
+      if ((err = arnoldi_launch<double>(c, N, j, Vb, w))) return err;
+      if (pipe && j + 1 < m && its + 1 < o.maxit) {  // next direction while the host waits
+        if ((err = direction(j + 1))) return err;
+        launched = j + 1;
+      }
+      const double hn = arnoldi_finish(c, j, H, &err);
       if (err) return err;
       if (use_learned && !std::isfinite(hn)) {
         failed = true;
@@ -691,7 +734,6 @@ int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dg
       ++its;
       jj = j + 1;
       if (hn <= 1e-300) break;  // happy breakdown
-      vec_scale_by_inv_sqrt<double>(N, c->red_out + 128, w, Vb + (size_t)(j + 1) * N, c->stream);
       if (res <= o.tol * bn || its >= o.maxit) break;
     }
     if (!failed) {
@@ -893,6 +935,7 @@ void dgx_destroy(dgx_ctx *c) {
   if (c->red) cudaFree(c->red);
   if (c->red_out) cudaFree(c->red_out);
   if (c->host_red) cudaFreeHost(c->host_red);
+  if (c->arn_ev) cudaEventDestroy(c->arn_ev);
   delete c;
 }
 

@@ -180,6 +180,7 @@ struct dgx_ctx {
   double *red = nullptr;       // reduction partials
   double *red_out = nullptr;   // reduced scalars (device)
   double *host_red = nullptr;  // pinned host mirror
+  cudaEvent_t arn_ev = nullptr;  // marks the Arnoldi scalars' copy to host_red
   size_t red_elems = 0;
 
   // IMEX step: tableaux (s <= 4, row-major), time step, fixed-point iterations
