@@ -115,8 +115,12 @@ typedef struct {
   int status;          /* DGX_OK, DGX_NOT_CONVERGED or DGX_FALLBACK_USED                  */
   int iterations;      /* outer (FP64) Krylov iterations                                 */
   int inner_iterations;/* FP32 iterations (DGX_SOLVER_MIXED)                             */
-  int operator_f64;    /* FP64 operator applications                                     */
-  int operator_f32;    /* FP32 operator applications                                     */
+  int operator_f64;    /* FP64 operator applications, all that ran (on meshes up to 2^20
+                          unknowns, FGMRES applies the operator to the next direction
+                          while the host reads the Arnoldi scalars: one extra
+                          application at the end of each cycle)                          */
+  int operator_f32;    /* FP32 operator applications of the inner iterations (one each;
+                          the inner solve's speculative last one is not counted)         */
   int fallback;        /* DGX_PC_LEARNED: 1 if the solve switched to the Helmholtz Jacobi */
   double relres;       /* final relative residual ||b - S x|| / ||b|| in FP64 (see below)  */
   double seconds;      /* wall time of the call                                          */
