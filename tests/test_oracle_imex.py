@@ -239,3 +239,66 @@ def test_periodic_mass_conservation():
     mass = lambda r: O.apply_A(m, ones, np.concatenate([r, 0 * r, 0 * r]))[:N].sum()
     r, _, _, st, _ = O.imex_step(m, bg, rb, u, pb, 1.0)
     assert st == 0 and abs(mass(r) - mass(rb)) <= 1e-13 * mass(rb) and np.abs(r - rb).max() > 0
+
+
+def test_acoustic_standing_wave_closed_form():
+    """Linear acoustics (g = 0, uniform isothermal state, periodic in x):
+    p' = eps cos(k x) cos(w t), u = eps/(rho0 c) sin(k x) sin(w t) with
+    c^2 = gamma p0 / rho0 is the exact solution of the linearised equations
+    (rho0 u_t = -p'_x, p'_t = -gamma p0 u_x from the energy equation with
+    rho E = p/(gamma-1) + rho k).  The IMEX step converges to it at second
+    order in dt; a wrong enthalpy factor kappa, a flipped pressure-gradient or
+    enthalpy-flux sign, or a wrong velocity recovery changes the wave speed or
+    makes the wave grow."""
+    R, T, gam, p0 = 287.0, 250.0, 1.4, 1e5
+    bg = O.make_bg(kind=0, T=T, p0=p0, R=R, gamma=gam, g=0.0, ubar=0.0)
+    Lx, nx = 1000.0, 16
+    m = O.make_mesh(nx, 1, 1, 3, Lx=Lx, Ly=Lx / nx, Lz=Lx / nx, bc_lateral=2)
+    N = O.ndofs(m)
+    X = O.node_coords(m)
+    rb, pb = O.background(m, bg)
+    rho0 = p0 / (R * T)
+    assert np.allclose(rb, rho0, rtol=1e-15) and np.allclose(pb, p0, rtol=1e-15)
+    c = np.sqrt(gam * p0 / rho0)
+    k = 2 * np.pi / Lx
+    w = c * k
+    eps, t_end = 1.0, 0.8
+    ua = eps / (rho0 * c)
+
+    def errors(dt):
+        r, u, p = rb.copy(), np.zeros(3 * N), pb + eps * np.cos(k * X[0])
+        n = int(round(t_end / dt))
+        for _ in range(n):
+            r, u, p, st, _ = O.imex_step(m, bg, r, u, p, dt, K=2, tol=1e-12)
+            assert st == 0
+        t = n * dt
+        ep = np.abs((p - pb) - eps * np.cos(k * X[0]) * np.cos(w * t)).max() / eps
+        eu = np.abs(u[:N] - ua * np.sin(k * X[0]) * np.sin(w * t)).max() / ua
+        eyz = np.abs(u[N:]).max() / ua
+        return ep, eu, eyz
+
+    e1, e2 = errors(0.1), errors(0.05)  # w dt = 0.20 and 0.10
+    assert e1[0] < 4e-3 and e2[0] < 1e-3, (e1, e2)
+    assert e1[0] / e2[0] > 3.5, (e1, e2)  # second order towards the closed form
+    assert e1[1] < 1e-3 and e2[1] < 1e-3, (e1, e2)
+    assert e1[2] < 1e-8 and e2[2] < 1e-8, (e1, e2)
+
+
+def test_buoyancy_initial_acceleration():
+    """A density anomaly rho' at rest with p' = 0 accelerates vertically at
+    w_t = -g rho' / rho and not horizontally: after one short step,
+    w = -g rho'/rho dt up to the projection of the weak buoyancy term and
+    O(dt^2) (the pressure answers the compression at second order)."""
+    bg = O.make_bg(kind=0, T=250.0, g=G, ubar=0.0)
+    m = O.make_mesh(4, 1, 4, 2, Lx=2000.0, Ly=500.0, Lz=2000.0, bc_lateral=2)
+    N = O.ndofs(m)
+    X = O.node_coords(m)
+    rb, pb = O.background(m, bg)
+    delta = 1e-3 * np.exp(-((X[0] - 1000) ** 2 + (X[2] - 1000) ** 2) / (2 * 300.0 ** 2))
+    dt = 0.01
+    _, u, _, st, _ = O.imex_step(m, bg, rb * (1 + delta), np.zeros(3 * N), pb, dt)
+    assert st == 0
+    wref = -G * delta / (1 + delta) * dt
+    sc = np.abs(wref).max()
+    assert np.abs(u[2 * N:] - wref).max() <= 5e-3 * sc
+    assert np.abs(u[:N]).max() <= 1e-4 * sc and np.abs(u[N:2 * N]).max() <= 1e-12 * sc

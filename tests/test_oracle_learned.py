@@ -85,9 +85,9 @@ def test_backward_matches_finite_differences():
 
 
 def test_grid_map_follows_the_mesh():
-    """Along each grid axis the physical node coordinate is non-decreasing
-    (nodes shared by neighbouring cells appear twice), and the map is a
-    permutation."""
+    """Grid point (k, j, i) holds the node at x_i, y_j, z_k of the lattice of
+    every cell's GLL nodes (nodes shared by neighbouring cells appear twice),
+    and the map is a permutation."""
     m = O.make_mesh(3, 2, 2, 2, Lx=3000.0, Ly=2000.0, Lz=1500.0)
     perm = NL.dof_to_grid_index(3, 2, 2, 2)
     assert np.array_equal(np.sort(perm), np.arange(O.ndofs(m)))
@@ -96,7 +96,11 @@ def test_grid_map_follows_the_mesh():
     gx = NL.to_grid(X[0], shape, perm)
     gy = NL.to_grid(X[1], shape, perm)
     gz = NL.to_grid(X[2], shape, perm)
-    assert np.all(np.diff(gx, axis=2) >= 0) and np.all(np.diff(gy, axis=1) >= 0) and np.all(np.diff(gz, axis=0) >= 0)
+    xn, _ = O.gll(3)
+    lat = lambda nc, L: ((np.arange(nc)[:, None] + xn[None, :]) * L / nc).ravel()
+    assert np.allclose(gx, lat(3, 3000.0)[None, None, :], rtol=0, atol=1e-12)
+    assert np.allclose(gy, lat(2, 2000.0)[None, :, None], rtol=0, atol=1e-12)
+    assert np.allclose(gz, lat(2, 1500.0)[:, None, None], rtol=0, atol=1e-12)
     v = np.random.default_rng(4).standard_normal(O.ndofs(m))
     assert np.array_equal(NL.to_dof(NL.to_grid(v, shape, perm), perm), v)
 
@@ -123,6 +127,13 @@ def test_features_normalisation():
     assert np.all(f[2] == 0) and np.all(f[3] == 0)
     f2, s2 = NL.features(7.5 * v, d, np.full(n, 1.2), np.full(n, 9e4), np.zeros(n), perm, shape)
     assert np.allclose(f2[0], f[0], rtol=1e-14, atol=1e-14) and abs(s2 / s - 7.5) < 1e-13
+    # the diagonal and coefficient channels are invariant to uniform scaling
+    rho, pk = rng.uniform(1.0, 1.3, n), rng.uniform(8e4, 1e5, n)
+    f, _ = NL.features(v, d, rho, pk, np.zeros(n), perm, shape)
+    f3, _ = NL.features(v, 4.0 * d, 2.0 * rho, 0.5 * pk, np.zeros(n), perm, shape)
+    for ch in range(4):
+        assert np.allclose(f3[ch], f[ch], rtol=1e-13, atol=1e-13)
+    assert np.abs(f[1]).max() > 0.1 and np.abs(f[2]).max() > 0.01 and np.abs(f[3]).max() > 0.01
     # a zero network gives the Jacobi preconditioner
     params = [(np.zeros((4, 5, 3, 3, 3)), np.zeros(4)), (np.zeros((1, 4, 3, 3, 3)), np.zeros(1))]
     z = NL.apply_preconditioner(params, v, d, np.full(n, 1.2), np.full(n, 9e4), np.zeros(n), perm, shape)

@@ -195,6 +195,37 @@ def test_B_reproduces_gradient_of_linear_fields(geo, r):
 
 
 @pytest.mark.parametrize("geo", CURVED)
+def test_terrain_following_map(geo):
+    """Node coordinates of the terrain-following mesh: x and y on the uniform
+    lateral grid of each cell's GLL nodes, the bottom surface on the terrain
+    h(x, y), the top flat at Lz, and z affine in the computational vertical
+    coordinate along every vertical node column (the Gal-Chen map)."""
+    import oracle.learned as NL
+    nx, ny, nz, r = 3, 2, 4, 2
+    Lx, Ly, Lz = 3000.0, 2000.0, 1500.0
+    m = O.make_mesh(nx, ny, nz, r, Lx=Lx, Ly=Ly, Lz=Lz, **geo)
+    n = r + 1
+    shape = (nz * n, ny * n, nx * n)
+    perm = NL.dof_to_grid_index(nx, ny, nz, r)
+    Xg = [NL.to_grid(c, shape, perm) for c in O.node_coords(m)]
+    xn, _ = O.gll(n)
+    xs = ((np.arange(nx)[:, None] + xn[None, :]) * Lx / nx).ravel()
+    ys = ((np.arange(ny)[:, None] + xn[None, :]) * Ly / ny).ravel()
+    zeta = ((np.arange(nz)[:, None] + xn[None, :]) * Lz / nz).ravel()
+    assert np.array_equal(Xg[0], np.broadcast_to(xs, shape))
+    assert np.array_equal(Xg[1], np.broadcast_to(ys[None, :, None], shape))
+    h = np.array([[O.terrain_height(m, x, y) for x in xs] for y in ys])
+    assert h.max() > 0.5 * geo["hc"]
+    assert np.abs(Xg[2][0] - h).max() <= 1e-12 * Lz
+    assert np.abs(Xg[2][-1] - Lz).max() <= 1e-12 * Lz
+    # affine in zeta along each column: second differences vanish
+    Z = Xg[2].reshape(shape[0], -1)
+    ok = np.diff(zeta) > 0  # skip the repeated interface nodes
+    slope = (Z[1:] - Z[:-1])[ok] / np.diff(zeta)[ok][:, None]
+    assert np.abs(slope - slope[0]).max() <= 1e-12
+
+
+@pytest.mark.parametrize("geo", CURVED)
 def test_C_is_minus_kappa_B_transpose_on_curved_walls(geo):
     """With uniform kappa and slip walls the weak divergence with central
     fluxes is the negative adjoint of the weak gradient: C = -kappa B^T (cell
@@ -373,6 +404,38 @@ def test_fgmres_matches_dense_solve(geo):
         assert st == 0 and rel <= 1e-12
         assert np.linalg.norm(b - S @ x) <= 1.01e-12 * np.linalg.norm(b)
         assert np.abs(x - xref).max() <= 1e-9 * np.abs(xref).max()
+
+
+@pytest.mark.parametrize("pc", [O.PC_NONE, O.PC_HELMHOLTZ])
+@pytest.mark.parametrize("k", [3, 8])
+def test_fgmres_cycle_minimises_residual_over_krylov_space(pc, k):
+    """One FGMRES cycle of k steps from x = 0 with the fixed right
+    preconditioner M = diag(dinv) returns the x in M K_k(S M, b) that minimises
+    ||b - S x|| (Saad's minimal-residual property); the minimum is computed
+    here by a dense least-squares solve on an orthonormal Krylov basis."""
+    m = O.make_mesh(2, 2, 2, 2, Lx=2000.0, Ly=2000.0, Lz=1500.0, terrain=1, hc=300.0, ac=700.0)
+    N = O.ndofs(m)
+    rng = np.random.default_rng(11)
+    rho = 1.2 * (1 + 0.2 * rng.random(N))
+    pk = 1e5 * (1 + 0.2 * rng.random(N))
+    b = rng.standard_normal(N)
+    S = O.assemble(lambda v: O.apply_S(m, ALPHA, GAMMA, rho, pk, v), N, N)
+    Md = np.ones(N) if pc == O.PC_NONE else 1.0 / O.precond_diag(m, pc, ALPHA, GAMMA, rho, pk)
+    SM = S * Md[None, :]
+    K = [b / np.linalg.norm(b)]
+    for _ in range(k - 1):  # modified Gram-Schmidt, twice
+        w = SM @ K[-1]
+        for _ in range(2):
+            for q in K:
+                w = w - (q @ w) * q
+        K.append(w / np.linalg.norm(w))
+    Q = np.array(K).T
+    y = np.linalg.lstsq(SM @ Q, b, rcond=None)[0]
+    rmin = np.linalg.norm(b - SM @ Q @ y) / np.linalg.norm(b)
+    x, st, its, rel = O.solve(m, ALPHA, GAMMA, rho, pk, b, method="fgmres", pc=pc, tol=1e-14, restart=k, maxit=k)
+    assert st == 1 and its == k
+    assert rmin < 0.9 and abs(rel - rmin) <= 1e-8 * rmin
+    assert np.linalg.norm(x - Md * (Q @ y)) <= 1e-7 * np.linalg.norm(x)
 
 
 def test_cg_matches_dense_solve_spd():
