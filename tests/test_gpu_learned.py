@@ -195,8 +195,8 @@ def _solve(c, b, pc, tol=1e-10, restart=30, maxit=600):
 
 def test_fgmres_with_learned_preconditioner():
     """FGMRES accepts the (untrained, random) network as a variable
-    preconditioner and reaches the oracle's solution; the FP64 residual is
-    the judge."""
+    preconditioner and reaches the oracle's solution; the FP64 residual
+    decides convergence."""
     c = _case(4, 4, 4, 2)
     dgx.dgx_learned_create(c.ctx, 4, 8, SEED)
     dgx.dgx_learned_set_params(c.ctx, _random_params(4, 8, 13, scale=0.5))
