@@ -60,10 +60,12 @@ def parse():
     ap.add_argument("--mesh", default=None, help="NXxNYxNZ cells at the same cell size as the 64x64x32 workload")
     ap.add_argument("--profile", action="store_true",
                     help="only the warm-up and timed steps (for profiler launch lists); no side measurements")
-    ap.add_argument("--workload", default="hill", choices=["hill", "ensemble", "learned", "mixed"],
+    ap.add_argument("--workload", default="hill", choices=["hill", "ensemble", "learned", "mixed", "paper"],
                     help="hill: one IMEX step of the 64x64x32 hill (default); ensemble: 16-member batched solve; "
                          "learned: pressure solves of held-out hill systems with the trained network; "
-                         "mixed: mixed-precision solves on the 4x4x4 box at degrees 2, 3, 5 against the oracle")
+                         "mixed: mixed-precision solves on the 4x4x4 box at degrees 2, 3, 5 against the oracle; "
+                         "paper: the Sec. 3 test case (120x80x32 cells, r = 4, stratified), Helmholtz vs "
+                         "internal-energy Jacobi")
     ap.add_argument("--epochs", type=int, default=100, help="learned workload: training epochs (batch 32)")
     ap.add_argument("--members", type=int, default=16, help="ensemble members (first k of the 16)")
     ap.add_argument("--inner-maxit", type=int, default=None, help="override the FP32 GMRES cycle length")
@@ -381,6 +383,102 @@ def run_mixed(args):
     return 0
 
 
+def run_paper(args):
+    """The test case of Sec. 3 on its uniform mesh: (0, 60) x (0, 40) x (0, 16) km,
+    120 x 80 x 32 cells at degree 4 (38 400 000 DoFs per scalar, 125 m), the -3/2
+    bell hill h_c = 400 m, a_c = 1 km at (30, 20) km, the constant-N background
+    (N = 0.01 1/s, T_ref = 293.15 K, p_ref = 1e5 Pa), u_bar = 10 m/s, far-field
+    lateral faces, slip walls at bottom and top; ARS(2,2,2) with two fixed-point
+    iterations, dt = 1 s.  From the initial state, one IMEX step with plain FP64
+    FGMRES(30) solves to 1e-8 preconditioned by the Helmholtz Jacobi diagonal, the
+    step with the mixed-precision solver, then the step with FP64 FGMRES(30) and the
+    internal-energy (D) diagonal (the comparison of Sec. 3.1).  One line per solver
+    is printed as soon as it is measured, then the summary line."""
+    import torch
+    from paper_2505_00384_gb300 import dgx
+    torch.cuda.set_device(0)
+    dgx.load()
+    stream = torch.cuda.current_stream()
+    ctx = dgx.dgx_create(0, stream.cuda_stream)
+    desc = dgx.mesh_desc(120, 80, 32, 4, 60000.0, 40000.0, 16000.0, terrain=2, h_c=400.0, a_c=1000.0,
+                         x_c=30000.0, y_c=20000.0, bc_lateral=1)
+    t0 = time.perf_counter()
+    dgx.dgx_mesh_build(ctx, desc)
+    N = dgx.dgx_num_dofs(ctx)
+    dgx.dgx_set_background(ctx, dgx.background(kind=1, T=293.15, p0=1e5, N_bv=0.01, R=287.0, gamma=1.4, g=9.81,
+                                               u_bar=10.0))
+    A, At = dgx.ars222()
+    dgx.dgx_set_imex(ctx, A, At, 1.0, 2)
+    f64 = torch.float64
+    rho0 = torch.zeros(N, dtype=f64, device="cuda")
+    p0 = torch.zeros(N, dtype=f64, device="cuda")
+    dgx.dgx_background_fields(ctx, rho0.data_ptr(), p0.data_ptr())
+    u0 = torch.zeros(3 * N, dtype=f64, device="cuda")
+    u0[:N] = 10.0
+    # first applications in each precision (the per-context choice of threads per
+    # CTA runs there), outside the measured steps
+    dgx.dgx_set_coefficients(ctx, rho0.data_ptr(), p0.data_ptr(), A_LL, 1.4)
+    y = torch.empty(N, dtype=f64, device="cuda")
+    dgx.dgx_apply_operator(ctx, dgx.DGX_F64, p0.data_ptr(), y.data_ptr())
+    x32, y32 = p0.float(), torch.empty(N, dtype=torch.float32, device="cuda")
+    dgx.dgx_apply_operator(ctx, dgx.DGX_F32, x32.data_ptr(), y32.data_ptr())
+    del y, x32, y32
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+
+    def opts(method, pc, maxit=3000):
+        o = dgx.dgx_default_solve_opts()
+        o.method, o.pc, o.tol, o.maxit = method, pc, 1e-8, maxit
+        o.restart = 20 if method == dgx.DGX_SOLVER_MIXED else 30
+        o.inner_maxit, o.inner_tol = 25, 3e-6
+        return o
+
+    # the internal-energy solves are capped at 150 iterations each (about 4.5x the
+    # Helmholtz count of the hill workload) to bound the run; a capped solve is
+    # reported as not converged and the saving is then a lower bound
+    runs = [("fgmres_helmholtz", opts(dgx.DGX_SOLVER_FGMRES, dgx.DGX_PC_HELMHOLTZ)),
+            ("mixed_helmholtz", opts(dgx.DGX_SOLVER_MIXED, dgx.DGX_PC_HELMHOLTZ)),
+            ("fgmres_internal_energy", opts(dgx.DGX_SOLVER_FGMRES, dgx.DGX_PC_INTERNAL_ENERGY, 150))]
+    res, pres = {}, {}
+    for name, o in runs:
+        r, u, p = rho0.clone(), u0.clone(), p0.clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, info = dgx.dgx_imex_step(ctx, r.data_ptr(), u.data_ptr(), p.data_ptr(), 1, o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if st != dgx.DGX_OK and name != "fgmres_internal_energy":
+            raise RuntimeError("%s: a pressure solve did not converge (relres %g)" % (name, info.max_relres))
+        pres[name] = p - p0
+        res[name] = {"converged": st == dgx.DGX_OK, "s_per_step": e0.elapsed_time(e1) / 1e3,
+                     "pressure_solve_s": info.seconds_solve,
+                     "solves": info.solves, "krylov_iterations": info.krylov_iterations,
+                     "inner_iterations": info.inner_iterations, "operator_f64": info.operator_f64,
+                     "operator_f32": info.operator_f32, "max_relres": info.max_relres}
+        print(json.dumps({"paper_case_solver": name, **res[name]}), flush=True)
+        del r, u, p
+    ref = pres["fgmres_helmholtz"]
+    sc = float(ref.abs().max().clamp_min(1e-30))
+    for name in pres:
+        res[name]["p_prime_max_rel_diff_vs_fgmres_helmholtz"] = float((pres[name] - ref).abs().max()) / sc
+    h, ie = res["fgmres_helmholtz"], res["fgmres_internal_energy"]
+    out = {"metric": "pressure solve s/step @1e-8 rel residual, Helmholtz vs internal-energy Jacobi",
+           "value": h["pressure_solve_s"], "unit": "s/step", "n_gpus": 1, "steps": 1, "warmup": 0,
+           "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "paper_sec3_120x80x32_r4_38.4M_dofs_stratified", "dofs_per_scalar": N,
+                      "terrain": "-3/2 bell h_c=400 m a_c=1 km at (30, 20) km, Gal-Chen",
+                      "background": "constant N = 0.01 1/s, T_ref = 293.15 K", "lateral": "far field",
+                      "dt_s": 1.0, "setup_s": t_setup},
+           "solvers": res,
+           "helmholtz_time_saving_vs_internal_energy": 1.0 - h["pressure_solve_s"] / ie["pressure_solve_s"],
+           "helmholtz_iteration_ratio_vs_internal_energy": h["krylov_iterations"] / ie["krylov_iterations"],
+           "mixed_speedup_vs_fgmres_helmholtz": h["pressure_solve_s"] / res["mixed_helmholtz"]["pressure_solve_s"]}
+    print(json.dumps(out), flush=True)
+    dgx.dgx_destroy(ctx)
+    return 0
+
+
 def run_learned(args):
     """Learned preconditioner: 400 pressure systems recorded along IMEX
     trajectories over 16 seeded hills (h_c ~ U[200, 800] m, 25 steps each, the
@@ -690,6 +788,8 @@ def main():
         return run_learned(args)
     if args.workload == "mixed":
         return run_mixed(args)
+    if args.workload == "paper":
+        return run_paper(args)
 
     import torch
     from paper_2505_00384_gb300 import dgx
