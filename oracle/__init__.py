@@ -101,18 +101,23 @@ def apply_B(m, alpha, p):
     return out
 
 
-def apply_A(m, rho, V):
+def _mass(m, rho, V, inverse, consistent):
     out = np.zeros(3 * ndofs(m))
-    assert lib().orc_apply_A(C.byref(m), _dp(np.ascontiguousarray(rho, dtype=np.float64)),
-                             _dp(np.ascontiguousarray(V, dtype=np.float64)), _dp(out)) == 0
-    return out
-
-
-def apply_Ainv(m, rho, V):
-    out = np.zeros(3 * ndofs(m))
-    assert lib().orc_apply_Ainv(C.byref(m), _dp(np.ascontiguousarray(rho, dtype=np.float64)),
+    assert lib().orc_apply_mass(C.byref(m), int(bool(consistent)), int(inverse),
+                                _dp(np.ascontiguousarray(rho, dtype=np.float64)),
                                 _dp(np.ascontiguousarray(V, dtype=np.float64)), _dp(out)) == 0
     return out
+
+
+def apply_A(m, rho, V, consistent=False):
+    """Density-weighted mass A_rho V (3 components); the r+1 point rule of the
+    fast inverse, or the consistent 2r+1 point rule with ``consistent``."""
+    return _mass(m, rho, V, 0, consistent)
+
+
+def apply_Ainv(m, rho, V, consistent=False):
+    """A_rho^-1 V with the same choice of rule as apply_A."""
+    return _mass(m, rho, V, 1, consistent)
 
 
 def apply_C(m, alpha, gamma, pk, V):
@@ -133,20 +138,22 @@ def apply_D(m, gamma, p):
     return apply_M(m, p, 1.0 / (gamma - 1.0))
 
 
-def apply_S(m, alpha, gamma, rho, pk, p, cells=None):
+def apply_S(m, alpha, gamma, rho, pk, p, cells=None, consistent=False):
     """y = S p = D p - C A^-1 B p.  With ``cells`` (indices), only those
-    cells' entries are computed; the rest of y is NaN."""
+    cells' entries are computed; the rest of y is NaN.  ``consistent``: A with
+    the 2r+1 point rule instead of the fast inverse's r+1 points."""
     N = ndofs(m)
     y = np.zeros(N)
-    args = [C.byref(m), C.c_double(alpha), C.c_double(gamma), _dp(np.ascontiguousarray(rho, dtype=np.float64)),
-            _dp(np.ascontiguousarray(pk, dtype=np.float64)), _dp(np.ascontiguousarray(p, dtype=np.float64))]
+    args = [C.byref(m), int(bool(consistent)), C.c_double(alpha), C.c_double(gamma),
+            _dp(np.ascontiguousarray(rho, dtype=np.float64)), _dp(np.ascontiguousarray(pk, dtype=np.float64)),
+            _dp(np.ascontiguousarray(p, dtype=np.float64))]
     if cells is None:
-        assert lib().orc_apply_S_masked(*args, None, _dp(y)) == 0
+        assert lib().orc_apply_S_rule(*args, None, _dp(y)) == 0
         return y
     y[:] = np.nan
     mask = np.zeros(m.nx * m.ny * m.nz, dtype=np.uint8)
     mask[np.asarray(cells)] = 1
-    assert lib().orc_apply_S_masked(*args, mask.ctypes.data_as(C.c_void_p), _dp(y)) == 0
+    assert lib().orc_apply_S_rule(*args, mask.ctypes.data_as(C.c_void_p), _dp(y)) == 0
     return y
 
 
@@ -161,8 +168,10 @@ def precond_diag(m, kind, alpha, gamma, rho, pk):
     return d
 
 
-def solve(m, alpha, gamma, rho, pk, b, method="fgmres", pc=PC_HELMHOLTZ, tol=1e-10, restart=30, maxit=1000, x0=None):
-    """Solve S x = b.  Returns (x, status, iterations, relative residual)."""
+def solve(m, alpha, gamma, rho, pk, b, method="fgmres", pc=PC_HELMHOLTZ, tol=1e-10, restart=30, maxit=1000, x0=None,
+          consistent=False):
+    """Solve S x = b.  Returns (x, status, iterations, relative residual).
+    ``consistent`` (FGMRES only): S with the 2r+1 point rule for A."""
     N = ndofs(m)
     x = np.zeros(N) if x0 is None else np.array(x0, dtype=np.float64)
     rho = np.ascontiguousarray(rho, dtype=np.float64)
@@ -175,9 +184,12 @@ def solve(m, alpha, gamma, rho, pk, b, method="fgmres", pc=PC_HELMHOLTZ, tol=1e-
     rel = C.c_double(0.0)
     dptr = _dp(dinv) if dinv is not None else None
     if method == "fgmres":
-        st = lib().orc_fgmres(C.byref(m), C.c_double(alpha), C.c_double(gamma), _dp(rho), _dp(pk), dptr, _dp(b),
-                              _dp(x), C.c_double(tol), restart, maxit, C.byref(its), C.byref(rel))
+        st = lib().orc_fgmres_rule(C.byref(m), int(bool(consistent)), C.c_double(alpha), C.c_double(gamma),
+                                   _dp(rho), _dp(pk), dptr, _dp(b), _dp(x), C.c_double(tol), restart, maxit,
+                                   C.byref(its), C.byref(rel))
     elif method == "cg":
+        if consistent:
+            raise ValueError("CG runs with the fast inverse only")
         st = lib().orc_cg(C.byref(m), C.c_double(alpha), C.c_double(gamma), _dp(rho), _dp(pk), dptr, _dp(b),
                           _dp(x), C.c_double(tol), maxit, C.byref(its), C.byref(rel))
     else:
@@ -261,8 +273,10 @@ def ars222():
     return A, At
 
 
-def imex_step(m, bg, rho, u, p, dt, A=None, At=None, K=2, tol=1e-12):
-    """One IMEX step; returns (rho, u, p, status, Krylov iterations)."""
+def imex_step(m, bg, rho, u, p, dt, A=None, At=None, K=2, tol=1e-12, consistent=False):
+    """One IMEX step; returns (rho, u, p, status, Krylov iterations).
+    ``consistent``: every density-weighted mass and inverse with the 2r+1
+    point rule instead of the fast inverse's r+1 points (Sec. 3.3)."""
     if A is None:
         A, At = ars222()
     A = np.ascontiguousarray(A, dtype=np.float64)
@@ -271,6 +285,6 @@ def imex_step(m, bg, rho, u, p, dt, A=None, At=None, K=2, tol=1e-12):
     v = np.array(u, dtype=np.float64)
     q = np.array(p, dtype=np.float64)
     its = C.c_int(0)
-    st = lib().orc_imex_step(C.byref(m), C.byref(bg), A.shape[0], _dp(A), _dp(At), C.c_double(dt), int(K),
-                             C.c_double(tol), _dp(r), _dp(v), _dp(q), C.byref(its))
+    st = lib().orc_imex_step_rule(C.byref(m), int(bool(consistent)), C.byref(bg), A.shape[0], _dp(A), _dp(At),
+                                  C.c_double(dt), int(K), C.c_double(tol), _dp(r), _dp(v), _dp(q), C.byref(its))
     return r, v, q, st, its.value

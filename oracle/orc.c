@@ -165,15 +165,19 @@ static void cell_B(const orc_mesh *m, const tabs *T, const cgeo *G, long cell, d
   for (int i = 0; i < 3 * n3; ++i) out[i] *= alpha;
 }
 
-/* Dense density-weighted mass of one cell with the r+1 point Gauss rule,
- * A_ij = sum_q rho(x_q) psi_i(x_q) psi_j(x_q) w_q det J(x_q). */
-static void cell_A_matrix(const tabs *T, const cgeo *G, long cell, const double *rho, double *A) {
+/* Dense density-weighted mass of one cell,
+ * A_ij = sum_q rho(x_q) psi_i(x_q) psi_j(x_q) w_q det J(x_q),
+ * with the r+1 point Gauss rule of the fast inverse (consistent = 0, Sec. 3.3)
+ * or the consistent 2r+1 point rule of the other integrals (consistent = 1,
+ * the integration the fast inverse replaces). */
+static void cell_A_matrix(const tabs *T, const cgeo *G, long cell, const double *rho, double *A, int consistent) {
   int n3 = T->n3;
+  int nq = consistent ? T->q3 : n3;
   const double *rc = rho + cell * n3;
   memset(A, 0, sizeof(double) * n3 * n3);
-  for (int qp = 0; qp < n3; ++qp) {
-    const double *ps = T->psia + (size_t)qp * n3;
-    double c = dotn(n3, rc, ps) * G->wdeta[qp];
+  for (int qp = 0; qp < nq; ++qp) {
+    const double *ps = (consistent ? T->psi : T->psia) + (size_t)qp * n3;
+    double c = dotn(n3, rc, ps) * (consistent ? G->wdet[qp] : G->wdeta[qp]);
     for (int i = 0; i < n3; ++i)
       for (int j = 0; j < n3; ++j) A[i * n3 + j] += c * ps[i] * ps[j];
   }
@@ -289,8 +293,10 @@ int orc_apply_B(const orc_mesh *m, double alpha, const double *p, double *out) {
   return 0;
 }
 
-/* inverse = 0: out = A_rho in ; inverse = 1: out = A_rho^-1 in (per component). */
-static int apply_A_impl(const orc_mesh *m, const double *rho, const double *in, double *out, int inverse) {
+/* inverse = 0: out = A_rho in ; inverse = 1: out = A_rho^-1 in (per component);
+ * consistent selects the quadrature of A_rho (see cell_A_matrix). */
+static int apply_A_impl(const orc_mesh *m, const double *rho, const double *in, double *out, int inverse,
+                        int consistent) {
   orc_setup S;
   if (setup(&S, m)) return -1;
   int n3 = S.T.n3;
@@ -303,7 +309,7 @@ static int apply_A_impl(const orc_mesh *m, const double *rho, const double *in, 
 #pragma omp for schedule(dynamic, 4)
     for (long c = 0; c < S.nc; ++c) {
       cell_geometry(m, &S.T, c, &G);
-      cell_A_matrix(&S.T, &G, c, rho, A);
+      cell_A_matrix(&S.T, &G, c, rho, A, consistent);
       for (int d = 0; d < 3; ++d) memcpy(B + d * n3, in + d * S.N + c * n3, sizeof(double) * n3);
       if (inverse) {
         if (lu_solve(n3, A, 3, B)) err = -2;
@@ -326,10 +332,15 @@ static int apply_A_impl(const orc_mesh *m, const double *rho, const double *in, 
 }
 
 int orc_apply_A(const orc_mesh *m, const double *rho, const double *in, double *out) {
-  return apply_A_impl(m, rho, in, out, 0);
+  return apply_A_impl(m, rho, in, out, 0, 0);
 }
 int orc_apply_Ainv(const orc_mesh *m, const double *rho, const double *in, double *out) {
-  return apply_A_impl(m, rho, in, out, 1);
+  return apply_A_impl(m, rho, in, out, 1, 0);
+}
+/* A_rho or its inverse with either quadrature (consistent = 1: 2r+1 points). */
+int orc_apply_mass(const orc_mesh *m, int consistent, int inverse, const double *rho, const double *in,
+                   double *out) {
+  return apply_A_impl(m, rho, in, out, inverse, consistent);
 }
 
 int orc_apply_C(const orc_mesh *m, double alpha, double gamma, const double *pk, const double *V, double *out) {
@@ -371,9 +382,10 @@ int orc_apply_M(const orc_mesh *m, double scale, const double *f, double *out) {
 
 /* y = S P = D P - C A^-1 B P on the cells flagged in mask (all cells when
  * mask is NULL); y is left untouched elsewhere.  Needs V = A^-1 B P on the
- * flagged cells and on their face neighbours. */
-int orc_apply_S_masked(const orc_mesh *m, double alpha, double gamma, const double *rho, const double *pk,
-                       const double *p, const unsigned char *mask, double *y) {
+ * flagged cells and on their face neighbours.  consistent selects the
+ * quadrature of A (see cell_A_matrix). */
+int orc_apply_S_rule(const orc_mesh *m, int consistent, double alpha, double gamma, const double *rho,
+                     const double *pk, const double *p, const unsigned char *mask, double *y) {
   orc_setup S;
   if (setup(&S, m)) return -1;
   int n3 = S.T.n3;
@@ -400,7 +412,7 @@ int orc_apply_S_masked(const orc_mesh *m, double alpha, double gamma, const doub
       if (!need[c]) continue;
       cell_geometry(m, &S.T, c, &G);
       cell_B(m, &S.T, &G, c, alpha, p, B);
-      cell_A_matrix(&S.T, &G, c, rho, A);
+      cell_A_matrix(&S.T, &G, c, rho, A, consistent);
       if (lu_solve(n3, A, 3, B)) err = -2;
       for (int d = 0; d < 3; ++d) memcpy(V + d * N + c * n3, B + d * n3, sizeof(double) * n3);
     }
@@ -419,9 +431,14 @@ int orc_apply_S_masked(const orc_mesh *m, double alpha, double gamma, const doub
   return err;
 }
 
+int orc_apply_S_masked(const orc_mesh *m, double alpha, double gamma, const double *rho, const double *pk,
+                       const double *p, const unsigned char *mask, double *y) {
+  return orc_apply_S_rule(m, 0, alpha, gamma, rho, pk, p, mask, y);
+}
+
 int orc_apply_S(const orc_mesh *m, double alpha, double gamma, const double *rho, const double *pk,
                 const double *p, double *y) {
-  return orc_apply_S_masked(m, alpha, gamma, rho, pk, p, NULL, y);
+  return orc_apply_S_rule(m, 0, alpha, gamma, rho, pk, p, NULL, y);
 }
 
 /* Jacobi diagonal (Sec. 3.1):
@@ -482,10 +499,11 @@ typedef struct {
   const orc_mesh *m;
   double alpha, gamma;
   const double *rho, *pk;
+  int consistent;  /* quadrature of A in S */
 } sctx;
 
 static void S_apply(const sctx *c, const double *x, double *y) {
-  orc_apply_S(c->m, c->alpha, c->gamma, c->rho, c->pk, x, y);
+  orc_apply_S_rule(c->m, c->consistent, c->alpha, c->gamma, c->rho, c->pk, x, NULL, y);
 }
 
 /* Flexible GMRES(restart), right preconditioned by the diagonal scaling
@@ -493,10 +511,10 @@ static void S_apply(const sctx *c, const double *x, double *y) {
  * Convergence: true residual ||b - S x|| / ||b|| <= tol, checked at every
  * restart (the Arnoldi estimate ends a cycle early).  Returns 0 converged,
  * 1 not converged within maxit, <0 error. */
-int orc_fgmres(const orc_mesh *m, double alpha, double gamma, const double *rho, const double *pk,
-               const double *dinv, const double *b, double *x, double tol, int restart, int maxit,
-               int *its_out, double *relres_out) {
-  sctx c = {m, alpha, gamma, rho, pk};
+int orc_fgmres_rule(const orc_mesh *m, int consistent, double alpha, double gamma, const double *rho,
+                    const double *pk, const double *dinv, const double *b, double *x, double tol, int restart,
+                    int maxit, int *its_out, double *relres_out) {
+  sctx c = {m, alpha, gamma, rho, pk, consistent};
   long N = orc_num_cells(m) * (long)(m->r + 1) * (m->r + 1) * (m->r + 1);
   int mm = restart;
   double *Vb = malloc(sizeof(double) * N * (mm + 1));
@@ -575,12 +593,18 @@ done:
   return status;
 }
 
+int orc_fgmres(const orc_mesh *m, double alpha, double gamma, const double *rho, const double *pk,
+               const double *dinv, const double *b, double *x, double tol, int restart, int maxit,
+               int *its_out, double *relres_out) {
+  return orc_fgmres_rule(m, 0, alpha, gamma, rho, pk, dinv, b, x, tol, restart, maxit, its_out, relres_out);
+}
+
 /* Preconditioned conjugate gradients (for the symmetric positive definite
  * case); same stopping rule on the true recursive residual. */
 int orc_cg(const orc_mesh *m, double alpha, double gamma, const double *rho, const double *pk,
            const double *dinv, const double *b, double *x, double tol, int maxit, int *its_out,
            double *relres_out) {
-  sctx c = {m, alpha, gamma, rho, pk};
+  sctx c = {m, alpha, gamma, rho, pk, 0};
   long N = orc_num_cells(m) * (long)(m->r + 1) * (m->r + 1) * (m->r + 1);
   double *r = malloc(sizeof(double) * N), *z = malloc(sizeof(double) * N);
   double *p = malloc(sizeof(double) * N), *q = malloc(sizeof(double) * N);

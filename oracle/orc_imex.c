@@ -31,15 +31,15 @@
 
 /* defined in orc.c */
 int orc_apply_B(const orc_mesh *m, double alpha, const double *p, double *out);
-int orc_apply_A(const orc_mesh *m, const double *rho, const double *in, double *out);
-int orc_apply_Ainv(const orc_mesh *m, const double *rho, const double *in, double *out);
 int orc_apply_C(const orc_mesh *m, double alpha, double gamma, const double *pk, const double *V, double *out);
 int orc_apply_M(const orc_mesh *m, double scale, const double *f, double *out);
 int orc_precond_diag(const orc_mesh *m, int kind, double alpha, double gamma, const double *rho, const double *pk,
                      double *dg);
-int orc_fgmres(const orc_mesh *m, double alpha, double gamma, const double *rho, const double *pk,
-               const double *dinv, const double *b, double *x, double tol, int restart, int maxit, int *its_out,
-               double *relres_out);
+int orc_apply_mass(const orc_mesh *m, int consistent, int inverse, const double *rho, const double *in,
+                   double *out);
+int orc_fgmres_rule(const orc_mesh *m, int consistent, double alpha, double gamma, const double *rho,
+                    const double *pk, const double *dinv, const double *b, double *x, double tol, int restart,
+                    int maxit, int *its_out, double *relres_out);
 
 typedef struct {
   int kind;   /* 0 isothermal, 1 constant buoyancy frequency (Sec. 3) */
@@ -230,10 +230,14 @@ static void implicit_terms(const orc_mesh *m, const orc_bg *b, long N, const dou
 /* One IMEX step of the stage equations (Sec. 2) in place on (rho, u, p).
  * A, At: s x s row-major tableaux (explicit, implicit); dt; K fixed-point
  * iterations per implicit stage; each linear solve by FGMRES(30) with the
- * Helmholtz preconditioner to relative tolerance `tol`.  Returns 0 or the
- * first nonzero solver status; *total_its = Krylov iterations. */
-int orc_imex_step(const orc_mesh *m, const orc_bg *b, int s, const double *A, const double *At, double dt, int K,
-                  double tol, double *rho, double *u, double *p, int *total_its) {
+ * Helmholtz preconditioner to relative tolerance `tol`.  consistent selects
+ * the quadrature of every density-weighted mass and its inverse: 0 the r+1
+ * point rule of the fast inverse, 1 the consistent 2r+1 point rule (Sec. 3.3).
+ * Returns 0 or the first nonzero solver status; *total_its = Krylov
+ * iterations. */
+int orc_imex_step_rule(const orc_mesh *m, int consistent, const orc_bg *b, int s, const double *A,
+                       const double *At, double dt, int K, double tol, double *rho, double *u, double *p,
+                       int *total_its) {
   long N = orc_num_cells(m) * (long)(m->r + 1) * (m->r + 1) * (m->r + 1);
   double gm = b->gamma;
   /* per-stage tendencies: Erho, Em(3), Ee, Im(3), Ie = 9 N each */
@@ -264,10 +268,10 @@ int orc_imex_step(const orc_mesh *m, const orc_bg *b, int s, const double *A, co
         const double *E = Ten + (size_t)9 * N * mm;
         for (long i = 0; i < N; ++i) t1[i] += dt * A[l * s + mm] * E[i];
       }
-      orc_apply_Ainv(m, ones, t1, t2);
+      orc_apply_mass(m, consistent, 1, ones, t1, t2);
       for (long i = 0; i < N; ++i) rl[i] = rn[i] + t2[i];
       /* F static: A(rho^n) u^n + dt sum (a Em + a~ Im) + al int rho'^(l) g.phi */
-      orc_apply_A(m, rn, un, Fs);
+      orc_apply_mass(m, consistent, 0, rn, un, Fs);
       for (int mm = 0; mm < l; ++mm) {
         const double *E = Ten + (size_t)9 * N * mm;
         for (long i = 0; i < 3 * N; ++i) Fs[i] += dt * (A[l * s + mm] * E[N + i] + At[l * s + mm] * E[5 * N + i]);
@@ -289,18 +293,18 @@ int orc_imex_step(const orc_mesh *m, const orc_bg *b, int s, const double *A, co
         for (int k = 0; k < K; ++k) {
           orc_kinetic_mass(m, rl, ul, t2);
           for (long i = 0; i < N; ++i) rhs[i] = Gs[i] - t2[i];
-          orc_apply_Ainv(m, rl, Fs, W);
+          orc_apply_mass(m, consistent, 1, rl, Fs, W);
           orc_apply_C(m, al, gm, pl, W, t2);
           for (long i = 0; i < N; ++i) rhs[i] -= t2[i];
           orc_precond_diag(m, 1, al, gm, rl, pl, dinv);
           for (long i = 0; i < N; ++i) { dinv[i] = 1.0 / dinv[i]; x[i] = pl[i] - pb[i]; }
           int its = 0;
           double rel = 0.0;
-          int st = orc_fgmres(m, al, gm, rl, pl, dinv, rhs, x, tol, 30, 2000, &its, &rel);
+          int st = orc_fgmres_rule(m, consistent, al, gm, rl, pl, dinv, rhs, x, tol, 30, 2000, &its, &rel);
           if (st && !status) status = st;
           its_sum += its;
           orc_apply_B(m, al, x, t1);
-          orc_apply_Ainv(m, rl, t1, t2);
+          orc_apply_mass(m, consistent, 1, rl, t1, t2);
           for (long i = 0; i < 3 * N; ++i) ul[i] = W[i] - t2[i];
           for (long i = 0; i < N; ++i) pl[i] = pb[i] + x[i];
         }
@@ -321,4 +325,9 @@ int orc_imex_step(const orc_mesh *m, const orc_bg *b, int s, const double *A, co
   free(Ten); free(rb); free(pb); free(rn); free(un); free(pn); free(rl); free(ul); free(pl);
   free(Fs); free(Gs); free(W); free(rhs); free(x); free(t1); free(t2); free(dinv); free(ones);
   return status;
+}
+
+int orc_imex_step(const orc_mesh *m, const orc_bg *b, int s, const double *A, const double *At, double dt, int K,
+                  double tol, double *rho, double *u, double *p, int *total_its) {
+  return orc_imex_step_rule(m, 0, b, s, A, At, dt, K, tol, rho, u, p, total_its);
 }

@@ -76,10 +76,10 @@ C_MUTANTS = [
      [(I.test_mass_conservation_of_explicit_tendency, ())]),
     ("buoyancy of the stage with the wrong sign", "orc_imex.c",
      "orc_apply_M(m, -b->g * al, t1, t2);", "orc_apply_M(m, b->g * al, t1, t2);",
-     [(I.test_buoyancy_initial_acceleration, ())]),
+     [(I.test_buoyancy_initial_acceleration, (False,))]),
     ("velocity recovery with the wrong sign", "orc_imex.c",
      "ul[i] = W[i] - t2[i];", "ul[i] = W[i] + t2[i];",
-     [(I.test_buoyancy_initial_acceleration, ()), (I.test_acoustic_standing_wave_closed_form, ())]),
+     [(I.test_buoyancy_initial_acceleration, (False,)), (I.test_acoustic_standing_wave_closed_form, ())]),
 ]
 
 PY_MUTANTS = [

@@ -334,6 +334,55 @@ def test_fast_mass_aliasing_for_variable_density():
     Ma = np.array([[sum(w[k] * (1 + g[k] ** 2) * O.lagrange(np.array([0, .5, 1.]), g[k])[0][a]
                         * O.lagrange(np.array([0, .5, 1.]), g[k])[0][b] for k in range(3)) for b in range(3)] for a in range(3)])
     assert np.abs(A - _k3(Ma, M1, M1)).max() <= 1e-13 * np.abs(exact).max()
+    # the consistent 2r+1 point rule integrates the degree-3r integrand exactly
+    Ac = O.assemble(lambda v: O.apply_A(m, rho, v, consistent=True), 3 * N, 3 * N)[:N, :N]
+    assert np.abs(Ac - exact).max() <= 1e-13 * np.abs(exact).max()
+
+
+@pytest.mark.parametrize("geo", [dict(terrain=0)] + CURVED)
+def test_consistent_mass_and_its_inverse(geo):
+    """The consistent density-weighted mass (2r+1 points, the integration the
+    fast inverse replaces, Sec. 3.3) is the mass matrix M for rho = 1 on
+    curved cells, is symmetric positive definite for positive rho, and its
+    inverse inverts it; the fast (r+1 point) mass differs from it on curved
+    cells (aliasing of the metric) and for variable rho."""
+    m = O.make_mesh(2, 1, 2, 2, Lx=2000.0, Ly=1000.0, Lz=1500.0, **geo)
+    N = O.ndofs(m)
+    one = np.ones(N)
+    Mfull = O.assemble(lambda v: O.apply_M(m, v), N, N)
+    A1 = O.assemble(lambda v: O.apply_A(m, one, v, consistent=True), 3 * N, 3 * N)
+    for d in range(3):
+        assert np.abs(A1[d * N:(d + 1) * N, d * N:(d + 1) * N] - Mfull).max() <= 1e-13 * np.abs(Mfull).max()
+    rng = np.random.default_rng(12)
+    rho = 1.2 * (1 + 0.3 * rng.random(N))
+    A = O.assemble(lambda v: O.apply_A(m, rho, v, consistent=True), 3 * N, 3 * N)[:N, :N]
+    assert np.abs(A - A.T).max() <= 1e-13 * np.abs(A).max() and np.linalg.eigvalsh(A).min() > 0
+    v = rng.standard_normal(3 * N)
+    back = O.apply_A(m, rho, O.apply_Ainv(m, rho, v, consistent=True), consistent=True)
+    assert np.abs(back - v).max() <= 1e-11 * np.abs(v).max()
+    Af = O.assemble(lambda v: O.apply_A(m, rho, v), 3 * N, 3 * N)[:N, :N]
+    assert np.abs(Af - A).max() > 1e-6 * np.abs(A).max()
+
+
+@pytest.mark.parametrize("geo", [dict(terrain=0)] + CURVED)
+def test_S_with_consistent_mass(geo):
+    """With the consistent mass the Schur operator keeps its structure: S 1 =
+    D 1 and 1^T S = 1^T D for random coefficients, and S is symmetric positive
+    definite for uniform coefficients with slip walls."""
+    m = O.make_mesh(2, 2, 1, 2, Lx=2000.0, Ly=1600.0, Lz=1500.0, **geo)
+    N = O.ndofs(m)
+    rng = np.random.default_rng(13)
+    rho, pk = 1.2 * (1 + 0.2 * rng.random(N)), 1e5 * (1 + 0.2 * rng.random(N))
+    one = np.ones(N)
+    D1 = O.apply_D(m, GAMMA, one)
+    assert np.abs(O.apply_S(m, ALPHA, GAMMA, rho, pk, one, consistent=True) - D1).max() <= 1e-13 * np.abs(D1).max()
+    S = O.assemble(lambda v: O.apply_S(m, ALPHA, GAMMA, rho, pk, v, consistent=True), N, N)
+    assert np.abs(S.sum(axis=0) - D1).max() <= 1e-12 * np.abs(D1).max()
+    Su = O.assemble(lambda v: O.apply_S(m, ALPHA, GAMMA, np.full(N, 1.1), np.full(N, 9e4), v, consistent=True), N, N)
+    assert np.abs(Su - Su.T).max() <= 1e-13 * np.abs(Su).max() and np.linalg.eigvalsh(Su).min() > 0
+    b = rng.standard_normal(N)
+    x, st, its, rel = O.solve(m, ALPHA, GAMMA, rho, pk, b, tol=1e-12, consistent=True)
+    assert st == 0 and np.abs(x - np.linalg.solve(S, b)).max() <= 1e-9 * np.abs(x).max()
 
 
 # ------------------------------------------------ convergence (MMS)
