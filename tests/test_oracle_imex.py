@@ -326,3 +326,24 @@ def test_fast_and_consistent_mass_agree():
     wmax = np.abs(out[0]).max()
     diff = np.abs(out[0] - out[1]).max()
     assert wmax > 0.1 and 0 < diff <= 0.01 * wmax, (wmax, diff)  # measured 1.8e-3
+
+
+def test_explicit_momentum_and_energy_budgets():
+    """Periodic lateral faces and flat slip walls, random rho and u: the
+    interior Lax-Friedrichs fluxes cancel pairwise and the mirror state at a
+    horizontal wall carries vertical momentum only, so the x and y momentum
+    tendencies sum to zero; the kinetic-energy tendencies sum to the gravity
+    work -g int rho w (no energy crosses the walls).  On a curved bottom the
+    wall flux has horizontal components, so the check uses a flat mesh."""
+    m = O.make_mesh(3, 3, 3, 2, Lx=3000.0, Ly=3000.0, Lz=1500.0, bc_lateral=2)
+    N = O.ndofs(m)
+    rng = np.random.default_rng(14)
+    rho = 1.0 + 0.1 * rng.random(N)
+    u = rng.standard_normal(3 * N)
+    Er, Em, Ee = O.explicit(m, O.make_bg(g=G), rho, u, rho)
+    sc = np.abs(Em).max()
+    assert abs(Em[:N].sum()) <= 1e-13 * sc * N ** 0.5 and abs(Em[N:2 * N].sum()) <= 1e-13 * sc * N ** 0.5
+    assert abs(Em[2 * N:].sum()) > 1e-3 * sc  # the walls do act on vertical momentum
+    # int rho w with the consistent rule (exact for the degree-3r integrand)
+    rw = O.apply_A(m, rho, np.concatenate([u[2 * N:], np.zeros(2 * N)]), consistent=True)[:N].sum()
+    assert abs(Ee.sum() + G * rw) <= 1e-13 * np.abs(Ee).max() * N ** 0.5

@@ -74,6 +74,10 @@ C_MUTANTS = [
     ("slip wall reflecting half the normal velocity", "orc_imex.c",
      "vp[d] = vm[d] - 2.0 * un * nh[d];", "vp[d] = vm[d] - un * nh[d];",
      [(I.test_mass_conservation_of_explicit_tendency, ())]),
+    ("own velocity on both sides of the momentum flux", "orc_imex.c",
+     "double qpv[5] = {rp, rp * vp[0], rp * vp[1], rp * vp[2], rp * kp};",
+     "double qpv[5] = {rp, rp * vm[0], rp * vm[1], rp * vm[2], rp * kp};",
+     [(I.test_explicit_momentum_and_energy_budgets, ())]),
     ("buoyancy of the stage with the wrong sign", "orc_imex.c",
      "orc_apply_M(m, -b->g * al, t1, t2);", "orc_apply_M(m, b->g * al, t1, t2);",
      [(I.test_buoyancy_initial_acceleration, (False,))]),
