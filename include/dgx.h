@@ -355,6 +355,19 @@ int dgx_operator_threads(const dgx_ctx *ctx, int prec);
  * contexts); a diagnostic counter for benchmarks. */
 long long dgx_kernel_launches(void);
 
+/* The 1D tables every kernel of degree `degree` (1..6) works from, as built
+ * on the host: N = degree+1 Gauss-Lobatto-Legendre nodes carry the nodal
+ * basis (Sec. 2), Q = 2 degree + 1 Gauss points the consistent integrals, and
+ * N Gauss points the fast inverse (Sec. 3.3).  Layout, row-major, x in [0, 1]:
+ *   I [Q][N] l_a(g_q)     D [Q][N] l_a'(g_q)    IT, DT [N][Q] their transposes
+ *   Ia [N][N] l_a(ga_q)   P [N][N] Ia^-1 [a][q]  PT [N][N] its transpose
+ *   IIT, DDT, IDT [N][Q]  l_a^2, l_a'^2, l_a l_a' at g_q
+ *   wq [Q], wa [N], gq [Q]  Gauss weights, fast-rule weights, Gauss points
+ * Writes min(capacity, size) doubles to out (out may be NULL) and returns
+ * size = 7QN + 3N^2 + 2Q + N; DGX_ERR_ARG for an unsupported degree.  Host
+ * only: needs no context and no GPU. */
+int dgx_basis_tables(int degree, double *out, int capacity);
+
 /* ---------------------------------------------------------------- ensembles
  * Several independent meshes (sizes, degrees, terrain) whose pressure
  * systems S_m p_m = b_m (Sec. 2, Sec. 3.1) are solved together.  Vectors are

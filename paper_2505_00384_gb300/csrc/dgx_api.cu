@@ -1218,6 +1218,15 @@ static double eo_line_flops(int MO, int MI) {
   return 2.0 * HI + 4.0 * HO * HI + ((MI & 1) ? HO : 0) + 2.0 * HO - (MO & 1);
 }
 
+int dgx_basis_tables(int degree, double *out, int capacity) {
+  if (degree < 1 || degree > kMaxDegree) return DGX_ERR_ARG;
+  std::vector<double> tab;
+  if (!build_table_block(degree, tab)) return DGX_ERR_ARG;
+  if (out)
+    for (int i = 0; i < capacity && i < (int)tab.size(); ++i) out[i] = tab[i];
+  return (int)tab.size();
+}
+
 int dgx_operator_threads(const dgx_ctx *c, int prec) {
   if (!c || (prec != DGX_F64 && prec != DGX_F32)) return -1;
   return c->op_threads[prec == DGX_F64 ? 0 : 1];

@@ -93,6 +93,7 @@ SIGNATURES = [
     ("dgx_operator_cost", C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("dgx_kernel_launches", C.c_longlong, []),
     ("dgx_operator_threads", C.c_int, [_P, C.c_int]),
+    ("dgx_basis_tables", C.c_int, [C.c_int, _P, C.c_int]),
     ("dgx_apply_operator_noalloc", C.c_int, [_P, C.c_int, _P, _P]),
     ("dgx_set_imex", C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int]),
     ("dgx_explicit_tendencies", C.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -454,6 +455,27 @@ def ars222():
     A = np.array([[0, 0, 0], [g, 0, 0], [d, 1 - d, 0]], dtype=np.float64)
     At = np.array([[0, 0, 0], [0, g, 0], [0, 1 - g, g]], dtype=np.float64)
     return A, At
+
+
+def dgx_basis_tables(degree):
+    """The host-built 1D tables of a degree (host only, no GPU): a dict of
+    numpy arrays I, D, IT, DT, Ia, P, PT, IIT, DDT, IDT, wq, wa, gq."""
+    import numpy as np
+    n = load().dgx_basis_tables(int(degree), None, 0)
+    if n < 0:
+        raise DgxError(n, "unsupported degree %d" % degree)
+    buf = np.zeros(n)
+    load().dgx_basis_tables(int(degree), buf.ctypes.data_as(C.c_void_p), n)
+    N, Q = degree + 1, 2 * degree + 1
+    out, o = {}, 0
+    for name, shape in [("I", (Q, N)), ("D", (Q, N)), ("IT", (N, Q)), ("DT", (N, Q)), ("Ia", (N, N)), ("P", (N, N)),
+                        ("PT", (N, N)), ("IIT", (N, Q)), ("DDT", (N, Q)), ("IDT", (N, Q)), ("wq", (Q,)),
+                        ("wa", (N,)), ("gq", (Q,))]:
+        k = int(np.prod(shape))
+        out[name] = buf[o:o + k].reshape(shape)
+        o += k
+    assert o == n
+    return out
 
 
 def dgx_operator_threads(ctx, prec):
