@@ -41,7 +41,7 @@ long orc_num_cells(const orc_mesh *m);
 /* ------------------------------------------------------------------ */
 
 /* P_k(x) and P_k'(x) by the three-term recurrence; |x| < 1 for P'. */
-static void legendre(int k, double x, double *P, double *dP) {
+static inline void legendre(int k, double x, double *P, double *dP) {
   double p0 = 1.0, p1 = x;
   if (k == 0) { *P = 1.0; *dP = 0.0; return; }
   for (int j = 1; j < k; ++j) {
@@ -281,7 +281,7 @@ static double dotn(int n3, const double *f, const double *psi) {
 
 /* LU with partial pivoting, in place; solves A x = b for nrhs right-hand
  * sides stored as rows of B ([nrhs][n]). */
-static int lu_solve(int n, double *A, int nrhs, double *B) {
+static inline int lu_solve(int n, double *A, int nrhs, double *B) {
   int piv[ORC_MAXN * ORC_MAXN * ORC_MAXN];
   for (int k = 0; k < n; ++k) {
     int pk = k;
