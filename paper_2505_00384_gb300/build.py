@@ -32,8 +32,13 @@ def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+def _headers():
+    return (glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
+            + glob.glob(os.path.join(ROOT, "include", "*.h")))
+
+
 def _deps():
-    return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    return _sources() + _headers()
 
 
 def stale():
@@ -50,7 +55,7 @@ def build(force=False, verbose=False, extra_flags=()):
     nv = nvcc()
     srcs = _sources()
 
-    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    headers = _headers()
     newest_header = max([os.path.getmtime(h) for h in headers] + [0.0])
 
     def compile_one(src):
