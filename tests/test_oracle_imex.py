@@ -347,3 +347,17 @@ def test_explicit_momentum_and_energy_budgets():
     # int rho w with the consistent rule (exact for the degree-3r integrand)
     rw = O.apply_A(m, rho, np.concatenate([u[2 * N:], np.zeros(2 * N)]), consistent=True)[:N].sum()
     assert abs(Ee.sum() + G * rw) <= 1e-13 * np.abs(Ee).max() * N ** 0.5
+
+
+def test_far_field_free_stream():
+    """Uniform density rho_bar and wind (u_bar, 0, 0) equal to the far-field
+    ghost state, g = 0, far-field lateral faces and flat walls: every cell's
+    tendencies vanish, the boundary cells included."""
+    bg = O.make_bg(g=0.0, ubar=10.0)
+    m = O.make_mesh(2, 2, 2, 2, Lx=2000.0, Ly=2000.0, Lz=1500.0, bc_lateral=1)
+    N = O.ndofs(m)
+    rho = np.full(N, 1.1)
+    u = np.concatenate([np.full(N, 10.0), np.zeros(2 * N)])
+    Er, Em, Ee = O.explicit(m, bg, rho, u, rho)
+    sc = np.abs(O.explicit(m, bg, rho * (1 + 0.01 * np.random.default_rng(15).random(N)), u, rho)[0]).max()
+    assert np.abs(Er).max() <= 1e-12 * sc and np.abs(Em).max() <= 1e-11 * sc and np.abs(Ee).max() <= 1e-10 * sc

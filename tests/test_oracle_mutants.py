@@ -34,6 +34,9 @@ C_MUTANTS = [
     ("central average of p without the 1/2", "orc.c",
      "ph = 0.5 * (pm + dotn(", "ph = (pm + dotn(",
      [(P.test_interior_face_fluxes_closed_form, (1,))]),
+    ("transmissive pressure at far-field faces", "orc.c",
+     "if (ff) ph = 0.0;", "if (ff) ph = pm;",
+     [(P.test_far_field_pressure_flux_closed_form, (1,))]),
     ("volume term of B with the wrong sign", "orc.c",
      "out[d * n3 + i] -= pq * gd;", "out[d * n3 + i] += pq * gd;",
      [(P.test_single_cell_matrices_closed_form, (1,))]),
@@ -78,6 +81,9 @@ C_MUTANTS = [
      "double qpv[5] = {rp, rp * vp[0], rp * vp[1], rp * vp[2], rp * kp};",
      "double qpv[5] = {rp, rp * vm[0], rp * vm[1], rp * vm[2], rp * kp};",
      [(I.test_explicit_momentum_and_energy_budgets, ())]),
+    ("far-field wind along y", "orc_imex.c",
+     "vp[0] = b->ubar; vp[1] = 0.0; vp[2] = 0.0;", "vp[0] = 0.0; vp[1] = b->ubar; vp[2] = 0.0;",
+     [(I.test_far_field_free_stream, ())]),
     ("buoyancy of the stage with the wrong sign", "orc_imex.c",
      "orc_apply_M(m, -b->g * al, t1, t2);", "orc_apply_M(m, b->g * al, t1, t2);",
      [(I.test_buoyancy_initial_acceleration, (False,))]),

@@ -172,6 +172,28 @@ def test_interior_face_fluxes_closed_form(r):
     assert np.abs(CV[n3:] - ref1).max() <= 1e-13 * sc
 
 
+@pytest.mark.parametrize("r", [1, 2])
+def test_far_field_pressure_flux_closed_form(r):
+    """One cell with far-field lateral faces and slip walls at bottom and top,
+    constant p = c: the far-field datum p^ = 0 (the perturbation pressure of the
+    background) leaves only the far-field faces' term, B p = -alpha c int_ff phi.n,
+    i.e. the x part -alpha c hy hz (W x W x (e_n - e_0)), y analogous, z zero."""
+    hx, hy, hz = 700.0, 500.0, 300.0
+    m = O.make_mesh(1, 1, 1, r, Lx=hx, Ly=hy, Lz=hz, bc_lateral=1)
+    N = O.ndofs(m)
+    n = r + 1
+    _, _, _, W1 = _sym_1d(r)
+    de = np.eye(n)[n - 1] - np.eye(n)[0]
+    c = 2.0
+    Bp = O.apply_B(m, ALPHA, np.full(N, c))
+    refx = -ALPHA * c * hy * hz * _k3(de, W1, W1)
+    refy = -ALPHA * c * hx * hz * _k3(W1, de, W1)
+    sc = np.abs(refx).max()
+    assert np.abs(Bp[:N] - refx).max() <= 1e-13 * sc
+    assert np.abs(Bp[N:2 * N] - refy).max() <= 1e-13 * sc
+    assert np.abs(Bp[2 * N:]).max() <= 1e-13 * sc
+
+
 # ------------------------------------------------------- curved geometry
 CURVED = [dict(terrain=1, hc=300.0, ac=800.0), dict(terrain=2, hc=250.0, ac=600.0, xc=1100.0, yc=900.0)]
 
