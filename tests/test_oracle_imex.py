@@ -361,3 +361,18 @@ def test_far_field_free_stream():
     Er, Em, Ee = O.explicit(m, bg, rho, u, rho)
     sc = np.abs(O.explicit(m, bg, rho * (1 + 0.01 * np.random.default_rng(15).random(N)), u, rho)[0]).max()
     assert np.abs(Er).max() <= 1e-12 * sc and np.abs(Em).max() <= 1e-11 * sc and np.abs(Ee).max() <= 1e-10 * sc
+
+
+def test_far_field_inflow_mass_budget():
+    """Uniform rho = 1.1 and wind (u_bar, 0, 0) against a far-field density
+    rho_bar = 1.0 (g = 0, flat walls): the Lax-Friedrichs flux at the far-field
+    faces is the upwind flux, so the inflow face brings rho_bar and the outflow
+    face takes rho; the continuity tendencies sum to -(rho - rho_bar) u_bar Ly Lz."""
+    bg = O.make_bg(g=0.0, ubar=10.0)
+    Ly, Lz = 1600.0, 1500.0
+    m = O.make_mesh(2, 2, 2, 2, Lx=2000.0, Ly=Ly, Lz=Lz, bc_lateral=1)
+    N = O.ndofs(m)
+    u = np.concatenate([np.full(N, 10.0), np.zeros(2 * N)])
+    Er, _, _ = O.explicit(m, bg, np.full(N, 1.1), u, np.full(N, 1.0))
+    ref = -(1.1 - 1.0) * 10.0 * Ly * Lz
+    assert abs(Er.sum() - ref) <= 1e-12 * abs(ref) * N ** 0.5

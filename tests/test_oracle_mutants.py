@@ -37,6 +37,9 @@ C_MUTANTS = [
     ("transmissive pressure at far-field faces", "orc.c",
      "if (ff) ph = 0.0;", "if (ff) ph = pm;",
      [(P.test_far_field_pressure_flux_closed_form, (1,))]),
+    ("far-field faces closed in C", "orc.c",
+     "if (nb < 0 && bk == 0) continue;", "if (nb < 0) continue;",
+     [(P.test_far_field_divergence_of_constant_field, ())]),
     ("volume term of B with the wrong sign", "orc.c",
      "out[d * n3 + i] -= pq * gd;", "out[d * n3 + i] += pq * gd;",
      [(P.test_single_cell_matrices_closed_form, (1,))]),
@@ -84,6 +87,9 @@ C_MUTANTS = [
     ("far-field wind along y", "orc_imex.c",
      "vp[0] = b->ubar; vp[1] = 0.0; vp[2] = 0.0;", "vp[0] = 0.0; vp[1] = b->ubar; vp[2] = 0.0;",
      [(I.test_far_field_free_stream, ())]),
+    ("far-field ghost density from the interior trace", "orc_imex.c",
+     "rp = dotn(n3, rho_bar + c * n3, ps);", "rp = rm;",
+     [(I.test_far_field_inflow_mass_budget, ())]),
     ("buoyancy of the stage with the wrong sign", "orc_imex.c",
      "orc_apply_M(m, -b->g * al, t1, t2);", "orc_apply_M(m, b->g * al, t1, t2);",
      [(I.test_buoyancy_initial_acceleration, (False,))]),

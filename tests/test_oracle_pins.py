@@ -194,6 +194,19 @@ def test_far_field_pressure_flux_closed_form(r):
     assert np.abs(Bp[2 * N:]).max() <= 1e-13 * sc
 
 
+def test_far_field_divergence_of_constant_field():
+    """Flat box, far-field lateral faces (transmissive (kappa V)^ in C) and
+    slip walls at bottom and top: a constant horizontal kappa V has zero weak
+    divergence, C V = 0 (the volume term and the far-field face terms cancel;
+    V.n = 0 on the walls)."""
+    m = O.make_mesh(2, 2, 2, 2, Lx=2000.0, Ly=1600.0, Lz=1500.0, bc_lateral=1)
+    N = O.ndofs(m)
+    V = np.concatenate([np.full(N, 3.0), np.full(N, -2.0), np.zeros(N)])
+    CV = O.apply_C(m, ALPHA, GAMMA, np.full(N, 1e5), V)
+    kappa = GAMMA * 1e5 / (GAMMA - 1)
+    assert np.abs(CV).max() <= 1e-13 * ALPHA * kappa * 3.0 * 1e6
+
+
 # ------------------------------------------------------- curved geometry
 CURVED = [dict(terrain=1, hc=300.0, ac=800.0), dict(terrain=2, hc=250.0, ac=600.0, xc=1100.0, yc=900.0)]
 
