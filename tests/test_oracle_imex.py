@@ -376,3 +376,33 @@ def test_far_field_inflow_mass_budget():
     Er, _, _ = O.explicit(m, bg, np.full(N, 1.1), u, np.full(N, 1.0))
     ref = -(1.1 - 1.0) * 10.0 * Ly * Lz
     assert abs(Er.sum() - ref) <= 1e-12 * abs(ref) * N ** 0.5
+
+
+def test_imex_euler_acoustics_closed_form():
+    """The IMEX Euler pair (explicit stage, then one implicit stage: A =
+    [[0, 0], [1, 0]], A~ = [[0, 0], [0, 1]]) is backward Euler for linear
+    acoustics: each step multiplies the mode (p', i rho0 c u) by
+    g = 1 / (1 - i w dt), so after n steps p' = eps cos(kx) Re(g^n) and
+    u = eps/(rho0 c) sin(kx) Im(g^n).  Pins the stage machinery with a
+    tableau other than ARS(2,2,2)."""
+    R, T, gam, p0 = 287.0, 250.0, 1.4, 1e5
+    bg = O.make_bg(kind=0, T=T, p0=p0, R=R, gamma=gam, g=0.0, ubar=0.0)
+    Lx, nx = 1000.0, 16
+    m = O.make_mesh(nx, 1, 1, 3, Lx=Lx, Ly=Lx / nx, Lz=Lx / nx, bc_lateral=2)
+    N = O.ndofs(m)
+    X = O.node_coords(m)
+    rb, pb = O.background(m, bg)
+    rho0 = p0 / (R * T)
+    c = np.sqrt(gam * p0 / rho0)
+    k = 2 * np.pi / Lx
+    wdt, n = 0.5, 4
+    A = np.array([[0.0, 0.0], [1.0, 0.0]])
+    At = np.array([[0.0, 0.0], [0.0, 1.0]])
+    r, u, p = rb.copy(), np.zeros(3 * N), pb + np.cos(k * X[0])
+    for _ in range(n):
+        r, u, p, st, _ = O.imex_step(m, bg, r, u, p, wdt / (c * k), A=A, At=At, K=2, tol=1e-12)
+        assert st == 0
+    gn = (1.0 / (1.0 - 1j * wdt)) ** n
+    assert np.abs((p - pb) - gn.real * np.cos(k * X[0])).max() <= 2e-4
+    assert np.abs(u[:N] * rho0 * c - gn.imag * np.sin(k * X[0])).max() <= 2e-4
+    assert np.abs(u[N:]).max() * rho0 * c <= 1e-8

@@ -90,6 +90,10 @@ C_MUTANTS = [
     ("far-field ghost density from the interior trace", "orc_imex.c",
      "rp = dotn(n3, rho_bar + c * n3, ps);", "rp = rm;",
      [(I.test_far_field_inflow_mass_budget, ())]),
+    ("earlier implicit stage terms weighted by the explicit tableau", "orc_imex.c",
+     "Fs[i] += dt * (A[l * s + mm] * E[N + i] + At[l * s + mm] * E[5 * N + i]);",
+     "Fs[i] += dt * (A[l * s + mm] * E[N + i] + A[l * s + mm] * E[5 * N + i]);",
+     [(I.test_imex_euler_acoustics_closed_form, ())]),
     ("buoyancy of the stage with the wrong sign", "orc_imex.c",
      "orc_apply_M(m, -b->g * al, t1, t2);", "orc_apply_M(m, b->g * al, t1, t2);",
      [(I.test_buoyancy_initial_acceleration, (False,))]),
