@@ -406,3 +406,18 @@ def test_imex_euler_acoustics_closed_form():
     assert np.abs((p - pb) - gn.real * np.cos(k * X[0])).max() <= 2e-4
     assert np.abs(u[:N] * rho0 * c - gn.imag * np.sin(k * X[0])).max() <= 2e-4
     assert np.abs(u[N:]).max() * rho0 * c <= 1e-8
+
+
+@pytest.mark.parametrize("geo", [dict(terrain=0), dict(terrain=1, hc=300.0, ac=800.0)])
+def test_kinetic_mass_closed_form(geo):
+    """int rho |u|^2/2 psi_i for constant rho and u = (x, y, 0): the
+    integrand rho (x^2 + y^2)/2 is the degree-2 polynomial the r = 2 nodal
+    basis holds exactly, so the result is rho/2 M (x^2 + y^2) with M the
+    (pinned) consistent mass, on flat and terrain-following cells."""
+    m = O.make_mesh(2, 2, 2, 2, Lx=2000.0, Ly=1600.0, Lz=1500.0, **geo)
+    N = O.ndofs(m)
+    X = O.node_coords(m)
+    u = np.concatenate([X[0], X[1], np.zeros(N)])
+    out = O.kinetic_mass(m, np.full(N, 1.3), u)
+    ref = O.apply_M(m, 0.65 * (X[0] ** 2 + X[1] ** 2))
+    assert np.abs(out - ref).max() <= 1e-13 * np.abs(ref).max()

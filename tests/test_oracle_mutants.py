@@ -94,6 +94,10 @@ C_MUTANTS = [
      "Fs[i] += dt * (A[l * s + mm] * E[N + i] + At[l * s + mm] * E[5 * N + i]);",
      "Fs[i] += dt * (A[l * s + mm] * E[N + i] + A[l * s + mm] * E[5 * N + i]);",
      [(I.test_imex_euler_acoustics_closed_form, ())]),
+    ("kinetic energy without the 1/2", "orc_imex.c",
+     "double f = 0.5 * r * (v0 * v0 + v1 * v1 + v2 * v2) * G.wdet[qp];",
+     "double f = r * (v0 * v0 + v1 * v1 + v2 * v2) * G.wdet[qp];",
+     [(I.test_kinetic_mass_closed_form, (dict(terrain=0),))]),
     ("buoyancy of the stage with the wrong sign", "orc_imex.c",
      "orc_apply_M(m, -b->g * al, t1, t2);", "orc_apply_M(m, b->g * al, t1, t2);",
      [(I.test_buoyancy_initial_acceleration, (False,))]),
