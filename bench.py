@@ -140,12 +140,46 @@ def workload(args):
     return work
 
 
-def oracle_step_cost(work, budget_s=15.0):
+def measured_hbm_gbs():
+    """(HBM copy bandwidth in GB/s, source): the measured figure of this machine's
+    GB300s when MEASURED_PEAKS.json is present, else the earlier measurement
+    used as the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        if v > 0:
+            return v, "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError, TypeError):
+        pass
+    return 6800.0, "fallback (earlier GB300 copy measurement)"
+
+
+def hbm_fractions(bytes_moved, seconds, hbm_gbs):
+    """Achieved GB/s of `bytes_moved` in `seconds` and its fraction of hbm_gbs
+    (None where the bytes are unknown)."""
+    if bytes_moved is None or not seconds > 0:
+        return None, None
+    gbs = bytes_moved / seconds / 1e9
+    return gbs, gbs / hbm_gbs
+
+
+def oracle_step_cost(work, budget_s=15.0, threads=None):
     """FP64 CPU oracle on a bounded sample of cells of this workload: seconds
     per full-mesh operator application and per explicit-tendency evaluation,
-    scaled by cells; returns (seconds per IMEX step, sample text, threads)."""
+    scaled by cells; returns (seconds per IMEX step, sample text, threads).
+    threads: OpenMP threads for this measurement (all cores when None)."""
     import numpy as np
     import oracle as O
+    prev = O.max_threads()
+    if threads:
+        O.set_threads(threads)
+    try:
+        return _oracle_step_cost(O, np, work, budget_s)
+    finally:
+        O.set_threads(prev)
+
+
+def _oracle_step_cost(O, np, work, budget_s):
     m = O.make_mesh(work["nx"], work["ny"], work["nz"], work["r"], Lx=work["Lx"], Ly=work["Ly"], Lz=work["Lz"],
                     terrain=work["terrain"], hc=work["hc"], ac=work["ac"], bc_lateral=work["bc_lateral"])
     bg = O.make_bg(kind=0, T=work["T"], p0=work["p0"], R=work["R"], gamma=work["gamma"], g=work["g"],
@@ -960,15 +994,22 @@ def main():
         peak, peak_src = peak64, "measured cuBLAS DGEMM (torch.matmul float64 4096^3) on this GPU"
     achieved = fl_k / t_k / 1e12
     traffic = DRAM_BYTES_PER_DOF_F64[kname] * N if kname in DRAM_BYTES_PER_DOF_F64 else None
+    hbm_gbs, hbm_src = measured_hbm_gbs()
+    k_gbs, k_hbm_frac = hbm_fractions(traffic, t_k, hbm_gbs)
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "traffic_source": "ncu DRAM bytes per DoF on the 48x48x24 r=4 mesh, scaled by DoFs" if traffic else None,
-                "peak_source": peak_src, "flops_per_launch": fl_k, "launch_s": t_k, "step_share_estimate_s": share}
+                "peak_source": peak_src, "flops_per_launch": fl_k, "launch_s": t_k, "step_share_estimate_s": share,
+                "hbm": {"achieved_gbs": k_gbs, "frac": k_hbm_frac, "peak_gbs": hbm_gbs, "peak_source": hbm_src,
+                        "note": "the kernel's DRAM traffic per launch over its launch time: far below the copy "
+                                "bandwidth, the FP64 pipe binds"}}
 
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         v, sample, threads = oracle_step_cost(work, budget_s=15.0)
         cpu = {"value": v, "unit": "s/step", "cores": threads, "kind": "oracle", "sample": sample}
+        v1, sample1, _ = oracle_step_cost(work, budget_s=8.0, threads=1)
+        cpu["single_core"] = {"value": v1, "unit": "s/step", "cores": 1, "sample": sample1}
 
     value = t_dev / (args.steps * ws)
     mean = lambda k: statistics.mean(getattr(i, k) for i in step_infos)
@@ -1001,6 +1042,7 @@ def main():
                   "flops_per_apply": fl_grad + fl_div, "hbm_floor_bytes_f64": bytes64,
                   "f64_tflops": (fl_grad + fl_div) / t_app64 / 1e12, "f32_tflops": (fl_grad + fl_div) / t_app32 / 1e12,
                   "fp64_peak_measured_tflops": peak64,
+                  "f64_hbm_floor_frac": hbm_fractions(bytes64, t_app64, hbm_gbs)[1],
                   "threads_per_cta_autotuned": {"f64": dgx.dgx_operator_threads(ctx, dgx.DGX_F64),
                                                 "f32": dgx.dgx_operator_threads(ctx, dgx.DGX_F32)}},
     }

@@ -50,3 +50,34 @@ def test_bench_defaults():
     assert a.gpus == 1 and a.warmup >= 3 and a.workload == "hill" and a.impl == "ours"
     w = bench.workload(a)
     assert (w["nx"], w["ny"], w["nz"], w["r"]) == (64, 64, 32, 4) and w["bc_lateral"] == 2
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    return bench
+
+
+def test_bench_hbm_fractions():
+    bench = _bench()
+    gbs, src = bench.measured_hbm_gbs()
+    assert gbs > 1000.0 and isinstance(src, str)
+    a, f = bench.hbm_fractions(2e9, 0.5, 8000.0)
+    assert abs(a - 4.0) < 1e-12 and abs(f - 0.0005) < 1e-15
+    assert bench.hbm_fractions(None, 0.5, 8000.0) == (None, None)
+    assert bench.hbm_fractions(1e9, 0.0, 8000.0) == (None, None)
+
+
+def test_bench_oracle_baseline_on_one_core():
+    """The CPU-baseline leg on a bounded sample: all cores, then one thread
+    (restored afterwards), both positive and scaled to a step."""
+    import oracle as O
+    bench = _bench()
+    w = dict(bench.SMALL)
+    w.update(bench.COMMON)
+    before = O.max_threads()
+    v, sample, threads = bench.oracle_step_cost(w, budget_s=0.5)
+    v1, sample1, threads1 = bench.oracle_step_cost(w, budget_s=0.5, threads=1)
+    assert v > 0 and v1 > 0 and threads == before and threads1 == 1 and O.max_threads() == before
+    assert "random cells" in sample and "random cells" in sample1
