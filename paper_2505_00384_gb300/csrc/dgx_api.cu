@@ -1195,6 +1195,8 @@ int dgx_basis_tables(int degree, double *out, int capacity) {
   if (out)
     for (int i = 0; i < capacity && i < (int)tab.size(); ++i) out[i] = tab[i];
   return (int)tab.size();
+}
+
 int dgx_set_mass_rule(dgx_ctx *c, int rule, double cg_tol, int cg_maxit) {
   if (!c) return DGX_ERR_ARG;
   if (rule != DGX_MASS_FAST && rule != DGX_MASS_CONSISTENT) return set_error(c, DGX_ERR_ARG, "mass rule %d", rule);

@@ -479,6 +479,8 @@ def dgx_basis_tables(degree):
         o += k
     assert o == n
     return out
+
+
 def dgx_set_mass_rule(ctx, rule, cg_tol=1e-13, cg_maxit=50):
     """Quadrature of the density-weighted mass for every use in ctx: DGX_MASS_FAST
     (r+1 points, fast inverse) or DGX_MASS_CONSISTENT (2r+1 points, per-cell PCG)."""
