@@ -60,12 +60,13 @@ def parse():
     ap.add_argument("--mesh", default=None, help="NXxNYxNZ cells at the same cell size as the 64x64x32 workload")
     ap.add_argument("--profile", action="store_true",
                     help="only the warm-up and timed steps (for profiler launch lists); no side measurements")
-    ap.add_argument("--workload", default="hill", choices=["hill", "ensemble", "learned", "mixed", "paper"],
+    ap.add_argument("--workload", default="hill", choices=["hill", "ensemble", "learned", "mixed", "paper", "consistent"],
                     help="hill: one IMEX step of the 64x64x32 hill (default); ensemble: 16-member batched solve; "
                          "learned: pressure solves of held-out hill systems with the trained network; "
                          "mixed: mixed-precision solves on the 4x4x4 box at degrees 2, 3, 5 against the oracle; "
                          "paper: the Sec. 3 test case (120x80x32 cells, r = 4, stratified), Helmholtz vs "
-                         "internal-energy Jacobi")
+                         "internal-energy Jacobi; consistent: fast vs consistent density-weighted mass "
+                         "(Sec. 3.3) on the 60x40x16 r = 4 mesh")
     ap.add_argument("--epochs", type=int, default=100, help="learned workload: training epochs (batch 32)")
     ap.add_argument("--members", type=int, default=16, help="ensemble members (first k of the 16)")
     ap.add_argument("--inner-maxit", type=int, default=None, help="override the FP32 GMRES cycle length")
@@ -513,6 +514,73 @@ def run_paper(args):
     return 0
 
 
+def run_consistent(args):
+    """Fast against consistent density-weighted mass (Sec. 3.3) on the Sec. 3
+    domain at 250 m resolution: 60 x 40 x 16 cells at degree 4 (4 800 000 DoFs
+    per scalar), -3/2 bell hill, constant-N background, u_bar = 10 m/s, far-field
+    lateral faces, dt = 1 s, mixed-precision solves to 1e-8.  For each rule, from
+    the same initial state: --warmup + --steps IMEX steps, the last --steps timed;
+    then the relative difference of the final vertical velocity and pressure
+    perturbation, and the consistent rule's PCG iteration counts."""
+    import torch
+    from paper_2505_00384_gb300 import dgx
+    torch.cuda.set_device(0)
+    dgx.load()
+    stream = torch.cuda.current_stream()
+    ctx = dgx.dgx_create(0, stream.cuda_stream)
+    desc = dgx.mesh_desc(60, 40, 16, 4, 60000.0, 40000.0, 16000.0, terrain=2, h_c=400.0, a_c=1000.0,
+                         x_c=30000.0, y_c=20000.0, bc_lateral=1)
+    dgx.dgx_mesh_build(ctx, desc)
+    N = dgx.dgx_num_dofs(ctx)
+    dgx.dgx_set_background(ctx, dgx.background(kind=1, T=293.15, p0=1e5, N_bv=0.01, R=287.0, gamma=1.4, g=9.81,
+                                               u_bar=10.0))
+    A, At = dgx.ars222()
+    dgx.dgx_set_imex(ctx, A, At, 1.0, 2)
+    f64 = torch.float64
+    rho0 = torch.zeros(N, dtype=f64, device="cuda")
+    p0 = torch.zeros(N, dtype=f64, device="cuda")
+    dgx.dgx_background_fields(ctx, rho0.data_ptr(), p0.data_ptr())
+    u0 = torch.zeros(3 * N, dtype=f64, device="cuda")
+    u0[:N] = 10.0
+    o = dgx.dgx_default_solve_opts()
+    o.method, o.pc, o.tol, o.maxit, o.restart = dgx.DGX_SOLVER_MIXED, dgx.DGX_PC_HELMHOLTZ, 1e-8, 2000, 20
+    o.inner_maxit, o.inner_tol = 25, 3e-6
+    res, final = {}, {}
+    for name, rule in (("fast", dgx.DGX_MASS_FAST), ("consistent", dgx.DGX_MASS_CONSISTENT)):
+        dgx.dgx_set_mass_rule(ctx, rule, 1e-13, 50)
+        r, u, p = rho0.clone(), u0.clone(), p0.clone()
+        for _ in range(args.warmup):
+            dgx.dgx_imex_step(ctx, r.data_ptr(), u.data_ptr(), p.data_ptr(), 1, o)
+        dgx.dgx_mass_cg_stats(ctx)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, info = dgx.dgx_imex_step(ctx, r.data_ptr(), u.data_ptr(), p.data_ptr(), args.steps, o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        its, bad = dgx.dgx_mass_cg_stats(ctx)
+        if st != dgx.DGX_OK or bad:
+            raise RuntimeError("%s: status %d, %d unconverged cell solves" % (name, st, bad))
+        res[name] = {"s_per_step": e0.elapsed_time(e1) / 1e3 / args.steps,
+                     "pressure_solve_s_per_step": info.seconds_solve / args.steps,
+                     "krylov_iterations_per_step": info.krylov_iterations / args.steps,
+                     "max_relres": info.max_relres, "mass_cg_max_iterations": its}
+        final[name] = (u[2 * N:].clone(), p - p0)
+        del r, u, p
+    wf, wc = final["fast"][0], final["consistent"][0]
+    pf, pc = final["fast"][1], final["consistent"][1]
+    out = {"metric": "IMEX s/step, fast vs consistent density-weighted mass", "value": res["consistent"]["s_per_step"],
+           "unit": "s/step", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+           "dtype": "f64 (FP32 inner solves)", "data": "synthetic",
+           "config": {"workload": "paper_sec3_60x40x16_r4_4.8M_dofs_stratified", "dofs_per_scalar": N, "dt_s": 1.0},
+           "rules": res, "consistent_over_fast_time": res["consistent"]["s_per_step"] / res["fast"]["s_per_step"],
+           "w_max_rel_diff": float((wf - wc).abs().max() / wc.abs().max().clamp_min(1e-30)),
+           "p_prime_max_rel_diff": float((pf - pc).abs().max() / pc.abs().max().clamp_min(1e-30))}
+    print(json.dumps(out), flush=True)
+    dgx.dgx_destroy(ctx)
+    return 0
+
+
 def run_learned(args):
     """Learned preconditioner: 400 pressure systems recorded along IMEX
     trajectories over 16 seeded hills (h_c ~ U[200, 800] m, 25 steps each, the
@@ -824,6 +892,8 @@ def main():
         return run_mixed(args)
     if args.workload == "paper":
         return run_paper(args)
+    if args.workload == "consistent":
+        return run_consistent(args)
 
     import torch
     from paper_2505_00384_gb300 import dgx

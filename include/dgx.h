@@ -155,15 +155,39 @@ int dgx_background_fields(dgx_ctx *ctx, double *rho_bar, double *p_bar);
  * when only the mixed solver's FP32 inner solve needs them). */
 int dgx_set_coefficients(dgx_ctx *ctx, const double *rho_l, const double *p_k, double a_dt, double gamma);
 
+/* Quadrature of the density-weighted mass A(rho) (Sec. 3.3), a setting of
+ * the context that holds for every application or inversion of A in it: the
+ * operator S (both precisions), dgx_apply_grad, dgx_apply_mass_inverse,
+ * dgx_apply_mass and dgx_imex_step.  The ensemble solver and
+ * dgx_apply_operator_noalloc always use the fast rule.
+ *   DGX_MASS_FAST        r+1 Gauss points per direction, inverted in closed form
+ *                        by the fast inverse S^-T J^-1 S^-1 (the default).
+ *   DGX_MASS_CONSISTENT  the consistent 2r+1 point rule of the other integrals;
+ *                        A^-1 by preconditioned conjugate gradients inside each
+ *                        cell, preconditioned by the fast inverse, to relative
+ *                        residual cg_tol (FP32: at least 1e-5) within cg_maxit
+ *                        iterations.
+ * Errors: DGX_ERR_ARG for an unknown rule, cg_tol <= 0 or cg_maxit < 1. */
+#define DGX_MASS_FAST 0
+#define DGX_MASS_CONSISTENT 1
+int dgx_set_mass_rule(dgx_ctx *ctx, int rule, double cg_tol, int cg_maxit);
+/* Statistics of the consistent-mass conjugate gradients since the previous
+ * call (synchronises the context's stream, then resets them): the largest
+ * iteration count of any cell solve and the number of cell solves that
+ * stopped at cg_maxit or met a non-finite residual. */
+int dgx_mass_cg_stats(dgx_ctx *ctx, int *max_iterations, int *unconverged);
+
 /* y = S x = D x - C A^-1 B x, the matrix-free Schur operator of the
- * fixed-point equation of Sec. 2 with the fast block-diagonal inverse of
- * Sec. 3.3; x, y: N elements of type `prec`.  x and y must not alias. */
+ * fixed-point equation of Sec. 2 with the block-diagonal inverse of Sec. 3.3
+ * (the fast inverse, or the consistent mass's, per dgx_set_mass_rule);
+ * x, y: N elements of type `prec`.  x and y must not alias. */
 int dgx_apply_operator(dgx_ctx *ctx, int prec, const void *x, void *y);
 /* V = A^-1 B p (the pressure-gradient step, 3N out) and y = D p - C V
  * (the divergence step, N out): the two halves of dgx_apply_operator. */
 int dgx_apply_grad(dgx_ctx *ctx, int prec, const void *p, void *V);
 int dgx_apply_div(dgx_ctx *ctx, int prec, const void *V, const void *p, void *y);
-/* out = A_rho^-1 in (3N -> 3N), fast inverse S^-T J^-1 S^-1 of Sec. 3.3. */
+/* out = A_rho^-1 in (3N -> 3N): the fast inverse S^-T J^-1 S^-1 of Sec. 3.3,
+ * or the consistent mass's inverse (dgx_set_mass_rule). */
 int dgx_apply_mass_inverse(dgx_ctx *ctx, int prec, const void *in, void *out);
 /* y = P^-1 x for the Jacobi preconditioner `pc` (Sec. 3.1). */
 int dgx_apply_preconditioner(dgx_ctx *ctx, int pc, int prec, const void *x, void *y);
@@ -206,7 +230,8 @@ int dgx_set_imex(dgx_ctx *ctx, int s, const double *A, const double *At, double 
  * function): Erho (N) = weak -div(rho u), Em (3N) = weak -div(rho u_d u),
  * Ee (N) = weak -div(rho k u) + int rho g.u psi.  Needs the background. */
 int dgx_explicit_tendencies(dgx_ctx *ctx, const double *rho, const double *u, double *Erho, double *Em, double *Ee);
-/* out = A(rho) in (3N -> 3N): the fast density-weighted mass of Sec. 3.3 applied forward. */
+/* out = A(rho) in (3N -> 3N): the density-weighted mass of Sec. 3.3 applied
+ * forward, with the context's quadrature (dgx_set_mass_rule). */
 int dgx_apply_mass(dgx_ctx *ctx, const double *rho, const double *in, double *out);
 /* out_i = int rho |u|^2/2 psi_i (N), consistent rule. */
 int dgx_kinetic_mass(dgx_ctx *ctx, const double *rho, const double *u, double *out);

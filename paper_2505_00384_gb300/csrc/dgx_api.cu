@@ -433,7 +433,7 @@ int apply_S(dgx_ctx *c, const T *x, T *y) {
     rho = reinterpret_cast<const T *>(c->rho32);
     pk = reinterpret_cast<const T *>(c->pk32);
   }
-  if (int e = launch_grad<T>(c, x, rho, V, c->stream)) return e;
+  if (int e = grad_inverse_rule<T>(c, x, rho, V, c->stream)) return e;
   return launch_div<T>(c, V, x, pk, y, c->stream);
 }
 
@@ -861,7 +861,7 @@ int solve_pressure_vx(dgx_ctx *c, const double *b, double *x, const dgx_solve_op
     e = fgmres64(c, b, x, o, inf, Vx);
   } else if (o.method == DGX_SOLVER_CG) {
     e = cg64(c, b, x, o, inf);
-    if (!e && Vx) e = launch_grad<double>(c, x, c->rho64, Vx, c->stream);
+    if (!e && Vx) e = grad_inverse_rule<double>(c, x, c->rho64, Vx, c->stream);
   } else {
     return set_error(c, DGX_ERR_ARG, "solver %d", o.method);
   }
@@ -905,6 +905,7 @@ void dgx_destroy(dgx_ctx *c) {
   if (c->red_out) cudaFree(c->red_out);
   if (c->host_red) cudaFreeHost(c->host_red);
   if (c->arn_ev) cudaEventDestroy(c->arn_ev);
+  if (c->mass_stats) cudaFree(c->mass_stats);
   delete c;
 }
 
@@ -1125,8 +1126,8 @@ int dgx_apply_operator(dgx_ctx *c, int prec, const void *x, void *y) {
 int dgx_apply_grad(dgx_ctx *c, int prec, const void *p, void *V) {
   if (int e = check_ready(c, true)) return e;
   if (!p || !V) return set_error(c, DGX_ERR_ARG, "null array");
-  if (prec == DGX_F64) return launch_grad<double>(c, (const double *)p, c->rho64, (double *)V, c->stream);
-  if (prec == DGX_F32) return launch_grad<float>(c, (const float *)p, c->rho32, (float *)V, c->stream);
+  if (prec == DGX_F64) return grad_inverse_rule<double>(c, (const double *)p, c->rho64, (double *)V, c->stream);
+  if (prec == DGX_F32) return grad_inverse_rule<float>(c, (const float *)p, c->rho32, (float *)V, c->stream);
   return set_error(c, DGX_ERR_ARG, "precision %d", prec);
 }
 
@@ -1141,8 +1142,8 @@ int dgx_apply_div(dgx_ctx *c, int prec, const void *V, const void *p, void *y) {
 int dgx_apply_mass_inverse(dgx_ctx *c, int prec, const void *in, void *out) {
   if (int e = check_ready(c, true)) return e;
   if (!in || !out) return set_error(c, DGX_ERR_ARG, "null array");
-  if (prec == DGX_F64) return launch_mass_inverse<double>(c, (const double *)in, c->rho64, (double *)out, c->stream);
-  if (prec == DGX_F32) return launch_mass_inverse<float>(c, (const float *)in, c->rho32, (float *)out, c->stream);
+  if (prec == DGX_F64) return mass_inverse_rule<double>(c, (const double *)in, c->rho64, (double *)out, c->stream);
+  if (prec == DGX_F32) return mass_inverse_rule<float>(c, (const float *)in, c->rho32, (float *)out, c->stream);
   return set_error(c, DGX_ERR_ARG, "precision %d", prec);
 }
 
@@ -1194,6 +1195,37 @@ int dgx_basis_tables(int degree, double *out, int capacity) {
   if (out)
     for (int i = 0; i < capacity && i < (int)tab.size(); ++i) out[i] = tab[i];
   return (int)tab.size();
+}
+
+int dgx_set_mass_rule(dgx_ctx *c, int rule, double cg_tol, int cg_maxit) {
+  if (!c) return DGX_ERR_ARG;
+  if (rule != DGX_MASS_FAST && rule != DGX_MASS_CONSISTENT) return set_error(c, DGX_ERR_ARG, "mass rule %d", rule);
+  if (!(cg_tol > 0) || cg_maxit < 1) return set_error(c, DGX_ERR_ARG, "need cg_tol > 0 and cg_maxit >= 1");
+  cudaSetDevice(c->device);
+  if (!c->mass_stats) {
+    if (int e = check_cuda(c, cudaMalloc(&c->mass_stats, 2 * sizeof(int)), "cudaMalloc mass stats")) return e;
+    if (int e = check_cuda(c, cudaMemsetAsync(c->mass_stats, 0, 2 * sizeof(int), c->stream), "memset")) return e;
+  }
+  c->mass_rule = rule;
+  c->mass_tol = cg_tol;
+  c->mass_maxit = cg_maxit;
+  c->op_tuned[0] = c->op_tuned[1] = false;  // the operator's cost changed: choose its threads again
+  return 0;
+}
+
+int dgx_mass_cg_stats(dgx_ctx *c, int *max_iterations, int *unconverged) {
+  if (!c) return DGX_ERR_ARG;
+  int h[2] = {0, 0};
+  if (c->mass_stats) {
+    cudaSetDevice(c->device);
+    if (int e = check_cuda(c, cudaMemcpyAsync(h, c->mass_stats, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "memcpy"))
+      return e;
+    if (int e = check_cuda(c, cudaMemsetAsync(c->mass_stats, 0, sizeof(h), c->stream), "memset")) return e;
+    if (int e = check_cuda(c, cudaStreamSynchronize(c->stream), "mass stats")) return e;
+  }
+  if (max_iterations) *max_iterations = h[0];
+  if (unconverged) *unconverged = h[1];
+  return 0;
 }
 
 int dgx_operator_threads(const dgx_ctx *c, int prec) {

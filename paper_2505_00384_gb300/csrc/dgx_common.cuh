@@ -167,6 +167,15 @@ struct dgx_ctx {
   double *V64 = nullptr;
   float *V32 = nullptr;
 
+  // quadrature of the density-weighted mass A(rho) wherever it is applied or
+  // inverted: DGX_MASS_FAST (r+1 points, closed-form inverse) or
+  // DGX_MASS_CONSISTENT (2r+1 points, inverse by per-cell PCG to mass_tol
+  // relative residual, at most mass_maxit iterations; FP32 uses max(mass_tol, 1e-5))
+  int mass_rule = DGX_MASS_FAST;
+  double mass_tol = 1e-13;
+  int mass_maxit = 50;
+  int *mass_stats = nullptr;  // device [2]: largest PCG iteration count, unconverged cells
+
   // threads per CTA of k_grad / k_div chosen by the timing autotuner per
   // precision ([0] FP64, [1] FP32; 0 = the default of the degree)
   int op_threads[2] = {0, 0};
@@ -223,6 +232,28 @@ template <typename T>
 int launch_div(dgx_ctx *c, const T *V, const T *p, const T *pk, T *y, cudaStream_t s, double alpha = -1.0);
 template <typename T>
 int launch_mass_inverse(dgx_ctx *c, const T *in, const T *rho, T *out, cudaStream_t s, int nf = 3);
+// consistent (2r+1 point) density-weighted mass of nf fields (dgx_mass.cu):
+// inverse = 0: out = A_c(rho) in; inverse = 1: out = A_c(rho)^-1 in by per-cell PCG
+template <typename T>
+int launch_mass_cons(dgx_ctx *c, const T *in, const T *rho, T *out, cudaStream_t s, int nf, int inverse);
+// the context's mass rule: A(rho)^-1 of nf fields, A(rho) v of 3 fields (FP64),
+// and V = A(rho)^-1 B p (B scaled by the context's a~_ll dt)
+template <typename T>
+inline int mass_inverse_rule(dgx_ctx *c, const T *in, const T *rho, T *out, cudaStream_t s, int nf = 3) {
+  if (c->mass_rule == DGX_MASS_CONSISTENT) return launch_mass_cons<T>(c, in, rho, out, s, nf, 1);
+  return launch_mass_inverse<T>(c, in, rho, out, s, nf);
+}
+int launch_mass_fwd(dgx_ctx *c, const double *rho, const double *v, double *out, cudaStream_t s);
+inline int mass_forward_rule(dgx_ctx *c, const double *rho, const double *v, double *out, cudaStream_t s) {
+  if (c->mass_rule == DGX_MASS_CONSISTENT) return launch_mass_cons<double>(c, v, rho, out, s, 3, 0);
+  return launch_mass_fwd(c, rho, v, out, s);
+}
+template <typename T>
+inline int grad_inverse_rule(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s) {
+  if (c->mass_rule != DGX_MASS_CONSISTENT) return launch_grad<T>(c, p, rho, V, s);  // fused B and fast A^-1
+  if (int e = launch_grad<T>(c, p, rho, V, s, false)) return e;
+  return launch_mass_cons<T>(c, V, rho, V, s, 3, 1);  // in place: each cell reads its block first
+}
 // multi-mesh operator y = S x for members of one degree (N = r+1) and terrain kind;
 // `mem` is a device array of nmem members with consecutive cell ranges totalling ncell_total
 template <typename T>

@@ -106,7 +106,7 @@ int dgx_apply_mass(dgx_ctx *c, const double *rho, const double *in, double *out)
   if (!c) return DGX_ERR_ARG;
   if (!c->has_mesh) return set_error(c, DGX_ERR_STATE, "no mesh (call dgx_mesh_build)");
   if (!rho || !in || !out || in == out) return set_error(c, DGX_ERR_ARG, "null or aliased array");
-  return launch_mass_fwd(c, rho, in, out, c->stream);
+  return mass_forward_rule(c, rho, in, out, c->stream);
 }
 
 int dgx_kinetic_mass(dgx_ctx *c, const double *rho, const double *u, double *out) {
@@ -157,11 +157,11 @@ int dgx_imex_step(dgx_ctx *c, double *rho, double *u, double *p, int nsteps, con
           const double *Erm = w.Ten + (size_t)9 * N * m;
           if (c->imex_A[l * s + m] != 0.0) vec_axpby<double>(N, dt * c->imex_A[l * s + m], Erm, 1.0, w.t1, st);
         }
-        if ((e = launch_mass_inverse<double>(c, w.t1, w.ones, w.t2, st, 1))) return e;
+        if ((e = mass_inverse_rule<double>(c, w.t1, w.ones, w.t2, st, 1))) return e;
         if ((e = cp(w.rl, w.rn, b1))) return e;
         vec_axpby<double>(N, 1.0, w.t2, 1.0, w.rl, st);
         // momentum right-hand side
-        if ((e = launch_mass_fwd(c, w.rn, w.un, w.Fs, st))) return e;
+        if ((e = mass_forward_rule(c, w.rn, w.un, w.Fs, st))) return e;
         for (int m = 0; m < l; ++m) {
           const double *Erm = w.Ten + (size_t)9 * N * m;
           if (c->imex_A[l * s + m] != 0.0) vec_axpby<double>(3 * N, dt * c->imex_A[l * s + m], Erm + N, 1.0, w.Fs, st);
@@ -185,7 +185,7 @@ int dgx_imex_step(dgx_ctx *c, double *rho, double *u, double *p, int nsteps, con
             vec_axpby<double>(N, dt * c->imex_At[l * s + m], Erm + 8 * N, 1.0, w.Gs, st);
         }
         // W = A(rho^(l))^-1 F: the same for every fixed-point iteration of the stage
-        if ((e = launch_mass_inverse<double>(c, w.Fs, w.rl, w.W, st, 3))) return e;
+        if ((e = mass_inverse_rule<double>(c, w.Fs, w.rl, w.W, st, 3))) return e;
         // fixed-point iterations from the previous stage (ul, pl)
         for (int k = 0; k < K; ++k) {
           if ((e = dgx_set_coefficients(c, w.rl, w.pl, al, gm))) return e;

@@ -24,6 +24,7 @@ DGX_ERR_STATE = -6
 DGX_F64, DGX_F32 = 0, 1
 DGX_PC_NONE, DGX_PC_HELMHOLTZ, DGX_PC_INTERNAL_ENERGY, DGX_PC_LEARNED = 0, 1, 2, 3
 DGX_SOLVER_FGMRES, DGX_SOLVER_CG, DGX_SOLVER_MIXED = 0, 1, 2
+DGX_MASS_FAST, DGX_MASS_CONSISTENT = 0, 1
 
 
 class dgx_mesh_desc(C.Structure):
@@ -94,6 +95,8 @@ SIGNATURES = [
     ("dgx_kernel_launches", C.c_longlong, []),
     ("dgx_operator_threads", C.c_int, [_P, C.c_int]),
     ("dgx_basis_tables", C.c_int, [C.c_int, _P, C.c_int]),
+    ("dgx_set_mass_rule", C.c_int, [_P, C.c_int, C.c_double, C.c_int]),
+    ("dgx_mass_cg_stats", C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("dgx_apply_operator_noalloc", C.c_int, [_P, C.c_int, _P, _P]),
     ("dgx_set_imex", C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int]),
     ("dgx_explicit_tendencies", C.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -476,6 +479,19 @@ def dgx_basis_tables(degree):
         o += k
     assert o == n
     return out
+
+
+def dgx_set_mass_rule(ctx, rule, cg_tol=1e-13, cg_maxit=50):
+    """Quadrature of the density-weighted mass for every use in ctx: DGX_MASS_FAST
+    (r+1 points, fast inverse) or DGX_MASS_CONSISTENT (2r+1 points, per-cell PCG)."""
+    return _check(ctx, load().dgx_set_mass_rule(ctx, int(rule), float(cg_tol), int(cg_maxit)))
+
+
+def dgx_mass_cg_stats(ctx):
+    """(largest PCG iteration count, unconverged cell solves) since the previous call."""
+    it, bad = C.c_int(), C.c_int()
+    _check(ctx, load().dgx_mass_cg_stats(ctx, C.byref(it), C.byref(bad)))
+    return it.value, bad.value
 
 
 def dgx_operator_threads(ctx, prec):
