@@ -489,30 +489,20 @@ double dev_norm(dgx_ctx *c, long long n, const double *x, int *err) {
 // host; arnoldi_finish waits for that copy only and fills H column j (the
 // next direction may already be in flight behind it).  Returns hn (the
 // subdiagonal) or NaN on error (err set).
-// FP32 steps on at most this many unknowns run as one CTA (vec_arnoldi_cta):
-// there the dozen launches of the multi-block step cost more than the
-// arithmetic.  FP64 keeps the multi-block step: one SM's FP64 rate is too low.
-constexpr long long kArnoldiCtaMaxF32 = 32768;
-
 template <typename T>
 int arnoldi_launch(dgx_ctx *c, long long N, int j, T *V, T *w) {
   double *h1 = c->red_out, *h2 = c->red_out + 64, *nrm = c->red_out + 128;
-  const bool one_cta = sizeof(T) == 4 && N <= kArnoldiCtaMaxF32;
-  if (one_cta) {
-    vec_arnoldi_cta<T>(N, j + 1, V, N, w, V + (size_t)(j + 1) * N, c->red_out, c->stream);
-  } else {
-    vec_mdot<T>(N, j + 1, V, N, w, c->red, h1, c->stream);
-    vec_mupdate<T>(N, j + 1, V, N, h1, w, c->red, nullptr, c->stream);
-    vec_mdot<T>(N, j + 1, V, N, w, c->red, h2, c->stream);
-    vec_mupdate<T>(N, j + 1, V, N, h2, w, c->red, nrm, c->stream);
-  }
+  vec_mdot<T>(N, j + 1, V, N, w, c->red, h1, c->stream);
+  vec_mupdate<T>(N, j + 1, V, N, h1, w, c->red, nullptr, c->stream);
+  vec_mdot<T>(N, j + 1, V, N, w, c->red, h2, c->stream);
+  vec_mupdate<T>(N, j + 1, V, N, h2, w, c->red, nrm, c->stream);
   if (!c->arn_ev)
     if (int e = check_cuda(c, cudaEventCreateWithFlags(&c->arn_ev, cudaEventDisableTiming), "event")) return e;
   if (int e = check_cuda(c, cudaMemcpyAsync(c->host_red, c->red_out, 129 * sizeof(double), cudaMemcpyDeviceToHost,
                                             c->stream), "memcpy"))
     return e;
   if (int e = check_cuda(c, cudaEventRecord(c->arn_ev, c->stream), "event")) return e;
-  if (!one_cta) vec_scale_by_inv_sqrt<T>(N, nrm, w, V + (size_t)(j + 1) * N, c->stream);
+  vec_scale_by_inv_sqrt<T>(N, nrm, w, V + (size_t)(j + 1) * N, c->stream);
   return 0;
 }
 

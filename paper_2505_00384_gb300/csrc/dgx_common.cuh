@@ -297,10 +297,6 @@ void vec_mdot(long long n, int nv, const T *V, long long ld, const T *w, double 
 template <typename T>
 void vec_mupdate(long long n, int nv, const T *V, long long ld, const double *h, T *w, double *partial,
                  double *out_norm2, cudaStream_t s);
-// whole CGS2 Arnoldi step in one CTA (short vectors, nv <= 64): h1 -> out[0..nv),
-// h2 -> out[64..), |w|^2 -> out[128], vnext = w / |w|
-template <typename T>
-void vec_arnoldi_cta(long long n, int nv, const T *V, long long ld, T *w, T *vnext, double *out, cudaStream_t s);
 // y = x * (1 / sqrt(*nrm2)) with the scalar read on the device
 template <typename T>
 void vec_scale_by_inv_sqrt(long long n, const double *nrm2, const T *x, T *y, cudaStream_t s);

@@ -208,68 +208,9 @@ __global__ void __launch_bounds__(kThreads) k_lincomb(long long n, int nv, const
   }
 }
 
-// A whole Arnoldi step (classical Gram-Schmidt applied twice) in one CTA,
-// for vectors short enough that the multi-kernel step is bound by its
-// launches: h1 = V^T w, w -= V h1, h2 = V^T w, w -= V h2, nrm2 = w.w,
-// vnext = w / sqrt(nrm2).  Writes h1 to out[0..nv), h2 to out[64..64+nv) and
-// nrm2 to out[128].  One warp per basis vector for the dot products
-// (lane-strided sums, then a shuffle reduction: fixed order), FP64
-// accumulation and FP64 updates rounded once to T.
-template <typename T>
-__global__ void __launch_bounds__(1024) k_arnoldi_cta(long long n, int nv, const T *__restrict__ V, long long ld,
-                                                      T *__restrict__ w, T *__restrict__ vnext,
-                                                      double *__restrict__ out) {
-  __shared__ double h[64];
-  __shared__ double part[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int k = warp; k < nv; k += nw) {
-      const T *v = V + (long long)k * ld;
-      double sdot = 0.0;
-      for (long long i = lane; i < n; i += 32) sdot += (double)v[i] * (double)w[i];
-      for (int o = 16; o > 0; o >>= 1) sdot += __shfl_down_sync(0xffffffffu, sdot, o);
-      if (lane == 0) {
-        h[k] = sdot;
-        out[64 * pass + k] = sdot;
-      }
-    }
-    __syncthreads();
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-      double a = (double)w[i];
-      for (int k = 0; k < nv; ++k) a -= h[k] * (double)V[(long long)k * ld + i];
-      w[i] = (T)a;
-    }
-    __syncthreads();
-  }
-  double sn = 0.0;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) sn += (double)w[i] * (double)w[i];
-  for (int o = 16; o > 0; o >>= 1) sn += __shfl_down_sync(0xffffffffu, sn, o);
-  if (lane == 0) part[warp] = sn;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int k = 0; k < nw; ++k) t += part[k];
-    out[128] = t;
-    h[0] = t;
-  }
-  __syncthreads();
-  const T sc = (T)(1.0 / sqrt(h[0]));
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) vnext[i] = w[i] * sc;
-}
-
 }  // namespace
 
 int vec_partials() { return kMaxBlocks; }
-
-template <typename T>
-void vec_arnoldi_cta(long long n, int nv, const T *V, long long ld, T *w, T *vnext, double *out, cudaStream_t s) {
-  count_launch();
-  k_arnoldi_cta<T><<<1, 1024, 0, s>>>(n, nv, V, ld, w, vnext, out);
-}
-template void vec_arnoldi_cta<float>(long long, int, const float *, long long, float *, float *, double *,
-                                     cudaStream_t);
-template void vec_arnoldi_cta<double>(long long, int, const double *, long long, double *, double *, double *,
-                                      cudaStream_t);
 
 template <typename T>
 void vec_axpby(long long n, double a, const T *x, double b, T *y, cudaStream_t s) {
