@@ -352,7 +352,9 @@ void dgx_default_train_opts(dgx_train_opts *opts);
  * N <= 699050 in FP64 and N <= 1398101 in FP32; larger meshes get
  * DGX_ERR_ARG with a message.  The first call on a device looks up the
  * array's device address with that device current; make that first call
- * before any stream capture.  All calls share the one array and it keeps the
+ * before any stream capture.  The address is kept for the life of the
+ * process: a cudaDeviceReset (or anything else that unloads the library's
+ * module from the device) between calls makes the entry point unusable.  All calls share the one array and it keeps the
  * last call's contents: calls whose GPU work overlaps (other streams or
  * contexts on the same device) race on it and must be serialised by the
  * caller.  Nothing needs clearing: each call writes all 3N entries it reads.

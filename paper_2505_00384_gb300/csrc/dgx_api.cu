@@ -562,6 +562,8 @@ int inner_gmres32(dgx_ctx *c, const float *v, float *z, const float *dinv, int m
     if (hn <= 1e-300 || res <= tol * beta) break;
   }
   H.solve(jj);
+  for (int k = 0; k < jj; ++k)
+    if (!std::isfinite(H.y[k])) return set_error(c, DGX_ERR_BREAKDOWN, "inner GMRES: non-finite least-squares solution");
   // z = dinv .* (V y)
   if ((err = check_cuda(c, cudaMemcpyAsync(c->red_out + 192, H.y.data(), jj * sizeof(double),
                                            cudaMemcpyHostToDevice, c->stream), "memcpy"))) return err;
@@ -719,8 +721,8 @@ int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dg
       }
       continue;
     }
-    for (int k = 0; k < jj; ++k)
-      if (std::isnan(H.y[k])) return set_error(c, DGX_ERR_BREAKDOWN, "NaN in least-squares solution");
+    for (int k = 0; k < jj; ++k)  // an infinite coefficient (h(j,j) = 0) is a breakdown too
+      if (!std::isfinite(H.y[k])) return set_error(c, DGX_ERR_BREAKDOWN, "non-finite least-squares solution");
     if ((err = check_cuda(c, cudaMemcpyAsync(c->red_out + 192, H.y.data(), jj * sizeof(double),
                                              cudaMemcpyHostToDevice, c->stream), "memcpy"))) return err;
     vec_lincomb<double, double>(N, jj, Zb, N, c->red_out + 192, x, c->stream);
