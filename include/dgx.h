@@ -371,11 +371,27 @@ int dgx_apply_operator_noalloc(dgx_ctx *ctx, int prec, const void *x, void *y);
  * DoF in FP64). */
 int dgx_operator_cost(const dgx_ctx *ctx, double *flops_grad, double *flops_div, double *bytes_f64);
 
-/* Threads per CTA of the operator kernels (k_grad, k_div) for prec on this
- * context's mesh: a timing autotuner picks 128, 192 or 256 before the first
- * application on meshes of 2048 cells or more (outside stream capture); the
- * result of the operator does not depend on it.  0 before the first
- * application (and on smaller meshes: the degree's default). */
+/* Launch variants of the operator kernels (the two halves V = A^-1 B p and
+ * y = D p - C V), all computing the same operator to rounding:
+ *   0, 1, 2  one cell per CTA, one thread per 1D line of each sum-factorisation
+ *            sweep, 128 / 192 / 256 threads per CTA;
+ *   3, 4     fused kernels with C cells per CTA, C = 1 / 2 (degree >= 3) or
+ *            4 / 8 (degree <= 2), and 32 ceil(C (2r+1)^2 / 32) threads.
+ * The fused kernels keep the last interpolation direction, the pointwise flux
+ * and the first test direction in registers and deal the lines of several
+ * cells to one CTA; a fused variant is available when its shared memory
+ * (cells per CTA x per-cell plan) fits in 227 KB.  A timing autotuner picks
+ * the fastest available variant before the first application on meshes of
+ * 2048 cells or more (outside stream capture); smaller meshes use the
+ * degree's default (-1).  dgx_mesh_build resets the choice. */
+#define DGX_OP_VARIANTS 5
+/* The variant in use for prec (-1: the default, not tuned; -2: bad argument). */
+int dgx_operator_variant(const dgx_ctx *ctx, int prec);
+/* Pin variant 0..4 for prec on the current mesh (the autotuner then leaves prec
+ * alone), or hand the choice back to the autotuner with -1.  DGX_ERR_ARG for a
+ * variant that is unknown or does not fit; DGX_ERR_STATE without a mesh. */
+int dgx_set_operator_variant(dgx_ctx *ctx, int prec, int variant);
+/* Threads per CTA of the variant in use (0 while it is the default). */
 int dgx_operator_threads(const dgx_ctx *ctx, int prec);
 
 /* Number of CUDA kernels this library has launched in this process (all

@@ -327,8 +327,11 @@ void free_mesh(dgx_ctx *c) {
   c->kry64 = nullptr;
   c->kry32 = nullptr;
   c->kry64_elems = c->kry32_elems = 0;
-  c->op_threads[0] = c->op_threads[1] = 0;
-  c->op_tuned[0] = c->op_tuned[1] = false;
+  for (int ix = 0; ix < 2; ++ix) {  // a new mesh: launch variants are chosen again
+    c->op_variant[ix] = -1;
+    c->op_tuned[ix] = false;
+    c->op_pinned[ix] = false;
+  }
   c->has_mesh = c->has_coef = c->has_bg = false;
   c->rec_store = nullptr;
   c->rec_cap = c->rec_count = c->rec_seen = 0;
@@ -373,15 +376,16 @@ NodeP node_params(const dgx_ctx *c, const Tables1D *T = nullptr) {
 template <typename T>
 int apply_S(dgx_ctx *c, const T *x, T *y);
 
-// Timing autotuner of the threads per CTA of k_grad / k_div (128, 192, 256)
-// for this mesh and precision, run once before the first application on
-// meshes of at least 2048 cells (outside stream capture).  The operator's
-// result does not depend on the choice (each line of a sweep is computed by
-// one thread whatever the CTA size).
+// Timing autotuner of the operator's launch variant (one cell per CTA with
+// 128, 192 or 256 threads; the fused multi-cell kernels in their
+// configurations) for this mesh and precision, run once before the first
+// application on meshes of at least 2048 cells (outside stream capture), unless
+// a variant is pinned.  The operator's result does not depend on the choice to
+// more than rounding (the parity tests check every variant).
 template <typename T>
 int tune_operator(dgx_ctx *c) {
   const int ix = sizeof(T) == 8 ? 0 : 1;
-  if (c->op_tuned[ix]) return 0;
+  if (c->op_tuned[ix] || c->op_pinned[ix]) return 0;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 0;
   c->op_tuned[ix] = true;
@@ -395,9 +399,10 @@ int tune_operator(dgx_ctx *c) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
-  int best_t = 0, err = 0;
-  for (int t : {128, 192, 256}) {
-    c->op_threads[ix] = t;
+  int best_v = -1, err = 0;
+  for (int v = 0; v < kOpVariants; ++v) {
+    if (!op_variant_ok<T>(c, v)) continue;
+    c->op_variant[ix] = v;
     if ((err = apply_S<T>(c, x, y))) break;
     cudaEventRecord(e0, c->stream);
     for (int r = 0; r < 2 && !err; ++r) err = apply_S<T>(c, x, y);
@@ -407,13 +412,13 @@ int tune_operator(dgx_ctx *c) {
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best) {
       best = ms;
-      best_t = t;
+      best_v = v;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(buf);
-  c->op_threads[ix] = err ? 0 : best_t;
+  c->op_variant[ix] = err ? -1 : best_v;
   return err;
 }
 
@@ -1211,7 +1216,8 @@ int dgx_set_mass_rule(dgx_ctx *c, int rule, double cg_tol, int cg_maxit) {
   c->mass_rule = rule;
   c->mass_tol = cg_tol;
   c->mass_maxit = cg_maxit;
-  c->op_tuned[0] = c->op_tuned[1] = false;  // the operator's cost changed: choose its threads again
+  for (int ix = 0; ix < 2; ++ix)  // the operator's cost changed: choose its variant again
+    if (!c->op_pinned[ix]) c->op_tuned[ix] = false;
   return 0;
 }
 
@@ -1232,7 +1238,31 @@ int dgx_mass_cg_stats(dgx_ctx *c, int *max_iterations, int *unconverged) {
 
 int dgx_operator_threads(const dgx_ctx *c, int prec) {
   if (!c || (prec != DGX_F64 && prec != DGX_F32)) return -1;
-  return c->op_threads[prec == DGX_F64 ? 0 : 1];
+  const int v = c->op_variant[prec == DGX_F64 ? 0 : 1];
+  return v < 0 ? 0 : op_variant_threads(c, v);
+}
+
+int dgx_operator_variant(const dgx_ctx *c, int prec) {
+  if (!c || (prec != DGX_F64 && prec != DGX_F32)) return -2;
+  return c->op_variant[prec == DGX_F64 ? 0 : 1];
+}
+
+int dgx_set_operator_variant(dgx_ctx *c, int prec, int variant) {
+  if (!c) return DGX_ERR_ARG;
+  if (prec != DGX_F64 && prec != DGX_F32) return set_error(c, DGX_ERR_ARG, "precision %d", prec);
+  const int ix = prec == DGX_F64 ? 0 : 1;
+  if (variant == -1) {  // back to the autotuner
+    c->op_pinned[ix] = false;
+    c->op_tuned[ix] = false;
+    c->op_variant[ix] = -1;
+    return 0;
+  }
+  if (!c->has_mesh) return set_error(c, DGX_ERR_STATE, "no mesh (call dgx_mesh_build)");
+  const bool ok = prec == DGX_F64 ? op_variant_ok<double>(c, variant) : op_variant_ok<float>(c, variant);
+  if (!ok) return set_error(c, DGX_ERR_ARG, "operator variant %d is not available for this mesh and precision", variant);
+  c->op_variant[ix] = variant;
+  c->op_pinned[ix] = true;
+  return 0;
 }
 
 int dgx_operator_cost(const dgx_ctx *c, double *flops_grad, double *flops_div, double *b64) {

@@ -47,12 +47,16 @@ __host__ __device__ constexpr int tab_size(int N, int Q) { return 7 * Q * N + 3 
 // their even-odd (centro-symmetric) storage in constant memory, all degrees
 // back to back.  A matrix of R rows and C columns stores E[(R+1)/2][C/2],
 // Od[(R+1)/2][C/2] and, for odd C, the middle column Mc[(R+1)/2].
-enum MatId : int { M_I = 0, M_D, M_IT, M_DT, M_IA, M_P, M_PT, M_IIT, M_DDT, M_IDT, M_IAT, M_COUNT };
+// M_PIT = PT IT and M_PDT = PT DT (N x Q): the test with the basis (or its
+// derivative) followed by the fast inverse's first factor, in one product.
+enum MatId : int { M_I = 0, M_D, M_IT, M_DT, M_IA, M_P, M_PT, M_IIT, M_DDT, M_IDT, M_IAT, M_PIT, M_PDT, M_COUNT };
 __host__ __device__ constexpr int mat_rows(int id, int N) { return (id == M_I || id == M_D) ? 2 * N - 1 : N; }
 __host__ __device__ constexpr int mat_cols(int id, int N) {
   return (id == M_I || id == M_D || id == M_IA || id == M_P || id == M_PT || id == M_IAT) ? N : 2 * N - 1;
 }
-__host__ __device__ constexpr int mat_parity(int id) { return (id == M_D || id == M_DT || id == M_IDT) ? -1 : 1; }
+__host__ __device__ constexpr int mat_parity(int id) {
+  return (id == M_D || id == M_DT || id == M_IDT || id == M_PDT) ? -1 : 1;
+}
 __host__ __device__ constexpr int eo_size(int R, int C) { return 2 * ((R + 1) / 2) * (C / 2) + ((C & 1) ? (R + 1) / 2 : 0); }
 __host__ __device__ constexpr int eo_deg_size(int N) {
   int s = 0;
@@ -176,10 +180,14 @@ struct dgx_ctx {
   int mass_maxit = 50;
   int *mass_stats = nullptr;  // device [2]: largest PCG iteration count, unconverged cells
 
-  // threads per CTA of k_grad / k_div chosen by the timing autotuner per
-  // precision ([0] FP64, [1] FP32; 0 = the default of the degree)
-  int op_threads[2] = {0, 0};
+  // launch variant of the operator kernels per precision ([0] FP64, [1] FP32):
+  // 0..2 one cell per CTA (k_grad / k_div) with 128 / 192 / 256 threads, 3..4
+  // the fused multi-cell kernels in configuration v - 3 (fused_cpb); -1 = the
+  // default of the degree.  Chosen by the timing autotuner (op_tuned) unless
+  // pinned by dgx_set_operator_variant (op_pinned).
+  int op_variant[2] = {-1, -1};
   bool op_tuned[2] = {false, false};
+  bool op_pinned[2] = {false, false};
 
   // Krylov workspace (grown on demand)
   double *kry64 = nullptr;
@@ -254,6 +262,23 @@ inline int grad_inverse_rule(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStr
   if (int e = launch_grad<T>(c, p, rho, V, s, false)) return e;
   return launch_mass_cons<T>(c, V, rho, V, s, 3, 1);  // in place: each cell reads its block first
 }
+// fused multi-cell operator kernels (dgx_fused.cuh): configuration cfg (0, 1)
+// of degree N = r+1 has fused_cpb cells and fused_nt threads per CTA, the
+// threads covering the cells' Q x Q Gauss-point columns of the z pass in one
+// round (whole warps); fused_grad with inv = false writes the dual vector
+// B p; fused_div uses kq (FP64 only) when not null
+__host__ __device__ constexpr int fused_cpb(int N, int cfg) { return N <= 3 ? (cfg ? 8 : 4) : (cfg ? 2 : 1); }
+__host__ __device__ constexpr int fused_nt(int N, int cfg) {
+  return ((fused_cpb(N, cfg) * (2 * N - 1) * (2 * N - 1) + 31) / 32) * 32;
+}
+constexpr size_t kFusedMaxSmem = 227 * 1024;
+template <typename T, int N, bool CURVED>
+int fused_grad(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s, bool inv, double alpha, int cfg);
+template <typename T, int N, bool CURVED>
+int fused_div(dgx_ctx *c, const T *V, const T *p, const T *pk, T *y, cudaStream_t s, double alpha, const T *kq,
+              int cfg);
+template <typename T, int N, bool CURVED>
+size_t fused_smem(int cfg);
 // multi-mesh operator y = S x for members of one degree (N = r+1) and terrain kind;
 // `mem` is a device array of nmem members with consecutive cell ranges totalling ncell_total
 template <typename T>
@@ -279,6 +304,12 @@ int launch_diag(dgx_ctx *c, const T *rho, const T *pk, T *dh, T *die, cudaStream
 int ensure_diag(dgx_ctx *c, bool f64);
 template <typename T>
 OpP<T> make_params(const dgx_ctx *c);
+// operator launch variants (see dgx_ctx::op_variant): count, whether variant v
+// fits this context's mesh and precision, and its threads per CTA
+constexpr int kOpVariants = 5;
+template <typename T>
+bool op_variant_ok(const dgx_ctx *c, int v);
+int op_variant_threads(const dgx_ctx *c, int v);
 
 // vector kernels (dgx_vector.cu)
 template <typename T>

@@ -1,0 +1,108 @@
+// Launchers of the fused operator kernels (dgx_fused.cuh), instantiated per
+// precision and degree by the small dgx_fused_*.cu translation units so that
+// the build compiles them in parallel.
+#pragma once
+
+#include <set>
+#include <utility>
+
+#include "dgx_fused.cuh"
+
+namespace dgx {
+namespace {
+
+// Dynamic shared memory above 48 KB and the maximum carveout, set once per
+// kernel and device (so that launches inside stream capture make no calls).
+template <typename Kern>
+int fprep(dgx_ctx *c, Kern k, size_t smem) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void *>> done;
+  const std::pair<int, const void *> key(c->device, reinterpret_cast<const void *>(k));
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(key)) return 0;
+  }
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(mu);
+    done.insert(key);
+  }
+  return check_cuda(c, e, "cudaFuncSetAttribute (fused operator)");
+}
+
+template <typename T, int N, bool CURVED, bool INV, int CPB, int NT>
+int fgrad_go(dgx_ctx *c, const OpP<T> &P, const T *p, const T *rho, T *V, cudaStream_t s) {
+  const size_t smem = sizeof(T) * (size_t)CPB * FGradL<N, CURVED>::per_cell;
+  if (smem > kFusedMaxSmem) return set_error(c, DGX_ERR_ARG, "fused gradient kernel: %zu bytes of shared memory", smem);
+  auto k = kf_grad<T, N, CURVED, INV, CPB, NT>;
+  if (int e = fprep(c, k, smem)) return e;
+  const int ncell = (int)c->ncell;
+  count_launch();
+  k<<<(unsigned)((ncell + CPB - 1) / CPB), NT, smem, s>>>(P, p, rho, V, c->N, ncell);
+  return check_cuda(c, cudaGetLastError(), "kf_grad launch");
+}
+
+template <typename T, int N, bool CURVED, bool KQ, int CPB, int NT>
+int fdiv_go(dgx_ctx *c, const OpP<T> &P, const T *V, const T *p, const T *pk, T *y, const T *kq, cudaStream_t s) {
+  const size_t smem = sizeof(T) * (size_t)CPB * FDivL<N, CURVED, KQ>::per_cell;
+  if (smem > kFusedMaxSmem) return set_error(c, DGX_ERR_ARG, "fused divergence kernel: %zu bytes of shared memory", smem);
+  auto k = kf_div<T, N, CURVED, KQ, CPB, NT>;
+  if (int e = fprep(c, k, smem)) return e;
+  const int ncell = (int)c->ncell;
+  count_launch();
+  k<<<(unsigned)((ncell + CPB - 1) / CPB), NT, smem, s>>>(P, V, p, pk, y, c->N, ncell, kq);
+  return check_cuda(c, cudaGetLastError(), "kf_div launch");
+}
+
+}  // namespace
+
+template <typename T, int N, bool CURVED>
+int fused_grad(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s, bool inv, double alpha, int cfg) {
+  if (int e = upload_fused_tables(c)) return e;
+  OpP<T> P = make_params<T>(c);
+  if (alpha >= 0.0) P.alpha = (T)alpha;
+  if (!inv) return fgrad_go<T, N, CURVED, false, fused_cpb(N, 0), fused_nt(N, 0)>(c, P, p, rho, V, s);
+  if (cfg == 1) return fgrad_go<T, N, CURVED, true, fused_cpb(N, 1), fused_nt(N, 1)>(c, P, p, rho, V, s);
+  return fgrad_go<T, N, CURVED, true, fused_cpb(N, 0), fused_nt(N, 0)>(c, P, p, rho, V, s);
+}
+
+template <typename T, int N, bool CURVED>
+int fused_div(dgx_ctx *c, const T *V, const T *p, const T *pk, T *y, cudaStream_t s, double alpha, const T *kq,
+              int cfg) {
+  if (int e = upload_fused_tables(c)) return e;
+  OpP<T> P = make_params<T>(c);
+  if (alpha >= 0.0) P.alpha = (T)alpha;
+  if constexpr (sizeof(T) == 8) {
+    if (kq) {
+      if (cfg == 1) return fdiv_go<T, N, CURVED, true, fused_cpb(N, 1), fused_nt(N, 1)>(c, P, V, p, pk, y, kq, s);
+      return fdiv_go<T, N, CURVED, true, fused_cpb(N, 0), fused_nt(N, 0)>(c, P, V, p, pk, y, kq, s);
+    }
+    return fdiv_go<T, N, CURVED, false, fused_cpb(N, 0), fused_nt(N, 0)>(c, P, V, p, pk, y, nullptr, s);
+  } else {
+    if (cfg == 1) return fdiv_go<T, N, CURVED, false, fused_cpb(N, 1), fused_nt(N, 1)>(c, P, V, p, pk, y, nullptr, s);
+    return fdiv_go<T, N, CURVED, false, fused_cpb(N, 0), fused_nt(N, 0)>(c, P, V, p, pk, y, nullptr, s);
+  }
+}
+
+// Shared memory of one fused configuration (bytes), for the variant list.
+template <typename T, int N, bool CURVED>
+size_t fused_smem(int cfg) {
+  const int cpb = fused_cpb(N, cfg);
+  const size_t g = sizeof(T) * (size_t)cpb * FGradL<N, CURVED>::per_cell;
+  const size_t d = sizeof(T) * (size_t)cpb * FDivL<N, CURVED, sizeof(T) == 8>::per_cell;
+  return g > d ? g : d;
+}
+
+#define DGX_FUSED_INSTANTIATE(T, NN)                                                                          \
+  template int fused_grad<T, NN, false>(dgx_ctx *, const T *, const T *, T *, cudaStream_t, bool, double, int); \
+  template int fused_grad<T, NN, true>(dgx_ctx *, const T *, const T *, T *, cudaStream_t, bool, double, int);  \
+  template int fused_div<T, NN, false>(dgx_ctx *, const T *, const T *, const T *, T *, cudaStream_t, double,   \
+                                       const T *, int);                                                        \
+  template int fused_div<T, NN, true>(dgx_ctx *, const T *, const T *, const T *, T *, cudaStream_t, double,    \
+                                      const T *, int);                                                         \
+  template size_t fused_smem<T, NN, false>(int);                                                               \
+  template size_t fused_smem<T, NN, true>(int);
+
+}  // namespace dgx

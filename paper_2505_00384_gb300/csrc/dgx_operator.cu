@@ -252,32 +252,6 @@ struct DivL {
   static constexpr int total = oX + 4 * N3;
 };
 
-// Face trace slot -> (face, side, field): field 0 = kappa, 1..3 = V_x,V_y,V_z.
-template <bool CURVED>
-__device__ __forceinline__ void div_slot(int sl, int &f, int &side, int &field) {
-  if (sl < 16) {
-    f = sl >> 2;
-    const int w = sl & 3;  // kappa-, Vk-, kappa+, Vk+
-    side = w >> 1;
-    field = (w & 1) ? 1 + (f >> 1) : 0;
-  } else if (CURVED) {
-    f = 4 + ((sl - 16) >> 3);
-    const int w = (sl - 16) & 7;  // kappa-, Vx-, Vy-, Vz-, kappa+, Vx+, Vy+, Vz+
-    side = w >> 2;
-    field = w & 3;
-  } else {
-    f = 4 + ((sl - 16) >> 2);
-    const int w = (sl - 16) & 3;
-    side = w >> 1;
-    field = (w & 1) ? 3 : 0;
-  }
-}
-
-template <bool CURVED>
-__device__ __forceinline__ int div_slot_base(int f) {
-  return f < 4 ? 4 * f : (CURVED ? 16 + 8 * (f - 4) : 16 + 4 * (f - 4));
-}
-
 template <typename T, int N, int Q, bool CURVED>
 __device__ __forceinline__ void div_body(const OpP<T> &P, const long long cell, const T *__restrict__ V,
                                          const T *__restrict__ p, const T *__restrict__ pk, T *__restrict__ y,
@@ -600,16 +574,25 @@ int prep(dgx_ctx *c, Kern k, size_t smem) {
 
 int threads_for(int N) { return N <= 3 ? 128 : 256; }
 
+constexpr int kLegacyThreads[3] = {128, 192, 256};
+
+// variant in use for precision T: the chosen one, else the default of the degree
+template <typename T>
+int op_variant(const dgx_ctx *c) {
+  return c->op_variant[sizeof(T) == 8 ? 0 : 1];
+}
+
 template <typename T>
 int op_threads(const dgx_ctx *c, int N) {
-  const int t = c->op_threads[sizeof(T) == 8 ? 0 : 1];
-  return t > 0 ? t : threads_for(N);
+  const int v = op_variant<T>(c);
+  return (v >= 0 && v < 3) ? kLegacyThreads[v] : threads_for(N);
 }
 
 template <typename T, int N, bool CURVED>
 int grad_impl(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s, bool inv, double alpha) {
   constexpr int Q = 2 * N - 1;
   const size_t smem = sizeof(T) * GradL<N, Q, CURVED>::total;
+  if (op_variant<T>(c) >= 3) return fused_grad<T, N, CURVED>(c, p, rho, V, s, inv, alpha, op_variant<T>(c) - 3);
   OpP<T> P = make_params<T>(c);
   if (alpha >= 0.0) P.alpha = (T)alpha;
   if (inv) {
@@ -629,16 +612,17 @@ int grad_impl(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s, bool i
 template <typename T, int N, bool CURVED>
 int div_impl(dgx_ctx *c, const T *V, const T *p, const T *pk, T *y, cudaStream_t s, double alpha) {
   constexpr int Q = 2 * N - 1;
-  const size_t smem = sizeof(T) * DivL<N, Q, CURVED>::total;
-  auto k = k_div<T, N, Q, CURVED>;
-  if (int e = prep(c, k, smem)) return e;
-  OpP<T> P = make_params<T>(c);
-  if (alpha >= 0.0) P.alpha = (T)alpha;
   // the precomputed kappa applies to the context's own p_k and alpha only, and
   // to FP64 (FP32 interpolates p_k faster than it loads the Q^3 values)
   const T *kq = nullptr;
   if constexpr (sizeof(T) == 8)
     if (alpha < 0.0 && pk == c->pk64 && c->kq64_version == c->coef_version) kq = reinterpret_cast<const T *>(c->kq64);
+  if (op_variant<T>(c) >= 3) return fused_div<T, N, CURVED>(c, V, p, pk, y, s, alpha, kq, op_variant<T>(c) - 3);
+  const size_t smem = sizeof(T) * DivL<N, Q, CURVED>::total;
+  auto k = k_div<T, N, Q, CURVED>;
+  if (int e = prep(c, k, smem)) return e;
+  OpP<T> P = make_params<T>(c);
+  if (alpha >= 0.0) P.alpha = (T)alpha;
   count_launch();
   k<<<(unsigned)c->ncell, op_threads<T>(c, N), smem, s>>>(P, V, p, pk, y, c->N, kq);
   return check_cuda(c, cudaGetLastError(), "k_div launch");
@@ -733,6 +717,33 @@ OpP<T> make_params(const dgx_ctx *c) {
 }
 template OpP<double> make_params<double>(const dgx_ctx *);
 template OpP<float> make_params<float>(const dgx_ctx *);
+
+template <typename T>
+bool op_variant_ok(const dgx_ctx *c, int v) {
+  if (v < 0 || v >= kOpVariants) return false;
+  if (v < 3) return true;
+  size_t smem = 0;
+#define FSM(NN) (c->curved ? fused_smem<T, NN, true>(v - 3) : fused_smem<T, NN, false>(v - 3))
+  switch (c->n) {
+    case 2: smem = FSM(2); break;
+    case 3: smem = FSM(3); break;
+    case 4: smem = FSM(4); break;
+    case 5: smem = FSM(5); break;
+    case 6: smem = FSM(6); break;
+    case 7: smem = FSM(7); break;
+    default: return false;
+  }
+#undef FSM
+  return smem <= kFusedMaxSmem;
+}
+template bool op_variant_ok<double>(const dgx_ctx *, int);
+template bool op_variant_ok<float>(const dgx_ctx *, int);
+
+int op_variant_threads(const dgx_ctx *c, int v) {
+  if (v >= 0 && v < 3) return kLegacyThreads[v];
+  if (v >= 3 && v < kOpVariants) return fused_nt(c->n, v - 3);
+  return threads_for(c->n);
+}
 
 template <typename T>
 int launch_grad(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s, bool inv, double alpha) {

@@ -172,6 +172,34 @@ __device__ __forceinline__ long long neighbour(const OpP<T> &P, const CellPos &c
   return x + (long long)P.nx * (y + (long long)P.ny * z);
 }
 
+// Face trace slots of the divergence kernels (k_div, kf_div): slot -> (face,
+// side, field), field 0 = kappa, 1..3 = V_x, V_y, V_z; x and y faces carry
+// (kappa-, V_k-, kappa+, V_k+), curved z faces all three components per side.
+template <bool CURVED>
+__device__ __forceinline__ void div_slot(int sl, int &f, int &side, int &field) {
+  if (sl < 16) {
+    f = sl >> 2;
+    const int w = sl & 3;  // kappa-, Vk-, kappa+, Vk+
+    side = w >> 1;
+    field = (w & 1) ? 1 + (f >> 1) : 0;
+  } else if (CURVED) {
+    f = 4 + ((sl - 16) >> 3);
+    const int w = (sl - 16) & 7;  // kappa-, Vx-, Vy-, Vz-, kappa+, Vx+, Vy+, Vz+
+    side = w >> 2;
+    field = w & 3;
+  } else {
+    f = 4 + ((sl - 16) >> 2);
+    const int w = (sl - 16) & 3;
+    side = w >> 1;
+    field = (w & 1) ? 3 : 0;
+  }
+}
+
+template <bool CURVED>
+__device__ __forceinline__ int div_slot_base(int f) {
+  return f < 4 ? 4 * f : (CURVED ? 16 + 8 * (f - 4) : 16 + 4 * (f - 4));
+}
+
 template <typename T, int N, int Q>
 __device__ __forceinline__ void load_tables(const T *__restrict__ g, T *s) {
   constexpr int TS = tab_size(N, Q);
@@ -267,13 +295,24 @@ static int upload_const_tables(dgx_ctx *c) {
     if (!build_table_block(r, tab)) return set_error(c, DGX_ERR_ARG, "table construction failed (r=%d)", r);
     const int off[M_COUNT] = {tab_off_I(N, Q),  tab_off_D(N, Q),  tab_off_IT(N, Q),  tab_off_DT(N, Q),
                               tab_off_Ia(N, Q), tab_off_P(N, Q),  tab_off_PT(N, Q),  tab_off_IIT(N, Q),
-                              tab_off_DDT(N, Q), tab_off_IDT(N, Q), tab_off_Ia(N, Q)};
+                              tab_off_DDT(N, Q), tab_off_IDT(N, Q), tab_off_Ia(N, Q), tab_off_IT(N, Q),
+                              tab_off_DT(N, Q)};
     for (int id = 0; id < M_COUNT; ++id) {
       const int R = mat_rows(id, N), C = mat_cols(id, N), HO = (R + 1) / 2, HI = C / 2;
-      std::vector<double> Mv(tab.begin() + off[id], tab.begin() + off[id] + R * C);
-      if (id == M_IAT)  // transpose of Ia (forward fast mass: Ia^T J Ia)
+      std::vector<double> Mv(R * C, 0.0);
+      if (id == M_IAT) {  // transpose of Ia (forward fast mass: Ia^T J Ia)
         for (int a = 0; a < R; ++a)
           for (int q = 0; q < C; ++q) Mv[a * C + q] = tab[off[id] + q * N + a];
+      } else if (id == M_PIT || id == M_PDT) {  // PT [q][a] times IT or DT [a][g]
+        for (int q = 0; q < R; ++q)
+          for (int g = 0; g < C; ++g) {
+            double acc = 0.0;
+            for (int a = 0; a < N; ++a) acc += tab[tab_off_PT(N, Q) + q * N + a] * tab[off[id] + a * Q + g];
+            Mv[q * C + g] = acc;
+          }
+      } else {
+        for (int k = 0; k < R * C; ++k) Mv[k] = tab[off[id] + k];
+      }
       const double *M = Mv.data();
       const double s = mat_parity(id);
       double mx = 0.0, asym = 0.0;

@@ -94,6 +94,8 @@ SIGNATURES = [
     ("dgx_operator_cost", C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("dgx_kernel_launches", C.c_longlong, []),
     ("dgx_operator_threads", C.c_int, [_P, C.c_int]),
+    ("dgx_operator_variant", C.c_int, [_P, C.c_int]),
+    ("dgx_set_operator_variant", C.c_int, [_P, C.c_int, C.c_int]),
     ("dgx_basis_tables", C.c_int, [C.c_int, _P, C.c_int]),
     ("dgx_set_mass_rule", C.c_int, [_P, C.c_int, C.c_double, C.c_int]),
     ("dgx_mass_cg_stats", C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
@@ -492,6 +494,19 @@ def dgx_mass_cg_stats(ctx):
     it, bad = C.c_int(), C.c_int()
     _check(ctx, load().dgx_mass_cg_stats(ctx, C.byref(it), C.byref(bad)))
     return it.value, bad.value
+
+
+DGX_OP_VARIANTS = 5
+
+
+def dgx_operator_variant(ctx, prec):
+    """Launch variant of the operator kernels in use for prec (-1: the default)."""
+    return load().dgx_operator_variant(ctx, prec)
+
+
+def dgx_set_operator_variant(ctx, prec, variant):
+    """Pin launch variant 0..4 for prec on the current mesh, or -1 for the autotuner."""
+    return _check(ctx, load().dgx_set_operator_variant(ctx, int(prec), int(variant)))
 
 
 def dgx_operator_threads(ctx, prec):

@@ -129,6 +129,68 @@ def test_operator_f32(case):
     assert rel_max_err(host(y), ref) <= TOL32
 
 
+def _pin(c, prec, variant):
+    """Pin a launch variant; False when it does not fit this mesh (shared memory)."""
+    try:
+        dgx.dgx_set_operator_variant(c.ctx, prec, variant)
+    except dgx.DgxError as e:
+        assert e.code == dgx.DGX_ERR_ARG
+        return False
+    assert dgx.dgx_operator_variant(c.ctx, prec) == variant
+    return True
+
+
+@pytest.mark.parametrize("variant", list(range(dgx.DGX_OP_VARIANTS)))
+def test_operator_variants(case, variant):
+    """Every launch variant of the operator kernels (one cell per CTA at three
+    thread counts, the fused multi-cell kernels in two configurations) against
+    the oracle: both halves and S in FP64 (1e-12), S in FP32 (2e-5)."""
+    import torch
+    ok64 = _pin(case, dgx.DGX_F64, variant)
+    ok32 = _pin(case, dgx.DGX_F32, variant)
+    assert ok64 or ok32 or variant >= 3
+    p = inputs.random_field(case.N, 81, scale=100.0)
+    pd = dev(p)
+    if ok64:
+        V = torch.zeros(3 * case.N, dtype=torch.float64, device="cuda")
+        dgx.dgx_apply_grad(case.ctx, dgx.DGX_F64, pd.data_ptr(), V.data_ptr())
+        assert rel_max_err(host(V), O.apply_Ainv(case.m, case.rho, O.apply_B(case.m, A_DT, p))) <= TOL64
+        W = inputs.random_field(3 * case.N, 82)
+        Wd = dev(W)
+        y = torch.zeros(case.N, dtype=torch.float64, device="cuda")
+        dgx.dgx_apply_div(case.ctx, dgx.DGX_F64, Wd.data_ptr(), pd.data_ptr(), y.data_ptr())
+        ref = O.apply_D(case.m, GAMMA, p) - O.apply_C(case.m, A_DT, GAMMA, case.pk, W)
+        assert rel_max_err(host(y), ref) <= TOL64
+        dgx.dgx_apply_operator(case.ctx, dgx.DGX_F64, pd.data_ptr(), y.data_ptr())
+        assert rel_max_err(host(y), O.apply_S(case.m, A_DT, GAMMA, case.rho, case.pk, p)) <= TOL64
+    if ok32:
+        p32 = p.astype(np.float32)
+        pf = dev(p32)
+        yf = torch.zeros(case.N, dtype=torch.float32, device="cuda")
+        dgx.dgx_apply_operator(case.ctx, dgx.DGX_F32, pf.data_ptr(), yf.data_ptr())
+        ref = O.apply_S(case.m, A_DT, GAMMA, case.rho, case.pk, p32.astype(np.float64))
+        assert rel_max_err(host(yf), ref) <= TOL32
+
+
+def test_variant_pinning_errors():
+    c = Case(2, 2, 2, 2)
+    for bad in (-3, dgx.DGX_OP_VARIANTS, 99):
+        with pytest.raises(dgx.DgxError) as e:
+            dgx.dgx_set_operator_variant(c.ctx, dgx.DGX_F64, bad)
+        assert e.value.code == dgx.DGX_ERR_ARG
+    with pytest.raises(dgx.DgxError):
+        dgx.dgx_set_operator_variant(c.ctx, 7, 0)
+    dgx.dgx_set_operator_variant(c.ctx, dgx.DGX_F64, 3)
+    assert dgx.dgx_operator_variant(c.ctx, dgx.DGX_F64) == 3
+    assert dgx.dgx_operator_threads(c.ctx, dgx.DGX_F64) == 128
+    dgx.dgx_set_operator_variant(c.ctx, dgx.DGX_F64, -1)
+    assert dgx.dgx_operator_variant(c.ctx, dgx.DGX_F64) == -1
+    dgx.dgx_set_operator_variant(c.ctx, dgx.DGX_F32, 4)
+    dgx.dgx_mesh_build(c.ctx, c.desc)  # a new mesh resets the choice
+    assert dgx.dgx_operator_variant(c.ctx, dgx.DGX_F32) == -1
+    c.close()
+
+
 def test_operator_is_deterministic(case):
     import torch
     p = dev(inputs.random_field(case.N, 61))
@@ -159,35 +221,77 @@ def test_errors_are_reported():
     c.close()
 
 
-@pytest.mark.parametrize("terrain", [0, 1])
-def test_full_size_sampled(terrain):
-    """64 x 64 x 32 cells, r = 4 (16 384 000 DoFs), terrain-following hill,
-    far-field lateral faces: GPU apply over the whole mesh, compared on
-    sampled cells (corners, edges, the hill top, random) with the oracle's
-    cell-by-cell evaluation."""
+def _sampled_cells(nx, ny, nz, seed):
+    """Corners, edges, the hill top and random cells of an nx x ny x nz mesh."""
+    cells = [0, nx - 1, nx * ny - 1, nx * ny * nz - 1, nx // 2 + nx * (ny // 2), nx // 2 + nx * ny * (nz - 1),
+             nx // 2 - 1 + nx * (ny // 2 - 1 + ny * (nz // 2 - 1)), nx * (ny - 1) + nx * ny * (nz // 2)]
+    rng = np.random.default_rng(seed)
+    cells += list(rng.integers(0, nx * ny * nz, 9))
+    return sorted(set(int(cc) for cc in cells))
+
+
+def _sampled_parity(c, nx, ny, nz, n3, precs, variants=(None,), seed=71):
+    """Apply S over the whole mesh with each pinned variant (None: the
+    autotuner's choice, as the bench runs it) and compare sampled cells with the
+    oracle's cell-by-cell evaluation."""
     import torch
-    c = Case(64, 64, 32, 4, Lx=60000.0, Ly=60000.0, Lz=20000.0, terrain=terrain, hc=400.0, ac=1000.0,
-             bc_lateral=1)
     X = torch.zeros(3 * c.N, dtype=torch.float64, device="cuda")
     dgx.dgx_node_coords(c.ctx, X.data_ptr())
     z = host(X)[2 * c.N:]
-    rho = inputs.perturbed_profile(z, 1.2, 7314.0, 0.05, 71)
-    pk = inputs.perturbed_profile(z, 1e5, 7314.0, 0.05, 72)
+    rho = inputs.perturbed_profile(z, 1.2, 7314.0, 0.05, seed)
+    pk = inputs.perturbed_profile(z, 1e5, 7314.0, 0.05, seed + 1)
     c.set_coefficients(rho, pk, A_DT)
-    p = inputs.random_field(c.N, 73, scale=50.0)
-    y = torch.zeros(c.N, dtype=torch.float64, device="cuda")
-    pd = dev(p)
-    dgx.dgx_apply_operator(c.ctx, dgx.DGX_F64, pd.data_ptr(), y.data_ptr())
-    yg = host(y)
-    nx, ny, nz = 64, 64, 32
-    cells = [0, nx - 1, nx * ny - 1, nx * ny * nz - 1, 32 + nx * 32, 32 + nx * (32 + ny * 0),
-             31 + nx * (31 + ny * 15)]
-    rng = np.random.default_rng(74)
-    cells += list(rng.integers(0, nx * ny * nz, 9))
-    ys = O.apply_S(c.m, A_DT, GAMMA, rho, pk, p, cells=cells)
-    n3 = 125
+    p = inputs.random_field(c.N, seed + 2, scale=50.0)
+    cells = _sampled_cells(nx, ny, nz, seed + 3)
     idx = np.concatenate([np.arange(cc * n3, (cc + 1) * n3) for cc in cells])
-    assert rel_max_err(yg[idx], ys[idx]) <= TOL64
+    ref = {}
+    for prec in precs:
+        pin = p if prec == dgx.DGX_F64 else p.astype(np.float32).astype(np.float64)
+        ref[prec] = O.apply_S(c.m, A_DT, GAMMA, rho, pk, pin, cells=cells)[idx]
+    tried = 0
+    for v in variants:
+        for prec in precs:
+            dt = torch.float64 if prec == dgx.DGX_F64 else torch.float32
+            if v is not None and not _pin(c, prec, v):
+                continue
+            pd = dev(p).to(dt)
+            y = torch.zeros(c.N, dtype=dt, device="cuda")
+            dgx.dgx_apply_operator(c.ctx, prec, pd.data_ptr(), y.data_ptr())
+            tol = TOL64 if prec == dgx.DGX_F64 else TOL32
+            err = rel_max_err(host(y)[idx], ref[prec])
+            assert err <= tol, (v, prec, dgx.dgx_operator_variant(c.ctx, prec), err)
+            tried += 1
+    assert tried > 0
+
+
+@pytest.mark.parametrize("terrain", [0, 1])
+def test_full_size_sampled(terrain):
+    """64 x 64 x 32 cells, r = 4 (16 384 000 DoFs), terrain-following hill,
+    far-field lateral faces: GPU apply over the whole mesh in FP64 and FP32
+    with the variant the autotuner picks (the bench's launch configuration),
+    compared on sampled cells (corners, edges, the hill top, random) with the
+    oracle's cell-by-cell evaluation."""
+    c = Case(64, 64, 32, 4, Lx=60000.0, Ly=60000.0, Lz=20000.0, terrain=terrain, hc=400.0, ac=1000.0,
+             bc_lateral=1)
+    _sampled_parity(c, 64, 64, 32, 125, (dgx.DGX_F64, dgx.DGX_F32))
+    assert dgx.dgx_operator_variant(c.ctx, dgx.DGX_F64) >= 0
+    assert dgx.dgx_operator_variant(c.ctx, dgx.DGX_F32) >= 0
+    c.close()
+
+
+@pytest.mark.parametrize("geo", [dict(nx=16, ny=16, nz=8, r=4, bc_lateral=1, terrain=1),
+                                 dict(nx=16, ny=16, nz=8, r=3, bc_lateral=2, terrain=2),
+                                 dict(nx=13, ny=11, nz=15, r=2, bc_lateral=0, terrain=0)],
+                         ids=["16x16x8_r4_hill_farfield", "16x16x8_r3_hill32_periodic", "13x11x15_r2_flat_walls"])
+def test_every_variant_on_a_tuned_size_mesh(geo):
+    """Meshes of at least 2048 cells (where the autotuner chooses among the
+    variants), the last one with a ragged cell count for the multi-cell CTAs:
+    every launch variant in FP64 and FP32 against the oracle on sampled cells."""
+    n = geo["nx"]
+    c = Case(geo["nx"], geo["ny"], geo["nz"], geo["r"], Lx=1000.0 * n, Ly=1000.0 * geo["ny"], Lz=5000.0,
+             terrain=geo["terrain"], hc=400.0, ac=2000.0, bc_lateral=geo["bc_lateral"])
+    _sampled_parity(c, geo["nx"], geo["ny"], geo["nz"], (geo["r"] + 1) ** 3, (dgx.DGX_F64, dgx.DGX_F32),
+                    variants=list(range(dgx.DGX_OP_VARIANTS)), seed=91)
     c.close()
 
 
