@@ -3,10 +3,11 @@
 
 Workload: flow over a bell-shaped hill (h = 400 m / (1 + r^2/(1 km)^2) at the
 domain centre) on a terrain-following 60 x 60 x 20 km mesh of 64 x 64 x 32
-cells at degree 4 (16 384 000 DoFs per scalar field), periodic lateral
-boundaries, slip walls at bottom and top, isothermal background at 250 K,
-initial state = background plus a uniform 10 m/s wind, dt = 1 s, ARS(2,2,2)
-with two fixed-point iterations per implicit stage.  Synthetic inputs.
+cells at degree 4 (16 384 000 DoFs per scalar field), far-field lateral
+boundaries (uniform 10 m/s inflow: the ghost state is the background plus the
+wind), slip walls at bottom and top, isothermal background at 250 K, initial
+state = background plus a uniform 10 m/s wind, dt = 1 s, ARS(2,2,2) with two
+fixed-point iterations per implicit stage.  Synthetic inputs.
 
 One step = one IMEX step through the public API (dgx_imex_step): explicit
 fluxes, stage assembly, four Helmholtz pressure solves to 1e-8 FP64 relative
@@ -32,7 +33,7 @@ METRIC = "pressure solve s/step @1e-8 rel residual (mixed/learned vs plain FP64)
 
 FULL = dict(name="hill_64x64x32_r4_16.4M_dofs_imex", nx=64, ny=64, nz=32, r=4, Lx=60000.0, Ly=60000.0, Lz=20000.0)
 SMALL = dict(name="hill_16x16x8_r4_256k_dofs_imex", nx=16, ny=16, nz=8, r=4, Lx=15000.0, Ly=15000.0, Lz=5000.0)
-COMMON = dict(terrain=1, hc=400.0, ac=1000.0, bc_lateral=2, T=250.0, p0=1e5, R=287.0, g=9.81, gamma=1.4, dt=1.0,
+COMMON = dict(terrain=1, hc=400.0, ac=1000.0, bc_lateral=1, T=250.0, p0=1e5, R=287.0, g=9.81, gamma=1.4, dt=1.0,
               ubar=10.0, K=2)
 A_LL = 1.0 - 1.0 / 2.0 ** 0.5
 # FP64 operator applications of one IMEX step of this workload with plain FP64 FGMRES(30) solves to 1e-8
@@ -71,6 +72,9 @@ def parse():
     ap.add_argument("--members", type=int, default=16, help="ensemble members (first k of the 16)")
     ap.add_argument("--inner-maxit", type=int, default=None, help="override the FP32 GMRES cycle length")
     ap.add_argument("--inner-tol", type=float, default=None, help="override the FP32 GMRES tolerance")
+    ap.add_argument("--plain-steps", type=int, default=3, help="hill workload: timed steps with plain FP64 solves")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="hill workload: skip the compact mixed and learned results (run as subprocesses)")
     return ap.parse_args()
 
 
@@ -967,23 +971,47 @@ def main():
         dgx.dgx_destroy(ctx)
         return 0
 
-    # ---- the same step with plain FP64 FGMRES solves (from the same state)
+    # ---- the same step with plain FP64 FGMRES solves (from the same state), --plain-steps
+    # steps timed with CUDA events; the first one is kept for the comparison below
     rp, up, pp = rho.clone(), u.clone(), p.clone()
     infos.clear()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    step(rp, up, pp, o_plain)
+    ep = [torch.cuda.Event(enable_timing=True) for _ in range(args.plain_steps + 1)]
+    p_first = None
+    ep[0].record(stream)
+    for k in range(args.plain_steps):
+        step(rp, up, pp, o_plain)
+        ep[k + 1].record(stream)
+        if k == 0:
+            p_first = pp.clone()
     torch.cuda.synchronize()
-    t_plain = time.perf_counter() - t0
-    plain = {"s_per_step": t_plain, "pressure_solve_s": infos[0].seconds_solve,
-             "krylov_iterations": infos[0].krylov_iterations, "operator_f64": infos[0].operator_f64,
-             "max_relres": infos[0].max_relres}
+    t_plain = [ep[k].elapsed_time(ep[k + 1]) / 1e3 for k in range(args.plain_steps)]
+    plain = {"s_per_step": statistics.mean(t_plain), "s_per_step_each": t_plain, "steps": args.plain_steps,
+             "timing": "CUDA events on the library's stream, per step",
+             "pressure_solve_s": statistics.mean(i.seconds_solve for i in infos),
+             "krylov_iterations": statistics.mean(i.krylov_iterations for i in infos),
+             "operator_f64": statistics.mean(i.operator_f64 for i in infos),
+             "max_relres": max(i.max_relres for i in infos)}
     infos.clear()
-    # mixed step from the same state for the difference of the results
+    del rp, up, pp
+    # mixed step from the same state: the difference of the results, and the true
+    # FP64 residual b - S x of its four solves (recorded systems, S applied afresh)
     rm, um, pm = rho.clone(), u.clone(), p.clone()
+    rec = torch.zeros(4 * (4 * N + 2), dtype=f64, device="cuda")
+    dgx.dgx_imex_record(ctx, rec.data_ptr(), 4, 1)
     step(rm, um, pm)
-    diff = float((pp - pm).abs().max() / (pm - p0).abs().max().clamp_min(1e-30))
-    del rp, up, pp, rm, um, pm
+    nrec = dgx.dgx_imex_recorded(ctx)
+    dgx.dgx_imex_record(ctx, 0, 0, 1)
+    diff = float((p_first - pm).abs().max() / (pm - p0).abs().max().clamp_min(1e-30))
+    true_res = []
+    yv = torch.zeros(N, dtype=f64, device="cuda")
+    for k in range(nrec):
+        r_ = rec[k * (4 * N + 2):(k + 1) * (4 * N + 2)]
+        rr, pk_, b_, x_ = r_[:N], r_[N:2 * N], r_[2 * N:3 * N], r_[3 * N:4 * N]
+        dgx.dgx_set_coefficients(ctx, rr.data_ptr(), pk_.data_ptr(), float(r_[4 * N]), float(r_[4 * N + 1]))
+        dgx.dgx_apply_operator(ctx, dgx.DGX_F64, x_.data_ptr(), yv.data_ptr())
+        true_res.append(float((b_ - yv).norm() / b_.norm()))
+    del rm, um, pm, rec, p_first
 
     # ---- end to end through the C ABI with host buffers: state in from pinned host memory, step, state out
     h_state = [t.cpu().pin_memory() for t in (rho, u, p)]
@@ -1052,15 +1080,20 @@ def main():
              "f32_operator": f32_applies * t_app32, "explicit": 2 * t_expl}
     peak64 = fp64_peak(torch)
     clocks = clk.summary()
-    fp32_nominal = 152 * 128 * 2 * 2.07e9 / 1e12
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    fp32_nominal = n_sm * 128 * 2 * sm_max_mhz * 1e6 / 1e12
     dom = max(share, key=share.get)
+    # kernel names of the launch variant the autotuner chose (0-2: k_grad / k_div, 3-4: fused kf_grad / kf_div)
+    pre = {prec: ("kf_" if dgx.dgx_operator_variant(ctx, prec) >= 3 else "k_") for prec in (dgx.DGX_F64, dgx.DGX_F32)}
     if dom == "f32_operator":
-        kname, t_k, fl_k = (("k_div<float>", t_div32, fl_div) if t_div32 >= t_grad32
-                            else ("k_grad<float>", t_grad32, fl_grad))
-        peak, peak_src = fp32_nominal, "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
+        kname, t_k, fl_k = ((pre[dgx.DGX_F32] + "div<float>", t_div32, fl_div) if t_div32 >= t_grad32
+                            else (pre[dgx.DGX_F32] + "grad<float>", t_grad32, fl_grad))
+        peak, peak_src = fp32_nominal, ("derived: %d SMs (device properties) x 128 FP32 lanes x 2 flop x %.0f MHz "
+                                         "(maximum SM clock)" % (n_sm, sm_max_mhz))
     else:
-        kname, t_k, fl_k = (("k_div<double>", t_div64, fl_div) if t_div64 >= t_grad64
-                            else ("k_grad<double>", t_grad64, fl_grad))
+        kname, t_k, fl_k = ((pre[dgx.DGX_F64] + "div<double>", t_div64, fl_div) if t_div64 >= t_grad64
+                            else (pre[dgx.DGX_F64] + "grad<double>", t_grad64, fl_grad))
         peak, peak_src = peak64, "measured cuBLAS DGEMM (torch.matmul float64 4096^3) on this GPU"
     achieved = fl_k / t_k / 1e12
     traffic = DRAM_BYTES_PER_DOF_F64[kname] * N if kname in DRAM_BYTES_PER_DOF_F64 else None
@@ -1090,7 +1123,8 @@ def main():
         "config": {"workload": work["name"],
                    "mesh": "%dx%dx%d cells, r=%d, N=%d per field" % (work["nx"], work["ny"], work["nz"], work["r"], N),
                    "terrain": "bell h_c=400 m a_c=1 km centred, Gal-Chen", "background": "isothermal 250 K",
-                   "boundaries": "periodic lateral, slip walls bottom/top", "initial": "background + 10 m/s wind",
+                   "boundaries": "far-field lateral (uniform 10 m/s inflow), slip walls bottom/top",
+                   "initial": "background + 10 m/s wind",
                    "step": "dgx_imex_step: ARS(2,2,2), 2 fixed-point its, 4 mixed FGMRES(20)/FP32 GMRES(25) "
                            "solves to 1e-8",
                    "l2": "state and Krylov bases larger than L2 (no flush needed)", "parallelism": "replicas"},
@@ -1103,6 +1137,10 @@ def main():
         "pressure_solve_s_per_step": mean("seconds_solve"),
         "plain_fp64": plain,
         "mixed_vs_plain_max_rel_diff_p_prime": diff,
+        "true_fp64_relres": {"values": true_res, "max": max(true_res) if true_res else None,
+                             "how": "one more mixed step from the final state with its 4 systems recorded; "
+                                    "||b - S x|| / ||b|| with S applied afresh in FP64 (outside the timed region)"},
+        "device": {"name": torch.cuda.get_device_name(local), "multi_processor_count": n_sm},
         "step": {"solves": mean("solves"), "krylov_iterations": mean("krylov_iterations"),
                  "inner_iterations": mean("inner_iterations"), "operator_f64": f64_applies,
                  "operator_f32": f32_applies, "max_relres": max(i.max_relres for i in step_infos), "finite": finite},
@@ -1114,13 +1152,45 @@ def main():
                   "fp64_peak_measured_tflops": peak64,
                   "f64_hbm_floor_frac": hbm_fractions(bytes64, t_app64, hbm_gbs)[1],
                   "threads_per_cta_autotuned": {"f64": dgx.dgx_operator_threads(ctx, dgx.DGX_F64),
-                                                "f32": dgx.dgx_operator_threads(ctx, dgx.DGX_F32)}},
+                                                "f32": dgx.dgx_operator_threads(ctx, dgx.DGX_F32)},
+                  "variant_autotuned": {"f64": dgx.dgx_operator_variant(ctx, dgx.DGX_F64),
+                                        "f32": dgx.dgx_operator_variant(ctx, dgx.DGX_F32)}},
     }
-    print(json.dumps(line), flush=True)
     dgx.dgx_destroy(ctx)
+    if ws == 1 and not args.no_extras:
+        line["extras"] = extras()
+    print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+def extras():
+    """Compact results of the mixed-precision (box at degrees 2, 3, 5) and
+    learned-preconditioner workloads, each run by this script as a subprocess
+    with its own defaults, so that a default run reports them as well."""
+    out = {}
+    for name, argv in (("mixed", ["--workload", "mixed", "--steps", "3", "--warmup", "3"]),
+                       ("learned", ["--workload", "learned", "--steps", "1", "--warmup", "3"])):
+        t0 = time.time()
+        r = subprocess.run([sys.executable, os.path.abspath(__file__)] + argv, capture_output=True, text=True)
+        js = [l for l in r.stdout.splitlines() if l.startswith("{")]
+        if r.returncode != 0 or not js:
+            out[name] = {"error": "rc %d: %s" % (r.returncode, (r.stderr or r.stdout)[-300:])}
+            continue
+        d = json.loads(js[-1])
+        if name == "mixed":
+            out[name] = {"unit": "s/solve", "wall_s": round(time.time() - t0, 1), "degrees": [
+                {"degree": g["degree"], "dofs": g["dofs"], "mixed": g["mixed"]["s_per_solve"],
+                 "plain_fp64": g["plain_fp64"]["s_per_solve"],
+                 "mixed_max_rel_err_vs_oracle": g["mixed"]["max_rel_err_vs_oracle"],
+                 "plain_max_rel_err_vs_oracle": g["plain_fp64"]["max_rel_err_vs_oracle"]} for g in d["degrees"]],
+                "imex_step_vs_oracle": d.get("imex_step_vs_oracle")}
+        else:
+            keep = ("value", "unit", "solvers", "speedup_vs_plain_fp64", "iterations_ratio_vs_plain", "training")
+            out[name] = {k: d[k] for k in keep if k in d}
+            out[name]["wall_s"] = round(time.time() - t0, 1)
+    return out
 
 
 if __name__ == "__main__":

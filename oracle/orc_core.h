@@ -54,17 +54,11 @@ static inline void legendre(int k, double x, double *P, double *dP) {
 
 
 
-/* Gauss-Lobatto-Legendre points and weights on [0,1] (n >= 2 points):
- * the end points and the roots of P'_{n-1}. */
-
-
-
+/* (orc_gauss and orc_gll, defined in orc.c, use legendre() above.) */
 
 /* ------------------------------------------------------------------ */
-/* Mesh and geometry                                                    */
+/* Basis tables at the quadrature points, mesh and geometry            */
 /* ------------------------------------------------------------------ */
-
-
 
 typedef struct {
   int n, q, n3, q3, q2;

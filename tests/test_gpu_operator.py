@@ -318,4 +318,15 @@ def test_operator_assembled_entry_by_entry(geo):
         S_gpu[:, j] = host(y)
     S_ref = O.assemble(lambda v: O.apply_S(c.m, A_DT, GAMMA, rho, pk, v), N, N)
     assert np.abs(S_gpu - S_ref).max() <= TOL64 * np.abs(S_ref).max()
+    # the Schur complement formed from the separately assembled blocks of Sec. 2:
+    # S = D - C A^-1 B with A the fast-rule density-weighted mass (3N x 3N),
+    # B (3N x N), C (N x 3N), D (N x N), and a dense solve for A^-1 B
+    D = O.assemble(lambda v: O.apply_D(c.m, GAMMA, v), N, N)
+    B = O.assemble(lambda v: O.apply_B(c.m, A_DT, v), N, 3 * N)
+    Cm = O.assemble(lambda v: O.apply_C(c.m, A_DT, GAMMA, pk, v), 3 * N, N)
+    A = O.assemble(lambda v: O.apply_A(c.m, rho, v), 3 * N, 3 * N)
+    S_blocks = D - Cm @ np.linalg.solve(A, B)
+    scale = np.abs(S_blocks).max()
+    assert np.abs(S_ref - S_blocks).max() <= TOL64 * scale
+    assert np.abs(S_gpu - S_blocks).max() <= TOL64 * scale
     c.close()

@@ -41,6 +41,55 @@ def test_noalloc_matches_operator_twice(prec):
     c.close()
 
 
+@pytest.mark.parametrize("prec", [dgx.DGX_F64, dgx.DGX_F32])
+def test_noalloc_on_a_fresh_context(prec):
+    """What an allocation-free caller gets: the entry point on a context that
+    never applied the operator (so never ran the timing autotuner, which
+    allocates), checked against the oracle's S."""
+    import torch
+    import oracle as O
+    dt = torch.float64 if prec == dgx.DGX_F64 else torch.float32
+    c = Case(3, 2, 2, 3, Lx=3000.0, Ly=2000.0, Lz=1500.0, terrain=1, hc=300.0, ac=700.0, bc_lateral=1)
+    rho, pk = c.random_coefficients(seed=94)
+    c.set_coefficients(rho, pk, A_DT)
+    assert dgx.dgx_operator_variant(c.ctx, prec) == -1
+    x = inputs.random_field(c.N, 95, scale=100.0)
+    if prec == dgx.DGX_F32:
+        x = x.astype(np.float32).astype(np.float64)
+    xd = dev(x).to(dt)
+    y = torch.full((c.N,), float("nan"), dtype=dt, device="cuda")
+    dgx.dgx_apply_operator_noalloc(c.ctx, prec, xd.data_ptr(), y.data_ptr())
+    assert rel_max_err(host(y), O.apply_S(c.m, A_DT, 1.4, rho, pk, x)) <= TOL[prec]
+    c.close()
+
+
+@pytest.mark.parametrize("prec,shape", [(dgx.DGX_F64, (26, 26, 16)), (dgx.DGX_F32, (32, 32, 21))],
+                         ids=["f64_26x26x16_r3", "f32_32x32x21_r3"])
+def test_noalloc_near_the_limit(prec, shape):
+    """Meshes whose V fills 98-99 % of the static array (3 N sizeof(T) just
+    below DGX_NOALLOC_SCRATCH_BYTES), random input: every component stride of
+    V up to the top of the array is exercised; result as dgx_apply_operator."""
+    import torch
+    dt = torch.float64 if prec == dgx.DGX_F64 else torch.float32
+    nx, ny, nz = shape
+    c = Case(nx, ny, nz, 3, Lx=500.0 * nx, Ly=500.0 * ny, Lz=400.0 * nz, terrain=1, hc=300.0, ac=2000.0,
+             bc_lateral=1)
+    elem = 8 if prec == dgx.DGX_F64 else 4
+    assert 0.97 * dgx.DGX_NOALLOC_SCRATCH_BYTES <= 3 * c.N * elem <= dgx.DGX_NOALLOC_SCRATCH_BYTES
+    rho, pk = c.random_coefficients(seed=96)
+    c.set_coefficients(rho, pk, A_DT)
+    for seed in (97, 98):
+        x = dev(inputs.random_field(c.N, seed, scale=100.0)).to(dt)
+        y_na = torch.full((c.N,), float("nan"), dtype=dt, device="cuda")
+        y_ref = torch.zeros(c.N, dtype=dt, device="cuda")
+        dgx.dgx_apply_operator_noalloc(c.ctx, prec, x.data_ptr(), y_na.data_ptr())
+        dgx.dgx_apply_operator(c.ctx, prec, x.data_ptr(), y_ref.data_ptr())
+        a, b = host(y_na), host(y_ref)
+        assert np.all(np.isfinite(a))
+        assert rel_max_err(a, b) <= TOL[prec]
+    c.close()
+
+
 def test_noalloc_rejects_meshes_above_the_limit():
     import torch
     # 40 x 40 x 8 cells at r = 3: N = 819200, 3N doubles = 19.7 MB > 16 MiB
