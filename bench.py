@@ -41,12 +41,16 @@ A_LL = 1.0 - 1.0 / 2.0 ** 0.5
 # terms, counted as half applications); used only to scale the oracle's sampled cost to a step.
 PLAIN_STEP_APPLIES = 138
 STEP_EXTRA_HALF_APPLIES = 12
-# DRAM bytes per DoF of one launch of the FP64 operator kernels, from one ncu capture
+# DRAM bytes per DoF of one launch of the operator kernels, from ncu captures
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the 48x48x24 r=4 hill mesh
 # (6 912 000 DoFs, inputs larger than L2); one launch reads each cell's data once,
-# so the traffic scales with the DoFs.  k_div as applied inside the solver (with the
-# per-coefficient-set kappa at the Gauss points).  Valid for the kernels as captured.
-DRAM_BYTES_PER_DOF_F64 = {"k_div<double>": 696.2e6 / 6912000, "k_grad<double>": 252.9e6 / 6912000}
+# so the traffic scales with the DoFs.  k_div / kf_div<df64> as applied inside the
+# solver (with the per-coefficient-set kappa at the Gauss points); the fused kernels
+# in the configuration the autotuner picks on the 64x64x32 mesh.  Valid for the
+# kernels as captured.
+DRAM_BYTES_PER_DOF_F64 = {"k_div<double>": 696.2e6 / 6912000, "k_grad<double>": 252.9e6 / 6912000,
+                          "kf_div<df64>": 688.5e6 / 6912000, "kf_grad<df64>": 245.5e6 / 6912000,
+                          "kf_div<float>": 162.2e6 / 6912000, "kf_grad<float>": 94.1e6 / 6912000}
 
 
 def parse():
@@ -61,7 +65,10 @@ def parse():
     ap.add_argument("--mesh", default=None, help="NXxNYxNZ cells at the same cell size as the 64x64x32 workload")
     ap.add_argument("--profile", action="store_true",
                     help="only the warm-up and timed steps (for profiler launch lists); no side measurements")
-    ap.add_argument("--workload", default="hill", choices=["hill", "ensemble", "learned", "mixed", "paper", "consistent"],
+    ap.add_argument("--variant-f64", type=int, default=None, help="vmult workload: pin this FP64 launch variant")
+    ap.add_argument("--variant-f32", type=int, default=None, help="vmult workload: pin this FP32 launch variant")
+    ap.add_argument("--workload", default="hill",
+                    choices=["hill", "ensemble", "learned", "mixed", "paper", "consistent", "vmult"],
                     help="hill: one IMEX step of the 64x64x32 hill (default); ensemble: 16-member batched solve; "
                          "learned: pressure solves of held-out hill systems with the trained network; "
                          "mixed: mixed-precision solves on the 4x4x4 box at degrees 2, 3, 5 against the oracle; "
@@ -585,6 +592,80 @@ def run_consistent(args):
     return 0
 
 
+def run_vmult(args):
+    """Operator application y = S x (the vmult of the metric) on the hill mesh
+    (64x64x32 r=4 unless --mesh): every launch variant in FP64 and FP32,
+    --warmup untimed and --steps timed applications each (CUDA events, inputs
+    larger than L2), GDoF/s and the agreement of each variant with variant 0.
+    Coefficients: isothermal hydrostatic profiles with 5 % seeded noise;
+    x: seeded N(0, 100^2).  With --profile and --variant-f64 / --variant-f32:
+    only those variants, --warmup + --steps applications each (profiler driver)."""
+    import torch
+    from paper_2505_00384_gb300 import dgx, inputs
+    torch.cuda.set_device(0)
+    dgx.load()
+    work = workload(args)
+    stream = torch.cuda.current_stream()
+    ctx = dgx.dgx_create(0, stream.cuda_stream)
+    desc = dgx.mesh_desc(work["nx"], work["ny"], work["nz"], work["r"], work["Lx"], work["Ly"], work["Lz"],
+                         terrain=work["terrain"], h_c=work["hc"], a_c=work["ac"], bc_lateral=work["bc_lateral"])
+    dgx.dgx_mesh_build(ctx, desc)
+    N = dgx.dgx_num_dofs(ctx)
+    X = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    dgx.dgx_node_coords(ctx, X.data_ptr())
+    z = X[2 * N:].cpu().numpy()
+    del X
+    rho = torch.from_numpy(inputs.perturbed_profile(z, 1.2, 7314.0, 0.05, 1)).cuda()
+    pk = torch.from_numpy(inputs.perturbed_profile(z, 1e5, 7314.0, 0.05, 2)).cuda()
+    dgx.dgx_set_coefficients(ctx, rho.data_ptr(), pk.data_ptr(), A_LL, work["gamma"])
+    x64 = torch.from_numpy(inputs.random_field(N, 3, 100.0)).cuda()
+    fl_grad, fl_div, bytes64 = dgx.dgx_operator_cost(ctx)
+    out, ref = {}, {}
+    pins = {dgx.DGX_F64: args.variant_f64, dgx.DGX_F32: args.variant_f32}
+    for prec, dt in ((dgx.DGX_F64, torch.float64), (dgx.DGX_F32, torch.float32)):
+        x = x64.to(dt)
+        y = torch.zeros(N, dtype=dt, device="cuda")
+        variants = [pins[prec]] if pins[prec] is not None else list(range(dgx.DGX_OP_VARIANTS))
+        if args.profile and pins[prec] is None:
+            continue
+        for v in variants:
+            try:
+                dgx.dgx_set_operator_variant(ctx, prec, v)
+            except dgx.DgxError:
+                continue
+            for _ in range(args.warmup):
+                dgx.dgx_apply_operator(ctx, prec, x.data_ptr(), y.data_ptr())
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                dgx.dgx_apply_operator(ctx, prec, x.data_ptr(), y.data_ptr())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if args.profile:
+                continue
+            ms = e0.elapsed_time(e1) / args.steps
+            yy = y.double()
+            if prec not in ref:
+                ref[prec] = yy.clone()
+            out["%s_v%d" % ("f64" if prec == dgx.DGX_F64 else "f32", v)] = {
+                "ms": ms, "gdofs": N / ms / 1e6, "tflops_counted": (fl_grad + fl_div) / ms / 1e9,
+                "threads_per_cta": dgx.dgx_operator_threads(ctx, prec),
+                "max_rel_diff_vs_first": float((yy - ref[prec]).abs().max() / ref[prec].abs().max())}
+    dgx.dgx_destroy(ctx)
+    if args.profile:
+        print(json.dumps({"profile_run": True, "workload": "vmult_" + work["name"], "N": N}), flush=True)
+        return 0
+    best = {p_: min((v for k, v in out.items() if k.startswith(p_)), key=lambda d: d["ms"]) for p_ in ("f64", "f32")}
+    line = {"metric": "vmult GDoF/s (operator application y = S x)", "value": best["f64"]["gdofs"], "unit": "GDoF/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (and f32)", "data": "synthetic",
+            "config": {"workload": "vmult_" + work["name"], "dofs": N, "l2": "inputs larger than L2"},
+            "best": best, "variants": out, "flops_per_apply": fl_grad + fl_div, "hbm_floor_bytes_f64": bytes64}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_learned(args):
     """Learned preconditioner: 400 pressure systems recorded along IMEX
     trajectories over 16 seeded hills (h_c ~ U[200, 800] m, 25 steps each, the
@@ -896,6 +977,8 @@ def main():
         return run_mixed(args)
     if args.workload == "paper":
         return run_paper(args)
+    if args.workload == "vmult":
+        return run_vmult(args)
     if args.workload == "consistent":
         return run_consistent(args)
 
@@ -1005,12 +1088,17 @@ def main():
     diff = float((p_first - pm).abs().max() / (pm - p0).abs().max().clamp_min(1e-30))
     true_res = []
     yv = torch.zeros(N, dtype=f64, device="cuda")
+    # native FP64 arithmetic for this check (variant 1: one cell per CTA, FP64 pipe),
+    # whatever variant the autotuner chose for the solves; restored afterwards
+    v_tuned = dgx.dgx_operator_variant(ctx, dgx.DGX_F64)
+    dgx.dgx_set_operator_variant(ctx, dgx.DGX_F64, 1)
     for k in range(nrec):
         r_ = rec[k * (4 * N + 2):(k + 1) * (4 * N + 2)]
         rr, pk_, b_, x_ = r_[:N], r_[N:2 * N], r_[2 * N:3 * N], r_[3 * N:4 * N]
         dgx.dgx_set_coefficients(ctx, rr.data_ptr(), pk_.data_ptr(), float(r_[4 * N]), float(r_[4 * N + 1]))
         dgx.dgx_apply_operator(ctx, dgx.DGX_F64, x_.data_ptr(), yv.data_ptr())
         true_res.append(float((b_ - yv).norm() / b_.norm()))
+    dgx.dgx_set_operator_variant(ctx, dgx.DGX_F64, v_tuned)
     del rm, um, pm, rec, p_first
 
     # ---- end to end through the C ABI with host buffers: state in from pinned host memory, step, state out
@@ -1084,17 +1172,30 @@ def main():
     sm_max_mhz = clocks.get("sm_max_mhz") or 2070.0
     fp32_nominal = n_sm * 128 * 2 * sm_max_mhz * 1e6 / 1e12
     dom = max(share, key=share.get)
-    # kernel names of the launch variant the autotuner chose (0-2: k_grad / k_div, 3-4: fused kf_grad / kf_div)
-    pre = {prec: ("kf_" if dgx.dgx_operator_variant(ctx, prec) >= 3 else "k_") for prec in (dgx.DGX_F64, dgx.DGX_F32)}
+    # kernel names of the launch variant the autotuner chose (0-2: k_grad / k_div, 3-4: fused kf_grad / kf_div,
+    # 5-6: the fused kernels in double-word arithmetic, kf_grad<df64> / kf_div<df64>)
+    v64, v32 = dgx.dgx_operator_variant(ctx, dgx.DGX_F64), dgx.dgx_operator_variant(ctx, dgx.DGX_F32)
+    pre32 = "kf_" if v32 >= 3 else "k_"
+    pre64, t64 = ("kf_", "df64") if v64 >= 5 else (("kf_" if v64 >= 3 else "k_"), "double")
+    fp32_src = ("derived: %d SMs (device properties) x 128 FP32 lanes x 2 flop x %.0f MHz (maximum SM clock)"
+                % (n_sm, sm_max_mhz))
+    extra = {}
     if dom == "f32_operator":
-        kname, t_k, fl_k = ((pre[dgx.DGX_F32] + "div<float>", t_div32, fl_div) if t_div32 >= t_grad32
-                            else (pre[dgx.DGX_F32] + "grad<float>", t_grad32, fl_grad))
-        peak, peak_src = fp32_nominal, ("derived: %d SMs (device properties) x 128 FP32 lanes x 2 flop x %.0f MHz "
-                                         "(maximum SM clock)" % (n_sm, sm_max_mhz))
+        kname, t_k, fl_k = ((pre32 + "div<float>", t_div32, fl_div) if t_div32 >= t_grad32
+                            else (pre32 + "grad<float>", t_grad32, fl_grad))
+        peak, peak_src = fp32_nominal, fp32_src
     else:
-        kname, t_k, fl_k = ((pre[dgx.DGX_F64] + "div<double>", t_div64, fl_div) if t_div64 >= t_grad64
-                            else (pre[dgx.DGX_F64] + "grad<double>", t_grad64, fl_grad))
-        peak, peak_src = peak64, "measured cuBLAS DGEMM (torch.matmul float64 4096^3) on this GPU"
+        kname, t_k, fl_k = ((pre64 + "div<%s>" % t64, t_div64, fl_div) if t_div64 >= t_grad64
+                            else (pre64 + "grad<%s>" % t64, t_grad64, fl_grad))
+        if t64 == "df64":
+            # FP64-accuracy arithmetic on the FP32 pipes: one multiply-add of the line products (2 flops)
+            # is a compensated dot-product term of 12 FP32 operations, so the roof in FP64-equivalent
+            # flops is the FP32 peak / 6
+            peak, peak_src = fp32_nominal / 6.0, ("derived: FP32 peak (%s) / 6 FP32 operations per FP64-"
+                                                  "equivalent flop of the double-word multiply-add" % fp32_src)
+            extra = {"fp64_dgemm_peak": peak64, "vs_fp64_dgemm_peak": fl_k / t_k / 1e12 / peak64}
+        else:
+            peak, peak_src = peak64, "measured cuBLAS DGEMM (torch.matmul float64 4096^3) on this GPU"
     achieved = fl_k / t_k / 1e12
     traffic = DRAM_BYTES_PER_DOF_F64[kname] * N if kname in DRAM_BYTES_PER_DOF_F64 else None
     hbm_gbs, hbm_src = measured_hbm_gbs()
@@ -1103,9 +1204,10 @@ def main():
                 "frac": achieved / peak, "traffic": traffic,
                 "traffic_source": "ncu DRAM bytes per DoF on the 48x48x24 r=4 mesh, scaled by DoFs" if traffic else None,
                 "peak_source": peak_src, "flops_per_launch": fl_k, "launch_s": t_k, "step_share_estimate_s": share,
+                **extra,
                 "hbm": {"achieved_gbs": k_gbs, "frac": k_hbm_frac, "peak_gbs": hbm_gbs, "peak_source": hbm_src,
                         "note": "the kernel's DRAM traffic per launch over its launch time: far below the copy "
-                                "bandwidth, the FP64 pipe binds"}}
+                                "bandwidth, the arithmetic pipes bind"}}
 
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
@@ -1139,7 +1241,8 @@ def main():
         "mixed_vs_plain_max_rel_diff_p_prime": diff,
         "true_fp64_relres": {"values": true_res, "max": max(true_res) if true_res else None,
                              "how": "one more mixed step from the final state with its 4 systems recorded; "
-                                    "||b - S x|| / ||b|| with S applied afresh in FP64 (outside the timed region)"},
+                                    "||b - S x|| / ||b|| with S applied afresh by the native FP64 kernels "
+                                    "(variant 1; outside the timed region)"},
         "device": {"name": torch.cuda.get_device_name(local), "multi_processor_count": n_sm},
         "step": {"solves": mean("solves"), "krylov_iterations": mean("krylov_iterations"),
                  "inner_iterations": mean("inner_iterations"), "operator_f64": f64_applies,

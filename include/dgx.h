@@ -376,7 +376,11 @@ int dgx_operator_cost(const dgx_ctx *ctx, double *flops_grad, double *flops_div,
  *   0, 1, 2  one cell per CTA, one thread per 1D line of each sum-factorisation
  *            sweep, 128 / 192 / 256 threads per CTA;
  *   3, 4     fused kernels with C cells per CTA, C = 1 / 2 (degree >= 3) or
- *            4 / 8 (degree <= 2), and 32 ceil(C (2r+1)^2 / 32) threads.
+ *            4 / 8 (degree <= 2), and 32 ceil(C (2r+1)^2 / 32) threads;
+ *   5, 6     (FP64 only) the fused kernels of 3, 4 computing in double-word
+ *            arithmetic (pairs of FP32 numbers, about 48 significant bits,
+ *            error-free transforms of Dekker, Knuth and Joldes-Muller-Popescu)
+ *            on the FP64 arrays: the FP32 pipes instead of the FP64 pipe.
  * The fused kernels keep the last interpolation direction, the pointwise flux
  * and the first test direction in registers and deal the lines of several
  * cells to one CTA; a fused variant is available when its shared memory
@@ -384,10 +388,10 @@ int dgx_operator_cost(const dgx_ctx *ctx, double *flops_grad, double *flops_div,
  * the fastest available variant before the first application on meshes of
  * 2048 cells or more (outside stream capture); smaller meshes use the
  * degree's default (-1).  dgx_mesh_build resets the choice. */
-#define DGX_OP_VARIANTS 5
+#define DGX_OP_VARIANTS 7
 /* The variant in use for prec (-1: the default, not tuned; -2: bad argument). */
 int dgx_operator_variant(const dgx_ctx *ctx, int prec);
-/* Pin variant 0..4 for prec on the current mesh (the autotuner then leaves prec
+/* Pin variant 0..6 for prec on the current mesh (the autotuner then leaves prec
  * alone), or hand the choice back to the autotuner with -1.  DGX_ERR_ARG for a
  * variant that is unknown or does not fit; DGX_ERR_STATE without a mesh. */
 int dgx_set_operator_variant(dgx_ctx *ctx, int prec, int variant);

@@ -306,6 +306,7 @@ void free_mesh(dgx_ctx *c) {
   c->tab32 = nullptr;
   c->col64 = nullptr;
   c->col32 = nullptr;
+  c->coldf = nullptr;
   c->rho_bar = c->p_bar = nullptr;
   c->rho64 = c->pk64 = nullptr;
   c->rho32 = c->pk32 = nullptr;
@@ -1041,10 +1042,17 @@ int dgx_mesh_build(dgx_ctx *c, const dgx_mesh_desc *d) {
     for (long long i = 0; i < ncol; ++i)
       for (int k = 0; k < Q * Q; ++k)
         if (col[(size_t)i * CS + k] >= d->Lz) return set_error(c, DGX_ERR_ARG, "terrain reaches the model top");
-    std::vector<float> c32(col.begin(), col.end());
-    if ((e = dalloc(c, &c->col64, col.size())) || (e = dalloc(c, &c->col32, col.size()))) return e;
+    std::vector<float> c32(col.begin(), col.end()), cdf(2 * col.size());
+    for (size_t k = 0; k < col.size(); ++k) {  // double-words: hi = RN(v), lo = RN(v - hi)
+      cdf[2 * k] = (float)col[k];
+      cdf[2 * k + 1] = (float)(col[k] - (double)cdf[2 * k]);
+    }
+    if ((e = dalloc(c, &c->col64, col.size())) || (e = dalloc(c, &c->col32, col.size())) ||
+        (e = dalloc(c, &c->coldf, cdf.size())))
+      return e;
     cudaMemcpy(c->col64, col.data(), col.size() * sizeof(double), cudaMemcpyHostToDevice);
     cudaMemcpy(c->col32, c32.data(), c32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->coldf, cdf.data(), cdf.size() * sizeof(float), cudaMemcpyHostToDevice);
   }
   const size_t Nn = (size_t)c->N;
   if ((e = dalloc(c, &c->V64, 3 * Nn)) || (e = dalloc(c, &c->V32, 3 * Nn)) || (e = dalloc(c, &c->rho64, Nn)) ||

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/dgx.h"
+#include "dgx_df64.cuh"
 
 namespace dgx {
 
@@ -146,6 +147,7 @@ struct dgx_ctx {
   float *tab32 = nullptr;
   double *col64 = nullptr;
   float *col32 = nullptr;
+  float *coldf = nullptr;  // the same values as double-words (hi, lo pairs)
 
   // background
   bool has_bg = false;
@@ -182,7 +184,8 @@ struct dgx_ctx {
 
   // launch variant of the operator kernels per precision ([0] FP64, [1] FP32):
   // 0..2 one cell per CTA (k_grad / k_div) with 128 / 192 / 256 threads, 3..4
-  // the fused multi-cell kernels in configuration v - 3 (fused_cpb); -1 = the
+  // the fused multi-cell kernels in configuration v - 3 (fused_cpb), 5..6 (FP64
+  // only) the fused kernels in double-word arithmetic, configuration v - 5; -1 = the
   // default of the degree.  Chosen by the timing autotuner (op_tuned) unless
   // pinned by dgx_set_operator_variant (op_pinned).
   int op_variant[2] = {-1, -1};
@@ -272,11 +275,13 @@ __host__ __device__ constexpr int fused_nt(int N, int cfg) {
   return ((fused_cpb(N, cfg) * (2 * N - 1) * (2 * N - 1) + 31) / 32) * 32;
 }
 constexpr size_t kFusedMaxSmem = 227 * 1024;
+// (T = df64: double-word arithmetic on FP64 arrays, store_t<df64> = double)
 template <typename T, int N, bool CURVED>
-int fused_grad(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s, bool inv, double alpha, int cfg);
+int fused_grad(dgx_ctx *c, const store_t<T> *p, const store_t<T> *rho, store_t<T> *V, cudaStream_t s, bool inv,
+               double alpha, int cfg);
 template <typename T, int N, bool CURVED>
-int fused_div(dgx_ctx *c, const T *V, const T *p, const T *pk, T *y, cudaStream_t s, double alpha, const T *kq,
-              int cfg);
+int fused_div(dgx_ctx *c, const store_t<T> *V, const store_t<T> *p, const store_t<T> *pk, store_t<T> *y,
+              cudaStream_t s, double alpha, const store_t<T> *kq, int cfg);
 template <typename T, int N, bool CURVED>
 size_t fused_smem(int cfg);
 // multi-mesh operator y = S x for members of one degree (N = r+1) and terrain kind;
@@ -304,9 +309,11 @@ int launch_diag(dgx_ctx *c, const T *rho, const T *pk, T *dh, T *die, cudaStream
 int ensure_diag(dgx_ctx *c, bool f64);
 template <typename T>
 OpP<T> make_params(const dgx_ctx *c);
+template <>
+OpP<df64> make_params<df64>(const dgx_ctx *c);
 // operator launch variants (see dgx_ctx::op_variant): count, whether variant v
 // fits this context's mesh and precision, and its threads per CTA
-constexpr int kOpVariants = 5;
+constexpr int kOpVariants = 7;
 template <typename T>
 bool op_variant_ok(const dgx_ctx *c, int v);
 int op_variant_threads(const dgx_ctx *c, int v);

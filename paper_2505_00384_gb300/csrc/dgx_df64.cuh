@@ -1,0 +1,93 @@
+// Double-word ("double-float") arithmetic: a value is the unevaluated sum
+// hi + lo of two FP32 numbers with |lo| <= ulp(hi)/2, about 48 significant
+// bits.  On GB300 the FP32 pipes are 64 times the FP64 pipe, so FP64-accuracy
+// kernels can run on FP32 arithmetic.  Building blocks (each FP32 operation
+// rounded to nearest, no contraction: the __f*_rn intrinsics):
+//   TwoSum (Knuth) and Fast2Sum (Dekker): the exact error of a sum;
+//   TwoProd with FMA: the exact error of a product;
+//   sum of two double-words: "SloppyDWPlusDW", product: "DWTimesDW2",
+//   quotient: "DWDivDW2" of Joldes, Muller and Popescu, "Tight and rigorous
+//   error bounds for basic building blocks of double-word arithmetic", ACM
+//   TOMS 44 (2017).  The product and quotient have relative errors of a few
+//   u^2 (u = 2^-24); the sloppy sum has an absolute error of a few
+//   u^2 (|x| + |y|) (no relative bound under cancellation), which is what a
+//   sum-factorised contraction needs: its error is measured against the size
+//   of the terms.
+// The exponent range is FP32's: values (and the low parts) must stay within
+// about 1e-30 .. 1e38 in magnitude for the full precision.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace dgx {
+
+struct df64 {
+  float hi, lo;
+  df64() = default;
+  __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ df64(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  __host__ __device__ df64(int i) : df64((double)i) {}
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+// storage type of a compute type: double-word kernels read and write FP64 arrays
+template <typename T>
+struct Store {
+  using type = T;
+};
+template <>
+struct Store<df64> {
+  using type = double;
+};
+template <typename T>
+using store_t = typename Store<T>::type;
+
+#ifdef __CUDACC__
+__device__ __forceinline__ df64 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float a1 = __fsub_rn(s, b);
+  const float b1 = __fsub_rn(s, a1);
+  const float da = __fsub_rn(a, a1);
+  const float db = __fsub_rn(b, b1);
+  return df64(s, __fadd_rn(da, db));
+}
+__device__ __forceinline__ df64 fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  return df64(s, __fsub_rn(b, z));
+}
+__device__ __forceinline__ df64 operator+(df64 x, df64 y) {
+  const df64 s = two_sum(x.hi, y.hi);
+  const float v = __fadd_rn(x.lo, y.lo);
+  const float w = __fadd_rn(s.lo, v);
+  return fast_two_sum(s.hi, w);
+}
+__device__ __forceinline__ df64 operator-(df64 x) { return df64(-x.hi, -x.lo); }
+__device__ __forceinline__ df64 operator-(df64 x, df64 y) { return x + (-y); }
+__device__ __forceinline__ df64 operator*(df64 x, df64 y) {
+  const float ch = __fmul_rn(x.hi, y.hi);
+  const float cl1 = __fmaf_rn(x.hi, y.hi, -ch);
+  const float tl = __fmul_rn(x.hi, y.lo);
+  const float cl2 = __fmaf_rn(x.lo, y.hi, tl);
+  const float cl3 = __fadd_rn(cl1, cl2);
+  return fast_two_sum(ch, cl3);
+}
+__device__ __forceinline__ df64 operator/(df64 x, df64 y) {
+  const float th = __fdiv_rn(x.hi, y.hi);
+  // r = y * th (double-word times float), then the remainder x - r
+  const float rh0 = __fmul_rn(y.hi, th);
+  const float rl0 = __fmaf_rn(y.hi, th, -rh0);
+  const float rl1 = __fmaf_rn(y.lo, th, rl0);
+  const df64 r = fast_two_sum(rh0, rl1);
+  const df64 pi = two_sum(x.hi, -r.hi);
+  const float dh = __fsub_rn(pi.lo, r.lo);
+  const float dl = __fadd_rn(dh, x.lo);
+  const float d = __fadd_rn(pi.hi, dl);
+  return fast_two_sum(th, __fdiv_rn(d, y.hi));
+}
+__device__ __forceinline__ df64 &operator+=(df64 &x, df64 y) { return x = x + y; }
+__device__ __forceinline__ df64 &operator-=(df64 &x, df64 y) { return x = x - y; }
+__device__ __forceinline__ df64 &operator*=(df64 &x, df64 y) { return x = x * y; }
+#endif
+
+}  // namespace dgx

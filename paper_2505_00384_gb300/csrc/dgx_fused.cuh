@@ -24,6 +24,8 @@
 // are kept differ, so the result equals k_grad / k_div to rounding.
 #pragma once
 
+#include <type_traits>
+
 #include "dgx_sweep.cuh"
 
 namespace dgx {
@@ -38,21 +40,40 @@ static __constant__ double c_wa64[kMaxDegree + 2][kMaxDegree + 1];
 static __constant__ float c_wq32[kMaxDegree + 2][2 * kMaxDegree + 1];
 static __constant__ float c_gq32[kMaxDegree + 2][2 * kMaxDegree + 1];
 static __constant__ float c_wa32[kMaxDegree + 2][kMaxDegree + 1];
+// the same rules and the even-odd 1D matrices as double-words (hi, lo)
+static __constant__ float2 c_wqdf[kMaxDegree + 2][2 * kMaxDegree + 1];
+static __constant__ float2 c_gqdf[kMaxDegree + 2][2 * kMaxDegree + 1];
+static __constant__ float2 c_wadf[kMaxDegree + 2][kMaxDegree + 1];
+static __constant__ float2 c_eodf[kEoTotal];
+
+template <>
+__device__ __forceinline__ df64 ceo<df64>(int i) {
+  return df64(c_eodf[i].x, c_eodf[i].y);
+}
 
 template <typename T, int N>
 __device__ __forceinline__ T cwq(int k) {
-  if constexpr (sizeof(T) == 8) return c_wq64[N][k];
+  if constexpr (std::is_same<T, df64>::value) return df64(c_wqdf[N][k].x, c_wqdf[N][k].y);
+  else if constexpr (sizeof(T) == 8) return c_wq64[N][k];
   else return c_wq32[N][k];
 }
 template <typename T, int N>
 __device__ __forceinline__ T cgq(int k) {
-  if constexpr (sizeof(T) == 8) return c_gq64[N][k];
+  if constexpr (std::is_same<T, df64>::value) return df64(c_gqdf[N][k].x, c_gqdf[N][k].y);
+  else if constexpr (sizeof(T) == 8) return c_gq64[N][k];
   else return c_gq32[N][k];
 }
 template <typename T, int N>
 __device__ __forceinline__ T cwa(int k) {
-  if constexpr (sizeof(T) == 8) return c_wa64[N][k];
+  if constexpr (std::is_same<T, df64>::value) return df64(c_wadf[N][k].x, c_wadf[N][k].y);
+  else if constexpr (sizeof(T) == 8) return c_wa64[N][k];
   else return c_wa32[N][k];
+}
+
+// double-word split of a host double: hi = RN(v), lo = RN(v - hi)
+static inline float2 dw_split(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
 }
 
 // Upload the even-odd matrices (dgx_sweep.cuh) and the rule tables into this
@@ -77,47 +98,126 @@ static int upload_fused_tables(dgx_ctx *c) {
   }
   float wq32[kMaxDegree + 2][2 * kMaxDegree + 1], gq32[kMaxDegree + 2][2 * kMaxDegree + 1];
   float wa32[kMaxDegree + 2][kMaxDegree + 1];
+  static float2 wqdf[kMaxDegree + 2][2 * kMaxDegree + 1], gqdf[kMaxDegree + 2][2 * kMaxDegree + 1];
+  static float2 wadf[kMaxDegree + 2][kMaxDegree + 1];
   for (int n = 0; n < kMaxDegree + 2; ++n) {
     for (int k = 0; k < 2 * kMaxDegree + 1; ++k) {
       wq32[n][k] = (float)wq[n][k];
       gq32[n][k] = (float)gq[n][k];
+      wqdf[n][k] = dw_split(wq[n][k]);
+      gqdf[n][k] = dw_split(gq[n][k]);
     }
-    for (int k = 0; k < kMaxDegree + 1; ++k) wa32[n][k] = (float)wa[n][k];
+    for (int k = 0; k < kMaxDegree + 1; ++k) {
+      wa32[n][k] = (float)wa[n][k];
+      wadf[n][k] = dw_split(wa[n][k]);
+    }
   }
+  // even-odd matrices as double-words, from this translation unit's FP64 copy
+  std::vector<double> eo(kEoTotal);
+  std::vector<float2> eodf(kEoTotal);
+  if (int err = check_cuda(c, cudaMemcpyFromSymbol(eo.data(), c_eo64, kEoTotal * sizeof(double)), "constant tables"))
+    return err;
+  for (int k = 0; k < kEoTotal; ++k) eodf[k] = dw_split(eo[k]);
   cudaError_t e = cudaMemcpyToSymbol(c_wq64, wq, sizeof(wq));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_gq64, gq, sizeof(gq));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_wa64, wa, sizeof(wa));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_wq32, wq32, sizeof(wq32));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_gq32, gq32, sizeof(gq32));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_wa32, wa32, sizeof(wa32));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_wqdf, wqdf, sizeof(wqdf));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_gqdf, gqdf, sizeof(gqdf));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_wadf, wadf, sizeof(wadf));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_eodf, eodf.data(), kEoTotal * sizeof(float2));
   if (int err = check_cuda(c, e, "constant rule tables")) return err;
   done[c->device] = true;
   return 0;
 }
 
 // ------------------------------------------------------------ line helpers
+// Double-word line product (same even-odd scheme as line_eo): the pair sums
+// e_m, d_m are kept unnormalised (TwoSum of the high parts, low parts added),
+// and each output is a compensated dot product (Ogita, Rump and Oishi,
+// "Accurate sum and dot product", SIAM J. Sci. Comput. 26 (2005), Dot2):
+// products of the high parts split exactly by FMA, their running sum by
+// TwoSum, all low-order terms gathered in one FP32 accumulator, one
+// normalisation at the end.
+__device__ __forceinline__ void dot2_term(float &sh, float &sl, bool first, float ch, float cl, float xh, float xl) {
+  const float p = __fmul_rn(ch, xh);
+  float lo = __fmaf_rn(ch, xh, -p);
+  lo = __fmaf_rn(ch, xl, lo);
+  lo = __fmaf_rn(cl, xh, lo);
+  if (first) {
+    sh = p;
+    sl = lo;
+  } else {
+    const df64 t = two_sum(sh, p);
+    sh = t.hi;
+    sl = __fadd_rn(sl, __fadd_rn(t.lo, lo));
+  }
+}
+
+template <int NN, int MAT, int MO, int MI>
+__device__ __forceinline__ void line_dw(const df64 *x, df64 *y) {
+  constexpr int HO = (MO + 1) / 2, HI = MI / 2;
+  constexpr int base = eo_mat_off(NN, MAT);
+  constexpr bool odd_in = (MI & 1) != 0;
+  constexpr int par = mat_parity(MAT);
+  float eh[HI > 0 ? HI : 1], el[HI > 0 ? HI : 1], dh[HI > 0 ? HI : 1], dl[HI > 0 ? HI : 1];
+#pragma unroll
+  for (int m = 0; m < HI; ++m) {
+    const df64 u = x[m], v = x[MI - 1 - m];
+    const df64 sp = two_sum(u.hi, v.hi), sm = two_sum(u.hi, -v.hi);
+    eh[m] = sp.hi;
+    el[m] = __fadd_rn(sp.lo, __fadd_rn(u.lo, v.lo));
+    dh[m] = sm.hi;
+    dl[m] = __fadd_rn(sm.lo, __fsub_rn(u.lo, v.lo));
+  }
+#pragma unroll
+  for (int o = 0; o < HO; ++o) {
+    float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
+    bool afirst = true;
+    if (odd_in) {
+      const float2 cm = c_eodf[base + 2 * HO * HI + o];
+      dot2_term(ah, al, true, cm.x, cm.y, x[HI].hi, x[HI].lo);
+      afirst = false;
+    }
+#pragma unroll
+    for (int m = 0; m < HI; ++m) {
+      const float2 ce = c_eodf[base + o * HI + m], cd = c_eodf[base + HO * HI + o * HI + m];
+      dot2_term(ah, al, afirst && m == 0, ce.x, ce.y, eh[m], el[m]);
+      dot2_term(bh, bl, m == 0, cd.x, cd.y, dh[m], dl[m]);
+    }
+    const df64 a = fast_two_sum(ah, al), b = fast_two_sum(bh, bl);
+    y[o] = a + b;
+    if (o != MO - 1 - o) y[MO - 1 - o] = par > 0 ? a - b : b - a;
+  }
+}
+
 // y = M x for register arrays (M: even-odd matrix MAT of degree NN, MO x MI).
 template <typename T, int NN, int MAT, int MO, int MI>
 __device__ __forceinline__ void mv(const T *x, T *y) {
-  line_eo<T, NN, MAT, MO, MI>(x, 1, y, 1);
+  if constexpr (std::is_same<T, df64>::value) line_dw<NN, MAT, MO, MI>(x, y);
+  else line_eo<T, NN, MAT, MO, MI>(x, 1, y, 1);
 }
 // y += M x
 template <typename T, int NN, int MAT, int MO, int MI>
 __device__ __forceinline__ void mv_acc(const T *x, T *y) {
   T t[MO];
-  line_eo<T, NN, MAT, MO, MI>(x, 1, t, 1);
+  mv<T, NN, MAT, MO, MI>(x, t);
 #pragma unroll
   for (int o = 0; o < MO; ++o) y[o] += t[o];
 }
-template <typename T, int M, int S>
-__device__ __forceinline__ void lds(const T *p, T *r) {
+// M values of stride S into / out of registers; U is the memory type (the
+// storage type for global arrays, converted to and from the compute type T)
+template <typename T, int M, int S, typename U>
+__device__ __forceinline__ void lds(const U *p, T *r) {
 #pragma unroll
-  for (int m = 0; m < M; ++m) r[m] = p[m * S];
+  for (int m = 0; m < M; ++m) r[m] = static_cast<T>(p[m * S]);
 }
-template <typename T, int M, int S>
-__device__ __forceinline__ void sts(T *p, const T *r) {
+template <typename T, int M, int S, typename U>
+__device__ __forceinline__ void sts(U *p, const T *r) {
 #pragma unroll
-  for (int m = 0; m < M; ++m) p[m * S] = r[m];
+  for (int m = 0; m < M; ++m) p[m * S] = static_cast<U>(r[m]);
 }
 
 // Neighbour across face f (2k+s) of cell `cell` (32-bit index arithmetic), -1 on
@@ -204,11 +304,14 @@ __device__ __forceinline__ T fnormal(const OpP<T> &P, const T *colp, T zeta0, in
 constexpr int fmax3(int a, int b, int c) { return a > b ? (a > c ? a : c) : (b > c ? b : c); }
 // Minimum resident CTAs asked of the compiler: FP32 kernels up to degree 4
 // are held to 64 registers per thread (they are latency bound, so occupancy
-// pays; higher degrees would spill); FP64 kernels are left free (bound by
-// the FP64 pipe).
+// pays; higher degrees would spill), double-word kernels to 224; FP64 kernels
+// are left free (bound by the FP64 pipe).
 template <typename T, int N, int NT>
 constexpr int fused_min_blocks() {
-  return (sizeof(T) == 4 && N <= 5) ? (65536 / (NT * 64) > 0 ? 65536 / (NT * 64) : 1) : 1;
+  if (sizeof(T) == 4 && N <= 5) return 65536 / (NT * 64) > 0 ? 65536 / (NT * 64) : 1;
+  // double-word kernels are latency bound at ~250 registers: ask for 224 (one more CTA at r = 4)
+  if (std::is_same<T, df64>::value && N <= 5) return 65536 / (NT * 224) > 0 ? 65536 / (NT * 224) : 1;
+  return 1;
 }
 constexpr int fmax2(int a, int b) { return a > b ? a : b; }
 
@@ -243,8 +346,9 @@ struct FGradL {
 };
 
 template <typename T, int N, bool CURVED, bool INV, int CPB, int NT>
-__global__ void __launch_bounds__(NT, fused_min_blocks<T, N, NT>()) kf_grad(const OpP<T> P, const T *__restrict__ p, const T *__restrict__ rho,
-                                              T *__restrict__ V, long long Ntot, int ncell) {
+__global__ void __launch_bounds__(NT, fused_min_blocks<T, N, NT>())
+    kf_grad(const OpP<T> P, const store_t<T> *__restrict__ p, const store_t<T> *__restrict__ rho,
+            store_t<T> *__restrict__ V, long long Ntot, int ncell) {
   using L = FGradL<N, CURVED>;
   constexpr int Q = L::Q, N2 = L::N2, N3 = L::N3, Q2 = L::Q2, NFP = L::NFP, NG = L::NG, PC = L::per_cell;
   constexpr int MIT = INV ? M_PIT : M_IT, MDT = INV ? M_PDT : M_DT;  // test matrices
@@ -620,9 +724,10 @@ struct FDivL {
 };
 
 template <typename T, int N, bool CURVED, bool KQ, int CPB, int NT>
-__global__ void __launch_bounds__(NT, fused_min_blocks<T, N, NT>()) kf_div(const OpP<T> P, const T *__restrict__ V, const T *__restrict__ p,
-                                             const T *__restrict__ pk, T *__restrict__ y, long long Ntot, int ncell,
-                                             const T *__restrict__ kq) {
+__global__ void __launch_bounds__(NT, fused_min_blocks<T, N, NT>())
+    kf_div(const OpP<T> P, const store_t<T> *__restrict__ V, const store_t<T> *__restrict__ p,
+           const store_t<T> *__restrict__ pk, store_t<T> *__restrict__ y, long long Ntot, int ncell,
+           const store_t<T> *__restrict__ kq) {
   using L = FDivL<N, CURVED, KQ>;
   constexpr int Q = L::Q, N2 = L::N2, N3 = L::N3, Q2 = L::Q2, NFI = L::NFI, NSL = L::NSL, PC = L::per_cell;
   constexpr int IP = KQ ? 3 : 4;  // field index of p (p_k is field 3 without KQ)
@@ -648,7 +753,7 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<T, N, NT>()) kf_div(const
       if (l < W1) {
         const int f = l / N2, m = l - f * N2;
         const long long off = (long long)cell * N3 + N * m;
-        const T *src = f < 3 ? V + f * Ntot + off : (f == IP ? p + off : pk + off);
+        const store_t<T> *src = f < 3 ? V + f * Ntot + off : (f == IP ? p + off : pk + off);
         T x[N], o[Q];
         lds<T, N, 1>(src, x);
         mv<T, N, M_I, Q, N>(x, o);

@@ -33,7 +33,8 @@ int fprep(dgx_ctx *c, Kern k, size_t smem) {
 }
 
 template <typename T, int N, bool CURVED, bool INV, int CPB, int NT>
-int fgrad_go(dgx_ctx *c, const OpP<T> &P, const T *p, const T *rho, T *V, cudaStream_t s) {
+int fgrad_go(dgx_ctx *c, const OpP<T> &P, const store_t<T> *p, const store_t<T> *rho, store_t<T> *V,
+             cudaStream_t s) {
   const size_t smem = sizeof(T) * (size_t)CPB * FGradL<N, CURVED>::per_cell;
   if (smem > kFusedMaxSmem) return set_error(c, DGX_ERR_ARG, "fused gradient kernel: %zu bytes of shared memory", smem);
   auto k = kf_grad<T, N, CURVED, INV, CPB, NT>;
@@ -45,7 +46,8 @@ int fgrad_go(dgx_ctx *c, const OpP<T> &P, const T *p, const T *rho, T *V, cudaSt
 }
 
 template <typename T, int N, bool CURVED, bool KQ, int CPB, int NT>
-int fdiv_go(dgx_ctx *c, const OpP<T> &P, const T *V, const T *p, const T *pk, T *y, const T *kq, cudaStream_t s) {
+int fdiv_go(dgx_ctx *c, const OpP<T> &P, const store_t<T> *V, const store_t<T> *p, const store_t<T> *pk,
+            store_t<T> *y, const store_t<T> *kq, cudaStream_t s) {
   const size_t smem = sizeof(T) * (size_t)CPB * FDivL<N, CURVED, KQ>::per_cell;
   if (smem > kFusedMaxSmem) return set_error(c, DGX_ERR_ARG, "fused divergence kernel: %zu bytes of shared memory", smem);
   auto k = kf_div<T, N, CURVED, KQ, CPB, NT>;
@@ -59,7 +61,8 @@ int fdiv_go(dgx_ctx *c, const OpP<T> &P, const T *V, const T *p, const T *pk, T 
 }  // namespace
 
 template <typename T, int N, bool CURVED>
-int fused_grad(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s, bool inv, double alpha, int cfg) {
+int fused_grad(dgx_ctx *c, const store_t<T> *p, const store_t<T> *rho, store_t<T> *V, cudaStream_t s, bool inv,
+               double alpha, int cfg) {
   if (int e = upload_fused_tables(c)) return e;
   OpP<T> P = make_params<T>(c);
   if (alpha >= 0.0) P.alpha = (T)alpha;
@@ -69,12 +72,12 @@ int fused_grad(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s, bool 
 }
 
 template <typename T, int N, bool CURVED>
-int fused_div(dgx_ctx *c, const T *V, const T *p, const T *pk, T *y, cudaStream_t s, double alpha, const T *kq,
-              int cfg) {
+int fused_div(dgx_ctx *c, const store_t<T> *V, const store_t<T> *p, const store_t<T> *pk, store_t<T> *y,
+              cudaStream_t s, double alpha, const store_t<T> *kq, int cfg) {
   if (int e = upload_fused_tables(c)) return e;
   OpP<T> P = make_params<T>(c);
   if (alpha >= 0.0) P.alpha = (T)alpha;
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (sizeof(store_t<T>) == 8) {
     if (kq) {
       if (cfg == 1) return fdiv_go<T, N, CURVED, true, fused_cpb(N, 1), fused_nt(N, 1)>(c, P, V, p, pk, y, kq, s);
       return fdiv_go<T, N, CURVED, true, fused_cpb(N, 0), fused_nt(N, 0)>(c, P, V, p, pk, y, kq, s);
@@ -91,18 +94,20 @@ template <typename T, int N, bool CURVED>
 size_t fused_smem(int cfg) {
   const int cpb = fused_cpb(N, cfg);
   const size_t g = sizeof(T) * (size_t)cpb * FGradL<N, CURVED>::per_cell;
-  const size_t d = sizeof(T) * (size_t)cpb * FDivL<N, CURVED, sizeof(T) == 8>::per_cell;
+  const size_t d = sizeof(T) * (size_t)cpb * FDivL<N, CURVED, sizeof(store_t<T>) == 8>::per_cell;
   return g > d ? g : d;
 }
 
-#define DGX_FUSED_INSTANTIATE(T, NN)                                                                          \
-  template int fused_grad<T, NN, false>(dgx_ctx *, const T *, const T *, T *, cudaStream_t, bool, double, int); \
-  template int fused_grad<T, NN, true>(dgx_ctx *, const T *, const T *, T *, cudaStream_t, bool, double, int);  \
-  template int fused_div<T, NN, false>(dgx_ctx *, const T *, const T *, const T *, T *, cudaStream_t, double,   \
-                                       const T *, int);                                                        \
-  template int fused_div<T, NN, true>(dgx_ctx *, const T *, const T *, const T *, T *, cudaStream_t, double,    \
-                                      const T *, int);                                                         \
-  template size_t fused_smem<T, NN, false>(int);                                                               \
+#define DGX_FUSED_INSTANTIATE(T, NN)                                                                           \
+  template int fused_grad<T, NN, false>(dgx_ctx *, const store_t<T> *, const store_t<T> *, store_t<T> *,       \
+                                        cudaStream_t, bool, double, int);                                      \
+  template int fused_grad<T, NN, true>(dgx_ctx *, const store_t<T> *, const store_t<T> *, store_t<T> *,        \
+                                       cudaStream_t, bool, double, int);                                       \
+  template int fused_div<T, NN, false>(dgx_ctx *, const store_t<T> *, const store_t<T> *, const store_t<T> *,  \
+                                       store_t<T> *, cudaStream_t, double, const store_t<T> *, int);           \
+  template int fused_div<T, NN, true>(dgx_ctx *, const store_t<T> *, const store_t<T> *, const store_t<T> *,   \
+                                      store_t<T> *, cudaStream_t, double, const store_t<T> *, int);            \
+  template size_t fused_smem<T, NN, false>(int);                                                                \
   template size_t fused_smem<T, NN, true>(int);
 
 }  // namespace dgx

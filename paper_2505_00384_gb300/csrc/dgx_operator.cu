@@ -592,6 +592,8 @@ template <typename T, int N, bool CURVED>
 int grad_impl(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s, bool inv, double alpha) {
   constexpr int Q = 2 * N - 1;
   const size_t smem = sizeof(T) * GradL<N, Q, CURVED>::total;
+  if constexpr (sizeof(T) == 8)
+    if (op_variant<T>(c) >= 5) return fused_grad<df64, N, CURVED>(c, p, rho, V, s, inv, alpha, op_variant<T>(c) - 5);
   if (op_variant<T>(c) >= 3) return fused_grad<T, N, CURVED>(c, p, rho, V, s, inv, alpha, op_variant<T>(c) - 3);
   OpP<T> P = make_params<T>(c);
   if (alpha >= 0.0) P.alpha = (T)alpha;
@@ -617,6 +619,8 @@ int div_impl(dgx_ctx *c, const T *V, const T *p, const T *pk, T *y, cudaStream_t
   const T *kq = nullptr;
   if constexpr (sizeof(T) == 8)
     if (alpha < 0.0 && pk == c->pk64 && c->kq64_version == c->coef_version) kq = reinterpret_cast<const T *>(c->kq64);
+  if constexpr (sizeof(T) == 8)
+    if (op_variant<T>(c) >= 5) return fused_div<df64, N, CURVED>(c, V, p, pk, y, s, alpha, kq, op_variant<T>(c) - 5);
   if (op_variant<T>(c) >= 3) return fused_div<T, N, CURVED>(c, V, p, pk, y, s, alpha, kq, op_variant<T>(c) - 3);
   const size_t smem = sizeof(T) * DivL<N, Q, CURVED>::total;
   auto k = k_div<T, N, Q, CURVED>;
@@ -717,13 +721,37 @@ OpP<T> make_params(const dgx_ctx *c) {
 }
 template OpP<double> make_params<double>(const dgx_ctx *);
 template OpP<float> make_params<float>(const dgx_ctx *);
+// double-word parameters: every scalar split from its double; the terrain
+// columns as double-words; the 1D tables live in constant memory only
+template <>
+OpP<df64> make_params<df64>(const dgx_ctx *c) {
+  OpP<df64> P;
+  P.nx = c->mesh.nx;
+  P.ny = c->mesh.ny;
+  P.nz = c->mesh.nz;
+  P.bc_lat = c->mesh.bc_lateral;
+  P.dx = df64(c->mesh.Lx / c->mesh.nx);
+  P.dy = df64(c->mesh.Ly / c->mesh.ny);
+  P.dz = df64(c->mesh.Lz / c->mesh.nz);
+  P.H = df64(c->mesh.Lz);
+  P.invH = df64(1.0 / c->mesh.Lz);
+  P.alpha = df64(c->alpha);
+  P.gfac = df64(c->gamma / (c->gamma - 1.0));
+  P.igm1 = df64(1.0 / (c->gamma - 1.0));
+  P.tab = nullptr;
+  P.col = reinterpret_cast<const df64 *>(c->coldf);
+  return P;
+}
 
 template <typename T>
 bool op_variant_ok(const dgx_ctx *c, int v) {
   if (v < 0 || v >= kOpVariants) return false;
   if (v < 3) return true;
+  if (v >= 5 && sizeof(T) != 8) return false;  // double-word kernels: FP64 arrays only
   size_t smem = 0;
-#define FSM(NN) (c->curved ? fused_smem<T, NN, true>(v - 3) : fused_smem<T, NN, false>(v - 3))
+#define FSM(NN)                                                                                                  \
+  (v >= 5 ? (c->curved ? fused_smem<df64, NN, true>(v - 5) : fused_smem<df64, NN, false>(v - 5))                  \
+          : (c->curved ? fused_smem<T, NN, true>(v - 3) : fused_smem<T, NN, false>(v - 3)))
   switch (c->n) {
     case 2: smem = FSM(2); break;
     case 3: smem = FSM(3); break;
@@ -741,7 +769,8 @@ template bool op_variant_ok<float>(const dgx_ctx *, int);
 
 int op_variant_threads(const dgx_ctx *c, int v) {
   if (v >= 0 && v < 3) return kLegacyThreads[v];
-  if (v >= 3 && v < kOpVariants) return fused_nt(c->n, v - 3);
+  if (v >= 3 && v < 5) return fused_nt(c->n, v - 3);
+  if (v >= 5 && v < kOpVariants) return fused_nt(c->n, v - 5);
   return threads_for(c->n);
 }
 

@@ -496,7 +496,7 @@ def dgx_mass_cg_stats(ctx):
     return it.value, bad.value
 
 
-DGX_OP_VARIANTS = 5
+DGX_OP_VARIANTS = 7
 
 
 def dgx_operator_variant(ctx, prec):
@@ -505,7 +505,7 @@ def dgx_operator_variant(ctx, prec):
 
 
 def dgx_set_operator_variant(ctx, prec, variant):
-    """Pin launch variant 0..4 for prec on the current mesh, or -1 for the autotuner."""
+    """Pin launch variant 0..6 for prec on the current mesh, or -1 for the autotuner."""
     return _check(ctx, load().dgx_set_operator_variant(ctx, int(prec), int(variant)))
 
 

@@ -138,14 +138,15 @@ def test_imex_step_matches_oracle(case, nsteps):
     _compare_steps(case, obg, rb, pb, rho, u, p, nsteps)
 
 
-@pytest.mark.parametrize("variant", [3, 4])
+@pytest.mark.parametrize("variant", [3, 4, 5, 6])
 def test_imex_step_with_fused_operator(case, variant):
-    """The step with the fused operator kernels pinned (both precisions): also
-    covers their uses inside the step (the dual B p' and -C u with the step's
-    own coefficients and a~ dt = 1)."""
+    """The step with the fused operator kernels pinned (FP64, and FP32 for the
+    variants that have an FP32 form; 5 and 6 compute the FP64 operator in
+    double-word arithmetic): also covers their uses inside the step (the dual
+    B p' and -C u with the step's own coefficients and a~ dt = 1)."""
     obg, rb, pb = _with_bg(case)
     rho, u, p = _state(case, rb, pb, 122)
-    for prec in (dgx.DGX_F64, dgx.DGX_F32):
+    for prec in ((dgx.DGX_F64, dgx.DGX_F32) if variant < 5 else (dgx.DGX_F64,)):
         try:
             dgx.dgx_set_operator_variant(case.ctx, prec, variant)
         except dgx.DgxError:
