@@ -851,8 +851,10 @@ def run_learned(args):
 def run_ensemble(args):
     """16 members (meshes 32^3 .. 96x96x48, degrees 3 + i mod 3, seeded hill
     heights 200-800 m and widths 0.5-2 km, 60 x 60 x 20 km, periodic lateral
-    faces): all pressure solves to 1e-8 in one call, each FP32 GMRES cycle of all
-    members one CUDA-graph launch, threads per CTA autotuned per degree."""
+    faces): all pressure solves to 1e-8 in one call, the whole FP64 refinement
+    loop around FP32 GMRES cycles of all members one CUDA-graph launch (a WHILE
+    conditional node), tile shapes (cells and threads per CTA) autotuned per
+    degree."""
     import numpy as np
     import torch
     from paper_2505_00384_gb300 import dgx, inputs
@@ -879,6 +881,9 @@ def run_ensemble(args):
         dgx.dgx_background_fields(c, rho[o:o + n].data_ptr(), pk[o:o + n].data_ptr())
         X = torch.zeros(3 * n, dtype=f64, device="cuda")
         dgx.dgx_node_coords(c, X.data_ptr())
+        # the member contexts work on the ensemble's own stream: wait for the
+        # coordinates (and fields) before torch reads them on its stream
+        torch.cuda.synchronize()
         x, y, z = X[:n], X[n:2 * n], X[2 * n:]
         ptrue[o:o + n] = 100.0 * torch.exp(-((x - 30000.0) ** 2 + (y - 30000.0) ** 2 + (z - 5000.0) ** 2)
                                            / (2 * 2000.0 ** 2))
@@ -944,7 +949,11 @@ def run_ensemble(args):
             deg, nmem, th64, th32 = dgx.dgx_ensemble_tuning(e, g)
         except dgx.DgxError:
             break
-        tuning.append({"degree": deg, "members": nmem, "threads_f64": th64, "threads_f32": th32})
+        f64k, c64 = dgx.dgx_ensemble_tile(e, g, dgx.DGX_F64)
+        f32k, c32 = dgx.dgx_ensemble_tile(e, g, dgx.DGX_F32)
+        tuning.append({"degree": deg, "members": nmem, "threads_f64": th64, "threads_f32": th32,
+                       "f64_kernels": "fused, double-word" if f64k else "one cell per CTA", "cells_per_cta_f64": c64,
+                       "f32_kernels": "fused" if f32k else "one cell per CTA", "cells_per_cta_f32": c32})
         g += 1
     v = statistics.median(ts)
     line = {"metric": "ensemble pressure solves s/solve @1e-8 rel residual (all members)", "value": v,
@@ -952,7 +961,8 @@ def run_ensemble(args):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
             "data": "synthetic",
             "config": {"workload": "ensemble_%d_members_%.1fM_dofs" % (nm, Nt / 1e6), "members": nm,
-                       "degrees": "3 + i mod 3", "solver": "FP64 refinement around FP32 GMRES(30) cycles (CUDA graph)"},
+                       "degrees": "3 + i mod 3",
+                       "solver": "FP64 refinement around FP32 GMRES(30) cycles, one CUDA-graph launch per solve"},
             "gdofs_solved_per_s": Nt / v / 1e9, "gpu_launches_host_side": launches,
             "sweeps": [i.iterations for i in infos], "max_relres": max(i.relres for i in infos),
             "max_rel_err_vs_p_true": err, "autotune": tuning,

@@ -422,10 +422,15 @@ int dgx_basis_tables(int degree, double *out, int capacity);
  * dgx_ensemble_offset(e, m)); all arrays are device FP64 unless stated.
  * The operator of all members of one degree runs as one kernel pair; the
  * solver is FP64 iterative refinement around an FP32 GMRES(inner_maxit)
- * cycle with the Helmholtz Jacobi preconditioner, every cycle of all members
- * being one CUDA-graph launch (per-member Hessenberg and Givens rotations on
- * the device); threads per CTA are chosen per degree group by a timing
- * autotuner before the graph is captured. */
+ * cycle with the Helmholtz Jacobi preconditioner (per-member Hessenberg and
+ * Givens rotations on the device).  A whole solve is one CUDA-graph launch: the
+ * refinement loop is a WHILE conditional node whose condition a device kernel
+ * sets from the members' FP64 residuals (bounded by maxit cycles); the host
+ * reads the per-member results once.  The tile shape of the multi-mesh
+ * operator (one cell per CTA at 128 / 192 / 256 threads, or the fused kernels
+ * with one or more cells per CTA, in FP64 computing in double-words) is chosen
+ * per degree group and precision by a timing autotuner before the graph is
+ * captured. */
 typedef struct dgx_ensemble dgx_ensemble;
 int dgx_ensemble_create(dgx_ensemble **e, int device, void *cuda_stream, int n_members, const dgx_mesh_desc *descs);
 void dgx_ensemble_destroy(dgx_ensemble *e);
@@ -434,17 +439,23 @@ const char *dgx_ensemble_last_error(const dgx_ensemble *e);
 long long dgx_ensemble_num_dofs(const dgx_ensemble *e, int m);
 long long dgx_ensemble_offset(const dgx_ensemble *e, int m);
 /* The member's own context (owned by the ensemble; for set-up calls such as
- * dgx_set_background / dgx_node_coords on that member). */
+ * dgx_set_background / dgx_node_coords on that member).  Its calls run on the
+ * ensemble's own stream: synchronise before reading their results on
+ * another stream. */
 int dgx_ensemble_member(dgx_ensemble *e, int m, dgx_ctx **ctx);
 /* Concatenated rho^(l), p_k of all members; same a~_ll dt and gamma for all. */
 int dgx_ensemble_set_coefficients(dgx_ensemble *e, const double *rho_all, const double *p_k_all, double a_dt,
                                   double gamma);
 /* y = S x for every member (prec: DGX_F64 or DGX_F32). */
 int dgx_ensemble_apply_operator(dgx_ensemble *e, int prec, const void *x_all, void *y_all);
-/* Choose threads per CTA of the multi-mesh operator per degree group (also done by the first solve). */
+/* Choose the tile shape of the multi-mesh operator per degree group (also done by the first solve). */
 int dgx_ensemble_autotune(dgx_ensemble *e);
-/* The autotuner's choice for degree group g (host outputs, any may be NULL). */
+/* The autotuner's choice for degree group g (host outputs, any may be NULL):
+ * threads per CTA in FP64 and FP32; and, for precision prec, the kernels
+ * (fused = 1: the fused kernels, in FP64 computing in double-words; 0: one cell
+ * per CTA) with their cells per CTA. */
 int dgx_ensemble_tuning(const dgx_ensemble *e, int g, int *degree, int *members, int *threads64, int *threads32);
+int dgx_ensemble_tile(const dgx_ensemble *e, int g, int prec, int *fused, int *cells_per_cta);
 /* Solve all members to ||b_m - S_m x_m|| <= tol ||b_m|| (FP64).  opts: tol, maxit
  * (refinement sweeps), inner_maxit (FP32 GMRES cycle length, <= 64), inner_tol,
  * use_x0.  info: array of n_members entries (host).  Returns DGX_OK,

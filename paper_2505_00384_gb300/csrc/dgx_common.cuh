@@ -114,11 +114,12 @@ struct OpP {
 
 // One member of a multi-mesh (ensemble) launch: its operator parameters, its
 // coefficient copies and V scratch, and its place in the concatenated vectors.
+// (T = df64: double-word parameters, FP64 arrays)
 template <typename T>
 struct EnsMember {
   OpP<T> P;
-  const T *rho, *pk;
-  T *V;
+  const store_t<T> *rho, *pk;
+  store_t<T> *V;
   long long cell_off, dof_off, N;
 };
 
@@ -284,6 +285,10 @@ int fused_div(dgx_ctx *c, const store_t<T> *V, const store_t<T> *p, const store_
               cudaStream_t s, double alpha, const store_t<T> *kq, int cfg);
 template <typename T, int N, bool CURVED>
 size_t fused_smem(int cfg);
+// multi-mesh fused operator (FP32, or FP64 arrays in double-words): members' CTA ranges in cta_off (nmem + 1 entries, device)
+template <typename T, int N, bool CURVED>
+int fused_operator_multi(dgx_ctx *c0, const EnsMember<T> *mem, int nmem, const int *cta_off, int nblocks,
+                         const store_t<T> *x, store_t<T> *y, cudaStream_t s, int cfg);
 // multi-mesh operator y = S x for members of one degree (N = r+1) and terrain kind;
 // `mem` is a device array of nmem members with consecutive cell ranges totalling ncell_total
 template <typename T>

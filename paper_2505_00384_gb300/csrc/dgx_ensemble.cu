@@ -7,13 +7,17 @@
 // diagonals; the ensemble owns concatenated vectors (member m at dof_off[m]).
 // The operator of all members of one degree runs as one kernel pair
 // (k_grad_multi / k_div_multi over the members' cells).  The solver is FP64
-// iterative refinement around an FP32 GMRES(m) cycle: each cycle -- for all
-// members at once, with per-member Hessenberg matrices and Givens rotations
-// kept on the device -- is captured once into a CUDA graph and replayed with
-// one cudaGraphLaunch; between cycles the FP64 residual b - S x of every
-// member is formed and its norms are read back (the only host round trip).
-// Threads per CTA of the multi-mesh operator are chosen per degree group by a
-// small timing autotuner before the graph is captured.
+// iterative refinement around an FP32 GMRES(m) cycle for all members at once,
+// with per-member Hessenberg matrices and Givens rotations kept on the
+// device.  The whole solve is one CUDA graph, launched once: a prologue forms
+// ||b_m||, the FP64 residual b - S x of every member and its norm, and a check
+// kernel that freezes converged members and sets the condition of a WHILE
+// conditional node; its body runs one inner cycle, adds the correction, forms
+// the new residuals and runs the check again.  The loop ends when every member
+// has converged, a residual is not finite, or maxit cycles have run (a bound
+// counted on the device); the host reads the per-member results once at the
+// end.  Threads per CTA of the multi-mesh operator are chosen per degree group
+// by a small timing autotuner before the graph is captured.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -43,6 +47,16 @@ struct Group {
   EnsMember<double> *d64 = nullptr;
   EnsMember<float> *d32 = nullptr;
   int threads64 = 256, threads32 = 256;
+  // FP32 tile shape: -1 = one cell per CTA (k_grad_multi / k_div_multi, threads32),
+  // 0 / 1 = the fused kernels in configuration tile32 (fused_cpb cells, fused_nt threads)
+  int tile32 = -1;
+  // FP64 tile shape: -1 = one cell per CTA (threads64), 0 / 1 = the fused kernels in
+  // double-word arithmetic in configuration tile64
+  int tile64 = -1;
+  EnsMember<df64> *ddf = nullptr;        // member tables for the double-word kernels
+  int *cta_off[2] = {nullptr, nullptr};  // per fused configuration: members' first CTA (device)
+  int nblocks[2] = {0, 0};
+  bool fits32[2] = {false, false}, fits64[2] = {false, false};
 };
 
 }  // namespace
@@ -72,10 +86,18 @@ struct dgx_ensemble {
   int *jj = nullptr, *act = nullptr;
   double *host = nullptr;  // pinned mirror of per-member scalars
   long long *seg_off = nullptr, *seg_len = nullptr;
-  // graph of one inner cycle
+  // graph of one whole solve (refinement loop in a WHILE conditional node) and
+  // the arguments it was captured with
   cudaGraphExec_t gexec = nullptr;
-  int graph_m = 0;
-  double graph_tol = 0.0;
+  const double *graph_b = nullptr;
+  double *graph_x = nullptr;
+  int graph_m = 0, graph_maxit = 0, graph_x0 = 0;
+  double graph_tol = 0.0, graph_itol = 0.0;
+  long long graph_pro_launches = 0, graph_body_launches = 0;
+  // per-member results of a solve on the device: relative residual, cycles;
+  // ctl[0] = cycles run, ctl[1] = 1 after a non-finite residual
+  double *relres_d = nullptr;
+  int *its_d = nullptr, *ctl_d = nullptr;
   std::vector<void *> owned;
 };
 
@@ -268,6 +290,51 @@ __global__ void __launch_bounds__(kT) k_resid(long long n, const double *__restr
     r[i] = b[i] - Sx[i];
 }
 
+// part[m][b][0] = block b's share of |v_m|^2 in FP64 (grid (kSegBlocks, nm))
+__global__ void __launch_bounds__(kT) k_seg_norm2_64(const long long *off, const long long *len,
+                                                     const double *__restrict__ v, double *__restrict__ part) {
+  __shared__ double sh[32];
+  const int m = blockIdx.y;
+  const long long o = off[m], n = len[m];
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    acc += v[o + i] * v[o + i];
+  const double t = bsum(acc, sh);
+  if (threadIdx.x == 0) part[((long long)m * kSegBlocks + blockIdx.x) * (kMaxRestart + 1)] = t;
+}
+
+__global__ void k_sqrt_members(int nm, const double *nrm, double *out) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < nm) out[m] = sqrt(nrm[m * (kMaxRestart + 1)]);
+}
+
+// Convergence check of the refinement loop (one CTA, one thread per member):
+// relres_m = |r_m| / |b_m|; a member at or below tol is frozen (its later inner
+// cycles leave it alone); the loop goes on while some member is above tol, all
+// residuals are finite and fewer than maxit cycles have run.  The decision sets
+// the WHILE node's condition; the cycle counters advance with it.
+__global__ void k_refine_check(int nm, double tol, int maxit, const double *nrm, const double *bn, int *frozen,
+                               double *relres, int *its, int *ctl, cudaGraphConditionalHandle cond) {
+  const int m = threadIdx.x;
+  bool d = true, bad = false;
+  if (m < nm) {
+    const double rel = bn[m] > 0.0 ? sqrt(nrm[m * (kMaxRestart + 1)]) / bn[m] : 0.0;
+    relres[m] = rel;
+    bad = !isfinite(rel);
+    d = rel <= tol;
+    frozen[m] = d ? 1 : 0;
+  }
+  const int cycles = ctl[0];
+  const bool all = __syncthreads_and(d), anybad = __syncthreads_or(bad);
+  const bool go = !all && !anybad && cycles < maxit;
+  if (m < nm && go && !d) its[m] += 1;
+  if (threadIdx.x == 0) {
+    if (anybad) ctl[1] = 1;
+    if (go) ctl[0] = cycles + 1;
+    cudaGraphSetConditional(cond, go ? 1u : 0u);
+  }
+}
+
 __global__ void __launch_bounds__(kT) k_addf(long long n, const float *__restrict__ d, double *__restrict__ x) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     x[i] += (double)d[i];
@@ -352,15 +419,51 @@ int vblocks(long long n) {
 }
 
 // ---------------------------------------------------------------- operations
+// the fused multi-mesh operator of one group (degree and terrain dispatch):
+// FP32, or FP64 arrays in double-word arithmetic
+template <typename T>
+int fused_group(dgx_ensemble *e, const Group &G, int cfg, const T *x, T *y) {
+  dgx_ctx *c0 = e->mem[G.idx[0]];
+  const int nm = (int)G.idx.size(), nb = G.nblocks[cfg];
+  const int *co = G.cta_off[cfg];
+  using C = typename std::conditional<sizeof(T) == 8, df64, float>::type;
+  const EnsMember<C> *tab;
+  if constexpr (sizeof(T) == 8) tab = G.ddf;
+  else tab = G.d32;
+#define FG(NN) (G.curved ? fused_operator_multi<C, NN, true>(c0, tab, nm, co, nb, x, y, e->stream, cfg) \
+                         : fused_operator_multi<C, NN, false>(c0, tab, nm, co, nb, x, y, e->stream, cfg))
+  int r;
+  switch (G.n) {
+    case 2: r = FG(2); break;
+    case 3: r = FG(3); break;
+    case 4: r = FG(4); break;
+    case 5: r = FG(5); break;
+    case 6: r = FG(6); break;
+    case 7: r = FG(7); break;
+    default: return eset(e, DGX_ERR_ARG, "unsupported degree %d", G.n - 1);
+  }
+#undef FG
+  if (r) e->err = c0->err;
+  return r;
+}
+
 template <typename T>
 int apply_all(dgx_ensemble *e, const T *x, T *y) {
   for (auto &G : e->groups) {
     const EnsMember<T> *d;
     int th;
     if constexpr (sizeof(T) == 8) {
+      if (G.tile64 >= 0) {
+        if (int r = fused_group<double>(e, G, G.tile64, x, y)) return r;
+        continue;
+      }
       d = G.d64;
       th = G.threads64;
     } else {
+      if (G.tile32 >= 0) {
+        if (int r = fused_group<float>(e, G, G.tile32, x, y)) return r;
+        continue;
+      }
       d = G.d32;
       th = G.threads32;
     }
@@ -478,8 +581,42 @@ int autotune(dgx_ensemble *e) {
           bt = th;
         }
       }
-      if (prec == 0) G.threads64 = bt;
-      else G.threads32 = bt;
+      if (prec == 0) {
+        G.threads64 = bt;
+        G.tile64 = -1;
+      } else {
+        G.threads32 = bt;
+        G.tile32 = -1;
+      }
+      // the fused kernels (FP32; FP64 in double-words) in each configuration that
+      // fits (cells per CTA x threads)
+      for (int cfg = 0; cfg < 2; ++cfg) {
+        if (!(prec == 0 ? G.fits64[cfg] : G.fits32[cfg])) continue;
+        for (int rep = 0; rep < 3; ++rep) {
+          if (rep == 1) cudaEventRecord(a, e->stream);
+          const int r = prec == 0 ? fused_group<double>(e, G, cfg, e->r64, e->t64)
+                                  : fused_group<float>(e, G, cfg, e->r32, e->w32);
+          if (r) {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            return r;
+          }
+        }
+        cudaEventRecord(b, e->stream);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best) {
+          best = ms;
+          if (prec == 0) {
+            G.tile64 = cfg;
+            G.threads64 = fused_nt(G.n, cfg);
+          } else {
+            G.tile32 = cfg;
+            G.threads32 = fused_nt(G.n, cfg);
+          }
+        }
+      }
     }
   }
   cudaEventDestroy(a);
@@ -549,7 +686,9 @@ int dgx_ensemble_create(dgx_ensemble **out, int device, void *stream, int n, con
       (r = ealloc(e, &e->y, (size_t)n * kMaxRestart)) || (r = ealloc(e, &e->scl, (size_t)n)) ||
       (r = ealloc(e, &e->beta0, (size_t)n)) ||
       (r = ealloc(e, &e->jj, (size_t)n)) || (r = ealloc(e, &e->act, (size_t)2 * n)) ||
-      (r = ealloc(e, &e->seg_off, (size_t)n)) || (r = ealloc(e, &e->seg_len, (size_t)n)))
+      (r = ealloc(e, &e->seg_off, (size_t)n)) || (r = ealloc(e, &e->seg_len, (size_t)n)) ||
+      (r = ealloc(e, &e->relres_d, (size_t)n)) || (r = ealloc(e, &e->its_d, (size_t)n)) ||
+      (r = ealloc(e, &e->ctl_d, (size_t)2)))
     return fail(r);
   if ((r = echeck(e, cudaMallocHost(&e->host, S * sizeof(double)), "cudaMallocHost"))) return fail(r);
   cudaMemset(e->r64, 0, Nt * sizeof(double));
@@ -612,6 +751,7 @@ int dgx_ensemble_set_coefficients(dgx_ensemble *e, const double *rho_all, const 
   for (auto &G : e->groups) {
     std::vector<EnsMember<double>> h64;
     std::vector<EnsMember<float>> h32;
+    std::vector<EnsMember<df64>> hdf;
     long long co = 0;
     for (int m : G.idx) {
       dgx_ctx *c = e->mem[m];
@@ -631,17 +771,44 @@ int dgx_ensemble_set_coefficients(dgx_ensemble *e, const double *rho_all, const 
       f.cell_off = co;
       f.dof_off = e->off[m];
       f.N = c->N;
+      EnsMember<df64> w;
+      w.P = make_params<df64>(c);
+      w.rho = c->rho64;
+      w.pk = c->pk64;
+      w.V = c->V64;
+      w.cell_off = co;
+      w.dof_off = e->off[m];
+      w.N = c->N;
       h64.push_back(a);
       h32.push_back(f);
+      hdf.push_back(w);
       co += c->ncell;
     }
     G.ncell = co;
     if (!G.d64) {
       int r;
-      if ((r = ealloc(e, &G.d64, G.idx.size())) || (r = ealloc(e, &G.d32, G.idx.size()))) return r;
+      if ((r = ealloc(e, &G.d64, G.idx.size())) || (r = ealloc(e, &G.d32, G.idx.size())) ||
+          (r = ealloc(e, &G.ddf, G.idx.size())))
+        return r;
     }
+    cudaMemcpyAsync(G.ddf, hdf.data(), hdf.size() * sizeof(EnsMember<df64>), cudaMemcpyHostToDevice, e->stream);
     cudaMemcpyAsync(G.d64, h64.data(), h64.size() * sizeof(EnsMember<double>), cudaMemcpyHostToDevice, e->stream);
     cudaMemcpyAsync(G.d32, h32.data(), h32.size() * sizeof(EnsMember<float>), cudaMemcpyHostToDevice, e->stream);
+    // CTA ranges of the fused configurations that fit in shared memory
+    for (int cfg = 0; cfg < 2; ++cfg) {
+      dgx_ctx *c0 = e->mem[G.idx[0]];
+      G.fits32[cfg] = op_variant_ok<float>(c0, 3 + cfg);
+      G.fits64[cfg] = op_variant_ok<double>(c0, 5 + cfg);
+      if (!G.fits32[cfg] && !G.fits64[cfg]) continue;
+      const int cpb = fused_cpb(G.n, cfg);
+      std::vector<int> co(G.idx.size() + 1, 0);
+      for (size_t k = 0; k < G.idx.size(); ++k)
+        co[k + 1] = co[k] + (int)((e->mem[G.idx[k]]->ncell + cpb - 1) / cpb);
+      if (!G.cta_off[cfg])
+        if (int r = ealloc(e, &G.cta_off[cfg], co.size())) return r;
+      G.nblocks[cfg] = co.back();
+      cudaMemcpyAsync(G.cta_off[cfg], co.data(), co.size() * sizeof(int), cudaMemcpyHostToDevice, e->stream);
+    }
   }
   if (int r = echeck(e, cudaStreamSynchronize(e->stream), "ensemble coefficients")) return r;
   e->has_coef = true;
@@ -666,6 +833,15 @@ int dgx_ensemble_autotune(dgx_ensemble *e) {
   const int r = autotune(e);
   leave(e);
   return r;
+}
+
+int dgx_ensemble_tile(const dgx_ensemble *e, int group, int prec, int *fused, int *cells_per_cta) {
+  if (!e || group < 0 || group >= (int)e->groups.size() || (prec != DGX_F64 && prec != DGX_F32)) return DGX_ERR_ARG;
+  const Group &G = e->groups[group];
+  const int t = prec == DGX_F64 ? G.tile64 : G.tile32;
+  if (fused) *fused = t >= 0 ? 1 : 0;
+  if (cells_per_cta) *cells_per_cta = t < 0 ? 1 : fused_cpb(G.n, t);
+  return DGX_OK;
 }
 
 int dgx_ensemble_tuning(const dgx_ensemble *e, int group, int *degree, int *members, int *threads64, int *threads32) {
@@ -696,89 +872,135 @@ int dgx_ensemble_solve(dgx_ensemble *e, const double *b, double *x, const dgx_so
   const long long Nt = e->Ntot;
   const int nm = e->nm;
   cudaStream_t s = e->stream;
-  std::vector<dgx_solve_info> inf(nm);
-  for (auto &i : inf) std::memset(&i, 0, sizeof(i));
   int *frozen = e->act + nm;  // device flags: member converged, stop correcting
-  cudaMemsetAsync(frozen, 0, nm * sizeof(int), s);
-  if (!o.use_x0) cudaMemsetAsync(x, 0, Nt * sizeof(double), s);
-  // ||b_m|| in FP64 (deterministic per-member reductions)
-  std::vector<double> bn(nm, 0.0);
-  for (int mm = 0; mm < nm; ++mm) {
-    dgx_ctx *c = e->mem[mm];
-    vec_dot<double>(c->N, b + e->off[mm], b + e->off[mm], c->red, c->red_out, s);
-    cudaMemcpyAsync(e->host + mm, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, s);
-  }
-  if ((r = echeck(e, cudaStreamSynchronize(s), "ensemble norms"))) return r;
-  for (int mm = 0; mm < nm; ++mm) bn[mm] = std::sqrt(e->host[mm]);
-  // graph of one inner cycle (captured once per restart length / tolerance)
-  if (!e->gexec || e->graph_m != m || e->graph_tol != o.inner_tol) {
+  const int x0 = o.use_x0 ? 1 : 0;
+  if (!e->gexec || e->graph_b != b || e->graph_x != x || e->graph_m != m || e->graph_tol != o.tol ||
+      e->graph_itol != o.inner_tol || e->graph_maxit != o.maxit || e->graph_x0 != x0) {
     if (e->gexec) {
       cudaGraphExecDestroy(e->gexec);
       e->gexec = nullptr;
     }
     // warm every kernel once outside capture (attributes, lazy loading)
+    cudaMemsetAsync(frozen, 0, nm * sizeof(int), s);
     if ((r = enqueue_cycle(e, 1, o.inner_tol, frozen))) return r;
-    if ((r = echeck(e, cudaStreamSynchronize(s), "warm-up cycle"))) return r;
-    cudaGraph_t graph;
-    if ((r = echeck(e, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture"))) return r;
-    const int rc = enqueue_cycle(e, m, o.inner_tol, frozen);
-    const cudaError_t ce = cudaStreamEndCapture(s, &graph);
-    if (rc) return rc;
-    if ((r = echeck(e, ce, "end capture"))) return r;
-    r = echeck(e, cudaGraphInstantiate(&e->gexec, graph, 0), "graph instantiate");
-    cudaGraphDestroy(graph);
-    if (r) return r;
-    e->graph_m = m;
-    e->graph_tol = o.inner_tol;
-  }
-  std::vector<int> done(nm, 0);
-  int sweeps = 0;
-  for (;;) {
-    // FP64 residual of every member and its norm
     if ((r = apply_all<double>(e, x, e->t64))) return r;
-    count_launch();
-    k_resid<<<vblocks(Nt), kT, 0, s>>>(Nt, b, e->t64, e->r64);
-    for (int mm = 0; mm < nm; ++mm) {
-      dgx_ctx *c = e->mem[mm];
-      vec_dot<double>(c->N, e->r64 + e->off[mm], e->r64 + e->off[mm], c->red, c->red_out, s);
-      cudaMemcpyAsync(e->host + mm, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, s);
-    }
-    if ((r = echeck(e, cudaStreamSynchronize(s), "ensemble residual"))) return r;
-    bool all = true;
-    std::vector<int> fz(nm, 0);
-    for (int mm = 0; mm < nm; ++mm) {
-      inf[mm].operator_f64 += 1;
-      const double rel = bn[mm] > 0 ? std::sqrt(e->host[mm]) / bn[mm] : 0.0;
-      if (std::isnan(rel)) return eset(e, DGX_ERR_BREAKDOWN, "member %d: NaN residual", mm);
-      inf[mm].relres = rel;
-      if (rel <= o.tol) {
-        done[mm] = 1;
-        fz[mm] = 1;
-      } else {
-        all = false;
+    if ((r = echeck(e, cudaStreamSynchronize(s), "warm-up cycle"))) return r;
+    const dim3 sgrid(kSegBlocks, nm);
+    // FP64 residual r = b - S x of every member and |r_m|^2 into nrm
+    auto residual = [&]() -> int {
+      if (int q = apply_all<double>(e, x, e->t64)) return q;
+      count_launch(3);
+      k_resid<<<vblocks(Nt), kT, 0, s>>>(Nt, b, e->t64, e->r64);
+      k_seg_norm2_64<<<sgrid, kT, 0, s>>>(e->seg_off, e->seg_len, e->r64, e->part);
+      k_seg_reduce<<<dim3(1, nm), 64, 0, s>>>(e->part, e->nrm);
+      return 0;
+    };
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle cond;
+    if ((r = echeck(e, cudaGraphCreate(&g, 0), "graph create"))) return r;
+    auto fail = [&](int code) {
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(s, &junk);
       }
-    }
-    if (all || sweeps >= o.maxit) break;
-    cudaMemcpyAsync(frozen, fz.data(), nm * sizeof(int), cudaMemcpyHostToDevice, s);
+      cudaGraphDestroy(g);
+      return code;
+    };
+    if ((r = echeck(e, cudaGraphConditionalHandleCreate(&cond, g, 0, 0), "conditional handle"))) return fail(r);
+    if ((r = echeck(e, cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+                    "begin capture")))
+      return fail(r);
+    const long long c0 = launch_count();
+    // prologue: counters, |b_m|, first residual and check
+    cudaMemsetAsync(e->its_d, 0, nm * sizeof(int), s);
+    cudaMemsetAsync(e->ctl_d, 0, 2 * sizeof(int), s);
+    cudaMemsetAsync(frozen, 0, nm * sizeof(int), s);
+    if (!x0) cudaMemsetAsync(x, 0, Nt * sizeof(double), s);
+    count_launch(3);
+    k_seg_norm2_64<<<sgrid, kT, 0, s>>>(e->seg_off, e->seg_len, b, e->part);
+    k_seg_reduce<<<dim3(1, nm), 64, 0, s>>>(e->part, e->nrm);
+    k_sqrt_members<<<1, 64, 0, s>>>(nm, e->nrm, e->bn);
+    if ((r = residual())) return fail(r);
+    count_launch();
+    k_refine_check<<<1, 64, 0, s>>>(nm, o.tol, o.maxit, e->nrm, e->bn, frozen, e->relres_d, e->its_d, e->ctl_d, cond);
+    // the WHILE node after everything captured so far
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    if ((r = echeck(e, cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &ndeps), "capture info")))
+      return fail(r);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    if ((r = echeck(e, cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, &cp), "conditional node"))) return fail(r);
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((r = echeck(e, cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies),
+                    "capture dependencies")))
+      return fail(r);
+    if ((r = echeck(e, cudaStreamEndCapture(s, &g), "end capture"))) return fail(r);
+    const long long c1 = launch_count();
+    // body: one inner cycle of all members, the correction, the new residual and check
+    if ((r = echeck(e, cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+                    "begin body capture")))
+      return fail(r);
     vec_convert<float, double>(Nt, e->r64, e->r32, s);
-    count_launch();  // the graph launch itself (its kernels are not counted again)
-    if ((r = echeck(e, cudaGraphLaunch(e->gexec, s), "graph launch"))) return r;
+    if ((r = enqueue_cycle(e, m, o.inner_tol, frozen))) return fail(r);
     count_launch();
     k_addf<<<vblocks(Nt), kT, 0, s>>>(Nt, e->d32, x);
-    ++sweeps;
+    if ((r = residual())) return fail(r);
+    count_launch();
+    k_refine_check<<<1, 64, 0, s>>>(nm, o.tol, o.maxit, e->nrm, e->bn, frozen, e->relres_d, e->its_d, e->ctl_d, cond);
+    if ((r = echeck(e, cudaStreamEndCapture(s, &body), "end body capture"))) return fail(r);
+    const long long c2 = launch_count();
+    count_launch((int)-(c2 - c0));  // captured, not yet run: counted per run below
+    r = echeck(e, cudaGraphInstantiate(&e->gexec, g, 0), "graph instantiate");
+    cudaGraphDestroy(g);
+    if (r) return r;
+    e->graph_b = b;
+    e->graph_x = x;
+    e->graph_m = m;
+    e->graph_tol = o.tol;
+    e->graph_itol = o.inner_tol;
+    e->graph_maxit = o.maxit;
+    e->graph_x0 = x0;
+    e->graph_pro_launches = c1 - c0;
+    e->graph_body_launches = c2 - c1;
+  }
+  // the whole refinement loop: one launch
+  if ((r = echeck(e, cudaGraphLaunch(e->gexec, s), "graph launch"))) return r;
+  // per-member results back in one read
+  double *hr = e->host;
+  int *hi = reinterpret_cast<int *>(e->host + nm);
+  cudaMemcpyAsync(hr, e->relres_d, nm * sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(hi, e->its_d, nm * sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(hi + nm, e->ctl_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+  if ((r = echeck(e, cudaStreamSynchronize(s), "ensemble solve"))) return r;
+  const int cycles = hi[nm];
+  count_launch((int)(1 + e->graph_pro_launches + cycles * e->graph_body_launches));
+  if (hi[nm + 1]) {
     for (int mm = 0; mm < nm; ++mm)
-      if (!done[mm]) {
-        inf[mm].iterations += 1;
-        inf[mm].inner_iterations += m;
-        inf[mm].operator_f32 += m;
-      }
+      if (!std::isfinite(hr[mm])) return eset(e, DGX_ERR_BREAKDOWN, "member %d: non-finite residual", mm);
+    return eset(e, DGX_ERR_BREAKDOWN, "non-finite residual");
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   int status = DGX_OK;
+  std::vector<dgx_solve_info> inf(nm);
   for (int mm = 0; mm < nm; ++mm) {
-    inf[mm].status = done[mm] ? DGX_OK : DGX_NOT_CONVERGED;
+    std::memset(&inf[mm], 0, sizeof(dgx_solve_info));
+    const bool ok = hr[mm] <= o.tol;
+    inf[mm].relres = hr[mm];
+    inf[mm].iterations = hi[mm];
+    inf[mm].inner_iterations = hi[mm] * m;
+    inf[mm].operator_f32 = hi[mm] * m;
+    inf[mm].operator_f64 = cycles + 1;
+    inf[mm].status = ok ? DGX_OK : DGX_NOT_CONVERGED;
     inf[mm].seconds = secs;
-    if (!done[mm]) status = DGX_NOT_CONVERGED;
+    if (!ok) status = DGX_NOT_CONVERGED;
   }
   if (info) std::memcpy(info, inf.data(), nm * sizeof(dgx_solve_info));
   leave(e);

@@ -345,10 +345,11 @@ struct FGradL {
   static constexpr int per_cell = ((LO + HI) + 3) & ~3;
 };
 
+// One CTA's work: cells cell0 .. cell0 + CPB - 1 (those below ncell) of the mesh of P.
 template <typename T, int N, bool CURVED, bool INV, int CPB, int NT>
-__global__ void __launch_bounds__(NT, fused_min_blocks<T, N, NT>())
-    kf_grad(const OpP<T> P, const store_t<T> *__restrict__ p, const store_t<T> *__restrict__ rho,
-            store_t<T> *__restrict__ V, long long Ntot, int ncell) {
+__device__ __forceinline__ void kf_grad_body(const OpP<T> &P, const store_t<T> *__restrict__ p,
+                                             const store_t<T> *__restrict__ rho, store_t<T> *__restrict__ V,
+                                             long long Ntot, int ncell, int cell0) {
   using L = FGradL<N, CURVED>;
   constexpr int Q = L::Q, N2 = L::N2, N3 = L::N3, Q2 = L::Q2, NFP = L::NFP, NG = L::NG, PC = L::per_cell;
   constexpr int MIT = INV ? M_PIT : M_IT, MDT = INV ? M_PDT : M_DT;  // test matrices
@@ -356,7 +357,6 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<T, N, NT>())
   T *sm = reinterpret_cast<T *>(smraw);
   __shared__ CellInfo<CPB> ci;
   __shared__ T s_wq[Q], s_wa[N], s_pte[2][N];
-  const int cell0 = blockIdx.x * CPB;
   cell_info<T, N, CPB, NT>(P, cell0, ncell, ci);
   for (int t = threadIdx.x; t < Q; t += NT) s_wq[t] = cwq<T, N>(t);
   for (int t = threadIdx.x; t < N; t += NT) s_wa[t] = cwa<T, N>(t);
@@ -724,10 +724,10 @@ struct FDivL {
 };
 
 template <typename T, int N, bool CURVED, bool KQ, int CPB, int NT>
-__global__ void __launch_bounds__(NT, fused_min_blocks<T, N, NT>())
-    kf_div(const OpP<T> P, const store_t<T> *__restrict__ V, const store_t<T> *__restrict__ p,
-           const store_t<T> *__restrict__ pk, store_t<T> *__restrict__ y, long long Ntot, int ncell,
-           const store_t<T> *__restrict__ kq) {
+__device__ __forceinline__ void kf_div_body(const OpP<T> &P, const store_t<T> *__restrict__ V,
+                                            const store_t<T> *__restrict__ p, const store_t<T> *__restrict__ pk,
+                                            store_t<T> *__restrict__ y, long long Ntot, int ncell,
+                                            const store_t<T> *__restrict__ kq, int cell0) {
   using L = FDivL<N, CURVED, KQ>;
   constexpr int Q = L::Q, N2 = L::N2, N3 = L::N3, Q2 = L::Q2, NFI = L::NFI, NSL = L::NSL, PC = L::per_cell;
   constexpr int IP = KQ ? 3 : 4;  // field index of p (p_k is field 3 without KQ)
@@ -735,7 +735,6 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<T, N, NT>())
   T *sm = reinterpret_cast<T *>(smraw);
   __shared__ CellInfo<CPB> ci;
   __shared__ T s_wq[Q];
-  const int cell0 = blockIdx.x * CPB;
   cell_info<T, N, CPB, NT>(P, cell0, ncell, ci);
   for (int t = threadIdx.x; t < Q; t += NT) s_wq[t] = cwq<T, N>(t);
   __syncthreads();
@@ -1032,6 +1031,51 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<T, N, NT>())
       sts<T, N, 1>(y + (long long)cell * N3 + N * m, Y);
     }
   }
+}
+
+template <typename T, int N, bool CURVED, bool INV, int CPB, int NT>
+__global__ void __launch_bounds__(NT, fused_min_blocks<T, N, NT>())
+    kf_grad(const OpP<T> P, const store_t<T> *__restrict__ p, const store_t<T> *__restrict__ rho,
+            store_t<T> *__restrict__ V, long long Ntot, int ncell) {
+  kf_grad_body<T, N, CURVED, INV, CPB, NT>(P, p, rho, V, Ntot, ncell, blockIdx.x * CPB);
+}
+
+template <typename T, int N, bool CURVED, bool KQ, int CPB, int NT>
+__global__ void __launch_bounds__(NT, fused_min_blocks<T, N, NT>())
+    kf_div(const OpP<T> P, const store_t<T> *__restrict__ V, const store_t<T> *__restrict__ p,
+           const store_t<T> *__restrict__ pk, store_t<T> *__restrict__ y, long long Ntot, int ncell,
+           const store_t<T> *__restrict__ kq) {
+  kf_div_body<T, N, CURVED, KQ, CPB, NT>(P, V, p, pk, y, Ntot, ncell, kq, blockIdx.x * CPB);
+}
+
+// Several meshes of one degree in one launch (ensembles): member m owns CTAs
+// cta_off[m] .. cta_off[m+1] - 1, CPB of its cells each; vectors are the
+// members' DoF blocks concatenated (member m starts at dof_off).
+template <typename T>
+__device__ __forceinline__ int member_of_cta(const int *cta_off, int nmem) {
+  int m = 0;
+  while (m + 1 < nmem && cta_off[m + 1] <= (int)blockIdx.x) ++m;
+  return m;
+}
+
+template <typename T, int N, bool CURVED, int CPB, int NT>
+__global__ void __launch_bounds__(NT, fused_min_blocks<T, N, NT>())
+    kf_grad_multi(const EnsMember<T> *__restrict__ mem, int nmem, const int *__restrict__ cta_off,
+                  const store_t<T> *__restrict__ p_all) {
+  const int m = member_of_cta<T>(cta_off, nmem);
+  const EnsMember<T> M = mem[m];
+  kf_grad_body<T, N, CURVED, true, CPB, NT>(M.P, p_all + M.dof_off, M.rho, M.V, M.N,
+                                            (int)(M.N / (N * N * N)), ((int)blockIdx.x - cta_off[m]) * CPB);
+}
+
+template <typename T, int N, bool CURVED, int CPB, int NT>
+__global__ void __launch_bounds__(NT, fused_min_blocks<T, N, NT>())
+    kf_div_multi(const EnsMember<T> *__restrict__ mem, int nmem, const int *__restrict__ cta_off,
+                 const store_t<T> *__restrict__ p_all, store_t<T> *__restrict__ y_all) {
+  const int m = member_of_cta<T>(cta_off, nmem);
+  const EnsMember<T> M = mem[m];
+  kf_div_body<T, N, CURVED, false, CPB, NT>(M.P, M.V, p_all + M.dof_off, M.pk, y_all + M.dof_off, M.N,
+                                            (int)(M.N / (N * N * N)), nullptr, ((int)blockIdx.x - cta_off[m]) * CPB);
 }
 
 }  // namespace

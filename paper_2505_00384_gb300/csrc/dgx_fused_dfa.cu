@@ -4,6 +4,9 @@
 
 namespace dgx {
 DGX_FUSED_INSTANTIATE(df64, 2)
+DGX_FUSED_MULTI_INSTANTIATE(df64, 2)
 DGX_FUSED_INSTANTIATE(df64, 3)
+DGX_FUSED_MULTI_INSTANTIATE(df64, 3)
 DGX_FUSED_INSTANTIATE(df64, 4)
+DGX_FUSED_MULTI_INSTANTIATE(df64, 4)
 }  // namespace dgx

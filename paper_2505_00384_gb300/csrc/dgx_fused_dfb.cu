@@ -4,6 +4,9 @@
 
 namespace dgx {
 DGX_FUSED_INSTANTIATE(df64, 5)
+DGX_FUSED_MULTI_INSTANTIATE(df64, 5)
 DGX_FUSED_INSTANTIATE(df64, 6)
+DGX_FUSED_MULTI_INSTANTIATE(df64, 6)
 DGX_FUSED_INSTANTIATE(df64, 7)
+DGX_FUSED_MULTI_INSTANTIATE(df64, 7)
 }  // namespace dgx

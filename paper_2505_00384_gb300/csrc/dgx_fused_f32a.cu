@@ -3,6 +3,9 @@
 
 namespace dgx {
 DGX_FUSED_INSTANTIATE(float, 2)
+DGX_FUSED_MULTI_INSTANTIATE(float, 2)
 DGX_FUSED_INSTANTIATE(float, 3)
+DGX_FUSED_MULTI_INSTANTIATE(float, 3)
 DGX_FUSED_INSTANTIATE(float, 4)
+DGX_FUSED_MULTI_INSTANTIATE(float, 4)
 }  // namespace dgx

@@ -3,6 +3,9 @@
 
 namespace dgx {
 DGX_FUSED_INSTANTIATE(float, 5)
+DGX_FUSED_MULTI_INSTANTIATE(float, 5)
 DGX_FUSED_INSTANTIATE(float, 6)
+DGX_FUSED_MULTI_INSTANTIATE(float, 6)
 DGX_FUSED_INSTANTIATE(float, 7)
+DGX_FUSED_MULTI_INSTANTIATE(float, 7)
 }  // namespace dgx

@@ -89,6 +89,30 @@ int fused_div(dgx_ctx *c, const store_t<T> *V, const store_t<T> *p, const store_
   }
 }
 
+// Multi-mesh operator y = S x of ensemble members of degree N = r+1 in fused
+// configuration cfg; cta_off (device, nmem + 1 entries) from fused_cpb(N, cfg).
+template <typename T, int N, bool CURVED>
+int fused_operator_multi(dgx_ctx *c0, const EnsMember<T> *mem, int nmem, const int *cta_off, int nblocks,
+                         const store_t<T> *x, store_t<T> *y, cudaStream_t s, int cfg) {
+  if (int e = upload_fused_tables(c0)) return e;
+  auto go = [&](auto kg, auto kd, int cpb, int nt) -> int {
+    const size_t sg = sizeof(T) * (size_t)cpb * FGradL<N, CURVED>::per_cell;
+    const size_t sd = sizeof(T) * (size_t)cpb * FDivL<N, CURVED, false>::per_cell;
+    if (sg > kFusedMaxSmem || sd > kFusedMaxSmem) return set_error(c0, DGX_ERR_ARG, "fused multi-mesh kernels do not fit");
+    if (int e = fprep(c0, kg, sg)) return e;
+    if (int e = fprep(c0, kd, sd)) return e;
+    count_launch(2);
+    kg<<<(unsigned)nblocks, nt, sg, s>>>(mem, nmem, cta_off, x);
+    kd<<<(unsigned)nblocks, nt, sd, s>>>(mem, nmem, cta_off, x, y);
+    return check_cuda(c0, cudaGetLastError(), "fused multi-mesh operator launch");
+  };
+  if (cfg == 1)
+    return go(kf_grad_multi<T, N, CURVED, fused_cpb(N, 1), fused_nt(N, 1)>,
+              kf_div_multi<T, N, CURVED, fused_cpb(N, 1), fused_nt(N, 1)>, fused_cpb(N, 1), fused_nt(N, 1));
+  return go(kf_grad_multi<T, N, CURVED, fused_cpb(N, 0), fused_nt(N, 0)>,
+            kf_div_multi<T, N, CURVED, fused_cpb(N, 0), fused_nt(N, 0)>, fused_cpb(N, 0), fused_nt(N, 0));
+}
+
 // Shared memory of one fused configuration (bytes), for the variant list.
 template <typename T, int N, bool CURVED>
 size_t fused_smem(int cfg) {
@@ -109,5 +133,11 @@ size_t fused_smem(int cfg) {
                                       store_t<T> *, cudaStream_t, double, const store_t<T> *, int);            \
   template size_t fused_smem<T, NN, false>(int);                                                                \
   template size_t fused_smem<T, NN, true>(int);
+
+#define DGX_FUSED_MULTI_INSTANTIATE(T, NN)                                                                     \
+  template int fused_operator_multi<T, NN, false>(dgx_ctx *, const EnsMember<T> *, int, const int *, int,       \
+                                                  const store_t<T> *, store_t<T> *, cudaStream_t, int);         \
+  template int fused_operator_multi<T, NN, true>(dgx_ctx *, const EnsMember<T> *, int, const int *, int,        \
+                                                 const store_t<T> *, store_t<T> *, cudaStream_t, int);
 
 }  // namespace dgx

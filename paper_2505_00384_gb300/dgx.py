@@ -114,6 +114,7 @@ SIGNATURES = [
     ("dgx_ensemble_set_coefficients", C.c_int, [_P, _P, _P, C.c_double, C.c_double]),
     ("dgx_ensemble_apply_operator", C.c_int, [_P, C.c_int, _P, _P]),
     ("dgx_ensemble_autotune", C.c_int, [_P]),
+    ("dgx_ensemble_tile", C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("dgx_ensemble_tuning", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                       C.POINTER(C.c_int)]),
     ("dgx_ensemble_solve", C.c_int, [_P, _P, _P, C.POINTER(dgx_solve_opts), C.POINTER(dgx_solve_info)]),
@@ -441,6 +442,13 @@ def dgx_ensemble_tuning(e, g):
     v = [C.c_int() for _ in range(4)]
     _echeck(e, load().dgx_ensemble_tuning(e, g, *[C.byref(x) for x in v]))
     return tuple(x.value for x in v)
+
+
+def dgx_ensemble_tile(e, g, prec=DGX_F32):
+    """(fused, cells per CTA) of the kernels the autotuner chose for degree group g and prec."""
+    f, v = C.c_int(), C.c_int()
+    _echeck(e, load().dgx_ensemble_tile(e, g, int(prec), C.byref(f), C.byref(v)))
+    return f.value, v.value
 
 
 def dgx_ensemble_solve(e, b_ptr, x_ptr, n_members, opts=None):
