@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--variant-f64", type=int, default=None, help="vmult workload: pin this FP64 launch variant")
     ap.add_argument("--variant-f32", type=int, default=None, help="vmult workload: pin this FP32 launch variant")
     ap.add_argument("--workload", default="hill",
-                    choices=["hill", "ensemble", "learned", "mixed", "paper", "consistent", "vmult"],
+                    choices=["hill", "ensemble", "learned", "mixed", "paper", "consistent", "vmult", "mg"],
                     help="hill: one IMEX step of the 64x64x32 hill (default); ensemble: 16-member batched solve; "
                          "learned: pressure solves of held-out hill systems with the trained network; "
                          "mixed: mixed-precision solves on the 4x4x4 box at degrees 2, 3, 5 against the oracle; "
@@ -666,6 +666,107 @@ def run_vmult(args):
     return 0
 
 
+def run_mg(args):
+    """Geometric multigrid (Sec. 3.1): (1) the SPD case -- a 64 x 64 x 32-cell box
+    of 64 x 64 x 20 km at degree 3 (8 388 608 DoFs), slip walls, uniform
+    coefficients (rho = 1.2, p_k = 1e5: S symmetric positive definite), seeded
+    N(0, 1) right-hand side -- solved to 1e-8 from zero by CG with the Helmholtz
+    Jacobi and by CG with one V-cycle per iteration (4 levels, Chebyshev degree
+    3, coarsest CG to 1e-10); (2) the experiment on the non-symmetric Schur
+    system of the hill workload (64 x 64 x 32 cells, r = 4, far-field faces,
+    background coefficients with 5 % seeded noise): FGMRES(30) with the
+    Helmholtz Jacobi against FGMRES with the V-cycle (3 levels, coarsest FGMRES).
+    --warmup untimed and --steps timed solves each (CUDA events)."""
+    import torch
+    from paper_2505_00384_gb300 import dgx, inputs
+    torch.cuda.set_device(0)
+    dgx.load()
+    stream = torch.cuda.current_stream()
+    f64 = torch.float64
+    out = {}
+
+    def timed(ctx, b, o):
+        x = torch.zeros_like(b)
+        for _ in range(args.warmup):
+            dgx.dgx_solve_pressure(ctx, b.data_ptr(), x.data_ptr(), o)
+        ts, info = [], None
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, info = dgx.dgx_solve_pressure(ctx, b.data_ptr(), x.data_ptr(), o)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if st != dgx.DGX_OK:
+                raise RuntimeError("solve did not converge (relres %g)" % info.relres)
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return {"s_per_solve": statistics.median(ts), "iterations": info.iterations, "relres": info.relres,
+                "operator_f64": info.operator_f64}
+
+    # (1) SPD box
+    ctx = dgx.dgx_create(0, stream.cuda_stream)
+    dgx.dgx_mesh_build(ctx, dgx.mesh_desc(64, 64, 32, 3, 64000.0, 64000.0, 20000.0))
+    N = dgx.dgx_num_dofs(ctx)
+    rho = torch.full((N,), 1.2, dtype=f64, device="cuda")
+    pk = torch.full((N,), 1e5, dtype=f64, device="cuda")
+    dgx.dgx_set_coefficients(ctx, rho.data_ptr(), pk.data_ptr(), A_LL, 1.4)
+    mo = dgx.dgx_default_mg_opts()
+    mo.levels, mo.coarse_tol = 4, 1e-10
+    t0 = time.perf_counter()
+    dgx.dgx_mg_setup(ctx, mo)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    b = torch.from_numpy(inputs.normal(inputs.DEFAULT_SEED + 11, N)).cuda()
+    o = dgx.dgx_default_solve_opts()
+    o.method, o.tol, o.maxit = dgx.DGX_SOLVER_CG, 1e-8, 5000
+    o.pc = dgx.DGX_PC_HELMHOLTZ
+    jac = timed(ctx, b, o)
+    o.pc = dgx.DGX_PC_MULTIGRID
+    mgr = timed(ctx, b, o)
+    out["spd_box"] = {"mesh": "64x64x32 cells, r=3, %d DoFs, slip walls, uniform coefficients" % N,
+                      "cg_jacobi": jac, "cg_multigrid": mgr, "multigrid_setup_s": t_setup,
+                      "levels": dgx.dgx_mg_levels(ctx)[0], "speedup": jac["s_per_solve"] / mgr["s_per_solve"]}
+    dgx.dgx_destroy(ctx)
+    del rho, pk, b
+    # (2) the hill Schur system
+    ctx = dgx.dgx_create(0, stream.cuda_stream)
+    work = dict(FULL)
+    work.update(COMMON)
+    dgx.dgx_mesh_build(ctx, dgx.mesh_desc(64, 64, 32, 4, work["Lx"], work["Ly"], work["Lz"], terrain=1, h_c=400.0,
+                                          a_c=1000.0, bc_lateral=1))
+    N = dgx.dgx_num_dofs(ctx)
+    dgx.dgx_set_background(ctx, dgx.background(kind=0, T=250.0))
+    rho = torch.zeros(N, dtype=f64, device="cuda")
+    pk = torch.zeros_like(rho)
+    dgx.dgx_background_fields(ctx, rho.data_ptr(), pk.data_ptr())
+    noise = torch.from_numpy(inputs.normal(inputs.DEFAULT_SEED + 12, N)).cuda()
+    rho *= 1.0 + 0.05 * noise
+    pk *= 1.0 - 0.05 * noise
+    del noise
+    dgx.dgx_set_coefficients(ctx, rho.data_ptr(), pk.data_ptr(), A_LL, 1.4)
+    mo = dgx.dgx_default_mg_opts()
+    mo.levels, mo.coarse_solver, mo.coarse_tol = 3, 1, 1e-6
+    dgx.dgx_mg_setup(ctx, mo)
+    b = torch.from_numpy(inputs.normal(inputs.DEFAULT_SEED + 13, N)).cuda()
+    o = dgx.dgx_default_solve_opts()
+    o.method, o.tol, o.maxit, o.restart = dgx.DGX_SOLVER_FGMRES, 1e-8, 2000, 30
+    o.pc = dgx.DGX_PC_HELMHOLTZ
+    jac = timed(ctx, b, o)
+    o.pc = dgx.DGX_PC_MULTIGRID
+    mgr = timed(ctx, b, o)
+    out["schur_hill_experiment"] = {"mesh": "64x64x32 cells, r=4, %d DoFs, hill, far-field faces" % N,
+                                    "fgmres_helmholtz_jacobi": jac, "fgmres_multigrid": mgr,
+                                    "speedup": jac["s_per_solve"] / mgr["s_per_solve"]}
+    dgx.dgx_destroy(ctx)
+    line = {"metric": "pressure solve s/solve @1e-8 rel residual, CG + geometric multigrid (SPD case)",
+            "value": out["spd_box"]["cg_multigrid"]["s_per_solve"], "unit": "s/solve", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "mg_spd_box_64x64x32_r3_and_hill_schur_64x64x32_r4"}, **out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_learned(args):
     """Learned preconditioner: 400 pressure systems recorded along IMEX
     trajectories over 16 seeded hills (h_c ~ U[200, 800] m, 25 steps each, the
@@ -989,6 +1090,8 @@ def main():
         return run_paper(args)
     if args.workload == "vmult":
         return run_vmult(args)
+    if args.workload == "mg":
+        return run_mg(args)
     if args.workload == "consistent":
         return run_consistent(args)
 

@@ -56,6 +56,9 @@ extern "C" {
                                     residual, or a non-finite direction, switches the
                                     rest of the solve to DGX_PC_HELMHOLTZ and the call
                                     returns DGX_FALLBACK_USED                           */
+#define DGX_PC_MULTIGRID 4       /* one geometric-multigrid V-cycle (dgx_mg_setup first);
+                                    DGX_SOLVER_CG (SPD systems, Sec. 3.1) or
+                                    DGX_SOLVER_FGMRES                                     */
 
 /* Krylov methods (Sec. 3.1: GMRES for the non-symmetric Schur system, CG
  * for the symmetric positive definite case). */
@@ -414,6 +417,46 @@ long long dgx_kernel_launches(void);
  * size = 7QN + 3N^2 + 2Q + N; DGX_ERR_ARG for an unsupported degree.  Host
  * only: needs no context and no GPU. */
 int dgx_basis_tables(int degree, double *out, int capacity);
+
+/* ------------------------------------------------------ geometric multigrid
+ * Sec. 3.1 solves the SPD systems with CG preconditioned by geometric
+ * multigrid (and notes that no theory covers multigrid for the non-symmetric
+ * Schur system, where it is an experiment here).  Hierarchy: level 0 is the
+ * context's mesh and coefficients, level l halves nx, ny, nz l times (same
+ * domain, degree, terrain, boundaries), so a coarse cell is 2 x 2 x 2 fine
+ * cells.  Transfers: prolongation = the coarse cell's polynomial at the fine
+ * GLL nodes of its children; restriction = its transpose; coarse rho, p_k = the
+ * fine fields at the coarse nodes (the child holding the node, the lower one
+ * at an interface).  Each level applies its own S (rediscretisation) and
+ * Helmholtz Jacobi diagonal D.  Smoother: `degree` steps of Chebyshev
+ * iteration on D^-1 S (Saad, Alg. 12.1) over [lambda_max / smooth_range,
+ * 1.1 lambda_max], lambda_max by `power_its` power steps on D^-1 S from the
+ * fixed vector v_i = frac(0.6180339887498949 (i + 1)) - 1/2.  Coarsest level:
+ * CG (coarse_solver 0, SPD) or FGMRES (1) with the Helmholtz Jacobi to
+ * coarse_tol within coarse_maxit iterations.  V-cycle from zero: pre-smooth,
+ * restrict the residual, one cycle on the next level, prolong and correct,
+ * post-smooth. */
+typedef struct {
+  int levels;        /* 2..12; nx, ny, nz divisible by 2^(levels-1)                 */
+  int degree;        /* Chebyshev steps per smoothing (>= 1)                         */
+  int power_its;     /* power iterations for lambda_max per level (>= 1)            */
+  int coarse_maxit;  /* iteration bound of the coarsest solve (>= 1)                */
+  int coarse_solver; /* 0: CG (SPD systems), 1: FGMRES                             */
+  int reserved;
+  double smooth_range; /* lambda_max / lambda_min of the smoother (> 1)             */
+  double coarse_tol;   /* relative residual of the coarsest solve (> 0)             */
+} dgx_mg_opts;
+void dgx_default_mg_opts(dgx_mg_opts *opts); /* 3 levels, degree 3, 15 power its, 500, CG, 15, 1e-10 */
+/* Build the hierarchy for the context's current mesh and coefficients
+ * (allocates the coarse levels; later dgx_set_coefficients calls are picked
+ * up by the next V-cycle, which restricts the new coefficients and re-estimates
+ * the bounds).  dgx_mesh_build and dgx_destroy release it.  Errors: DGX_ERR_ARG
+ * (options, divisibility), DGX_ERR_STATE (no mesh / coefficients). */
+int dgx_mg_setup(dgx_ctx *ctx, const dgx_mg_opts *opts);
+/* z = one V-cycle applied to r (device FP64, N each, distinct). */
+int dgx_mg_vcycle(dgx_ctx *ctx, const double *r, double *z);
+/* Number of levels and the lambda_max estimate of each (host, capacity entries). */
+int dgx_mg_levels(dgx_ctx *ctx, int *levels, double *lambda_max, int capacity);
 
 /* ---------------------------------------------------------------- ensembles
  * Several independent meshes (sizes, degrees, terrain) whose pressure

@@ -25,14 +25,14 @@ terrain-following meshes of the operator:
   Linear Systems, 2nd ed., Algorithm 12.1) over [lambda_max / range, 1.1
   lambda_max], lambda_max from power iteration on D^-1 S from a fixed start
   vector v_i = frac(0.6180339887498949 (i + 1)) - 1/2;
-* coarsest level: conjugate gradients preconditioned by D^-1 to a relative
-  residual (at most coarse_its iterations);
+* coarsest level: conjugate gradients preconditioned by D^-1 (SPD systems) or
+  FGMRES(30) with D^-1, to a relative residual (at most coarse_its iterations);
 * V-cycle with zero initial guess: pre-smooth, restrict the residual, cycle on
   the next level, prolong and correct, post-smooth.
 """
 import numpy as np
 
-from . import apply_S, gll, lagrange, make_mesh, ndofs, precond_diag, PC_HELMHOLTZ
+from . import apply_S, gll, lagrange, make_mesh, ndofs, precond_diag, solve, PC_HELMHOLTZ
 
 GOLDEN = 0.6180339887498949
 
@@ -181,9 +181,9 @@ class Hierarchy:
     diagonals and eigenvalue bounds."""
 
     def __init__(self, m, alpha, gamma, rho, pk, levels, degree=3, smooth_range=15.0, power_its=15,
-                 coarse_tol=1e-10, coarse_its=500):
+                 coarse_tol=1e-10, coarse_its=500, coarse="cg"):
         self.alpha, self.gamma, self.degree = alpha, gamma, degree
-        self.coarse_tol, self.coarse_its = coarse_tol, coarse_its
+        self.coarse_tol, self.coarse_its, self.coarse = coarse_tol, coarse_its, coarse
         self.meshes, self.rho, self.pk, self.dinv, self.lmax = [m], [rho], [pk], [], []
         for _ in range(levels - 1):
             mc = coarse_mesh(self.meshes[-1])
@@ -204,6 +204,10 @@ class Hierarchy:
         """z = M^-1 b: one V-cycle from zero."""
         S = self.op(l)
         if l == len(self.meshes) - 1:
+            if self.coarse == "fgmres":  # the library's FGMRES(30) with the Helmholtz Jacobi
+                x, _, _, _ = solve(self.meshes[l], self.alpha, self.gamma, self.rho[l], self.pk[l], b,
+                                   method="fgmres", tol=self.coarse_tol, maxit=self.coarse_its)
+                return x
             return pcg(S, self.dinv[l], b, self.coarse_tol, self.coarse_its)
         lmax = 1.1 * self.lmax[l]
         lmin = self.lmax[l] / self.smooth_range

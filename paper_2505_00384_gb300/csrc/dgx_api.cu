@@ -218,6 +218,28 @@ bool make_tables(int r, Tables1D &T) {
 
 }  // namespace
 
+bool child_tables(int r, std::vector<double> &E, std::vector<int> &side, std::vector<double> &F) {
+  const int N = r + 1;
+  if (r < 1 || r > kMaxDegree) return false;
+  std::vector<double> x, w, l(N);
+  gll_rule(N, x, w);
+  Lagrange L(x);
+  E.assign((size_t)2 * N * N, 0.0);
+  for (int s = 0; s < 2; ++s)
+    for (int af = 0; af < N; ++af) {
+      L.eval(0.5 * (x[af] + s), l.data(), nullptr);
+      for (int ac = 0; ac < N; ++ac) E[((size_t)s * N + af) * N + ac] = l[ac];
+    }
+  side.assign(N, 0);
+  F.assign((size_t)N * N, 0.0);
+  for (int a = 0; a < N; ++a) {
+    side[a] = x[a] > 0.5 ? 1 : 0;
+    L.eval(2.0 * x[a] - side[a], l.data(), nullptr);
+    for (int i = 0; i < N; ++i) F[(size_t)a * N + i] = l[i];
+  }
+  return true;
+}
+
 bool build_table_block(int r, std::vector<double> &tab) {
   Tables1D T;
   if (!make_tables(r, T)) return false;
@@ -337,6 +359,7 @@ void free_mesh(dgx_ctx *c) {
   c->rec_store = nullptr;
   c->rec_cap = c->rec_count = c->rec_seen = 0;
   learned_mesh_changed(c);
+  mg_free(c);  // the hierarchy belongs to the old mesh
 }
 
 template <typename T>
@@ -602,7 +625,8 @@ int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dg
   double *VZ = SZ + (size_t)m * N;  // A^-1 B z_j of the cycle (3N each), with Vx
   const size_t b3 = (size_t)3 * N * sizeof(double);
   // the learned preconditioner falls back to the Helmholtz Jacobi diagonal
-  const int pcd = o.pc == DGX_PC_LEARNED ? DGX_PC_HELMHOLTZ : o.pc;
+  const bool use_mg = o.pc == DGX_PC_MULTIGRID;
+  const int pcd = (o.pc == DGX_PC_LEARNED || use_mg) ? DGX_PC_HELMHOLTZ : o.pc;
   const double *dinv = o.pc == DGX_PC_NONE ? nullptr : c->dinv64[pcd];
   const float *dinv32 = o.pc == DGX_PC_NONE ? nullptr : c->dinv32[pcd];
   bool use_learned = o.pc == DGX_PC_LEARNED;
@@ -670,6 +694,8 @@ int fgmres64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dg
       int e2 = 0;
       if (use_learned) {
         if ((err = learned_apply<double>(c, vj, zj))) return err;
+      } else if (use_mg) {
+        if ((err = mg_vcycle(c, vj, zj))) return err;
       } else if (mixed) {
         // z_j ~= S^-1 v_j by FP32 GMRES on the FP32 operator and diagonal
         vec_convert<float, double>(N, vj, io32, c->stream);
@@ -749,8 +775,9 @@ int cg64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dgx_so
   const long long N = c->N;
   if (int e = grow<double>(c, (size_t)4 * N)) return e;
   double *r = c->kry64, *z = r + N, *p = z + N, *q = p + N;
-  const double *dinv = o.pc == DGX_PC_NONE ? nullptr : c->dinv64[o.pc];
-  if (o.pc != DGX_PC_NONE)
+  const bool use_mg = o.pc == DGX_PC_MULTIGRID;
+  const double *dinv = (o.pc == DGX_PC_NONE || use_mg) ? nullptr : c->dinv64[o.pc];
+  if (o.pc != DGX_PC_NONE && !use_mg)
     if (int e = ensure_diag(c, true)) return e;
   int err = 0;
   double bn = dev_norm(c, N, b, &err);
@@ -761,11 +788,13 @@ int cg64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dgx_so
   ++info.operator_f64;
   cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   vec_axpby<double>(N, -1.0, q, 1.0, r, c->stream);
-  auto precond = [&](const double *in, double *out) {
+  auto precond = [&](const double *in, double *out) -> int {
+    if (use_mg) return mg_vcycle(c, in, out);
     if (dinv) vec_mul<double>(N, dinv, in, out, c->stream);
     else cudaMemcpyAsync(out, in, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    return 0;
   };
-  precond(r, z);
+  if ((err = precond(r, z))) return err;
   cudaMemcpyAsync(p, z, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   vec_dot<double>(N, r, z, c->red, c->red_out, c->stream);
   vec_dot<double>(N, r, r, c->red, c->red_out + 1, c->stream);
@@ -785,7 +814,7 @@ int cg64(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts &o, dgx_so
     vec_axpby<double>(N, a, p, 1.0, x, c->stream);
     vec_axpby<double>(N, -a, q, 1.0, r, c->stream);
     ++its;
-    precond(r, z);
+    if ((err = precond(r, z))) return err;
     vec_dot<double>(N, r, z, c->red, c->red_out, c->stream);
     vec_dot<double>(N, r, r, c->red, c->red_out + 1, c->stream);
     if ((err = fetch(c, 2))) return err;
@@ -854,7 +883,9 @@ int solve_pressure_vx(dgx_ctx *c, const double *b, double *x, const dgx_solve_op
   dgx_solve_opts o;
   if (opts) o = *opts;
   else dgx_default_solve_opts(&o);
-  if (o.pc < 0 || o.pc > 3) return set_error(c, DGX_ERR_ARG, "preconditioner %d", o.pc);
+  if (o.pc < 0 || o.pc > 4) return set_error(c, DGX_ERR_ARG, "preconditioner %d", o.pc);
+  if (o.pc == DGX_PC_MULTIGRID && (o.method == DGX_SOLVER_MIXED || !mg_ready(c)))
+    return set_error(c, DGX_ERR_ARG, "the multigrid preconditioner needs DGX_SOLVER_CG or _FGMRES and dgx_mg_setup");
   if (o.pc == DGX_PC_LEARNED && (o.method != DGX_SOLVER_FGMRES || !learned_ready(c)))
     return set_error(c, DGX_ERR_ARG, "the learned preconditioner needs DGX_SOLVER_FGMRES and dgx_learned_create");
   if (o.restart < 1 || o.restart > 64 || o.maxit < 0 || !(o.tol > 0))
@@ -909,6 +940,7 @@ void dgx_destroy(dgx_ctx *c) {
   cudaStreamSynchronize(c->stream);
   free_mesh(c);
   learned_free(c);
+  mg_free(c);
   if (c->red) cudaFree(c->red);
   if (c->red_out) cudaFree(c->red_out);
   if (c->host_red) cudaFreeHost(c->host_red);

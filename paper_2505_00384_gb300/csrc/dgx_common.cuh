@@ -129,7 +129,8 @@ struct Buf {
   size_t bytes = 0;
 };
 
-struct Learned;  // learned preconditioner state (dgx_learned.cu)
+struct Learned;    // learned preconditioner state (dgx_learned.cu)
+struct Multigrid;  // geometric multigrid hierarchy (dgx_mg.cu)
 
 }  // namespace dgx
 
@@ -218,6 +219,7 @@ struct dgx_ctx {
   // incremented by every dgx_set_coefficients (invalidates derived caches)
   long long coef_version = 0;
   dgx::Learned *learned = nullptr;
+  dgx::Multigrid *mg = nullptr;
 
   std::vector<void *> owned;  // everything cudaMalloc'd for the mesh
 };
@@ -232,6 +234,10 @@ int check_cuda(dgx_ctx *c, cudaError_t e, const char *what);
 
 // host 1D table block of degree r (layout above), dgx_api.cu
 bool build_table_block(int r, std::vector<double> &tab);
+// multigrid transfer tables of degree r (dgx_api.cu), GLL nodes x_a on [0, 1]:
+//   E[s][a_f][a_c] = l_{a_c}((x_{a_f} + s) / 2)  (coarse basis at child s's nodes)
+//   side[a] = 1 if x_a > 1/2 else 0, F[a][i] = l_i(2 x_a - side[a])  (fine basis at coarse node a)
+bool child_tables(int r, std::vector<double> &E, std::vector<int> &side, std::vector<double> &F);
 // upload the even-odd matrices of all degrees to constant memory of the
 // context's device (once per device), dgx_operator.cu
 int ensure_const_tables(dgx_ctx *c);
@@ -353,6 +359,11 @@ int vec_partials();  // number of reduction blocks per vector pass
 // dgx_solve_pressure that also returns Vx = A^-1 B x (3N) of the solution (dgx_api.cu)
 int solve_pressure_vx(dgx_ctx *c, const double *b, double *x, const dgx_solve_opts *opts, dgx_solve_info *info,
                       double *Vx);
+
+// geometric multigrid (dgx_mg.cu): z = one V-cycle applied to b (FP64); release
+int mg_vcycle(dgx_ctx *c, const double *b, double *z);
+bool mg_ready(const dgx_ctx *c);
+void mg_free(dgx_ctx *c);
 
 // learned preconditioner (dgx_learned.cu)
 void learned_free(dgx_ctx *c);          // release everything (dgx_destroy)

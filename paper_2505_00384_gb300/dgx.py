@@ -22,7 +22,7 @@ DGX_ERR_DEVICE_TIMEOUT = -5
 DGX_ERR_STATE = -6
 
 DGX_F64, DGX_F32 = 0, 1
-DGX_PC_NONE, DGX_PC_HELMHOLTZ, DGX_PC_INTERNAL_ENERGY, DGX_PC_LEARNED = 0, 1, 2, 3
+DGX_PC_NONE, DGX_PC_HELMHOLTZ, DGX_PC_INTERNAL_ENERGY, DGX_PC_LEARNED, DGX_PC_MULTIGRID = 0, 1, 2, 3, 4
 DGX_SOLVER_FGMRES, DGX_SOLVER_CG, DGX_SOLVER_MIXED = 0, 1, 2
 DGX_MASS_FAST, DGX_MASS_CONSISTENT = 0, 1
 
@@ -44,6 +44,12 @@ class dgx_solve_opts(C.Structure):
     _fields_ = [("method", C.c_int), ("pc", C.c_int), ("restart", C.c_int), ("maxit", C.c_int),
                 ("tol", C.c_double), ("inner_restart", C.c_int), ("inner_maxit", C.c_int),
                 ("inner_tol", C.c_double), ("use_x0", C.c_int), ("reserved", C.c_int)]
+
+
+class dgx_mg_opts(C.Structure):
+    _fields_ = [("levels", C.c_int), ("degree", C.c_int), ("power_its", C.c_int), ("coarse_maxit", C.c_int),
+                ("coarse_solver", C.c_int), ("reserved", C.c_int), ("smooth_range", C.c_double),
+                ("coarse_tol", C.c_double)]
 
 
 class dgx_step_info(C.Structure):
@@ -94,6 +100,10 @@ SIGNATURES = [
     ("dgx_operator_cost", C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("dgx_kernel_launches", C.c_longlong, []),
     ("dgx_operator_threads", C.c_int, [_P, C.c_int]),
+    ("dgx_default_mg_opts", None, [C.POINTER(dgx_mg_opts)]),
+    ("dgx_mg_setup", C.c_int, [_P, C.POINTER(dgx_mg_opts)]),
+    ("dgx_mg_vcycle", C.c_int, [_P, _P, _P]),
+    ("dgx_mg_levels", C.c_int, [_P, C.POINTER(C.c_int), _P, C.c_int]),
     ("dgx_operator_variant", C.c_int, [_P, C.c_int]),
     ("dgx_set_operator_variant", C.c_int, [_P, C.c_int, C.c_int]),
     ("dgx_basis_tables", C.c_int, [C.c_int, _P, C.c_int]),
@@ -233,6 +243,30 @@ def dgx_apply_preconditioner(ctx, pc, prec, x_ptr, y_ptr):
 
 def dgx_preconditioner_diagonal(ctx, pc, d_ptr):
     return _check(ctx, load().dgx_preconditioner_diagonal(ctx, pc, C.c_void_p(d_ptr)))
+
+
+def dgx_default_mg_opts():
+    o = dgx_mg_opts()
+    load().dgx_default_mg_opts(C.byref(o))
+    return o
+
+
+def dgx_mg_setup(ctx, opts=None):
+    """Build the geometric-multigrid hierarchy for the current mesh and coefficients."""
+    return _check(ctx, load().dgx_mg_setup(ctx, C.byref(opts) if opts is not None else None))
+
+
+def dgx_mg_vcycle(ctx, r_ptr, z_ptr):
+    """z = one V-cycle applied to r (device FP64)."""
+    return _check(ctx, load().dgx_mg_vcycle(ctx, C.c_void_p(r_ptr), C.c_void_p(z_ptr)))
+
+
+def dgx_mg_levels(ctx, capacity=12):
+    """(levels, [lambda_max of each level])."""
+    n = C.c_int()
+    lam = (C.c_double * capacity)()
+    _check(ctx, load().dgx_mg_levels(ctx, C.byref(n), lam, capacity))
+    return n.value, [lam[i] for i in range(min(n.value, capacity))]
 
 
 def dgx_default_solve_opts():
