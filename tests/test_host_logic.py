@@ -49,7 +49,7 @@ def test_bench_defaults():
         sys.argv = argv
     assert a.gpus == 1 and a.warmup >= 3 and a.workload == "hill" and a.impl == "ours"
     w = bench.workload(a)
-    assert (w["nx"], w["ny"], w["nz"], w["r"]) == (64, 64, 32, 4) and w["bc_lateral"] == 2
+    assert (w["nx"], w["ny"], w["nz"], w["r"]) == (64, 64, 32, 4) and w["bc_lateral"] == 1  # far field
 
 
 def _bench():
