@@ -28,6 +28,7 @@ class OrcMesh(C.Structure):
         ("r", C.c_int), ("q", C.c_int), ("terrain", C.c_int), ("bc_lateral", C.c_int), ("pad", C.c_int),
         ("Lx", C.c_double), ("Ly", C.c_double), ("Lz", C.c_double),
         ("hc", C.c_double), ("ac", C.c_double), ("xc", C.c_double), ("yc", C.c_double),
+        ("ref", C.c_int * 6),
     ]
 
 
@@ -45,9 +46,12 @@ def _dp(a):
 
 
 def make_mesh(nx, ny, nz, r, Lx=1000.0, Ly=1000.0, Lz=1000.0, q=None, terrain=0, hc=0.0, ac=1000.0,
-              xc=None, yc=None, bc_lateral=0):
+              xc=None, yc=None, bc_lateral=0, refine=None):
     """Structured hexahedral mesh on [0,Lx]x[0,Ly]x[0,Lz] (terrain-following
-    in z when ``terrain`` > 0).  ``q`` defaults to the consistent rule 2r+1."""
+    in z when ``terrain`` > 0).  ``q`` defaults to the consistent rule 2r+1.
+    ``refine`` = (x0, x1, y0, y1, z0, z1): the base cells of that box are split
+    2 x 2 x 2 (a non-conforming mesh with 2:1 hanging faces; the base cells
+    first, those in the box without unknowns, then the children)."""
     m = OrcMesh()
     m.nx, m.ny, m.nz, m.r = nx, ny, nz, r
     m.q = 2 * r + 1 if q is None else q
@@ -56,11 +60,50 @@ def make_mesh(nx, ny, nz, r, Lx=1000.0, Ly=1000.0, Lz=1000.0, q=None, terrain=0,
     m.hc, m.ac = hc, ac
     m.xc = Lx / 2 if xc is None else xc
     m.yc = Ly / 2 if yc is None else yc
+    if refine is not None:
+        for i, v in enumerate(refine):
+            m.ref[i] = int(v)
     return m
 
 
+def is_refined(m):
+    return m.ref[1] > m.ref[0] and m.ref[3] > m.ref[2] and m.ref[5] > m.ref[4]
+
+
+def num_cells(m):
+    n = m.nx * m.ny * m.nz
+    if is_refined(m):
+        n += 8 * (m.ref[1] - m.ref[0]) * (m.ref[3] - m.ref[2]) * (m.ref[5] - m.ref[4])
+    return n
+
+
+def dead_cells(m):
+    """Indices of the base cells replaced by their children (no unknowns)."""
+    if not is_refined(m):
+        return np.zeros(0, dtype=np.int64)
+    z, y, x = np.meshgrid(np.arange(m.ref[4], m.ref[5]), np.arange(m.ref[2], m.ref[3]),
+                          np.arange(m.ref[0], m.ref[1]), indexing="ij")
+    return (x + m.nx * (y + m.ny * z)).reshape(-1)
+
+
+def active_mask(m):
+    """Per-DoF flag: 1 where the mesh has unknowns."""
+    a = np.ones(num_cells(m), dtype=bool)
+    a[dead_cells(m)] = False
+    return np.repeat(a, (m.r + 1) ** 3)
+
+
+def face_info(m, cell, f):
+    """(relation, neighbours) of face f of a cell: -1 boundary, 0 conforming,
+    1 base cell's hanging face (four children), 2 child's hanging face (base
+    cell, child position), 3 dead cell."""
+    nb = (C.c_long * 4)()
+    rel = lib().orc_face_info(C.byref(m), C.c_long(cell), f, nb)
+    return rel, list(nb)
+
+
 def ndofs(m):
-    return m.nx * m.ny * m.nz * (m.r + 1) ** 3
+    return num_cells(m) * (m.r + 1) ** 3
 
 
 def gauss(q):
@@ -151,7 +194,7 @@ def apply_S(m, alpha, gamma, rho, pk, p, cells=None, consistent=False):
         assert lib().orc_apply_S_rule(*args, None, _dp(y)) == 0
         return y
     y[:] = np.nan
-    mask = np.zeros(m.nx * m.ny * m.nz, dtype=np.uint8)
+    mask = np.zeros(num_cells(m), dtype=np.uint8)
     mask[np.asarray(cells)] = 1
     assert lib().orc_apply_S_rule(*args, mask.ctypes.data_as(C.c_void_p), _dp(y)) == 0
     return y
@@ -248,7 +291,7 @@ def explicit(m, bg, rho, u, rho_bar, cells=None):
     if cells is not None:
         for a in (Er, Em, Ee):
             a[:] = np.nan
-        mk = np.zeros(m.nx * m.ny * m.nz, dtype=np.uint8)
+        mk = np.zeros(num_cells(m), dtype=np.uint8)
         mk[np.asarray(cells)] = 1
         mask = mk.ctypes.data_as(C.c_void_p)
     c = lambda a: np.ascontiguousarray(a, dtype=np.float64)

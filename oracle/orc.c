@@ -115,7 +115,25 @@ double orc_terrain_height(const orc_mesh *m, double x, double y) {
   return m->hc * pow(s, -1.5);
 }
 
-long orc_num_cells(const orc_mesh *m) { return (long)m->nx * m->ny * m->nz; }
+long orc_num_cells(const orc_mesh *m) {
+  long fd[3];
+  fine_dims(m, fd);
+  return base_cells(m) + fd[0] * fd[1] * fd[2];
+}
+
+/* Face relation for the tests: -1 domain boundary, 0 conforming neighbour
+ * nb[0], 1 hanging face of a base cell (the four children nb[sig1 + 2 sig2]),
+ * 2 hanging face of a child (the base cell nb[0], the child's position
+ * sig1 + 2 sig2 in nb[1]), 3 dead cell. */
+int orc_face_info(const orc_mesh *m, long cell, int f, long *nb) {
+  if (cell_dead(m, cell)) return 3;
+  long r = neighbour(m, cell, f / 2, f % 2);
+  if (r >= -1) { nb[0] = r; return r < 0 ? -1 : 0; }
+  int sig;
+  if (hanging_cells(m, cell, f, nb, &sig) == 4) return 1;
+  nb[1] = sig;
+  return 2;
+}
 
 /* ------------------------------------------------------------------ */
 /* Cell operators                                                       */
@@ -128,7 +146,7 @@ long orc_num_cells(const orc_mesh *m) { return (long)m->nx * m->ny * m->nz; }
  * datum of the perturbation pressure, p_hat = 0, imposed weakly (the
  * transmissive choice p+ = p- there makes the acoustic subsystem gain energy
  * through the boundary). */
-static void cell_B(const orc_mesh *m, const tabs *T, const cgeo *G, long cell, double alpha,
+static void cell_B(const orc_mesh *m, const tabs *T, const cgeo *G, hang_buf *H, long cell, double alpha,
                    const double *p, double *out) {
   int n3 = T->n3;
   const double *pc = p + cell * n3;
@@ -148,6 +166,16 @@ static void cell_B(const orc_mesh *m, const tabs *T, const cgeo *G, long cell, d
   for (int f = 0; f < 6; ++f) {
     int k = f / 2, s = f % 2;
     long nb = neighbour(m, cell, k, s);
+    if (nb == -2) { /* hanging face: central p_hat at the child faces' points */
+      int np = hanging_points(m, T, cell, f, H->nb, H->ps, H->psn, H->nA);
+      for (int qp = 0; qp < np; ++qp) {
+        const double *ps = H->ps + (size_t)qp * n3;
+        double ph = 0.5 * (dotn(n3, pc, ps) + dotn(n3, p + H->nb[qp] * n3, H->psn + (size_t)qp * n3));
+        for (int i = 0; i < n3; ++i)
+          for (int d = 0; d < 3; ++d) out[d * n3 + i] += ph * ps[i] * H->nA[3 * qp + d];
+      }
+      continue;
+    }
     const double *fps = T->fpsi[f], *fpsn = T->fpsi[2 * k + (1 - s)];
     int ff = nb < 0 && boundary_kind(m, k) == 1;
     for (int qp = 0; qp < T->q2; ++qp) {
@@ -189,7 +217,7 @@ static void cell_A_matrix(const tabs *T, const cgeo *G, long cell, const double 
  * Reading of the flux: (kappa V)^ = average of both traces on interior faces;
  * zero normal flux on slip walls ((V.n)+ = -(V.n)-); far-field faces are
  * transmissive in the pressure operator ((kappa V)+ = (kappa V)-). */
-static void cell_C(const orc_mesh *m, const tabs *T, const cgeo *G, long cell, double alpha,
+static void cell_C(const orc_mesh *m, const tabs *T, const cgeo *G, hang_buf *H, long cell, double alpha,
                    double gamma, const double *pk, const double *V, long N, double *out) {
   int n3 = T->n3;
   double kf = gamma / (gamma - 1.0);
@@ -211,6 +239,18 @@ static void cell_C(const orc_mesh *m, const tabs *T, const cgeo *G, long cell, d
   for (int f = 0; f < 6; ++f) {
     int k = f / 2, s = f % 2;
     long nb = neighbour(m, cell, k, s);
+    if (nb == -2) { /* hanging face: central flux at the child faces' points */
+      int np = hanging_points(m, T, cell, f, H->nb, H->ps, H->psn, H->nA);
+      for (int qp = 0; qp < np; ++qp) {
+        const double *ps = H->ps + (size_t)qp * n3, *pn = H->psn + (size_t)qp * n3, *nA = H->nA + 3 * qp;
+        long o = H->nb[qp] * n3;
+        double vm = dotn(n3, V0, ps) * nA[0] + dotn(n3, V1, ps) * nA[1] + dotn(n3, V2, ps) * nA[2];
+        double vp = dotn(n3, V + o, pn) * nA[0] + dotn(n3, V + N + o, pn) * nA[1] + dotn(n3, V + 2 * N + o, pn) * nA[2];
+        double flux = 0.5 * (kf * dotn(n3, kc, ps) * vm + kf * dotn(n3, pk + o, pn) * vp);
+        for (int i = 0; i < n3; ++i) out[i] += flux * ps[i];
+      }
+      continue;
+    }
     int bk = boundary_kind(m, k);
     if (nb < 0 && bk == 0) continue; /* slip wall: no normal flux */
     const double *fps = T->fpsi[f], *fpsn = T->fpsi[2 * k + (1 - s)];
@@ -280,14 +320,18 @@ int orc_apply_B(const orc_mesh *m, double alpha, const double *p, double *out) {
 #pragma omp parallel
   {
     cgeo G; cgeo_alloc(&G, &S.T);
+    hang_buf H; hang_alloc(&H, &S.T);
     double *loc = malloc(sizeof(double) * 3 * n3);
 #pragma omp for schedule(dynamic, 4)
     for (long c = 0; c < S.nc; ++c) {
-      cell_geometry(m, &S.T, c, &G);
-      cell_B(m, &S.T, &G, c, alpha, p, loc);
+      if (cell_dead(m, c)) memset(loc, 0, sizeof(double) * 3 * n3);
+      else {
+        cell_geometry(m, &S.T, c, &G);
+        cell_B(m, &S.T, &G, &H, c, alpha, p, loc);
+      }
       for (int d = 0; d < 3; ++d) memcpy(out + d * S.N + c * n3, loc + d * n3, sizeof(double) * n3);
     }
-    free(loc); cgeo_free(&G);
+    free(loc); hang_free(&H); cgeo_free(&G);
   }
   tabs_free(&S.T);
   return 0;
@@ -308,6 +352,10 @@ static int apply_A_impl(const orc_mesh *m, const double *rho, const double *in, 
     double *B = malloc(sizeof(double) * 3 * n3);
 #pragma omp for schedule(dynamic, 4)
     for (long c = 0; c < S.nc; ++c) {
+      if (cell_dead(m, c)) {
+        for (int d = 0; d < 3; ++d) memset(out + d * S.N + c * n3, 0, sizeof(double) * n3);
+        continue;
+      }
       cell_geometry(m, &S.T, c, &G);
       cell_A_matrix(&S.T, &G, c, rho, A, consistent);
       for (int d = 0; d < 3; ++d) memcpy(B + d * n3, in + d * S.N + c * n3, sizeof(double) * n3);
@@ -350,12 +398,14 @@ int orc_apply_C(const orc_mesh *m, double alpha, double gamma, const double *pk,
 #pragma omp parallel
   {
     cgeo G; cgeo_alloc(&G, &S.T);
+    hang_buf H; hang_alloc(&H, &S.T);
 #pragma omp for schedule(dynamic, 4)
     for (long c = 0; c < S.nc; ++c) {
+      if (cell_dead(m, c)) { memset(out + c * n3, 0, sizeof(double) * n3); continue; }
       cell_geometry(m, &S.T, c, &G);
-      cell_C(m, &S.T, &G, c, alpha, gamma, pk, V, S.N, out + c * n3);
+      cell_C(m, &S.T, &G, &H, c, alpha, gamma, pk, V, S.N, out + c * n3);
     }
-    cgeo_free(&G);
+    hang_free(&H); cgeo_free(&G);
   }
   tabs_free(&S.T);
   return 0;
@@ -371,6 +421,7 @@ int orc_apply_M(const orc_mesh *m, double scale, const double *f, double *out) {
     cgeo G; cgeo_alloc(&G, &S.T);
 #pragma omp for schedule(dynamic, 4)
     for (long c = 0; c < S.nc; ++c) {
+      if (cell_dead(m, c)) { memset(out + c * n3, 0, sizeof(double) * n3); continue; }
       cell_geometry(m, &S.T, c, &G);
       cell_M(&S.T, &G, c, scale, f, out + c * n3);
     }
@@ -392,11 +443,14 @@ int orc_apply_S_rule(const orc_mesh *m, int consistent, double alpha, double gam
   long nc = S.nc, N = S.N;
   unsigned char *need = calloc(nc, 1);
   for (long c = 0; c < nc; ++c) {
-    if (mask && !mask[c]) continue;
+    if ((mask && !mask[c]) || cell_dead(m, c)) continue;
     need[c] = 1;
     for (int f = 0; f < 6; ++f) {
-      long nb = neighbour(m, c, f / 2, f % 2);
-      if (nb >= 0) need[nb] = 1;
+      long nb[4];
+      int rel = orc_face_info(m, c, f, nb);
+      if (rel == 0) need[nb[0]] = 1;
+      if (rel == 1) for (int j = 0; j < 4; ++j) need[nb[j]] = 1;
+      if (rel == 2) need[nb[0]] = 1;
     }
   }
   double *V = calloc((size_t)3 * N, sizeof(double));
@@ -404,6 +458,7 @@ int orc_apply_S_rule(const orc_mesh *m, int consistent, double alpha, double gam
 #pragma omp parallel
   {
     cgeo G; cgeo_alloc(&G, &S.T);
+    hang_buf H; hang_alloc(&H, &S.T);
     double *A = malloc(sizeof(double) * n3 * n3);
     double *B = malloc(sizeof(double) * 3 * n3);
     double *loc = malloc(sizeof(double) * 2 * n3);
@@ -411,7 +466,7 @@ int orc_apply_S_rule(const orc_mesh *m, int consistent, double alpha, double gam
     for (long c = 0; c < nc; ++c) {
       if (!need[c]) continue;
       cell_geometry(m, &S.T, c, &G);
-      cell_B(m, &S.T, &G, c, alpha, p, B);
+      cell_B(m, &S.T, &G, &H, c, alpha, p, B);
       cell_A_matrix(&S.T, &G, c, rho, A, consistent);
       if (lu_solve(n3, A, 3, B)) err = -2;
       for (int d = 0; d < 3; ++d) memcpy(V + d * N + c * n3, B + d * n3, sizeof(double) * n3);
@@ -419,12 +474,13 @@ int orc_apply_S_rule(const orc_mesh *m, int consistent, double alpha, double gam
 #pragma omp for schedule(dynamic, 4)
     for (long c = 0; c < nc; ++c) {
       if (mask && !mask[c]) continue;
+      if (cell_dead(m, c)) { memset(y + c * n3, 0, sizeof(double) * n3); continue; }
       cell_geometry(m, &S.T, c, &G);
       cell_M(&S.T, &G, c, 1.0 / (gamma - 1.0), p, loc);
-      cell_C(m, &S.T, &G, c, alpha, gamma, pk, V, N, loc + n3);
+      cell_C(m, &S.T, &G, &H, c, alpha, gamma, pk, V, N, loc + n3);
       for (int i = 0; i < n3; ++i) y[c * n3 + i] = loc[i] - loc[n3 + i];
     }
-    free(A); free(B); free(loc); cgeo_free(&G);
+    free(A); free(B); free(loc); hang_free(&H); cgeo_free(&G);
   }
   free(V); free(need);
   tabs_free(&S.T);
@@ -456,8 +512,9 @@ int orc_precond_diag(const orc_mesh *m, int kind, double alpha, double gamma, co
     cgeo G; cgeo_alloc(&G, &S.T);
 #pragma omp for schedule(dynamic, 4)
     for (long c = 0; c < S.nc; ++c) {
-      cell_geometry(m, &S.T, c, &G);
       double *o = dg + c * n3;
+      if (cell_dead(m, c)) { for (int i = 0; i < n3; ++i) o[i] = 1.0; continue; } /* no unknowns */
+      cell_geometry(m, &S.T, c, &G);
       for (int i = 0; i < n3; ++i) o[i] = 0.0;
       for (int qp = 0; qp < S.T.q3; ++qp) {
         const double *ps = S.T.psi + (size_t)qp * n3, *dps = S.T.dpsi + (size_t)qp * 3 * n3;

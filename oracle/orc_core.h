@@ -26,6 +26,9 @@ typedef struct {
   int pad;
   double Lx, Ly, Lz;
   double hc, ac, xc, yc;
+  /* 2:1 refinement box in base cells, [ref[0], ref[1]) x [ref[2], ref[3]) x
+   * [ref[4], ref[5]); no refinement when the box is empty */
+  int ref[6];
 } orc_mesh;
 
 /* exported 1D rules and helpers (defined in orc.c) */
@@ -88,6 +91,12 @@ static void basis3(const tabs *T, const double xi[3], double *psi, double *dpsi)
       }
 }
 
+static double dotn(int n3, const double *f, const double *psi) {
+  double s = 0.0;
+  for (int i = 0; i < n3; ++i) s += f[i] * psi[i];
+  return s;
+}
+
 static int tabs_init(tabs *T, const orc_mesh *m) {
   memset(T, 0, sizeof(*T));
   int n = m->r + 1, q = m->q;
@@ -145,11 +154,76 @@ static void tabs_free(tabs *T) {
 
 
 
+/* ------------------------------------------------------------------ */
+/* Non-conforming meshes (Sec. 3: neighbouring cells of different        */
+/* resolution horizontally and vertically)                              */
+/* ------------------------------------------------------------------ */
+/* The nx*ny*nz base mesh with the cells of the box ref[] split into
+ * 2 x 2 x 2 children.  Cell numbering: the base cells first, x fastest (those
+ * inside the box are "dead": they hold no unknowns and every operator gives 0
+ * there), then the (2bx)(2by)(2bz) children as one structured block, x
+ * fastest.  A face between a child and a base cell is "hanging": the base
+ * cell's face is the union of four children's faces (2:1 in both tangential
+ * directions).  Reading of the geometry: a child's map is its parent's
+ * isoparametric map restricted to the child, so hanging faces are watertight. */
+static int refined(const orc_mesh *m) {
+  return m->ref[1] > m->ref[0] && m->ref[3] > m->ref[2] && m->ref[5] > m->ref[4];
+}
+static long base_cells(const orc_mesh *m) { return (long)m->nx * m->ny * m->nz; }
+static void fine_dims(const orc_mesh *m, long fd[3]) {
+  for (int d = 0; d < 3; ++d) fd[d] = refined(m) ? 2L * (m->ref[2 * d + 1] - m->ref[2 * d]) : 0;
+}
+static void base_coords(const orc_mesh *m, long cell, long c[3]) {
+  c[0] = cell % m->nx; c[1] = (cell / m->nx) % m->ny; c[2] = cell / ((long)m->nx * m->ny);
+}
+static int in_box(const orc_mesh *m, const long c[3]) {
+  if (!refined(m)) return 0;
+  for (int d = 0; d < 3; ++d)
+    if (c[d] < m->ref[2 * d] || c[d] >= m->ref[2 * d + 1]) return 0;
+  return 1;
+}
+/* a base cell replaced by its children */
+static int cell_dead(const orc_mesh *m, long cell) {
+  if (cell >= base_cells(m)) return 0;
+  long c[3];
+  base_coords(m, cell, c);
+  return in_box(m, c);
+}
+static int cell_fine(const orc_mesh *m, long cell) { return cell >= base_cells(m); }
+static void fine_coords(const orc_mesh *m, long cell, long f[3]) {
+  long fd[3], l = cell - base_cells(m);
+  fine_dims(m, fd);
+  f[0] = l % fd[0]; f[1] = (l / fd[0]) % fd[1]; f[2] = l / (fd[0] * fd[1]);
+}
+static long fine_index(const orc_mesh *m, const long f[3]) {
+  long fd[3];
+  fine_dims(m, fd);
+  return base_cells(m) + f[0] + fd[0] * (f[1] + fd[1] * f[2]);
+}
+static long base_index(const orc_mesh *m, const long c[3]) { return c[0] + m->nx * (c[1] + (long)m->ny * c[2]); }
+
 /* Physical coordinates of the (r+1)^3 GLL nodes of a cell.  Reading of the
  * terrain-following mapping: Gal-Chen, z = zeta + h(x,y) (1 - zeta/Lz) with
- * zeta uniform on [0, Lz]; x, y affine. */
+ * zeta uniform on [0, Lz]; x, y affine.  A child's nodes are its parent's
+ * isoparametric map evaluated at the child's nodes, xi = (sigma + x_a) / 2. */
 static void cell_nodes(const orc_mesh *m, const tabs *T, long cell, double *Xn /* [3][n3] */) {
   int n = T->n, n3 = T->n3;
+  if (cell_fine(m, cell)) {
+    long f[3], pc[3];
+    fine_coords(m, cell, f);
+    for (int d = 0; d < 3; ++d) pc[d] = m->ref[2 * d] + f[d] / 2;
+    double Xp[3 * ORC_MAXN * ORC_MAXN * ORC_MAXN], ps[ORC_MAXN * ORC_MAXN * ORC_MAXN];
+    cell_nodes(m, T, base_index(m, pc), Xp);
+    for (int c = 0; c < n; ++c)
+      for (int b = 0; b < n; ++b)
+        for (int a = 0; a < n; ++a) {
+          double xi[3] = {0.5 * (f[0] % 2 + T->gll[a]), 0.5 * (f[1] % 2 + T->gll[b]), 0.5 * (f[2] % 2 + T->gll[c])};
+          basis3(T, xi, ps, NULL);
+          int i = a + n * (b + n * c);
+          for (int d = 0; d < 3; ++d) Xn[d * n3 + i] = dotn(n3, Xp + d * n3, ps);
+        }
+    return;
+  }
   long cx = cell % m->nx, cy = (cell / m->nx) % m->ny, cz = cell / ((long)m->nx * m->ny);
   double dx = m->Lx / m->nx, dy = m->Ly / m->ny, dz = m->Lz / m->nz;
   for (int c = 0; c < n; ++c)
@@ -194,6 +268,25 @@ static void inv3(double J[3][3], double det, double Ji[3][3]) {
   Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
 }
 
+/* Outward normal times area element times weight, nA [q2][3], at the face
+ * points of face f = 2k+s of a cell with nodes Xn. */
+static void face_normals(const tabs *T, const double *Xn, int f, double *nA) {
+  int n3 = T->n3;
+  int k = f / 2, s = f % 2;
+  int t1 = (k == 0) ? 1 : 0, t2 = (k == 2) ? 1 : 2;
+  for (int p = 0; p < T->q2; ++p) {
+    double J[3][3];
+    jacobian(n3, Xn, T->fdpsi[f] + (size_t)p * 3 * n3, J);
+    double a[3] = {J[0][t1], J[1][t1], J[2][t1]};
+    double b[3] = {J[0][t2], J[1][t2], J[2][t2]};
+    double N[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+    /* outward: along +xi_k on side 1, -xi_k on side 0 */
+    double dk = N[0] * J[0][k] + N[1] * J[1][k] + N[2] * J[2][k];
+    double sg = ((dk > 0) == (s == 1)) ? 1.0 : -1.0;
+    for (int d = 0; d < 3; ++d) nA[3 * p + d] = sg * N[d] * T->fw[f][p];
+  }
+}
+
 /* Per-cell geometry at the quadrature points. */
 typedef struct {
   double *wdet;   /* [q3]  w_q det J                                   */
@@ -232,45 +325,138 @@ static void cell_geometry(const orc_mesh *m, const tabs *T, long cell, cgeo *G) 
     jacobian(n3, G->Xn, T->dpsia + (size_t)p * 3 * n3, J);
     G->wdeta[p] = T->wa[p] * det3(J);
   }
-  for (int f = 0; f < 6; ++f) {
-    int k = f / 2, s = f % 2;
-    int t1 = (k == 0) ? 1 : 0, t2 = (k == 2) ? 1 : 2;
-    for (int p = 0; p < T->q2; ++p) {
-      double J[3][3];
-      jacobian(n3, G->Xn, T->fdpsi[f] + (size_t)p * 3 * n3, J);
-      double a[3] = {J[0][t1], J[1][t1], J[2][t1]};
-      double b[3] = {J[0][t2], J[1][t2], J[2][t2]};
-      double N[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
-      /* outward: along +xi_k on side 1, -xi_k on side 0 */
-      double dk = N[0] * J[0][k] + N[1] * J[1][k] + N[2] * J[2][k];
-      double sg = ((dk > 0) == (s == 1)) ? 1.0 : -1.0;
-      for (int d = 0; d < 3; ++d) G->nA[f][3 * p + d] = sg * N[d] * T->fw[f][p];
-    }
-  }
+  for (int f = 0; f < 6; ++f) face_normals(T, G->Xn, f, G->nA[f]);
 }
 
 /* Neighbour across face (k, s); -1 on the domain boundary.  With periodic
- * lateral boundaries (bc_lateral 2) the x and y directions wrap around. */
-static long neighbour(const orc_mesh *m, long cell, int k, int s) {
-  long c[3] = {cell % m->nx, (cell / m->nx) % m->ny, cell / ((long)m->nx * m->ny)};
+ * lateral boundaries (bc_lateral 2) the x and y directions wrap around (a
+ * refinement box must then stay clear of the periodic faces).  -2: a hanging
+ * face (see hanging_points). */
+static long base_neighbour(const orc_mesh *m, const long c0[3], int k, int s, long c[3]) {
   long nn[3] = {m->nx, m->ny, m->nz};
+  for (int d = 0; d < 3; ++d) c[d] = c0[d];
   c[k] += s ? 1 : -1;
   if (c[k] < 0 || c[k] >= nn[k]) {
     if (k == 2 || m->bc_lateral != 2) return -1;
     c[k] = (c[k] + nn[k]) % nn[k];
   }
-  return c[0] + m->nx * (c[1] + m->ny * c[2]);
+  return base_index(m, c);
 }
+static long neighbour(const orc_mesh *m, long cell, int k, int s) {
+  long c[3], nc[3];
+  if (cell_fine(m, cell)) {
+    long f[3], fd[3];
+    fine_coords(m, cell, f);
+    fine_dims(m, fd);
+    f[k] += s ? 1 : -1;
+    if (f[k] >= 0 && f[k] < fd[k]) return fine_index(m, f);
+    for (int d = 0; d < 3; ++d) c[d] = m->ref[2 * d] + (d == k ? (s ? fd[k] / 2 - 1 : 0) : f[d] / 2);
+    return base_neighbour(m, c, k, s, nc) < 0 ? -1 : -2;
+  }
+  base_coords(m, cell, c);
+  long nb = base_neighbour(m, c, k, s, nc);
+  if (nb >= 0 && in_box(m, nc)) return -2;
+  return nb;
+}
+
+/* Cells across the hanging face f = 2k+s of `cell`: for a base cell the four
+ * children nb[sig1 + 2 sig2] whose faces make up its face (sig1, sig2 the
+ * children's positions along the face's tangential directions t1, t2),
+ * returns 4; for a child the base cell nb[0], with the child's position
+ * *sig = sig1 + 2 sig2, returns 1. */
+static int hanging_cells(const orc_mesh *m, long cell, int f, long *nb, int *sig) {
+  int k = f / 2, s = f % 2;
+  int t1 = (k == 0) ? 1 : 0, t2 = (k == 2) ? 1 : 2;
+  long c[3], nc[3];
+  if (cell_fine(m, cell)) {
+    long fc[3], fd[3];
+    fine_coords(m, cell, fc);
+    fine_dims(m, fd);
+    for (int d = 0; d < 3; ++d) c[d] = m->ref[2 * d] + (d == k ? (s ? fd[k] / 2 - 1 : 0) : fc[d] / 2);
+    nb[0] = base_neighbour(m, c, k, s, nc);
+    *sig = (int)(fc[t1] % 2 + 2 * (fc[t2] % 2));
+    return 1;
+  }
+  base_coords(m, cell, c);
+  base_neighbour(m, c, k, s, nc);
+  for (int sg2 = 0; sg2 < 2; ++sg2)
+    for (int sg1 = 0; sg1 < 2; ++sg1) {
+      long fc[3];
+      fc[k] = 2 * (nc[k] - m->ref[2 * k]) + (s ? 0 : 1);
+      fc[t1] = 2 * (c[t1] - m->ref[2 * t1]) + sg1;
+      fc[t2] = 2 * (c[t2] - m->ref[2 * t2]) + sg2;
+      nb[sg1 + 2 * sg2] = fine_index(m, fc);
+    }
+  *sig = -1;
+  return 4;
+}
+
+/* Quadrature points of the hanging face f = 2k+s of `cell`: the face rule of
+ * each child face it consists of (four for a base cell, its own for a child).
+ * Per point: the neighbour cell nb, this cell's basis ps [n3] and the
+ * neighbour's basis psn [n3] there, and nA [3] outward from this cell (the
+ * child's face geometry on both sides, so the two sides' fluxes cancel).
+ * The child face at position (sig1, sig2) covers the base face's reference
+ * square [sig1/2, (sig1+1)/2] x [sig2/2, (sig2+1)/2].  Returns the number of
+ * points; the arrays hold 4 q2 points. */
+static int hanging_points(const orc_mesh *m, const tabs *T, long cell, int f, long *nb, double *ps, double *psn,
+                          double *nA) {
+  int k = f / 2, s = f % 2, q = T->q, q2 = T->q2, n3 = T->n3;
+  int t1 = (k == 0) ? 1 : 0, t2 = (k == 2) ? 1 : 2;
+  int fo = 2 * k + (1 - s); /* the same face seen from the other side */
+  double Xn[3 * ORC_MAXN * ORC_MAXN * ORC_MAXN];
+  long cells[4];
+  int sig;
+  int nh = hanging_cells(m, cell, f, cells, &sig);
+  if (nh == 1) {
+    int sg1 = sig % 2, sg2 = sig / 2;
+    cell_nodes(m, T, cell, Xn);
+    face_normals(T, Xn, f, nA);
+    for (int j = 0; j < q; ++j)
+      for (int i = 0; i < q; ++i) {
+        int p = i + q * j;
+        double xi[3];
+        xi[k] = (double)(1 - s); xi[t1] = 0.5 * (sg1 + T->gq[i]); xi[t2] = 0.5 * (sg2 + T->gq[j]);
+        nb[p] = cells[0];
+        memcpy(ps + (size_t)p * n3, T->fpsi[f] + (size_t)p * n3, sizeof(double) * n3);
+        basis3(T, xi, psn + (size_t)p * n3, NULL);
+      }
+    return q2;
+  }
+  double nAc[3 * ORC_MAXQ * ORC_MAXQ];
+  for (int sg2 = 0; sg2 < 2; ++sg2)
+    for (int sg1 = 0; sg1 < 2; ++sg1) {
+      long child = cells[sg1 + 2 * sg2];
+      cell_nodes(m, T, child, Xn);
+      face_normals(T, Xn, fo, nAc);
+      for (int j = 0; j < q; ++j)
+        for (int i = 0; i < q; ++i) {
+          int p = (sg1 + 2 * sg2) * q2 + i + q * j;
+          double xi[3];
+          xi[k] = (double)s; xi[t1] = 0.5 * (sg1 + T->gq[i]); xi[t2] = 0.5 * (sg2 + T->gq[j]);
+          nb[p] = child;
+          basis3(T, xi, ps + (size_t)p * n3, NULL);
+          memcpy(psn + (size_t)p * n3, T->fpsi[fo] + (size_t)(i + q * j) * n3, sizeof(double) * n3);
+          for (int d = 0; d < 3; ++d) nA[3 * p + d] = -nAc[3 * (i + q * j) + d];
+        }
+    }
+  return 4 * q2;
+}
+
+/* Scratch of hanging_points for one face. */
+typedef struct { long *nb; double *ps, *psn, *nA; } hang_buf;
+static void hang_alloc(hang_buf *H, const tabs *T) {
+  H->nb = malloc(sizeof(long) * 4 * T->q2);
+  H->ps = malloc(sizeof(double) * 4 * T->q2 * T->n3);
+  H->psn = malloc(sizeof(double) * 4 * T->q2 * T->n3);
+  H->nA = malloc(sizeof(double) * 4 * T->q2 * 3);
+}
+static void hang_free(hang_buf *H) { free(H->nb); free(H->ps); free(H->psn); free(H->nA); }
 
 /* Boundary kind of face direction k: 0 slip wall, 1 far field (periodic
  * lateral faces have neighbours and never reach this). */
 static int boundary_kind(const orc_mesh *m, int k) { return (k == 2) ? 0 : m->bc_lateral; }
 
-static double dotn(int n3, const double *f, const double *psi) {
-  double s = 0.0;
-  for (int i = 0; i < n3; ++i) s += f[i] * psi[i];
-  return s;
-}
 
 
 /* LU with partial pivoting, in place; solves A x = b for nrhs right-hand

@@ -98,12 +98,15 @@ int orc_explicit_masked(const orc_mesh *m, const orc_bg *b, const double *rho, c
   {
     cgeo G;
     cgeo_alloc(&G, &T);
+    hang_buf H;
+    hang_alloc(&H, &T);
     double *loc = malloc(sizeof(double) * 5 * n3);
 #pragma omp for schedule(dynamic, 4)
     for (long c = 0; c < nc; ++c) {
       if (mask && !mask[c]) continue;
-      cell_geometry(m, &T, c, &G);
       memset(loc, 0, sizeof(double) * 5 * n3);
+      if (cell_dead(m, c)) goto store; /* no unknowns: zero tendencies */
+      cell_geometry(m, &T, c, &G);
       const double *rc = rho + c * n3;
       for (int qp = 0; qp < T.q3; ++qp) {
         const double *ps = T.psi + (size_t)qp * n3, *dps = T.dpsi + (size_t)qp * 3 * n3;
@@ -124,6 +127,29 @@ int orc_explicit_masked(const orc_mesh *m, const orc_bg *b, const double *rho, c
       for (int f = 0; f < 6; ++f) {
         int kd = f / 2, s = f % 2;
         long nb = neighbour(m, c, kd, s);
+        if (nb == -2) { /* hanging face: the flux at the child faces' points, neighbour state from nb */
+          int np = hanging_points(m, &T, c, f, H.nb, H.ps, H.psn, H.nA);
+          for (int qp = 0; qp < np; ++qp) {
+            const double *ps = H.ps + (size_t)qp * n3, *pn = H.psn + (size_t)qp * n3, *nA = H.nA + 3 * qp;
+            long o = H.nb[qp] * n3;
+            double an = sqrt(nA[0] * nA[0] + nA[1] * nA[1] + nA[2] * nA[2]);
+            double rm = dotn(n3, rc, ps), rp = dotn(n3, rho + o, pn);
+            double vm[3] = {dotn(n3, u0 + c * n3, ps), dotn(n3, u1 + c * n3, ps), dotn(n3, u2 + c * n3, ps)};
+            double vp[3] = {dotn(n3, u0 + o, pn), dotn(n3, u1 + o, pn), dotn(n3, u2 + o, pn)};
+            double km = 0.5 * (vm[0] * vm[0] + vm[1] * vm[1] + vm[2] * vm[2]);
+            double kp = 0.5 * (vp[0] * vp[0] + vp[1] * vp[1] + vp[2] * vp[2]);
+            double qm[5] = {rm, rm * vm[0], rm * vm[1], rm * vm[2], rm * km};
+            double qn[5] = {rp, rp * vp[0], rp * vp[1], rp * vp[2], rp * kp};
+            double unm = vm[0] * nA[0] + vm[1] * nA[1] + vm[2] * nA[2];
+            double unp = vp[0] * nA[0] + vp[1] * nA[1] + vp[2] * nA[2];
+            double lam = fmax(fabs(unm), fabs(unp)) / an;
+            for (int fl = 0; fl < 5; ++fl) {
+              double F = 0.5 * (qm[fl] * unm + qn[fl] * unp) + 0.5 * lam * an * (qm[fl] - qn[fl]);
+              for (int i = 0; i < n3; ++i) loc[fl * n3 + i] -= F * ps[i];
+            }
+          }
+          continue;
+        }
         int bk = boundary_kind(m, kd);
         const double *fps = T.fpsi[f], *fpsn = T.fpsi[2 * kd + (1 - s)];
         for (int qp = 0; qp < T.q2; ++qp) {
@@ -161,6 +187,7 @@ int orc_explicit_masked(const orc_mesh *m, const orc_bg *b, const double *rho, c
           }
         }
       }
+    store:
       for (int i = 0; i < n3; ++i) {
         Erho[c * n3 + i] = loc[i];
         Em[c * n3 + i] = loc[n3 + i];
@@ -170,6 +197,7 @@ int orc_explicit_masked(const orc_mesh *m, const orc_bg *b, const double *rho, c
       }
     }
     free(loc);
+    hang_free(&H);
     cgeo_free(&G);
   }
   tabs_free(&T);
@@ -194,9 +222,10 @@ int orc_kinetic_mass(const orc_mesh *m, const double *rho, const double *u, doub
     cgeo_alloc(&G, &T);
 #pragma omp for schedule(dynamic, 4)
     for (long c = 0; c < nc; ++c) {
-      cell_geometry(m, &T, c, &G);
       double *o = out + c * n3;
       for (int i = 0; i < n3; ++i) o[i] = 0.0;
+      if (cell_dead(m, c)) continue;
+      cell_geometry(m, &T, c, &G);
       for (int qp = 0; qp < T.q3; ++qp) {
         const double *ps = T.psi + (size_t)qp * n3;
         double r = dotn(n3, rho + c * n3, ps);

@@ -20,6 +20,7 @@ import oracle as O
 import oracle.learned as NL
 import test_oracle_imex as I
 import test_oracle_learned as TL
+import test_oracle_nonconf as NC
 import test_oracle_pins as P
 
 ORACLE = os.path.dirname(os.path.abspath(O.__file__))
@@ -101,6 +102,27 @@ C_MUTANTS = [
     ("buoyancy of the stage with the wrong sign", "orc_imex.c",
      "orc_apply_M(m, -b->g * al, t1, t2);", "orc_apply_M(m, b->g * al, t1, t2);",
      [(I.test_buoyancy_initial_acceleration, (False,))]),
+    ("hanging-face points of a base cell ignoring the child's position", "orc_core.h",
+     "xi[k] = (double)s; xi[t1] = 0.5 * (sg1 + T->gq[i]);", "xi[k] = (double)s; xi[t1] = 0.5 * T->gq[i];",
+     [(NC.test_B_reproduces_gradient_of_linear_fields, (2,))]),
+    ("child's face normal not reversed on the base side", "orc_core.h",
+     "nA[3 * p + d] = -nAc[3 * (i + q * j) + d];", "nA[3 * p + d] = nAc[3 * (i + q * j) + d];",
+     [(NC.test_hanging_fluxes_cancel, ())]),
+    ("child nodes all in the parent's first octant", "orc_core.h",
+     "double xi[3] = {0.5 * (f[0] % 2 + T->gll[a]),", "double xi[3] = {0.5 * (T->gll[a]),",
+     [(NC.test_cells_partition_the_domain, (NC.HILL,))]),
+    ("children numbered y fastest", "orc_core.h",
+     "return base_cells(m) + f[0] + fd[0] * (f[1] + fd[1] * f[2]);",
+     "return base_cells(m) + f[1] + fd[1] * (f[0] + fd[0] * f[2]);",
+     [(NC.test_fully_refined_mesh_is_the_conforming_fine_mesh, ())]),
+    ("hanging C flux with the own kappa on both sides", "orc.c",
+     "double flux = 0.5 * (kf * dotn(n3, kc, ps) * vm + kf * dotn(n3, pk + o, pn) * vp);",
+     "double flux = 0.5 * (kf * dotn(n3, kc, ps) * vm + kf * dotn(n3, kc, ps) * vp);",
+     [(NC.test_hanging_fluxes_cancel, ())]),
+    ("hanging Lax-Friedrichs dissipation with the wrong sign", "orc_imex.c",
+     "double F = 0.5 * (qm[fl] * unm + qn[fl] * unp) + 0.5 * lam * an * (qm[fl] - qn[fl]);",
+     "double F = 0.5 * (qm[fl] * unm + qn[fl] * unp) - 0.5 * lam * an * (qm[fl] - qn[fl]);",
+     [(NC.test_explicit_upwinds_a_density_jump_across_hanging_faces, ())]),
     ("velocity recovery with the wrong sign", "orc_imex.c",
      "ul[i] = W[i] - t2[i];", "ul[i] = W[i] + t2[i];",
      [(I.test_buoyancy_initial_acceleration, (False,)), (I.test_acoustic_standing_wave_closed_form, ())]),
