@@ -79,7 +79,25 @@ typedef struct dgx_ctx dgx_ctx;
  * match on opposite faces, e.g. a centred hill).  Bottom and top are slip
  * walls.
  * n_q: Gauss points per direction of the consistent rule; 0 selects 2r+1
- * (Sec. 3.3), the only value the GPU kernels accept. */
+ * (Sec. 3.3), the only value the GPU kernels accept.
+ * refine: a non-conforming mesh (Sec. 3: neighbouring cells of different
+ * resolution horizontally and vertically) when the box [refine[0], refine[1])
+ * x [refine[2], refine[3]) x [refine[4], refine[5]) of base cells is not
+ * empty: each base cell of the box is split 2 x 2 x 2.  Layout of every
+ * per-DoF array: the nx*ny*nz base cells first (x fastest), those inside the
+ * box "dead" (they hold no unknowns: inputs must be 0 there, outputs are 0
+ * there), then the children as one structured block of (2 bx)(2 by)(2 bz)
+ * cells, x fastest; (r+1)^3 nodes per cell as on conforming meshes.  A
+ * child's map is its parent's isoparametric map restricted to the child, so
+ * the faces between children and base cells (2:1 "hanging" faces) are
+ * watertight; their face terms are integrated with the children's face rule
+ * on both sides (conservative).  The box must leave at least one base cell
+ * outside it and, with periodic lateral faces, stay clear of them.  On
+ * non-conforming meshes the operator, its parts, the diagonals, the FP64, CG
+ * and mixed solvers with the Jacobi preconditioners, node coordinates,
+ * background and explicit tendencies are available; the IMEX step, the
+ * learned and multigrid preconditioners, the consistent mass rule, ensembles
+ * and dgx_apply_operator_noalloc return DGX_ERR_STATE. */
 typedef struct {
   int nx, ny, nz;
   int degree;
@@ -89,6 +107,7 @@ typedef struct {
   int reserved;
   double Lx, Ly, Lz;
   double h_c, a_c, x_c, y_c;
+  int refine[6];
 } dgx_mesh_desc;
 
 /* Hydrostatic background (Sec. 3): kind 0 isothermal at T (p = p0 exp(-g z/(R T))),

@@ -71,7 +71,7 @@ def build(force=False, verbose=False, extra_flags=()):
             print(r.stdout + r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(len(srcs), max(8, os.cpu_count() or 8))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".%d.tmp" % os.getpid()
     r = subprocess.run([nv] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"], capture_output=True, text=True)

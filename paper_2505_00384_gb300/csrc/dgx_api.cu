@@ -218,6 +218,9 @@ bool make_tables(int r, Tables1D &T) {
 
 }  // namespace
 
+void rule_gauss(int q, std::vector<double> &x, std::vector<double> &w) { gauss_rule(q, x, w); }
+void rule_gll(int n, std::vector<double> &x, std::vector<double> &w) { gll_rule(n, x, w); }
+
 bool child_tables(int r, std::vector<double> &E, std::vector<int> &side, std::vector<double> &F) {
   const int N = r + 1;
   if (r < 1 || r > kMaxDegree) return false;
@@ -259,6 +262,8 @@ double terrain_h(const dgx_mesh_desc &m, double x, double y) {
 struct NodeP {
   int nx, ny, n, terrain;
   double dx, dy, dz, H, hc, ac, xc, yc;
+  double x0, y0, zeta0;  // origin of the patch
+  const double *hn;      // nodal terrain heights per column (children block), else the analytic terrain
   double gll[8];
 };
 
@@ -268,17 +273,20 @@ __device__ double dev_terrain(const NodeP &p, double x, double y) {
   return p.terrain == 1 ? p.hc / s : p.hc * pow(s, -1.5);
 }
 
-__global__ void k_node_coords(NodeP p, long long N, double *__restrict__ X) {
+// nodes of one patch: n of them, components with stride N
+__global__ void k_node_coords(NodeP p, long long n, long long N, double *__restrict__ X) {
   const int n3 = p.n * p.n * p.n;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const long long cell = i / n3;
     const int node = (int)(i % n3);
     const int a = node % p.n, b = (node / p.n) % p.n, c = node / (p.n * p.n);
     const long long cx = cell % p.nx, cy = (cell / p.nx) % p.ny, cz = cell / ((long long)p.nx * p.ny);
-    const double x = (cx + p.gll[a]) * p.dx, y = (cy + p.gll[b]) * p.dy, zeta = (cz + p.gll[c]) * p.dz;
+    const double x = p.x0 + (cx + p.gll[a]) * p.dx, y = p.y0 + (cy + p.gll[b]) * p.dy;
+    const double zeta = p.zeta0 + (cz + p.gll[c]) * p.dz;
+    const double h = p.hn ? p.hn[(cx + p.nx * cy) * p.n * p.n + a + p.n * b] : dev_terrain(p, x, y);
     X[i] = x;
     X[N + i] = y;
-    X[2 * N + i] = zeta + dev_terrain(p, x, y) * (1.0 - zeta / p.H);
+    X[2 * N + i] = zeta + h * (1.0 - zeta / p.H);
   }
 }
 
@@ -329,6 +337,13 @@ void free_mesh(dgx_ctx *c) {
   c->col64 = nullptr;
   c->col32 = nullptr;
   c->coldf = nullptr;
+  c->nc = false;
+  c->ncell0 = 0;
+  c->hn1 = nullptr;
+  c->hang64 = nullptr;
+  c->hang32 = nullptr;
+  c->hcells = nullptr;
+  c->nhcell = 0;
   c->rho_bar = c->p_bar = nullptr;
   c->rho64 = c->pk64 = nullptr;
   c->rho32 = c->pk32 = nullptr;
@@ -376,7 +391,7 @@ int grid_for(long long n) {
   return (int)std::min<long long>(std::max<long long>(b, 1), 4 * 152);
 }
 
-NodeP node_params(const dgx_ctx *c, const Tables1D *T = nullptr) {
+NodeP node_params(const dgx_ctx *c, int patch = 0) {
   NodeP p{};
   p.nx = c->mesh.nx;
   p.ny = c->mesh.ny;
@@ -385,6 +400,17 @@ NodeP node_params(const dgx_ctx *c, const Tables1D *T = nullptr) {
   p.dx = c->mesh.Lx / c->mesh.nx;
   p.dy = c->mesh.Ly / c->mesh.ny;
   p.dz = c->mesh.Lz / c->mesh.nz;
+  if (patch == 1) {  // the children block: half sizes from the box's corner, heights from the parents' maps
+    p.x0 = c->mesh.refine[0] * p.dx;
+    p.y0 = c->mesh.refine[2] * p.dy;
+    p.zeta0 = c->zoff;
+    p.nx = c->fine[0];
+    p.ny = c->fine[1];
+    p.dx *= 0.5;
+    p.dy *= 0.5;
+    p.dz *= 0.5;
+    p.hn = c->hn1;
+  }
   p.H = c->mesh.Lz;
   p.hc = c->mesh.h_c;
   p.ac = c->mesh.a_c;
@@ -393,8 +419,16 @@ NodeP node_params(const dgx_ctx *c, const Tables1D *T = nullptr) {
   std::vector<double> x, w;
   gll_rule(c->n, x, w);
   for (int i = 0; i < c->n; ++i) p.gll[i] = x[i];
-  (void)T;
   return p;
+}
+
+// node coordinates of every patch (3N doubles)
+void launch_node_coords(dgx_ctx *c, double *X) {
+  for (int pi = 0; pi < num_patches(c); ++pi) {
+    const long long o = patch_cell0(c, pi) * c->n * c->n * c->n, n = patch_ncell(c, pi) * c->n * c->n * c->n;
+    count_launch();
+    k_node_coords<<<grid_for(n), 256, 0, c->stream>>>(node_params(c, pi), n, c->N, X + o);
+  }
 }
 
 template <typename T>
@@ -987,7 +1021,24 @@ int dgx_mesh_build(dgx_ctx *c, const dgx_mesh_desc *d) {
                                          "(centre the hill)");
     }
   }
-  const long long ncell = (long long)d->nx * d->ny * d->nz;
+  // non-conforming meshes: a box of base cells split 2 x 2 x 2
+  const int *rf = d->refine;
+  const bool nc = rf[1] > rf[0] || rf[3] > rf[2] || rf[5] > rf[4];
+  long long nfine = 0;
+  if (nc) {
+    const int ext[3] = {d->nx, d->ny, d->nz};
+    for (int k = 0; k < 3; ++k)
+      if (rf[2 * k] < 0 || rf[2 * k + 1] > ext[k] || rf[2 * k + 1] <= rf[2 * k])
+        return set_error(c, DGX_ERR_ARG, "refinement box [%d, %d) outside 0..%d in direction %d", rf[2 * k],
+                         rf[2 * k + 1], ext[k], k);
+    if (r > 5) return set_error(c, DGX_ERR_ARG, "non-conforming meshes: degree %d above 5", r);
+    nfine = 8LL * (rf[1] - rf[0]) * (rf[3] - rf[2]) * (rf[5] - rf[4]);
+    if (nfine == 8LL * d->nx * d->ny * d->nz)
+      return set_error(c, DGX_ERR_ARG, "the refinement box must leave base cells outside it");
+    if (d->bc_lateral == 2 && (rf[0] == 0 || rf[1] == d->nx || rf[2] == 0 || rf[3] == d->ny))
+      return set_error(c, DGX_ERR_ARG, "with periodic lateral faces the refinement box must stay clear of them");
+  }
+  const long long ncell0 = (long long)d->nx * d->ny * d->nz, ncell = ncell0 + nfine;
   if (ncell > 2000000000LL) return set_error(c, DGX_ERR_ARG, "too many cells");
   if (cudaSetDevice(c->device) != cudaSuccess) return set_error(c, DGX_ERR_CUDA, "cudaSetDevice");
   cudaStreamSynchronize(c->stream);
@@ -1000,6 +1051,11 @@ int dgx_mesh_build(dgx_ctx *c, const dgx_mesh_desc *d) {
   c->ncell = ncell;
   c->N = ncell * c->n * c->n * c->n;
   c->curved = d->terrain != 0;
+  c->nc = nc;
+  c->ncell0 = ncell0;
+  c->zoff = nc ? rf[4] * (d->Lz / d->nz) : 0.0;
+  for (int k = 0; k < 3; ++k) c->fine[k] = nc ? 2 * (rf[2 * k + 1] - rf[2 * k]) : 0;
+  c->col1_off = (long long)d->nx * d->ny;
   Tables1D T;
   if (!make_tables(r, T)) return set_error(c, DGX_ERR_ARG, "table construction failed");
   const int N = c->n, Q = c->q;
@@ -1010,70 +1066,102 @@ int dgx_mesh_build(dgx_ctx *c, const dgx_mesh_desc *d) {
   cudaMemcpy(c->tab32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (c->curved) {
     const int CS = col_size(N, Q);
-    const long long ncol = (long long)d->nx * d->ny;
-    std::vector<double> col((size_t)ncol * CS);
+    const long long ncol0 = (long long)d->nx * d->ny, ncol1 = nc ? (long long)c->fine[0] * c->fine[1] : 0;
+    std::vector<double> col((size_t)(ncol0 + ncol1) * CS);
     Lagrange L(T.gll);
     std::vector<double> lq(Q * N), dq(Q * N), la(N * N), l0(N), l1(N);
     for (int q = 0; q < Q; ++q) L.eval(T.gq[q], &lq[q * N], &dq[q * N]);
     for (int q = 0; q < N; ++q) L.eval(T.ga[q], &la[q * N], nullptr);
-    const double dx = d->Lx / d->nx, dy = d->Ly / d->ny;
+    // the tables of one column from its nodal heights hn (N x N) and cell sizes
+    auto column = [&](const double *hn, double dx, double dy, double dz, double H, double *cp) {
+      for (int j = 0; j < Q; ++j)
+        for (int i = 0; i < Q; ++i) {
+          double h = 0, h1 = 0, h2 = 0;
+          for (int b = 0; b < N; ++b)
+            for (int a = 0; a < N; ++a) {
+              const double v = hn[a + N * b];
+              h += lq[i * N + a] * lq[j * N + b] * v;
+              h1 += dq[i * N + a] * lq[j * N + b] * v;
+              h2 += lq[i * N + a] * dq[j * N + b] * v;
+            }
+          cp[col_off_hq(N, Q) + i + Q * j] = h;
+          cp[col_off_h1q(N, Q) + i + Q * j] = h1;
+          cp[col_off_h2q(N, Q) + i + Q * j] = h2;
+        }
+      for (int s = 0; s < 2; ++s)
+        for (int j = 0; j < Q; ++j) {
+          double hx = 0, hy = 0;
+          const int e0 = s ? N - 1 : 0;
+          for (int m = 0; m < N; ++m) {
+            hx += lq[j * N + m] * hn[e0 + N * m];
+            hy += lq[j * N + m] * hn[m + N * e0];
+          }
+          cp[col_off_hx(N, Q, s) + j] = hx;
+          cp[col_off_hy(N, Q, s) + j] = hy;
+        }
+      for (int j = 0; j < N; ++j)
+        for (int i = 0; i < N; ++i) {
+          double h = 0;
+          for (int b = 0; b < N; ++b)
+            for (int a = 0; a < N; ++a) h += la[i * N + a] * la[j * N + b] * hn[a + N * b];
+          cp[col_off_hqa(N, Q) + i + N * j] = h;
+        }
+      const double invH = 1.0 / H;
+      for (int j = 0; j < Q; ++j)
+        for (int i = 0; i < Q; ++i) {
+          const int t = i + Q * j;
+          const double w = T.gw[i] * T.gw[j], e = 1.0 - cp[col_off_hq(N, Q) + t] * invH;
+          cp[col_off_w(N, Q, 0) + t] = w * dy * dz * e;
+          cp[col_off_w(N, Q, 1) + t] = w * dx * dz * e;
+          cp[col_off_w(N, Q, 2) + t] = w * dx * dy;
+          cp[col_off_w(N, Q, 3) + t] = -w * dy * cp[col_off_h1q(N, Q) + t];
+          cp[col_off_w(N, Q, 4) + t] = -w * dx * cp[col_off_h2q(N, Q) + t];
+          cp[col_off_w(N, Q, 5) + t] = w * dx * dy * dz * e;
+        }
+      // positive cell heights: h < H at every point
+      for (int k = 0; k < Q * Q; ++k)
+        if (cp[k] >= H) return false;
+      return true;
+    };
+    const double dx = d->Lx / d->nx, dy = d->Ly / d->ny, dz = d->Lz / d->nz;
     std::vector<double> hn(N * N);
+    auto base_heights = [&](long long cx, long long cy, double *h) {
+      for (int b = 0; b < N; ++b)
+        for (int a = 0; a < N; ++a) h[a + N * b] = terrain_h(*d, (cx + T.gll[a]) * dx, (cy + T.gll[b]) * dy);
+    };
     for (long long cy = 0; cy < d->ny; ++cy)
       for (long long cx = 0; cx < d->nx; ++cx) {
-        for (int b = 0; b < N; ++b)
-          for (int a = 0; a < N; ++a) hn[a + N * b] = terrain_h(*d, (cx + T.gll[a]) * dx, (cy + T.gll[b]) * dy);
-        double *cp = &col[(size_t)(cx + d->nx * cy) * CS];
-        for (int j = 0; j < Q; ++j)
-          for (int i = 0; i < Q; ++i) {
-            double h = 0, h1 = 0, h2 = 0;
-            for (int b = 0; b < N; ++b)
-              for (int a = 0; a < N; ++a) {
-                const double v = hn[a + N * b];
-                h += lq[i * N + a] * lq[j * N + b] * v;
-                h1 += dq[i * N + a] * lq[j * N + b] * v;
-                h2 += lq[i * N + a] * dq[j * N + b] * v;
-              }
-            cp[col_off_hq(N, Q) + i + Q * j] = h;
-            cp[col_off_h1q(N, Q) + i + Q * j] = h1;
-            cp[col_off_h2q(N, Q) + i + Q * j] = h2;
-          }
-        for (int s = 0; s < 2; ++s)
-          for (int j = 0; j < Q; ++j) {
-            double hx = 0, hy = 0;
-            const int e0 = s ? N - 1 : 0;
-            for (int m = 0; m < N; ++m) {
-              hx += lq[j * N + m] * hn[e0 + N * m];
-              hy += lq[j * N + m] * hn[m + N * e0];
-            }
-            cp[col_off_hx(N, Q, s) + j] = hx;
-            cp[col_off_hy(N, Q, s) + j] = hy;
-          }
-        for (int j = 0; j < N; ++j)
-          for (int i = 0; i < N; ++i) {
-            double h = 0;
-            for (int b = 0; b < N; ++b)
-              for (int a = 0; a < N; ++a) h += la[i * N + a] * la[j * N + b] * hn[a + N * b];
-            cp[col_off_hqa(N, Q) + i + N * j] = h;
-          }
-        {
-          const double dz = d->Lz / d->nz, invH = 1.0 / d->Lz;
-          for (int j = 0; j < Q; ++j)
-            for (int i = 0; i < Q; ++i) {
-              const int t = i + Q * j;
-              const double w = T.gw[i] * T.gw[j], e = 1.0 - cp[col_off_hq(N, Q) + t] * invH;
-              cp[col_off_w(N, Q, 0) + t] = w * dy * dz * e;
-              cp[col_off_w(N, Q, 1) + t] = w * dx * dz * e;
-              cp[col_off_w(N, Q, 2) + t] = w * dx * dy;
-              cp[col_off_w(N, Q, 3) + t] = -w * dy * cp[col_off_h1q(N, Q) + t];
-              cp[col_off_w(N, Q, 4) + t] = -w * dx * cp[col_off_h2q(N, Q) + t];
-              cp[col_off_w(N, Q, 5) + t] = w * dx * dy * dz * e;
-            }
-        }
+        base_heights(cx, cy, hn.data());
+        if (!column(hn.data(), dx, dy, dz, d->Lz, &col[(size_t)(cx + d->nx * cy) * CS]))
+          return set_error(c, DGX_ERR_ARG, "terrain reaches the model top");
       }
-    // each column must keep positive cell heights: h < Lz at every point
-    for (long long i = 0; i < ncol; ++i)
-      for (int k = 0; k < Q * Q; ++k)
-        if (col[(size_t)i * CS + k] >= d->Lz) return set_error(c, DGX_ERR_ARG, "terrain reaches the model top");
+    if (nc) {
+      // children's columns: the parent column's interpolant of h at the child's
+      // nodes (its map restricted), scaled to the block's frame (h' = h (1 - zeta0/H))
+      std::vector<double> hp(N * N), h1((size_t)ncol1 * N * N), lx(N * N * 2);
+      for (int sg = 0; sg < 2; ++sg)
+        for (int a = 0; a < N; ++a) L.eval(0.5 * (sg + T.gll[a]), &lx[(sg * N + a) * N], nullptr);
+      const double H1 = d->Lz - c->zoff, sc = 1.0 - c->zoff / d->Lz;
+      for (long long fy = 0; fy < c->fine[1]; ++fy)
+        for (long long fx = 0; fx < c->fine[0]; ++fx) {
+          base_heights(rf[0] + fx / 2, rf[2] + fy / 2, hp.data());
+          const int sx = (int)(fx % 2), sy = (int)(fy % 2);
+          double *hc = &h1[(size_t)(fx + c->fine[0] * fy) * N * N];
+          for (int b = 0; b < N; ++b)
+            for (int a = 0; a < N; ++a) {
+              double v = 0;
+              for (int bb = 0; bb < N; ++bb)
+                for (int aa = 0; aa < N; ++aa)
+                  v += lx[(sx * N + a) * N + aa] * lx[(sy * N + b) * N + bb] * hp[aa + N * bb];
+              hc[a + N * b] = v;
+              hn[a + N * b] = sc * v;
+            }
+          if (!column(hn.data(), 0.5 * dx, 0.5 * dy, 0.5 * dz, H1, &col[(size_t)(ncol0 + fx + c->fine[0] * fy) * CS]))
+            return set_error(c, DGX_ERR_ARG, "terrain reaches the model top");
+        }
+      if ((e = dalloc(c, &c->hn1, h1.size()))) return e;
+      cudaMemcpy(c->hn1, h1.data(), h1.size() * sizeof(double), cudaMemcpyHostToDevice);
+    }
     std::vector<float> c32(col.begin(), col.end()), cdf(2 * col.size());
     for (size_t k = 0; k < col.size(); ++k) {  // double-words: hi = RN(v), lo = RN(v - hi)
       cdf[2 * k] = (float)col[k];
@@ -1086,6 +1174,8 @@ int dgx_mesh_build(dgx_ctx *c, const dgx_mesh_desc *d) {
     cudaMemcpy(c->col32, c32.data(), c32.size() * sizeof(float), cudaMemcpyHostToDevice);
     cudaMemcpy(c->coldf, cdf.data(), cdf.size() * sizeof(float), cudaMemcpyHostToDevice);
   }
+  if (nc)
+    if ((e = nonconf_setup(c))) return e;
   const size_t Nn = (size_t)c->N;
   if ((e = dalloc(c, &c->V64, 3 * Nn)) || (e = dalloc(c, &c->V32, 3 * Nn)) || (e = dalloc(c, &c->rho64, Nn)) ||
       (e = dalloc(c, &c->pk64, Nn)) || (e = dalloc(c, &c->rho32, Nn)) || (e = dalloc(c, &c->pk32, Nn)))
@@ -1104,8 +1194,7 @@ long long dgx_num_dofs(const dgx_ctx *c) { return (c && c->has_mesh) ? c->N : -1
 int dgx_node_coords(dgx_ctx *c, double *X) {
   if (int e = check_ready(c, false)) return e;
   if (!X) return set_error(c, DGX_ERR_ARG, "null output");
-  count_launch();
-  k_node_coords<<<grid_for(c->N), 256, 0, c->stream>>>(node_params(c), c->N, X);
+  launch_node_coords(c, X);
   return check_cuda(c, cudaGetLastError(), "k_node_coords");
 }
 
@@ -1119,8 +1208,7 @@ int dgx_set_background(dgx_ctx *c, const dgx_background *bg) {
     if ((e = dalloc(c, &c->rho_bar, c->N)) || (e = dalloc(c, &c->p_bar, c->N))) return e;
   }
   double *X = c->V64;  // 3N scratch
-  count_launch();
-  k_node_coords<<<grid_for(c->N), 256, 0, c->stream>>>(node_params(c), c->N, X);
+  launch_node_coords(c, X);
   BgP b{bg->kind, bg->T, bg->p0, bg->N_bv, bg->R, bg->gamma, bg->g};
   count_launch();
   k_background<<<grid_for(c->N), 256, 0, c->stream>>>(b, c->N, X, c->rho_bar, c->p_bar);
@@ -1147,6 +1235,12 @@ int dgx_set_coefficients(dgx_ctx *c, const double *rho, const double *pk, double
   cudaMemcpyAsync(c->pk64, pk, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   vec_convert<float, double>(N, rho, c->rho32, c->stream);
   vec_convert<float, double>(N, pk, c->pk32, c->stream);
+  if (c->nc) {  // dead cells hold no unknowns: benign coefficients keep every kernel finite there
+    int e;
+    if ((e = fill_dead<double>(c, c->rho64, 1, 1.0, c->stream)) || (e = fill_dead<double>(c, c->pk64, 1, 1.0, c->stream)) ||
+        (e = fill_dead<float>(c, c->rho32, 1, 1.0, c->stream)) || (e = fill_dead<float>(c, c->pk32, 1, 1.0, c->stream)))
+      return e;
+  }
   c->alpha = a_dt;
   c->gamma = gamma;
   ++c->coef_version;
@@ -1248,6 +1342,8 @@ int dgx_set_mass_rule(dgx_ctx *c, int rule, double cg_tol, int cg_maxit) {
   if (!c) return DGX_ERR_ARG;
   if (rule != DGX_MASS_FAST && rule != DGX_MASS_CONSISTENT) return set_error(c, DGX_ERR_ARG, "mass rule %d", rule);
   if (!(cg_tol > 0) || cg_maxit < 1) return set_error(c, DGX_ERR_ARG, "need cg_tol > 0 and cg_maxit >= 1");
+  if (c->nc && rule == DGX_MASS_CONSISTENT)
+    return set_error(c, DGX_ERR_STATE, "the consistent mass rule is not available on non-conforming meshes");
   cudaSetDevice(c->device);
   if (!c->mass_stats) {
     if (int e = check_cuda(c, cudaMalloc(&c->mass_stats, 2 * sizeof(int)), "cudaMalloc mass stats")) return e;

@@ -103,6 +103,12 @@ __host__ __device__ constexpr int col_size(int N, int Q) { return 9 * Q * Q + 4 
 template <typename T>
 struct OpP {
   int nx, ny, nz, bc_lat;  // lateral faces: 0 slip wall, 1 far field, 2 periodic
+  // non-conforming meshes: the cells of `hole` (x0, x1, y0, y1, z0, z1) are
+  // dead and every face that touches them is skipped; a face of this patch's
+  // box whose bit (1 << f) is set in `iface` borders the other patch and is
+  // skipped too (its terms come from the hanging-face kernels)
+  int hole[6];
+  int iface, pad_;
   T dx, dy, dz, H;         // cell sizes (dz of the uniform zeta grid) and Lz
   T invH;                  // 1 / Lz (the map's factor 1 - zeta/H without a division per point)
   T alpha;                 // a~_ll * dt
@@ -184,6 +190,22 @@ struct dgx_ctx {
   int mass_maxit = 50;
   int *mass_stats = nullptr;  // device [2]: largest PCG iteration count, unconverged cells
 
+  // non-conforming mesh (mesh.refine box not empty): patch 0 = the nx*ny*nz
+  // base cells (those in the box dead), patch 1 = the children block fine[3]
+  // from cell ncell0 on; the terrain tables of patch 1 follow patch 0's in
+  // col64 / col32 / coldf at column col1_off; hang64 / hang32: the 1D tables
+  // of the hanging-face kernels; hcells: their work list (nhcell cells)
+  bool nc = false;
+  long long ncell0 = 0;
+  int fine[3] = {0, 0, 0};
+  long long col1_off = 0;
+  double zoff = 0.0;      // zeta of the children block's bottom
+  double *hn1 = nullptr;  // nodal terrain heights of the children's columns (node coordinates)
+  double *hang64 = nullptr;
+  float *hang32 = nullptr;
+  void *hcells = nullptr;
+  int nhcell = 0;
+
   // launch variant of the operator kernels per precision ([0] FP64, [1] FP32):
   // 0..2 one cell per CTA (k_grad / k_div) with 128 / 192 / 256 threads, 3..4
   // the fused multi-cell kernels in configuration v - 3 (fused_cpb), 5..6 (FP64
@@ -232,6 +254,9 @@ void count_launch(int n = 1);
 long long launch_count();
 int check_cuda(dgx_ctx *c, cudaError_t e, const char *what);
 
+// 1D Gauss and Gauss-Lobatto rules on [0, 1] (dgx_api.cu)
+void rule_gauss(int q, std::vector<double> &x, std::vector<double> &w);
+void rule_gll(int n, std::vector<double> &x, std::vector<double> &w);
 // host 1D table block of degree r (layout above), dgx_api.cu
 bool build_table_block(int r, std::vector<double> &tab);
 // multigrid transfer tables of degree r (dgx_api.cu), GLL nodes x_a on [0, 1]:
@@ -318,10 +343,34 @@ int launch_diag(dgx_ctx *c, const T *rho, const T *pk, T *dh, T *die, cudaStream
 // FP64 (diag64, dinv64, and dinv32 rounded from them) or, when only FP32 is
 // needed (the mixed solver's inner GMRES), the FP32 diagonal kernel (dinv32).
 int ensure_diag(dgx_ctx *c, bool f64);
+// kernel parameters of patch `patch` (0, or 1 = the children block of a
+// non-conforming mesh)
 template <typename T>
-OpP<T> make_params(const dgx_ctx *c);
+OpP<T> make_params(const dgx_ctx *c, int patch = 0);
 template <>
-OpP<df64> make_params<df64>(const dgx_ctx *c);
+OpP<df64> make_params<df64>(const dgx_ctx *c, int patch);
+// patches of the mesh: one, or two on non-conforming meshes (the base cells,
+// then the children block); first cell and number of cells of each
+inline int num_patches(const dgx_ctx *c) { return c->nc ? 2 : 1; }
+inline long long patch_cell0(const dgx_ctx *c, int i) { return i ? c->ncell0 : 0; }
+inline long long patch_ncell(const dgx_ctx *c, int i) {
+  return c->nc ? (i ? c->ncell - c->ncell0 : c->ncell0) : c->ncell;
+}
+// hanging-face terms of non-conforming meshes (dgx_nonconf.cu), added to what
+// the per-patch kernels wrote: V += A^-1 B_h p (inv) or V += B_h p; y -= C_h V;
+// explicit tendencies += the hanging faces' flux terms
+template <typename T>
+int launch_hang_grad(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s, bool inv, double alpha);
+template <typename T>
+int launch_hang_div(dgx_ctx *c, const T *V, const T *pk, T *y, cudaStream_t s, double alpha);
+int launch_hang_explicit(dgx_ctx *c, const double *rho, const double *u, double *Er, double *Em, double *Ee,
+                         cudaStream_t s);
+// x[cell * n3 + node] = v on the dead cells of a non-conforming mesh (nf fields of stride N)
+template <typename T>
+int fill_dead(dgx_ctx *c, T *x, int nf, double v, cudaStream_t s);
+// mesh set-up of a non-conforming mesh (dgx_nonconf.cu): the hanging-face work
+// list and tables (after the patches' cells and tables are known)
+int nonconf_setup(dgx_ctx *c);
 // operator launch variants (see dgx_ctx::op_variant): count, whether variant v
 // fits this context's mesh and precision, and its threads per CTA
 constexpr int kOpVariants = 7;

@@ -654,6 +654,7 @@ int dgx_ensemble_create(dgx_ensemble **out, int device, void *stream, int n, con
     e->mem.push_back(c);
     r = dgx_mesh_build(c, &descs[m]);
     if (r) return fail(eset(e, r, "member %d: %s", m, c->err.c_str()));
+    if (c->nc) return fail(eset(e, DGX_ERR_STATE, "member %d: ensembles take conforming meshes only", m));
     e->N.push_back(c->N);
     e->off.push_back(e->Ntot);
     e->Ntot += c->N;

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(256) k_explicit(const ExP X, const double *__r
   T *Wy = R1, *Wz = R2;
   const long long cell = blockIdx.x;
   const CellPos cp = cell_pos(P, cell);
-  __shared__ long long s_nb[6];  // the six face neighbours (-1: boundary), read after the first barrier
+  __shared__ long long s_nb[6];  // the six face neighbours (-1: boundary, -2: skipped), read after the first barrier
   if (threadIdx.x < 6) s_nb[threadIdx.x] = neighbour(P, cp, threadIdx.x);
   const T *colp = CURVED ? P.col + (long long)(cp.cx + P.nx * cp.cy) * col_size(N, Q) : nullptr;
   const T zeta0 = T(cp.cz) * P.dz;
@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(256) k_explicit(const ExP X, const double *__r
   for (int f = 0; f < 6; ++f) {
     const int kd = f >> 1, s = f & 1;
     const long long nb = s_nb[f];
+    if (nb == -2) continue;  // non-conforming meshes: the hanging-face kernel's (uniform per CTA)
     const bool wall = nb < 0 && (kd == 2 || P.bc_lat == 0);
     const bool far = nb < 0 && !wall;
     for (int idx = threadIdx.x; idx < 8 * N2; idx += blockDim.x) {
@@ -336,27 +337,27 @@ int explicit_impl(dgx_ctx *c, const double *rho, const double *u, const double *
   const size_t smem = sizeof(double) * ExL<N, Q>::total;
   auto k = k_explicit<N, Q, CURVED>;
   if (int e = prep2(c, k, smem)) return e;
-  ExP X{make_params<double>(c), c->bg.g, c->bg.u_bar};
-  count_launch();
-  k<<<(unsigned)c->ncell, 256, smem, s>>>(X, rho, u, rho_bar, Er, Em, Ee, c->N);
-  return check_cuda(c, cudaGetLastError(), "k_explicit launch");
+  for (int pi = 0; pi < num_patches(c); ++pi) {
+    ExP X{make_params<double>(c, pi), c->bg.g, c->bg.u_bar};
+    const long long o = patch_cell0(c, pi) * N * N * N;
+    count_launch();
+    k<<<(unsigned)patch_ncell(c, pi), 256, smem, s>>>(X, rho + o, u + o, rho_bar + o, Er + o, Em + o, Ee + o, c->N);
+  }
+  if (int e = check_cuda(c, cudaGetLastError(), "k_explicit launch")) return e;
+  return c->nc ? launch_hang_explicit(c, rho, u, Er, Em, Ee, s) : 0;
 }
 
 template <int N, bool CURVED>
 int cmass_impl(dgx_ctx *c, int mode, double scale, const double *f0, const double *fv, double *out, cudaStream_t s) {
   constexpr int Q = 2 * N - 1;
   const size_t smem = sizeof(double) * CmL<N, Q>::total;
-  const OpP<double> P = make_params<double>(c);
-  if (mode == 0) {
-    auto k = k_cmass<N, Q, CURVED, 0>;
-    if (int e = prep2(c, k, smem)) return e;
+  auto k = mode == 0 ? k_cmass<N, Q, CURVED, 0> : k_cmass<N, Q, CURVED, 1>;
+  if (int e = prep2(c, k, smem)) return e;
+  for (int pi = 0; pi < num_patches(c); ++pi) {
+    const long long o = patch_cell0(c, pi) * N * N * N;
     count_launch();
-    k<<<(unsigned)c->ncell, 128, smem, s>>>(P, scale, f0, fv, out, c->N);
-  } else {
-    auto k = k_cmass<N, Q, CURVED, 1>;
-    if (int e = prep2(c, k, smem)) return e;
-    count_launch();
-    k<<<(unsigned)c->ncell, 128, smem, s>>>(P, scale, f0, fv, out, c->N);
+    k<<<(unsigned)patch_ncell(c, pi), 128, smem, s>>>(make_params<double>(c, pi), scale, f0 + o, fv ? fv + o : nullptr,
+                                                      out + o, c->N);
   }
   return check_cuda(c, cudaGetLastError(), "k_cmass launch");
 }
@@ -367,8 +368,11 @@ int massfwd_impl(dgx_ctx *c, const double *rho, const double *v, double *out, cu
   const size_t smem = sizeof(double) * MfL<N, Q>::total;
   auto k = k_mass_fwd<N, Q, CURVED>;
   if (int e = prep2(c, k, smem)) return e;
-  count_launch();
-  k<<<(unsigned)c->ncell, 128, smem, s>>>(make_params<double>(c), rho, v, out, c->N);
+  for (int pi = 0; pi < num_patches(c); ++pi) {
+    const long long o = patch_cell0(c, pi) * N * N * N;
+    count_launch();
+    k<<<(unsigned)patch_ncell(c, pi), 128, smem, s>>>(make_params<double>(c, pi), rho + o, v + o, out + o, c->N);
+  }
   return check_cuda(c, cudaGetLastError(), "k_mass_fwd launch");
 }
 

@@ -221,27 +221,36 @@ __device__ __forceinline__ void sts(U *p, const T *r) {
 }
 
 // Neighbour across face f (2k+s) of cell `cell` (32-bit index arithmetic), -1 on
-// the boundary; x and y wrap around with periodic lateral faces.
+// the boundary; x and y wrap around with periodic lateral faces; -2 for a face
+// the kernel skips (non-conforming meshes: dead cells, the patch interface).
+template <typename T>
+__device__ __forceinline__ bool hole32(const OpP<T> &P, int x, int y, int z) {
+  return x >= P.hole[0] && x < P.hole[1] && y >= P.hole[2] && y < P.hole[3] && z >= P.hole[4] && z < P.hole[5];
+}
 template <typename T>
 __device__ __forceinline__ int nb32(const OpP<T> &P, int cx, int cy, int cz, int f) {
   const int k = f >> 1, s = f & 1;
   int x = cx, y = cy, z = cz;
+  if (hole32(P, x, y, z)) return -2;
   if (k == 0) {
     x += s ? 1 : -1;
     if (x < 0 || x >= P.nx) {
+      if (P.iface & (1 << f)) return -2;
       if (P.bc_lat != 2) return -1;
       x = x < 0 ? P.nx - 1 : 0;
     }
   } else if (k == 1) {
     y += s ? 1 : -1;
     if (y < 0 || y >= P.ny) {
+      if (P.iface & (1 << f)) return -2;
       if (P.bc_lat != 2) return -1;
       y = y < 0 ? P.ny - 1 : 0;
     }
   } else {
     z += s ? 1 : -1;
-    if (z < 0 || z >= P.nz) return -1;
+    if (z < 0 || z >= P.nz) return (P.iface & (1 << f)) ? -2 : -1;
   }
+  if (hole32(P, x, y, z)) return -2;
   return x + P.nx * (y + P.ny * z);
 }
 
@@ -403,7 +412,7 @@ __device__ __forceinline__ void kf_grad_body(const OpP<T> &P, const store_t<T> *
           const T own = p[(long long)cell * N3 + face_node<N>(k, s ? N - 1 : 0, t1, t2)];
           T ph = own;
           if (nb >= 0) ph = T(0.5) * (own + p[(long long)nb * N3 + face_node<N>(k, s ? 0 : N - 1, t1, t2)]);
-          else if (k < 2 && P.bc_lat == 1) ph = T(0);
+          else if (nb == -2 || (k < 2 && P.bc_lat == 1)) ph = T(0);
           x[t1] = ph;
         }
         mv<T, N, M_I, Q, N>(x, y);
@@ -764,7 +773,7 @@ __device__ __forceinline__ void kf_div_body(const OpP<T> &P, const store_t<T> *_
         const int k = f >> 1, s = f & 1, nb = ci.nb[cl][f];
         T x[N], o[Q];
         if (side == 0 || nb < 0) {
-          const bool wall = nb < 0 && (k == 2 || P.bc_lat == 0);
+          const bool wall = nb == -2 || (nb < 0 && (k == 2 || P.bc_lat == 0));
 #pragma unroll
           for (int t1 = 0; t1 < N; ++t1) {
             const long long node = (long long)cell * N3 + face_node<N>(k, s ? N - 1 : 0, t1, t2);

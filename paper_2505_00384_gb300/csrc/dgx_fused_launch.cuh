@@ -32,29 +32,42 @@ int fprep(dgx_ctx *c, Kern k, size_t smem) {
   return check_cuda(c, e, "cudaFuncSetAttribute (fused operator)");
 }
 
+// One launch per patch of the mesh (two on non-conforming meshes), each on its
+// own cells with its own parameters; the component stride stays c->N.
 template <typename T, int N, bool CURVED, bool INV, int CPB, int NT>
-int fgrad_go(dgx_ctx *c, const OpP<T> &P, const store_t<T> *p, const store_t<T> *rho, store_t<T> *V,
-             cudaStream_t s) {
+int fgrad_go(dgx_ctx *c, double alpha, const store_t<T> *p, const store_t<T> *rho, store_t<T> *V, cudaStream_t s) {
   const size_t smem = sizeof(T) * (size_t)CPB * FGradL<N, CURVED>::per_cell;
   if (smem > kFusedMaxSmem) return set_error(c, DGX_ERR_ARG, "fused gradient kernel: %zu bytes of shared memory", smem);
   auto k = kf_grad<T, N, CURVED, INV, CPB, NT>;
   if (int e = fprep(c, k, smem)) return e;
-  const int ncell = (int)c->ncell;
-  count_launch();
-  k<<<(unsigned)((ncell + CPB - 1) / CPB), NT, smem, s>>>(P, p, rho, V, c->N, ncell);
+  for (int pi = 0; pi < num_patches(c); ++pi) {
+    OpP<T> P = make_params<T>(c, pi);
+    if (alpha >= 0.0) P.alpha = (T)alpha;
+    const int ncell = (int)patch_ncell(c, pi);
+    const long long o = patch_cell0(c, pi) * N * N * N;
+    count_launch();
+    k<<<(unsigned)((ncell + CPB - 1) / CPB), NT, smem, s>>>(P, p + o, rho + o, V + o, c->N, ncell);
+  }
   return check_cuda(c, cudaGetLastError(), "kf_grad launch");
 }
 
 template <typename T, int N, bool CURVED, bool KQ, int CPB, int NT>
-int fdiv_go(dgx_ctx *c, const OpP<T> &P, const store_t<T> *V, const store_t<T> *p, const store_t<T> *pk,
-            store_t<T> *y, const store_t<T> *kq, cudaStream_t s) {
+int fdiv_go(dgx_ctx *c, double alpha, const store_t<T> *V, const store_t<T> *p, const store_t<T> *pk, store_t<T> *y,
+            const store_t<T> *kq, cudaStream_t s) {
   const size_t smem = sizeof(T) * (size_t)CPB * FDivL<N, CURVED, KQ>::per_cell;
   if (smem > kFusedMaxSmem) return set_error(c, DGX_ERR_ARG, "fused divergence kernel: %zu bytes of shared memory", smem);
   auto k = kf_div<T, N, CURVED, KQ, CPB, NT>;
   if (int e = fprep(c, k, smem)) return e;
-  const int ncell = (int)c->ncell;
-  count_launch();
-  k<<<(unsigned)((ncell + CPB - 1) / CPB), NT, smem, s>>>(P, V, p, pk, y, c->N, ncell, kq);
+  constexpr int Q = 2 * N - 1;
+  for (int pi = 0; pi < num_patches(c); ++pi) {
+    OpP<T> P = make_params<T>(c, pi);
+    if (alpha >= 0.0) P.alpha = (T)alpha;
+    const int ncell = (int)patch_ncell(c, pi);
+    const long long o = patch_cell0(c, pi) * N * N * N, oq = patch_cell0(c, pi) * Q * Q * Q;
+    count_launch();
+    k<<<(unsigned)((ncell + CPB - 1) / CPB), NT, smem, s>>>(P, V + o, p + o, pk + o, y + o, c->N, ncell,
+                                                           kq ? kq + oq : nullptr);
+  }
   return check_cuda(c, cudaGetLastError(), "kf_div launch");
 }
 
@@ -64,28 +77,24 @@ template <typename T, int N, bool CURVED>
 int fused_grad(dgx_ctx *c, const store_t<T> *p, const store_t<T> *rho, store_t<T> *V, cudaStream_t s, bool inv,
                double alpha, int cfg) {
   if (int e = upload_fused_tables(c)) return e;
-  OpP<T> P = make_params<T>(c);
-  if (alpha >= 0.0) P.alpha = (T)alpha;
-  if (!inv) return fgrad_go<T, N, CURVED, false, fused_cpb(N, 0), fused_nt(N, 0)>(c, P, p, rho, V, s);
-  if (cfg == 1) return fgrad_go<T, N, CURVED, true, fused_cpb(N, 1), fused_nt(N, 1)>(c, P, p, rho, V, s);
-  return fgrad_go<T, N, CURVED, true, fused_cpb(N, 0), fused_nt(N, 0)>(c, P, p, rho, V, s);
+  if (!inv) return fgrad_go<T, N, CURVED, false, fused_cpb(N, 0), fused_nt(N, 0)>(c, alpha, p, rho, V, s);
+  if (cfg == 1) return fgrad_go<T, N, CURVED, true, fused_cpb(N, 1), fused_nt(N, 1)>(c, alpha, p, rho, V, s);
+  return fgrad_go<T, N, CURVED, true, fused_cpb(N, 0), fused_nt(N, 0)>(c, alpha, p, rho, V, s);
 }
 
 template <typename T, int N, bool CURVED>
 int fused_div(dgx_ctx *c, const store_t<T> *V, const store_t<T> *p, const store_t<T> *pk, store_t<T> *y,
               cudaStream_t s, double alpha, const store_t<T> *kq, int cfg) {
   if (int e = upload_fused_tables(c)) return e;
-  OpP<T> P = make_params<T>(c);
-  if (alpha >= 0.0) P.alpha = (T)alpha;
   if constexpr (sizeof(store_t<T>) == 8) {
     if (kq) {
-      if (cfg == 1) return fdiv_go<T, N, CURVED, true, fused_cpb(N, 1), fused_nt(N, 1)>(c, P, V, p, pk, y, kq, s);
-      return fdiv_go<T, N, CURVED, true, fused_cpb(N, 0), fused_nt(N, 0)>(c, P, V, p, pk, y, kq, s);
+      if (cfg == 1) return fdiv_go<T, N, CURVED, true, fused_cpb(N, 1), fused_nt(N, 1)>(c, alpha, V, p, pk, y, kq, s);
+      return fdiv_go<T, N, CURVED, true, fused_cpb(N, 0), fused_nt(N, 0)>(c, alpha, V, p, pk, y, kq, s);
     }
-    return fdiv_go<T, N, CURVED, false, fused_cpb(N, 0), fused_nt(N, 0)>(c, P, V, p, pk, y, nullptr, s);
+    return fdiv_go<T, N, CURVED, false, fused_cpb(N, 0), fused_nt(N, 0)>(c, alpha, V, p, pk, y, nullptr, s);
   } else {
-    if (cfg == 1) return fdiv_go<T, N, CURVED, false, fused_cpb(N, 1), fused_nt(N, 1)>(c, P, V, p, pk, y, nullptr, s);
-    return fdiv_go<T, N, CURVED, false, fused_cpb(N, 0), fused_nt(N, 0)>(c, P, V, p, pk, y, nullptr, s);
+    if (cfg == 1) return fdiv_go<T, N, CURVED, false, fused_cpb(N, 1), fused_nt(N, 1)>(c, alpha, V, p, pk, y, nullptr, s);
+    return fdiv_go<T, N, CURVED, false, fused_cpb(N, 0), fused_nt(N, 0)>(c, alpha, V, p, pk, y, nullptr, s);
   }
 }
 

@@ -120,6 +120,7 @@ int dgx_imex_step(dgx_ctx *c, double *rho, double *u, double *p, int nsteps, con
                   dgx_step_info *info) {
   if (int e = ready(c)) return e;
   if (!c->has_imex) return set_error(c, DGX_ERR_STATE, "no tableau (call dgx_set_imex)");
+  if (c->nc) return set_error(c, DGX_ERR_STATE, "the IMEX step is not available on non-conforming meshes");
   if (!rho || !u || !p || nsteps < 0) return set_error(c, DGX_ERR_ARG, "null state array or negative step count");
   const auto t0 = std::chrono::steady_clock::now();
   dgx_solve_opts o;

@@ -187,6 +187,183 @@ __global__ void __launch_bounds__(16 * KS) k_conv(ConvArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- tensor-core convolution
+// Layers with 32 input and 32 output channels at training batch sizes run as
+// implicit GEMMs on the 5th-generation tensor cores: tcgen05.mma (kind::f16,
+// bf16 operands, FP32 accumulator in tensor memory), issued by one thread.
+// One CTA computes M = 128 output points (a tile of 8 x 16 x 1 points in x, y,
+// z) x N = 32 output channels; K runs over 27 taps x 32 input channels.
+//
+// The input halo (10 x 18 x 3 points) is staged once in shared memory in the
+// canonical no-swizzle K-major layout: channels in chunks of 8 (16 bytes),
+// chunk planes one after the other, x fastest within a plane.  Eight points
+// consecutive in x then form one 8 x 16-byte core matrix, so the A operand of
+// tap (dx, dy, dz) is just a descriptor at the halo point (dx, dy, dz): the
+// 16 rows of 8 points are one halo row (160 bytes) apart, the two channel
+// chunks of a K = 16 step one chunk plane apart.  No per-tap copy.  The
+// weights are staged as [tap][chunk][co][8 channels] (B operand, K-major).
+// FP32 activations are split into bf16 high parts and bf16 remainders, x = hi
+// + lo to 2^-16 relative; both are multiplied with the (exactly bf16) weights,
+// so the product keeps about FP32 accuracy (108 MMAs of 128 x 32 x 16 per tile).
+constexpr int kTcX = 8, kTcY = 16, kTcHX = kTcX + 2, kTcHY = kTcY + 2, kTcHZ = 3;
+constexpr int kTcHP = kTcHX * kTcHY * kTcHZ;      // 540 halo points
+constexpr int kTcPlane = kTcHP * 16;              // bytes of one 8-channel chunk plane
+constexpr int kTcHalo = 4 * kTcPlane;             // one part (hi or lo), 32 channels
+constexpr int kTcW = 27 * 4 * 32 * 16;            // weights
+constexpr int kTcMbar = 2 * kTcHalo + kTcW;       // mbarrier (8 bytes) and the TMEM address
+constexpr int kTcSmem = 200 * 1024;               // with headroom beyond the operands
+constexpr int kTcMinBatch = 8;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor, no swizzle: start address, byte offset
+// between core matrices along K (lbo) and along M / N (sbo), version 1.
+__device__ __forceinline__ unsigned long long tc_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+  return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both
+// K-major, N = 32, M = 128.
+constexpr unsigned kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(unsigned dtmem, unsigned long long a, unsigned long long b, unsigned acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(kTcIdesc), "r"(acc));
+}
+
+// Bounded wait for phase `ph` of the mbarrier: false after `limit` polls.
+__device__ __forceinline__ bool tc_wait(unsigned bar, unsigned ph, int limit) {
+  for (int i = 0; i < limit; ++i) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok) : "r"(bar), "r"(ph) : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs a, int *err) {
+  extern __shared__ __align__(128) unsigned char tsm[];
+  unsigned char *hi = tsm, *lo = tsm + kTcHalo, *ws = tsm + 2 * kTcHalo;
+  unsigned long long *bar = reinterpret_cast<unsigned long long *>(tsm + kTcMbar);
+  unsigned *taddr_s = reinterpret_cast<unsigned *>(tsm + kTcMbar + 8);
+  const Grid3 &g = a.g;
+  const int nxt = (g.X + kTcX - 1) / kTcX, nyt = (g.Y + kTcY - 1) / kTcY;
+  const int tile = blockIdx.x, b = blockIdx.z;
+  const int tx = tile % nxt, ty = (tile / nxt) % nyt, tz = tile / (nxt * nyt);
+  const int x0 = tx * kTcX - 1, y0 = ty * kTcY - 1, z0 = tz - 1;
+  const long long sb = a.bidx ? a.bidx[b] : b;
+  const float *in = a.in + sb * a.in_bs;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {  // 32 TMEM columns (FP32 accumulators of N = 32), address into shared memory
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(taddr_s)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // halo: (chunk, point) items, point fastest (coalesced along x); hi / lo bf16 parts of 8 channels
+  for (int it = threadIdx.x; it < 4 * kTcHP; it += blockDim.x) {
+    const int c = it / kTcHP, pnt = it - c * kTcHP;
+    const int hx = pnt % kTcHX, hy = (pnt / kTcHX) % kTcHY, hz = pnt / (kTcHX * kTcHY);
+    const int gx = x0 + hx, gy = y0 + hy, gz = z0 + hz;
+    unsigned short h[8], l[8];
+    if (gx >= 0 && gx < g.X && gy >= 0 && gy < g.Y && gz >= 0 && gz < g.Z) {
+      const float *src = in + (long long)(8 * c) * g.G + gx + (long long)g.X * (gy + (long long)g.Y * gz);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        float v = src[(long long)j * g.G];
+        if (a.relu_in) v = fmaxf(v, 0.f);
+        const __nv_bfloat16 vh = __float2bfloat16_rn(v);
+        const __nv_bfloat16 vl = __float2bfloat16_rn(v - __bfloat162float(vh));
+        h[j] = __bfloat16_as_ushort(vh);
+        l[j] = __bfloat16_as_ushort(vl);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) h[j] = l[j] = 0;
+    }
+    uint4 uh, ul;
+    uh.x = h[0] | ((unsigned)h[1] << 16); uh.y = h[2] | ((unsigned)h[3] << 16);
+    uh.z = h[4] | ((unsigned)h[5] << 16); uh.w = h[6] | ((unsigned)h[7] << 16);
+    ul.x = l[0] | ((unsigned)l[1] << 16); ul.y = l[2] | ((unsigned)l[3] << 16);
+    ul.z = l[4] | ((unsigned)l[5] << 16); ul.w = l[6] | ((unsigned)l[7] << 16);
+    *reinterpret_cast<uint4 *>(hi + c * kTcPlane + pnt * 16) = uh;
+    *reinterpret_cast<uint4 *>(lo + c * kTcPlane + pnt * 16) = ul;
+  }
+  // weights W[(ci 27 + tap) Co + co] -> [tap][ci / 8][co][ci % 8]; co fastest across threads
+  for (int it = threadIdx.x; it < 27 * 4 * 32; it += blockDim.x) {
+    const int co = it % 32, c = (it / 32) % 4, tap = it / 128;
+    unsigned short w[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) w[j] = __bfloat16_as_ushort(a.W[((long long)(8 * c + j) * 27 + tap) * 32 + co]);
+    uint4 u;
+    u.x = w[0] | ((unsigned)w[1] << 16); u.y = w[2] | ((unsigned)w[3] << 16);
+    u.z = w[4] | ((unsigned)w[5] << 16); u.w = w[6] | ((unsigned)w[7] << 16);
+    *reinterpret_cast<uint4 *>(ws + ((tap * 4 + c) * 32 + co) * 16) = u;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = *taddr_s;
+  if (threadIdx.x == 0) {
+    unsigned acc = 0;
+    for (int part = 0; part < 2; ++part) {
+      const unsigned base = smem_u32(part ? lo : hi);
+      for (int tap = 0; tap < 27; ++tap) {
+        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+        const unsigned aoff = ((dz * kTcHY + dy) * kTcHX + dx) * 16;
+        for (int ks = 0; ks < 2; ++ks) {
+          const unsigned long long ad = tc_desc(base + 2 * ks * kTcPlane + aoff, kTcPlane, kTcHX * 16);
+          const unsigned long long bd = tc_desc(smem_u32(ws) + (tap * 4 + 2 * ks) * 512, 512, 128);
+          tc_mma(tmem, ad, bd, acc);
+          acc = 1;
+        }
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+  }
+  const bool ok = tc_wait(smem_u32(bar), 0, 1 << 22);
+  if (!ok && lane == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    unsigned r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(tmem + ((unsigned)(warp * 32) << 16)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    // row m = 32 warp + lane of D: point (x0 + 1 + m % 8, y0 + 1 + m / 8, z0 + 1)
+    const int m = warp * 32 + lane;
+    const int gx = x0 + 1 + (m & 7), gy = y0 + 1 + (m >> 3), gz = z0 + 1;
+    if (gx < g.X && gy < g.Y) {
+      const long long gi = gx + (long long)g.X * (gy + (long long)g.Y * gz);
+#pragma unroll
+      for (int co = 0; co < 32; ++co) {
+        float v = __uint_as_float(r[co]);
+        if (a.bias) v += a.bias[co];
+        if (a.mask && !(a.mask[b * a.mask_bs + co * g.G + gi] > 0.f)) v = 0.f;
+        a.out[b * a.out_bs + co * g.G + gi] = v;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+}
+
 struct WgArgs {
   Grid3 g;
   int Ci, Co;
@@ -516,6 +693,7 @@ struct Learned {
   long long bidx_cap = 0;
   double *lpart = nullptr;
   double *host_lpart = nullptr;
+  int *tc_err = nullptr;  // set by a tensor-core convolution whose MMAs did not complete in time
 };
 
 namespace {
@@ -557,8 +735,10 @@ void free_graphs(Learned *m) {
 
 void free_net(Learned *m) {
   free_graphs(m);
-  for (void *p : {(void *)m->master, (void *)m->am, (void *)m->av, (void *)m->grad, (void *)m->wbf, (void *)m->wtbf})
+  for (void *p : {(void *)m->master, (void *)m->am, (void *)m->av, (void *)m->grad, (void *)m->wbf, (void *)m->wtbf,
+                  (void *)m->tc_err})
     if (p) cudaFree(p);
+  m->tc_err = nullptr;
   m->master = m->am = m->av = m->grad = nullptr;
   m->wtbf = nullptr;
   m->wbf = nullptr;
@@ -576,6 +756,19 @@ int dmalloc(dgx_ctx *c, T **p, size_t elems) {
   if (int e = check_cuda(c, cudaMalloc(&q, std::max<size_t>(1, elems) * sizeof(T)), "cudaMalloc (learned)")) return e;
   *p = reinterpret_cast<T *>(q);
   return 0;
+}
+
+// Error flag of the tensor-core convolutions (read after a synchronisation):
+// DGX_ERR_DEVICE_TIMEOUT (and the flag cleared) when an MMA batch did not complete.
+int tc_status(dgx_ctx *c) {
+  Learned *m = c->learned;
+  if (!m || !m->tc_err) return 0;
+  int flag = 0;
+  if (int e = check_cuda(c, cudaMemcpy(&flag, m->tc_err, sizeof(int), cudaMemcpyDeviceToHost), "tensor-core status"))
+    return e;
+  if (!flag) return 0;
+  cudaMemset(m->tc_err, 0, sizeof(int));
+  return set_error(c, DGX_ERR_DEVICE_TIMEOUT, "tensor-core convolution: MMAs did not complete within the wait limit");
 }
 
 // Host-to-device copy ordered on the context's stream; returns when done.
@@ -672,6 +865,14 @@ int launch_conv_t(dgx_ctx *c, const ConvArgs &a, int B) {
 // of CTAs fills the GPU several times over (training batches), else 4 x 16
 // (more, shorter threads for single-sample inference); output layer 1 x 16.
 int launch_conv(dgx_ctx *c, const ConvArgs &a, int B) {
+  if (a.Ci == 32 && a.Co == 32 && B >= kTcMinBatch) {  // training batches: tensor cores
+    Learned *m = c->learned;
+    if (int e = prep(c, (const void *)k_conv_tc)) return e;
+    const int tiles = ((a.g.X + kTcX - 1) / kTcX) * ((a.g.Y + kTcY - 1) / kTcY) * a.g.Z;
+    count_launch();
+    k_conv_tc<<<dim3(tiles, 1, B), 128, kTcSmem, c->stream>>>(a, m->tc_err);
+    return check_cuda(c, cudaGetLastError(), "k_conv_tc");
+  }
   if (a.Co % 8 == 0 && (long long)a.g.tiles() * (a.Co / 8) * B >= 4 * 152) return launch_conv_t<8, 8>(c, a, B);
   if (a.Co % 4 == 0) return launch_conv_t<4, 16>(c, a, B);
   return launch_conv_t<1, 16>(c, a, B);
@@ -946,6 +1147,7 @@ int check_learned(dgx_ctx *c) {
   if (!c) return DGX_ERR_ARG;
   if (int e = need_net(c)) return e;
   if (!c->has_mesh) return set_error(c, DGX_ERR_STATE, "no mesh (call dgx_mesh_build)");
+  if (c->nc) return set_error(c, DGX_ERR_STATE, "the learned preconditioner is not available on non-conforming meshes");
   return ensure_grid(c);
 }
 
@@ -1082,7 +1284,8 @@ int dgx_learned_create(dgx_ctx *c, int layers, int channels, unsigned long long 
   int e;
   if ((e = dmalloc(c, &m->master, m->P)) || (e = dmalloc(c, &m->am, m->P)) || (e = dmalloc(c, &m->av, m->P)) ||
       (e = dmalloc(c, &m->grad, m->P)) || (e = dmalloc(c, &m->wbf, m->nW)) ||
-      (e = dmalloc(c, &m->wtbf, m->nW))) {
+      (e = dmalloc(c, &m->wtbf, m->nW)) || (e = dmalloc(c, &m->tc_err, 1)) ||
+      (e = check_cuda(c, cudaMemset(m->tc_err, 0, sizeof(int)), "memset"))) {
     learned_free(c);
     return e;
   }
@@ -1215,6 +1418,7 @@ int dgx_learned_loss(dgx_ctx *c, int first, int count, double *loss, float *grad
   if (int e = check_cuda(c, cudaMemcpyAsync(m->host_lpart, m->lpart, (size_t)count * nb * sizeof(double),
                                             cudaMemcpyDeviceToHost, c->stream), "loss copy")) return e;
   if (int e = check_cuda(c, cudaStreamSynchronize(c->stream), "loss")) return e;
+  if (int e = tc_status(c)) return e;
   double s = 0.0;
   for (int k = 0; k < count * nb; ++k) s += m->host_lpart[k];
   if (loss) *loss = s / count;
@@ -1279,6 +1483,7 @@ int dgx_learned_train(dgx_ctx *c, const dgx_train_opts *opts, dgx_train_info *in
   }
   inf.steps = (int)step;
   if (int e = check_cuda(c, cudaStreamSynchronize(c->stream), "train")) return e;
+  if (int e = tc_status(c)) return e;
   if (int e = eval_loss(c, tr, &inf.loss_train)) return e;
   if (int e = eval_loss(c, te, &inf.loss_test)) return e;
   inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -380,6 +380,7 @@ int dgx_mg_setup(dgx_ctx *c, const dgx_mg_opts *opts) {
   if (!c) return DGX_ERR_ARG;
   if (!c->has_mesh) return set_error(c, DGX_ERR_STATE, "no mesh (call dgx_mesh_build)");
   if (!c->has_coef) return set_error(c, DGX_ERR_STATE, "no coefficients (call dgx_set_coefficients)");
+  if (c->nc) return set_error(c, DGX_ERR_STATE, "multigrid is not available on non-conforming meshes");
   dgx_mg_opts o;
   if (opts) o = *opts;
   else dgx_default_mg_opts(&o);

@@ -75,6 +75,7 @@ extern "C" int dgx_apply_operator_noalloc(dgx_ctx *c, int prec, const void *x, v
   if (!c) return DGX_ERR_ARG;
   if (!c->has_mesh) return dgx::set_error(c, DGX_ERR_STATE, "no mesh (call dgx_mesh_build)");
   if (!c->has_coef) return dgx::set_error(c, DGX_ERR_STATE, "no coefficients (call dgx_set_coefficients)");
+  if (c->nc) return dgx::set_error(c, DGX_ERR_STATE, "not available on non-conforming meshes (use dgx_apply_operator)");
   if (!x || !y || x == y) return dgx::set_error(c, DGX_ERR_ARG, "x, y must be distinct non-null arrays");
   if (prec == DGX_F64) return apply_noalloc<double>(c, (const double *)x, (double *)y);
   if (prec == DGX_F32) return apply_noalloc<float>(c, (const float *)x, (float *)y);

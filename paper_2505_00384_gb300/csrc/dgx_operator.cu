@@ -71,7 +71,7 @@ __device__ __forceinline__ void grad_body(const OpP<T> &P, const long long cell,
     *Wx = sm + L::oX, *Wf = sm + L::oFace;
 
   const CellPos cp = cell_pos(P, cell);
-  __shared__ long long s_nb[6];  // the six face neighbours (-1: boundary), read after the first barrier
+  __shared__ long long s_nb[6];  // the six face neighbours (-1: boundary, -2: skipped), read after the first barrier
   if (threadIdx.x < 6) s_nb[threadIdx.x] = neighbour(P, cp, threadIdx.x);
   const T *colp = CURVED ? P.col + (long long)(cp.cx + P.nx * cp.cy) * col_size(N, Q) : nullptr;
   const T zeta0 = T(cp.cz) * P.dz;
@@ -148,7 +148,7 @@ __device__ __forceinline__ void grad_body(const OpP<T> &P, const long long cell,
     const long long nb = s_nb[f];
     T ph = own;
     if (nb >= 0) ph = T(0.5) * (own + p[nb * N3 + face_node<N>(k, s ? 0 : N - 1, t1, t2)]);
-    else if (k < 2 && P.bc_lat == 1) ph = T(0);
+    else if (nb == -2 || (k < 2 && P.bc_lat == 1)) ph = T(0);
     Fg[idx] = ph;
   }
   __syncthreads();
@@ -266,7 +266,7 @@ __device__ __forceinline__ void div_body(const OpP<T> &P, const long long cell, 
     *Fb2 = Fb1 + 6 * N * Q;
 
   const CellPos cp = cell_pos(P, cell);
-  __shared__ long long s_nb[6];  // the six face neighbours (-1: boundary), read after the first barrier
+  __shared__ long long s_nb[6];  // the six face neighbours (-1: boundary, -2: skipped), read after the first barrier
   if (threadIdx.x < 6) s_nb[threadIdx.x] = neighbour(P, cp, threadIdx.x);
   const T *colp = CURVED ? P.col + (long long)(cp.cx + P.nx * cp.cy) * col_size(N, Q) : nullptr;
   const T zeta0 = T(cp.cz) * P.dz;
@@ -340,7 +340,7 @@ __device__ __forceinline__ void div_body(const OpP<T> &P, const long long cell, 
       const int node = face_node<N>(k, s ? N - 1 : 0, t1, t2);
       v = field == 0 ? P.gfac * s_in[ik * N3 + node] : s_in[(field - 1) * N3 + node];
       // slip wall: no normal flux (all traces of this face set to zero)
-      if (nb < 0 && (k == 2 || P.bc_lat == 0)) v = T(0);
+      if (nb == -2 || (nb < 0 && (k == 2 || P.bc_lat == 0))) v = T(0);
     } else {
       const long long node = nb * N3 + face_node<N>(k, s ? 0 : N - 1, t1, t2);
       v = field == 0 ? P.gfac * pk[node] : V[(field - 1) * Ntot + node];
@@ -589,26 +589,28 @@ int op_threads(const dgx_ctx *c, int N) {
 }
 
 template <typename T, int N, bool CURVED>
-int grad_impl(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s, bool inv, double alpha) {
+int grad_main(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s, bool inv, double alpha) {
   constexpr int Q = 2 * N - 1;
   const size_t smem = sizeof(T) * GradL<N, Q, CURVED>::total;
   if constexpr (sizeof(T) == 8)
     if (op_variant<T>(c) >= 5) return fused_grad<df64, N, CURVED>(c, p, rho, V, s, inv, alpha, op_variant<T>(c) - 5);
   if (op_variant<T>(c) >= 3) return fused_grad<T, N, CURVED>(c, p, rho, V, s, inv, alpha, op_variant<T>(c) - 3);
-  OpP<T> P = make_params<T>(c);
-  if (alpha >= 0.0) P.alpha = (T)alpha;
-  if (inv) {
-    auto k = k_grad<T, N, Q, CURVED, true>;
-    if (int e = prep(c, k, smem)) return e;
+  auto k = inv ? k_grad<T, N, Q, CURVED, true> : k_grad<T, N, Q, CURVED, false>;
+  if (int e = prep(c, k, smem)) return e;
+  for (int pi = 0; pi < num_patches(c); ++pi) {
+    OpP<T> P = make_params<T>(c, pi);
+    if (alpha >= 0.0) P.alpha = (T)alpha;
+    const long long o = patch_cell0(c, pi) * N * N * N;
     count_launch();
-    k<<<(unsigned)c->ncell, op_threads<T>(c, N), smem, s>>>(P, p, rho, V, c->N);
-  } else {
-    auto k = k_grad<T, N, Q, CURVED, false>;
-    if (int e = prep(c, k, smem)) return e;
-    count_launch();
-    k<<<(unsigned)c->ncell, op_threads<T>(c, N), smem, s>>>(P, p, rho, V, c->N);
+    k<<<(unsigned)patch_ncell(c, pi), op_threads<T>(c, N), smem, s>>>(P, p + o, rho + o, V + o, c->N);
   }
   return check_cuda(c, cudaGetLastError(), "k_grad launch");
+}
+
+template <typename T, int N, bool CURVED>
+int grad_impl(dgx_ctx *c, const T *p, const T *rho, T *V, cudaStream_t s, bool inv, double alpha) {
+  if (int e = grad_main<T, N, CURVED>(c, p, rho, V, s, inv, alpha)) return e;
+  return c->nc ? launch_hang_grad<T>(c, p, rho, V, s, inv, alpha) : 0;
 }
 
 template <typename T, int N, bool CURVED>
@@ -619,17 +621,29 @@ int div_impl(dgx_ctx *c, const T *V, const T *p, const T *pk, T *y, cudaStream_t
   const T *kq = nullptr;
   if constexpr (sizeof(T) == 8)
     if (alpha < 0.0 && pk == c->pk64 && c->kq64_version == c->coef_version) kq = reinterpret_cast<const T *>(c->kq64);
+  int e = 0;
   if constexpr (sizeof(T) == 8)
-    if (op_variant<T>(c) >= 5) return fused_div<df64, N, CURVED>(c, V, p, pk, y, s, alpha, kq, op_variant<T>(c) - 5);
-  if (op_variant<T>(c) >= 3) return fused_div<T, N, CURVED>(c, V, p, pk, y, s, alpha, kq, op_variant<T>(c) - 3);
+    if (op_variant<T>(c) >= 5) {
+      if ((e = fused_div<df64, N, CURVED>(c, V, p, pk, y, s, alpha, kq, op_variant<T>(c) - 5))) return e;
+      return c->nc ? launch_hang_div<T>(c, V, pk, y, s, alpha) : 0;
+    }
+  if (op_variant<T>(c) >= 3) {
+    if ((e = fused_div<T, N, CURVED>(c, V, p, pk, y, s, alpha, kq, op_variant<T>(c) - 3))) return e;
+    return c->nc ? launch_hang_div<T>(c, V, pk, y, s, alpha) : 0;
+  }
   const size_t smem = sizeof(T) * DivL<N, Q, CURVED>::total;
   auto k = k_div<T, N, Q, CURVED>;
-  if (int e = prep(c, k, smem)) return e;
-  OpP<T> P = make_params<T>(c);
-  if (alpha >= 0.0) P.alpha = (T)alpha;
-  count_launch();
-  k<<<(unsigned)c->ncell, op_threads<T>(c, N), smem, s>>>(P, V, p, pk, y, c->N, kq);
-  return check_cuda(c, cudaGetLastError(), "k_div launch");
+  if ((e = prep(c, k, smem))) return e;
+  for (int pi = 0; pi < num_patches(c); ++pi) {
+    OpP<T> P = make_params<T>(c, pi);
+    if (alpha >= 0.0) P.alpha = (T)alpha;
+    const long long o = patch_cell0(c, pi) * N * N * N, oq = patch_cell0(c, pi) * Q * Q * Q;
+    count_launch();
+    k<<<(unsigned)patch_ncell(c, pi), op_threads<T>(c, N), smem, s>>>(P, V + o, p + o, pk + o, y + o, c->N,
+                                                                      kq ? kq + oq : nullptr);
+  }
+  if ((e = check_cuda(c, cudaGetLastError(), "k_div launch"))) return e;
+  return c->nc ? launch_hang_div<T>(c, V, pk, y, s, alpha) : 0;
 }
 
 template <typename T, int N, bool CURVED>
@@ -649,8 +663,11 @@ int minv_impl(dgx_ctx *c, const T *in, const T *rho, T *out, cudaStream_t s, int
   const size_t smem = sizeof(T) * MinvL<N, Q>::total;
   auto k = k_minv<T, N, Q, CURVED>;
   if (int e = prep(c, k, smem)) return e;
-  count_launch();
-  k<<<(unsigned)c->ncell, 128, smem, s>>>(make_params<T>(c), in, rho, out, c->N, nf);
+  for (int pi = 0; pi < num_patches(c); ++pi) {
+    const long long o = patch_cell0(c, pi) * N * N * N;
+    count_launch();
+    k<<<(unsigned)patch_ncell(c, pi), 128, smem, s>>>(make_params<T>(c, pi), in + o, rho + o, out + o, c->N, nf);
+  }
   return check_cuda(c, cudaGetLastError(), "k_minv launch");
 }
 
@@ -660,8 +677,12 @@ int diag_impl(dgx_ctx *c, const T *rho, const T *pk, T *dh, T *die, cudaStream_t
   const size_t smem = sizeof(T) * DiagL<N, Q, CURVED>::total;
   auto k = k_diag<T, N, Q, CURVED>;
   if (int e = prep(c, k, smem)) return e;
-  count_launch();
-  k<<<(unsigned)c->ncell, threads_for(N), smem, s>>>(make_params<T>(c), rho, pk, dh, die);
+  for (int pi = 0; pi < num_patches(c); ++pi) {
+    const long long o = patch_cell0(c, pi) * N * N * N;
+    count_launch();
+    k<<<(unsigned)patch_ncell(c, pi), threads_for(N), smem, s>>>(make_params<T>(c, pi), rho + o, pk + o, dh + o,
+                                                                 die + o);
+  }
   return check_cuda(c, cudaGetLastError(), "k_diag launch");
 }
 
@@ -695,51 +716,100 @@ int opmulti_impl(dgx_ctx *c, const EnsMember<T> *mem, int nmem, long long ncell,
 
 int ensure_const_tables(dgx_ctx *c) { return upload_const_tables(c); }
 
+// Integer and geometric parameters of a patch, shared by every precision: the
+// children block of a non-conforming mesh has half the base cell sizes and,
+// relative to its own bottom zeta_0, the map z - zeta_0 = zeta' + h' (1 -
+// zeta'/H') with H' = Lz - zeta_0 and h' = h (1 - zeta_0/Lz) (the same points
+// as the base map; its terrain tables hold h').
+struct PatchGeo {
+  int nx, ny, nz, hole[6], iface;
+  double dx, dy, dz, H;
+  long long col_off;
+};
+static PatchGeo patch_geo(const dgx_ctx *c, int patch) {
+  const dgx_mesh_desc &m = c->mesh;
+  PatchGeo g{};
+  g.dx = m.Lx / m.nx;
+  g.dy = m.Ly / m.ny;
+  g.dz = m.Lz / m.nz;
+  g.H = m.Lz;
+  if (patch == 0) {
+    g.nx = m.nx;
+    g.ny = m.ny;
+    g.nz = m.nz;
+    if (c->nc)
+      for (int i = 0; i < 6; ++i) g.hole[i] = m.refine[i];
+    return g;
+  }
+  g.nx = c->fine[0];
+  g.ny = c->fine[1];
+  g.nz = c->fine[2];
+  g.dx *= 0.5;
+  g.dy *= 0.5;
+  g.dz *= 0.5;
+  g.H = m.Lz - c->zoff;
+  g.col_off = c->col1_off * col_size(c->n, c->q);
+  const int ext[3] = {m.nx, m.ny, m.nz};
+  for (int k = 0; k < 3; ++k) {
+    if (m.refine[2 * k] > 0) g.iface |= 1 << (2 * k);
+    if (m.refine[2 * k + 1] < ext[k]) g.iface |= 1 << (2 * k + 1);
+  }
+  return g;
+}
+
 template <typename T>
-OpP<T> make_params(const dgx_ctx *c) {
+OpP<T> make_params(const dgx_ctx *c, int patch) {
+  const PatchGeo g = patch_geo(c, patch);
   OpP<T> P;
-  P.nx = c->mesh.nx;
-  P.ny = c->mesh.ny;
-  P.nz = c->mesh.nz;
+  P.nx = g.nx;
+  P.ny = g.ny;
+  P.nz = g.nz;
   P.bc_lat = c->mesh.bc_lateral;
-  P.dx = (T)(c->mesh.Lx / c->mesh.nx);
-  P.dy = (T)(c->mesh.Ly / c->mesh.ny);
-  P.dz = (T)(c->mesh.Lz / c->mesh.nz);
-  P.H = (T)c->mesh.Lz;
-  P.invH = (T)(1.0 / c->mesh.Lz);
+  for (int i = 0; i < 6; ++i) P.hole[i] = g.hole[i];
+  P.iface = g.iface;
+  P.pad_ = 0;
+  P.dx = (T)g.dx;
+  P.dy = (T)g.dy;
+  P.dz = (T)g.dz;
+  P.H = (T)g.H;
+  P.invH = (T)(1.0 / g.H);
   P.alpha = (T)c->alpha;
   P.gfac = (T)(c->gamma / (c->gamma - 1.0));
   P.igm1 = (T)(1.0 / (c->gamma - 1.0));
   if constexpr (sizeof(T) == 8) {
     P.tab = reinterpret_cast<const T *>(c->tab64);
-    P.col = reinterpret_cast<const T *>(c->col64);
+    P.col = c->col64 ? reinterpret_cast<const T *>(c->col64 + g.col_off) : nullptr;
   } else {
     P.tab = reinterpret_cast<const T *>(c->tab32);
-    P.col = reinterpret_cast<const T *>(c->col32);
+    P.col = c->col32 ? reinterpret_cast<const T *>(c->col32 + g.col_off) : nullptr;
   }
   return P;
 }
-template OpP<double> make_params<double>(const dgx_ctx *);
-template OpP<float> make_params<float>(const dgx_ctx *);
+template OpP<double> make_params<double>(const dgx_ctx *, int);
+template OpP<float> make_params<float>(const dgx_ctx *, int);
 // double-word parameters: every scalar split from its double; the terrain
 // columns as double-words; the 1D tables live in constant memory only
 template <>
-OpP<df64> make_params<df64>(const dgx_ctx *c) {
+OpP<df64> make_params<df64>(const dgx_ctx *c, int patch) {
+  const PatchGeo g = patch_geo(c, patch);
   OpP<df64> P;
-  P.nx = c->mesh.nx;
-  P.ny = c->mesh.ny;
-  P.nz = c->mesh.nz;
+  P.nx = g.nx;
+  P.ny = g.ny;
+  P.nz = g.nz;
   P.bc_lat = c->mesh.bc_lateral;
-  P.dx = df64(c->mesh.Lx / c->mesh.nx);
-  P.dy = df64(c->mesh.Ly / c->mesh.ny);
-  P.dz = df64(c->mesh.Lz / c->mesh.nz);
-  P.H = df64(c->mesh.Lz);
-  P.invH = df64(1.0 / c->mesh.Lz);
+  for (int i = 0; i < 6; ++i) P.hole[i] = g.hole[i];
+  P.iface = g.iface;
+  P.pad_ = 0;
+  P.dx = df64(g.dx);
+  P.dy = df64(g.dy);
+  P.dz = df64(g.dz);
+  P.H = df64(g.H);
+  P.invH = df64(1.0 / g.H);
   P.alpha = df64(c->alpha);
   P.gfac = df64(c->gamma / (c->gamma - 1.0));
   P.igm1 = df64(1.0 / (c->gamma - 1.0));
   P.tab = nullptr;
-  P.col = reinterpret_cast<const df64 *>(c->coldf);
+  P.col = c->coldf ? reinterpret_cast<const df64 *>(c->coldf + 2 * g.col_off) : nullptr;
   return P;
 }
 

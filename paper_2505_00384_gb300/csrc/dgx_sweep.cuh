@@ -147,28 +147,41 @@ __device__ __forceinline__ CellPos cell_pos(const OpP<T> &P, long long cell) {
   return c;
 }
 
+// Whether patch cell (x, y, z) lies in the patch's hole (dead cells of a
+// non-conforming mesh's base patch).
+template <typename T>
+__device__ __forceinline__ bool in_hole(const OpP<T> &P, int x, int y, int z) {
+  return x >= P.hole[0] && x < P.hole[1] && y >= P.hole[2] && y < P.hole[3] && z >= P.hole[4] && z < P.hole[5];
+}
+
 // Neighbour across face f = 2k+s, or -1 on the boundary (x and y wrap around
-// with periodic lateral boundaries).
+// with periodic lateral boundaries); -2 for a face whose terms this kernel
+// skips (a face of a dead cell, a face to a dead cell, a face of the patch box
+// that borders the other patch).
 template <typename T>
 __device__ __forceinline__ long long neighbour(const OpP<T> &P, const CellPos &c, int f) {
   const int k = f >> 1, s = f & 1;
   int x = c.cx, y = c.cy, z = c.cz;
+  if (in_hole(P, x, y, z)) return -2;
   if (k == 0) {
     x += s ? 1 : -1;
     if (x < 0 || x >= P.nx) {
+      if (P.iface & (1 << f)) return -2;
       if (P.bc_lat != 2) return -1;
       x = (x + P.nx) % P.nx;  // periodic lateral boundaries
     }
   } else if (k == 1) {
     y += s ? 1 : -1;
     if (y < 0 || y >= P.ny) {
+      if (P.iface & (1 << f)) return -2;
       if (P.bc_lat != 2) return -1;
       y = (y + P.ny) % P.ny;
     }
   } else {
     z += s ? 1 : -1;
-    if (z < 0 || z >= P.nz) return -1;
+    if (z < 0 || z >= P.nz) return (P.iface & (1 << f)) ? -2 : -1;
   }
+  if (in_hole(P, x, y, z)) return -2;
   return x + (long long)P.nx * (y + (long long)P.ny * z);
 }
 

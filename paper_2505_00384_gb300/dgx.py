@@ -31,7 +31,8 @@ class dgx_mesh_desc(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("degree", C.c_int), ("n_q", C.c_int),
                 ("terrain", C.c_int), ("bc_lateral", C.c_int), ("reserved", C.c_int),
                 ("Lx", C.c_double), ("Ly", C.c_double), ("Lz", C.c_double),
-                ("h_c", C.c_double), ("a_c", C.c_double), ("x_c", C.c_double), ("y_c", C.c_double)]
+                ("h_c", C.c_double), ("a_c", C.c_double), ("x_c", C.c_double), ("y_c", C.c_double),
+                ("refine", C.c_int * 6)]
 
 
 class dgx_background(C.Structure):
@@ -560,7 +561,8 @@ def dgx_kernel_launches():
     return int(load().dgx_kernel_launches())
 
 
-def mesh_desc(nx, ny, nz, degree, Lx, Ly, Lz, terrain=0, h_c=0.0, a_c=1000.0, x_c=None, y_c=None, bc_lateral=0):
+def mesh_desc(nx, ny, nz, degree, Lx, Ly, Lz, terrain=0, h_c=0.0, a_c=1000.0, x_c=None, y_c=None, bc_lateral=0,
+              refine=None):
     d = dgx_mesh_desc()
     d.nx, d.ny, d.nz, d.degree, d.n_q = nx, ny, nz, degree, 0
     d.terrain, d.bc_lateral = terrain, bc_lateral
@@ -568,6 +570,9 @@ def mesh_desc(nx, ny, nz, degree, Lx, Ly, Lz, terrain=0, h_c=0.0, a_c=1000.0, x_
     d.h_c, d.a_c = h_c, a_c
     d.x_c = Lx / 2 if x_c is None else x_c
     d.y_c = Ly / 2 if y_c is None else y_c
+    if refine is not None:
+        for i, v in enumerate(refine):
+            d.refine[i] = int(v)
     return d
 
 

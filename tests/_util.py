@@ -32,12 +32,12 @@ class Case:
     """A mesh built identically for the CUDA library and the oracle."""
 
     def __init__(self, nx, ny, nz, r, Lx=1000.0, Ly=1000.0, Lz=1000.0, terrain=0, hc=0.0, ac=1000.0, xc=None,
-                 yc=None, bc_lateral=0):
+                 yc=None, bc_lateral=0, refine=None):
         torch = torch_cuda()
         self.m = O.make_mesh(nx, ny, nz, r, Lx=Lx, Ly=Ly, Lz=Lz, terrain=terrain, hc=hc, ac=ac, xc=xc, yc=yc,
-                             bc_lateral=bc_lateral)
+                             bc_lateral=bc_lateral, refine=refine)
         self.desc = dgx.mesh_desc(nx, ny, nz, r, Lx, Ly, Lz, terrain=terrain, h_c=hc, a_c=ac, x_c=self.m.xc,
-                                  y_c=self.m.yc, bc_lateral=bc_lateral)
+                                  y_c=self.m.yc, bc_lateral=bc_lateral, refine=refine)
         self.stream = torch.cuda.current_stream().cuda_stream
         self.ctx = dgx.dgx_create(0, self.stream)
         dgx.dgx_mesh_build(self.ctx, self.desc)

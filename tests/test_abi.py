@@ -39,8 +39,8 @@ def test_binding_signatures_load():
 
 def test_structs_match_header_layout():
     from paper_2505_00384_gb300 import dgx
-    # 8 ints then 7 doubles; 2 ints then 7 doubles; mixed int/double padding
-    assert ctypes.sizeof(dgx.dgx_mesh_desc) == 8 * 4 + 7 * 8
+    # 8 ints, 7 doubles, the 6-int refinement box; 2 ints then 7 doubles; mixed int/double padding
+    assert ctypes.sizeof(dgx.dgx_mesh_desc) == 8 * 4 + 7 * 8 + 6 * 4
     assert ctypes.sizeof(dgx.dgx_background) == 2 * 4 + 7 * 8
     assert ctypes.sizeof(dgx.dgx_solve_opts) == 4 * 4 + 8 + 2 * 4 + 8 + 2 * 4
     assert ctypes.sizeof(dgx.dgx_solve_info) == 6 * 4 + 2 * 8

@@ -132,9 +132,15 @@ def test_zero_network_is_jacobi():
     c.close()
 
 
-@pytest.mark.parametrize("mesh,L,Ch,B", [((3, 2, 2, 2), 3, 8, 3), ((4, 4, 4, 2), 9, 32, 2)],
-                         ids=["ragged_3layers_8ch", "box12_9layers_32ch"])
+@pytest.mark.parametrize("mesh,L,Ch,B", [((3, 2, 2, 2), 3, 8, 3), ((4, 4, 4, 2), 9, 32, 2),
+                                         ((4, 4, 4, 2), 9, 32, 8), ((3, 5, 2, 2), 4, 32, 9)],
+                         ids=["ragged_3layers_8ch", "box12_9layers_32ch", "box12_9layers_32ch_batch8_tensor_cores",
+                              "ragged_4layers_32ch_batch9_tensor_cores"])
 def test_loss_and_gradients(mesh, L, Ch, B):
+    """Loss and gradients against the oracle.  From batch 8 on, the 32-channel
+    hidden layers' forward and backward-data convolutions run on the tensor
+    cores (bf16 high parts and remainders of the activations against the bf16
+    weights, FP32 accumulation): the same 1e-4 bar."""
     c = _case(*mesh)
     dgx.dgx_learned_create(c.ctx, L, Ch, SEED)
     p = _random_params(L, Ch, 7)
