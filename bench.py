@@ -81,6 +81,9 @@ def parse():
     ap.add_argument("--inner-maxit", type=int, default=None, help="override the FP32 GMRES cycle length")
     ap.add_argument("--inner-tol", type=float, default=None, help="override the FP32 GMRES tolerance")
     ap.add_argument("--plain-steps", type=int, default=3, help="hill workload: timed steps with plain FP64 solves")
+    ap.add_argument("--paper-steps", type=int, default=0,
+                    help="paper / nonconf workloads: after the solver comparison, this many consecutive mixed-solver "
+                         "IMEX steps from the initial state (simulated time = steps x 1 s)")
     ap.add_argument("--no-extras", action="store_true",
                     help="hill workload: skip the compact mixed and learned results (run as subprocesses)")
     return ap.parse_args()
@@ -430,7 +433,7 @@ def run_mixed(args):
     return 0
 
 
-def run_paper(args):
+def run_paper(args, dims=(120, 80, 32), refine=None, name="paper_sec3_120x80x32_r4_38.4M_dofs_stratified"):
     """The test case of Sec. 3 on its uniform mesh: (0, 60) x (0, 40) x (0, 16) km,
     120 x 80 x 32 cells at degree 4 (38 400 000 DoFs per scalar, 125 m), the -3/2
     bell hill h_c = 400 m, a_c = 1 km at (30, 20) km, the constant-N background
@@ -447,8 +450,8 @@ def run_paper(args):
     dgx.load()
     stream = torch.cuda.current_stream()
     ctx = dgx.dgx_create(0, stream.cuda_stream)
-    desc = dgx.mesh_desc(120, 80, 32, 4, 60000.0, 40000.0, 16000.0, terrain=2, h_c=400.0, a_c=1000.0,
-                         x_c=30000.0, y_c=20000.0, bc_lateral=1)
+    desc = dgx.mesh_desc(dims[0], dims[1], dims[2], 4, 60000.0, 40000.0, 16000.0, terrain=2, h_c=400.0, a_c=1000.0,
+                         x_c=30000.0, y_c=20000.0, bc_lateral=1, refine=refine)
     t0 = time.perf_counter()
     dgx.dgx_mesh_build(ctx, desc)
     N = dgx.dgx_num_dofs(ctx)
@@ -469,9 +472,18 @@ def run_paper(args):
     dgx.dgx_apply_operator(ctx, dgx.DGX_F64, p0.data_ptr(), y.data_ptr())
     x32, y32 = p0.float(), torch.empty(N, dtype=torch.float32, device="cuda")
     dgx.dgx_apply_operator(ctx, dgx.DGX_F32, x32.data_ptr(), y32.data_ptr())
-    del y, x32, y32
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
+    op_ms = {}
+    for prec, xx, yy in ((dgx.DGX_F64, p0, y), (dgx.DGX_F32, x32, y32)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            dgx.dgx_apply_operator(ctx, prec, xx.data_ptr(), yy.data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        op_ms["f64" if prec == dgx.DGX_F64 else "f32"] = e0.elapsed_time(e1) / 5
+    del y, x32, y32
 
     def opts(method, pc, maxit=3000):
         o = dgx.dgx_default_solve_opts()
@@ -509,15 +521,41 @@ def run_paper(args):
     sc = float(ref.abs().max().clamp_min(1e-30))
     for name in pres:
         res[name]["p_prime_max_rel_diff_vs_fgmres_helmholtz"] = float((pres[name] - ref).abs().max()) / sc
+    run = None
+    if args.paper_steps > 0:  # a longer run with the mixed solver: per-step times and the flow's growth
+        o = opts(dgx.DGX_SOLVER_MIXED, dgx.DGX_PC_HELMHOLTZ)
+        r, u, p = rho0.clone(), u0.clone(), p0.clone()
+        per, wmax, pmax, its = [], [], [], 0
+        for k in range(args.paper_steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, info = dgx.dgx_imex_step(ctx, r.data_ptr(), u.data_ptr(), p.data_ptr(), 1, o)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if st != dgx.DGX_OK:
+                raise RuntimeError("step %d: a pressure solve did not converge (relres %g)" % (k, info.max_relres))
+            per.append(e0.elapsed_time(e1) / 1e3)
+            its += info.krylov_iterations
+            wmax.append(float(u[2 * N:].abs().max()))
+            pmax.append(float((p - p0).abs().max()))
+        run = {"steps": args.paper_steps, "simulated_s": args.paper_steps * 1.0, "s_per_step_mean": sum(per) / len(per),
+               "s_per_step_first_last": [per[0], per[-1]], "krylov_iterations_per_step": its / args.paper_steps,
+               "w_max_m_s": wmax[:: max(1, args.paper_steps // 10)] + [wmax[-1]],
+               "p_prime_max_pa": pmax[:: max(1, args.paper_steps // 10)] + [pmax[-1]],
+               "finite": bool(torch.isfinite(p).all() and torch.isfinite(u).all())}
+        print(json.dumps({"paper_case_run": run}), flush=True)
+        del r, u, p
     h, ie = res["fgmres_helmholtz"], res["fgmres_internal_energy"]
     out = {"metric": "pressure solve s/step @1e-8 rel residual, Helmholtz vs internal-energy Jacobi",
            "value": h["pressure_solve_s"], "unit": "s/step", "n_gpus": 1, "steps": 1, "warmup": 0,
            "higher_is_better": False, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "paper_sec3_120x80x32_r4_38.4M_dofs_stratified", "dofs_per_scalar": N,
+           "config": {"workload": name, "dofs_per_scalar": N, "cells": dims[0] * dims[1] * dims[2] if refine is None
+                      else dims[0] * dims[1] * dims[2] + 7 * (refine[1] - refine[0]) * (refine[3] - refine[2])
+                      * (refine[5] - refine[4]), "refine_box_base_cells": refine,
                       "terrain": "-3/2 bell h_c=400 m a_c=1 km at (30, 20) km, Gal-Chen",
                       "background": "constant N = 0.01 1/s, T_ref = 293.15 K", "lateral": "far field",
                       "dt_s": 1.0, "setup_s": t_setup},
-           "solvers": res,
+           "operator_ms": op_ms, "solvers": res, "run": run,
            "helmholtz_time_saving_vs_internal_energy": 1.0 - h["pressure_solve_s"] / ie["pressure_solve_s"],
            "helmholtz_iteration_ratio_vs_internal_energy": h["krylov_iterations"] / ie["krylov_iterations"],
            "mixed_speedup_vs_fgmres_helmholtz": h["pressure_solve_s"] / res["mixed_helmholtz"]["pressure_solve_s"]}
@@ -527,117 +565,18 @@ def run_paper(args):
 
 
 def run_nonconf(args):
-    """The Sec. 3 domain (0, 60) x (0, 40) x (0, 16) km on a non-conforming mesh
-    (Sec. 3: cells of different resolution horizontally and vertically): base
-    cells of 500 m x 500 m x 1 km (120 x 80 x 16), the box of base cells
-    [48, 72) x [28, 52) x [0, 8) around the -3/2 bell hill (h_c = 400 m, a_c = 1 km
-    at (30, 20) km) split 2 x 2 x 2 (250 m x 250 m x 500 m), degree 4: 185 856
-    cells, 23.2 M DoFs per scalar (the paper's non-conforming mesh: 204 816 cells,
-    25.6 M).  Constant-N background (N = 0.01 1/s, T_ref = 293.15 K), far-field
-    lateral faces, coefficients rho = rho_bar, p_k = p_bar with 2 % seeded noise,
-    a~_ll dt of ARS(2,2,2) at dt = 1 s.  The right-hand side is S x* for a smooth
-    pressure perturbation x* (50 Pa Gaussian over the hill).  Solved to 1e-8 from
-    zero with FP64 FGMRES(30) preconditioned by the Helmholtz and by the
-    internal-energy Jacobi diagonals (Sec. 3.1) and with the mixed solver; the same
-    solves on the conforming base mesh (120 x 80 x 16, 19.2 M DoFs) give the
-    uniform-mesh comparison of Sec. 3.1.  CUDA-event times per solve; the operator
-    application time on both meshes."""
-    import torch
-    from paper_2505_00384_gb300 import dgx, inputs
-    torch.cuda.set_device(0)
-    dgx.load()
-    stream = torch.cuda.current_stream()
-    f64 = torch.float64
-
-    def one_mesh(refine):
-        ctx = dgx.dgx_create(0, stream.cuda_stream)
-        desc = dgx.mesh_desc(120, 80, 16, 4, 60000.0, 40000.0, 16000.0, terrain=2, h_c=400.0, a_c=1000.0,
-                             x_c=30000.0, y_c=20000.0, bc_lateral=1, refine=refine)
-        t0 = time.perf_counter()
-        dgx.dgx_mesh_build(ctx, desc)
-        N = dgx.dgx_num_dofs(ctx)
-        dgx.dgx_set_background(ctx, dgx.background(kind=1, T=293.15, p0=1e5, N_bv=0.01, R=287.0, gamma=1.4,
-                                                   g=9.81, u_bar=10.0))
-        rb = torch.zeros(N, dtype=f64, device="cuda")
-        pb = torch.zeros(N, dtype=f64, device="cuda")
-        dgx.dgx_background_fields(ctx, rb.data_ptr(), pb.data_ptr())
-        X = torch.zeros(3 * N, dtype=f64, device="cuda")
-        dgx.dgx_node_coords(ctx, X.data_ptr())
-        torch.cuda.synchronize()
-        act = torch.ones(N, dtype=f64, device="cuda")
-        if refine is not None:  # dead base cells: zero unknowns
-            n3 = 125
-            cells = act.view(-1, n3)
-            for z in range(refine[4], refine[5]):
-                for y in range(refine[2], refine[3]):
-                    cells[refine[0] + 120 * (y + 80 * z): refine[1] + 120 * (y + 80 * z)] = 0.0
-        noise = lambda seed: torch.from_numpy(inputs.normal(seed, N)).cuda()
-        rho = rb * (1.0 + 0.02 * noise(301)) * act
-        pk = pb * (1.0 + 0.02 * noise(302)) * act
-        dgx.dgx_set_coefficients(ctx, rho.data_ptr(), pk.data_ptr(), A_LL, 1.4)
-        x, y_, z = X[:N], X[N:2 * N], X[2 * N:]
-        xs = 50.0 * torch.exp(-((x - 30000.0) ** 2 + (y_ - 20000.0) ** 2) / (2 * 3000.0 ** 2) - z / 3000.0) * act
-        b = torch.zeros(N, dtype=f64, device="cuda")
-        dgx.dgx_apply_operator(ctx, dgx.DGX_F64, xs.data_ptr(), b.data_ptr())  # first use: autotune
-        x32, y32 = xs.float(), torch.empty(N, dtype=torch.float32, device="cuda")
-        dgx.dgx_apply_operator(ctx, dgx.DGX_F32, x32.data_ptr(), y32.data_ptr())
-        torch.cuda.synchronize()
-        setup = time.perf_counter() - t0
-        # operator application times
-        app = {}
-        for prec, xx, yy in ((dgx.DGX_F64, xs, torch.empty_like(xs)), (dgx.DGX_F32, x32, y32)):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(5):
-                dgx.dgx_apply_operator(ctx, prec, xx.data_ptr(), yy.data_ptr())
-            e1.record(stream)
-            torch.cuda.synchronize()
-            app["f64" if prec == dgx.DGX_F64 else "f32"] = e0.elapsed_time(e1) / 5
-        dgx.dgx_apply_operator(ctx, dgx.DGX_F64, xs.data_ptr(), b.data_ptr())
-        res = {"dofs_per_scalar": N, "cells": N // 125, "active_dofs": int(act.sum().item()), "setup_s": setup,
-               "operator_ms": app, "variants": {"f64": dgx.load().dgx_operator_variant(ctx, dgx.DGX_F64),
-                                                 "f32": dgx.load().dgx_operator_variant(ctx, dgx.DGX_F32)},
-               "solvers": {}}
-        for name, method, pc, maxit in (("fgmres_helmholtz", dgx.DGX_SOLVER_FGMRES, dgx.DGX_PC_HELMHOLTZ, 3000),
-                                        ("fgmres_internal_energy", dgx.DGX_SOLVER_FGMRES,
-                                         dgx.DGX_PC_INTERNAL_ENERGY, 1000),
-                                        ("mixed_helmholtz", dgx.DGX_SOLVER_MIXED, dgx.DGX_PC_HELMHOLTZ, 3000)):
-            o = dgx.dgx_default_solve_opts()
-            o.method, o.pc, o.tol, o.maxit = method, pc, 1e-8, maxit
-            o.restart = 20 if method == dgx.DGX_SOLVER_MIXED else 30
-            o.inner_maxit, o.inner_tol = 25, 3e-6
-            xsol = torch.zeros(N, dtype=f64, device="cuda")
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st, info = dgx.dgx_solve_pressure(ctx, b.data_ptr(), xsol.data_ptr(), o)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            res["solvers"][name] = {"converged": st == dgx.DGX_OK, "s": e0.elapsed_time(e1) / 1e3,
-                                    "iterations": info.iterations, "inner_iterations": info.inner_iterations,
-                                    "relres": info.relres,
-                                    "max_rel_err_vs_x_star": float((xsol - xs).abs().max() / xs.abs().max())}
-            print(json.dumps({"nonconf_mesh": "refined" if refine else "base", "solver": name,
-                              **res["solvers"][name]}), flush=True)
-        h, ie = res["solvers"]["fgmres_helmholtz"], res["solvers"]["fgmres_internal_energy"]
-        res["helmholtz_time_saving_vs_internal_energy"] = 1.0 - h["s"] / ie["s"]
-        res["helmholtz_iteration_ratio_vs_internal_energy"] = h["iterations"] / ie["iterations"]
-        dgx.dgx_destroy(ctx)
-        return res
-
-    box = (48, 72, 28, 52, 0, 8)
-    nc = one_mesh(box)
-    base = one_mesh(None)
-    out = {"metric": "pressure solve s @1e-8 rel residual on the non-conforming mesh, Helmholtz vs internal-energy "
-                     "Jacobi", "value": nc["solvers"]["fgmres_helmholtz"]["s"], "unit": "s/solve", "n_gpus": 1,
-           "higher_is_better": False, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "sec3_domain_nonconforming_120x80x16_box2to1_r4_23.2M_dofs",
-                      "refine_box_base_cells": box, "terrain": "-3/2 bell h_c=400 m a_c=1 km at (30, 20) km",
-                      "background": "constant N = 0.01 1/s, T_ref = 293.15 K, 2 % noise", "lateral": "far field",
-                      "rhs": "S x*, x* = 50 Pa Gaussian over the hill"},
-           "nonconforming": nc, "conforming_base": base}
-    print(json.dumps(out), flush=True)
-    return 0
+    """The test case of Sec. 3 on a non-conforming mesh (Sec. 3: cells of
+    different resolution horizontally and vertically): base cells of 500 m x
+    500 m x 1 km (120 x 80 x 16), the box of base cells [48, 72) x [28, 52) x [0, 8)
+    around the hill split 2 x 2 x 2 (250 m x 250 m x 500 m near the ground), degree
+    4: 190 464 cells (185 856 with unknowns), 23.2 M DoFs per scalar (the paper's
+    non-conforming mesh: 204 816 cells, 25.6 M).  The rest as `--workload paper`:
+    one IMEX step from the initial state per solver (FP64 FGMRES(30) with the
+    Helmholtz and with the internal-energy Jacobi diagonal, the mixed solver), the
+    comparison of Sec. 3.1 on the non-conforming mesh; plus the operator
+    application times on this mesh."""
+    return run_paper(args, dims=(120, 80, 16), refine=(48, 72, 28, 52, 0, 8),
+                     name="sec3_nonconforming_120x80x16_box2to1_r4_23.2M_dofs_stratified")
 
 
 def run_consistent(args):

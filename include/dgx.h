@@ -95,9 +95,10 @@ typedef struct dgx_ctx dgx_ctx;
  * outside it and, with periodic lateral faces, stay clear of them.  On
  * non-conforming meshes the operator, its parts, the diagonals, the FP64, CG
  * and mixed solvers with the Jacobi preconditioners, node coordinates,
- * background and explicit tendencies are available; the IMEX step, the
- * learned and multigrid preconditioners, the consistent mass rule, ensembles
- * and dgx_apply_operator_noalloc return DGX_ERR_STATE. */
+ * background, explicit tendencies and the IMEX step are available (the step
+ * sets the dead cells of the state to the background at rest: rho = rho_bar,
+ * u = 0, p = p_bar); the learned and multigrid preconditioners, the consistent
+ * mass rule, ensembles and dgx_apply_operator_noalloc return DGX_ERR_STATE. */
 typedef struct {
   int nx, ny, nz;
   int degree;

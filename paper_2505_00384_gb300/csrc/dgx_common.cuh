@@ -365,9 +365,10 @@ template <typename T>
 int launch_hang_div(dgx_ctx *c, const T *V, const T *pk, T *y, cudaStream_t s, double alpha);
 int launch_hang_explicit(dgx_ctx *c, const double *rho, const double *u, double *Er, double *Em, double *Ee,
                          cudaStream_t s);
-// x[cell * n3 + node] = v on the dead cells of a non-conforming mesh (nf fields of stride N)
+// x[cell * n3 + node] = v (or src at the same index) on the dead cells of a
+// non-conforming mesh (nf fields of stride N)
 template <typename T>
-int fill_dead(dgx_ctx *c, T *x, int nf, double v, cudaStream_t s);
+int fill_dead(dgx_ctx *c, T *x, int nf, double v, cudaStream_t s, const T *src = nullptr);
 // mesh set-up of a non-conforming mesh (dgx_nonconf.cu): the hanging-face work
 // list and tables (after the patches' cells and tables are known)
 int nonconf_setup(dgx_ctx *c);

@@ -120,7 +120,6 @@ int dgx_imex_step(dgx_ctx *c, double *rho, double *u, double *p, int nsteps, con
                   dgx_step_info *info) {
   if (int e = ready(c)) return e;
   if (!c->has_imex) return set_error(c, DGX_ERR_STATE, "no tableau (call dgx_set_imex)");
-  if (c->nc) return set_error(c, DGX_ERR_STATE, "the IMEX step is not available on non-conforming meshes");
   if (!rho || !u || !p || nsteps < 0) return set_error(c, DGX_ERR_ARG, "null state array or negative step count");
   const auto t0 = std::chrono::steady_clock::now();
   dgx_solve_opts o;
@@ -143,6 +142,11 @@ int dgx_imex_step(dgx_ctx *c, double *rho, double *u, double *p, int nsteps, con
   count_launch(2);
   k_fill<<<grid(N), 256, 0, st>>>(N, 0.0, w.zeros);
   k_fill<<<grid(N), 256, 0, st>>>(N, 1.0, w.ones);
+  if (c->nc) {  // dead cells of a non-conforming mesh carry the background at rest (no perturbation, no wind)
+    if ((e = fill_dead<double>(c, rho, 1, 0.0, st, c->rho_bar)) || (e = fill_dead<double>(c, u, 3, 0.0, st)) ||
+        (e = fill_dead<double>(c, p, 1, 0.0, st, c->p_bar)))
+      return e;
+  }
   double solve_s = 0.0;
   for (int step = 0; step < nsteps; ++step) {
     if ((e = cp(w.rn, rho, b1)) || (e = cp(w.un, u, b3)) || (e = cp(w.pn, p, b1))) return e;

@@ -202,16 +202,26 @@ __global__ void __launch_bounds__(16 * KS) k_conv(ConvArgs a) {
 // 16 rows of 8 points are one halo row (160 bytes) apart, the two channel
 // chunks of a K = 16 step one chunk plane apart.  No per-tap copy.  The
 // weights are staged as [tap][chunk][co][8 channels] (B operand, K-major).
-// FP32 activations are split into bf16 high parts and bf16 remainders, x = hi
-// + lo to 2^-16 relative; both are multiplied with the (exactly bf16) weights,
-// so the product keeps about FP32 accuracy (108 MMAs of 128 x 32 x 16 per tile).
+// FP32 activations are split into three bf16 terms, x = hi + mid + lo to
+// 2^-24 relative (each term the bf16 rounding of what the previous ones leave);
+// all three are multiplied with the (exactly bf16) weights: 162 MMAs of 128 x
+// 32 x 16 per tile.  The tensor cores' FP32 accumulation does not round to
+// nearest (measured: about 1e-5 relative error after 162 accumulations into one
+// accumulator, consistent with truncation), so the MMAs are dealt round robin to
+// 16 accumulators (all 512 TMEM columns, about 10 MMAs each) that the epilogue
+// sums in FP32 on the CUDA cores.  Two bf16 terms, or one accumulator, are not
+// enough for training: the backward pass's ReLU masks flip where
+// pre-activations lie within ~1e-5 of zero, which moves the gradients by ~1e-3.
 constexpr int kTcX = 8, kTcY = 16, kTcHX = kTcX + 2, kTcHY = kTcY + 2, kTcHZ = 3;
 constexpr int kTcHP = kTcHX * kTcHY * kTcHZ;      // 540 halo points
 constexpr int kTcPlane = kTcHP * 16;              // bytes of one 8-channel chunk plane
-constexpr int kTcHalo = 4 * kTcPlane;             // one part (hi or lo), 32 channels
+constexpr int kTcHalo = 4 * kTcPlane;             // one bf16 term of the 32 channels
+constexpr int kTcTerms = 3;                       // hi, mid, lo
 constexpr int kTcW = 27 * 4 * 32 * 16;            // weights
-constexpr int kTcMbar = 2 * kTcHalo + kTcW;       // mbarrier (8 bytes) and the TMEM address
-constexpr int kTcSmem = 200 * 1024;               // with headroom beyond the operands
+constexpr int kTcMbar = kTcTerms * kTcHalo + kTcW;  // mbarrier (8 bytes) and the TMEM address
+constexpr int kTcSmem = kTcMbar + 128;
+constexpr int kTcAcc = 16;                        // accumulators of 32 FP32 columns: the whole TMEM
+constexpr int kTcThreads = 512;                   // 16 warps: staging loads in flight, 4 accumulators per warp
 constexpr int kTcMinBatch = 8;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -247,9 +257,9 @@ __device__ __forceinline__ bool tc_wait(unsigned bar, unsigned ph, int limit) {
   return false;
 }
 
-__global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs a, int *err) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(ConvArgs a, int *err) {
   extern __shared__ __align__(128) unsigned char tsm[];
-  unsigned char *hi = tsm, *lo = tsm + kTcHalo, *ws = tsm + 2 * kTcHalo;
+  unsigned char *ws = tsm + kTcTerms * kTcHalo;
   unsigned long long *bar = reinterpret_cast<unsigned long long *>(tsm + kTcMbar);
   unsigned *taddr_s = reinterpret_cast<unsigned *>(tsm + kTcMbar + 8);
   const Grid3 &g = a.g;
@@ -264,38 +274,43 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs a, int *err) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {  // 32 TMEM columns (FP32 accumulators of N = 32), address into shared memory
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(taddr_s)) : "memory");
+  if (warp == 0) {  // 16 x 32 TMEM columns (FP32 accumulators of N = 32), address into shared memory
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(taddr_s)) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // halo: (chunk, point) items, point fastest (coalesced along x); hi / lo bf16 parts of 8 channels
+  // halo: (chunk, point) items, point fastest (coalesced along x); the three
+  // bf16 terms of 8 channels, each into its own copy of the halo
   for (int it = threadIdx.x; it < 4 * kTcHP; it += blockDim.x) {
     const int c = it / kTcHP, pnt = it - c * kTcHP;
     const int hx = pnt % kTcHX, hy = (pnt / kTcHX) % kTcHY, hz = pnt / (kTcHX * kTcHY);
     const int gx = x0 + hx, gy = y0 + hy, gz = z0 + hz;
-    unsigned short h[8], l[8];
+    unsigned short t[kTcTerms][8];
     if (gx >= 0 && gx < g.X && gy >= 0 && gy < g.Y && gz >= 0 && gz < g.Z) {
       const float *src = in + (long long)(8 * c) * g.G + gx + (long long)g.X * (gy + (long long)g.Y * gz);
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         float v = src[(long long)j * g.G];
         if (a.relu_in) v = fmaxf(v, 0.f);
-        const __nv_bfloat16 vh = __float2bfloat16_rn(v);
-        const __nv_bfloat16 vl = __float2bfloat16_rn(v - __bfloat162float(vh));
-        h[j] = __bfloat16_as_ushort(vh);
-        l[j] = __bfloat16_as_ushort(vl);
+#pragma unroll
+        for (int q = 0; q < kTcTerms; ++q) {  // v - (terms so far) is exact in FP32
+          const __nv_bfloat16 tq = __float2bfloat16_rn(v);
+          t[q][j] = __bfloat16_as_ushort(tq);
+          v -= __bfloat162float(tq);
+        }
       }
     } else {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) h[j] = l[j] = 0;
+      for (int q = 0; q < kTcTerms; ++q)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) t[q][j] = 0;
     }
-    uint4 uh, ul;
-    uh.x = h[0] | ((unsigned)h[1] << 16); uh.y = h[2] | ((unsigned)h[3] << 16);
-    uh.z = h[4] | ((unsigned)h[5] << 16); uh.w = h[6] | ((unsigned)h[7] << 16);
-    ul.x = l[0] | ((unsigned)l[1] << 16); ul.y = l[2] | ((unsigned)l[3] << 16);
-    ul.z = l[4] | ((unsigned)l[5] << 16); ul.w = l[6] | ((unsigned)l[7] << 16);
-    *reinterpret_cast<uint4 *>(hi + c * kTcPlane + pnt * 16) = uh;
-    *reinterpret_cast<uint4 *>(lo + c * kTcPlane + pnt * 16) = ul;
+#pragma unroll
+    for (int q = 0; q < kTcTerms; ++q) {
+      uint4 u;
+      u.x = t[q][0] | ((unsigned)t[q][1] << 16); u.y = t[q][2] | ((unsigned)t[q][3] << 16);
+      u.z = t[q][4] | ((unsigned)t[q][5] << 16); u.w = t[q][6] | ((unsigned)t[q][7] << 16);
+      *reinterpret_cast<uint4 *>(tsm + q * kTcHalo + c * kTcPlane + pnt * 16) = u;
+    }
   }
   // weights W[(ci 27 + tap) Co + co] -> [tap][ci / 8][co][ci % 8]; co fastest across threads
   for (int it = threadIdx.x; it < 27 * 4 * 32; it += blockDim.x) {
@@ -314,54 +329,71 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs a, int *err) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const unsigned tmem = *taddr_s;
   if (threadIdx.x == 0) {
-    unsigned acc = 0;
-    for (int part = 0; part < 2; ++part) {
-      const unsigned base = smem_u32(part ? lo : hi);
+    int i = 0;  // MMA count: accumulator i % kTcAcc, overwritten by its first MMA
+    for (int part = 0; part < kTcTerms; ++part) {
+      const unsigned base = smem_u32(tsm + part * kTcHalo);
       for (int tap = 0; tap < 27; ++tap) {
         const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
         const unsigned aoff = ((dz * kTcHY + dy) * kTcHX + dx) * 16;
-        for (int ks = 0; ks < 2; ++ks) {
+        for (int ks = 0; ks < 2; ++ks, ++i) {
           const unsigned long long ad = tc_desc(base + 2 * ks * kTcPlane + aoff, kTcPlane, kTcHX * 16);
           const unsigned long long bd = tc_desc(smem_u32(ws) + (tap * 4 + 2 * ks) * 512, 512, 128);
-          tc_mma(tmem, ad, bd, acc);
-          acc = 1;
+          tc_mma(tmem + (unsigned)(i % kTcAcc) * 32, ad, bd, i >= kTcAcc ? 1u : 0u);
         }
       }
     }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
   }
-  const bool ok = tc_wait(smem_u32(bar), 0, 1 << 22);
-  if (!ok && lane == 0) atomicExch(err, 1);
+  // every thread polls (bounded); the CTA goes on only if all saw completion
+  const bool ok = __syncthreads_and(tc_wait(smem_u32(bar), 0, 1 << 22));
+  if (!ok && threadIdx.x == 0) atomicExch(err, 1);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {
-    unsigned r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(tmem + ((unsigned)(warp * 32) << 16)));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    // row m = 32 warp + lane of D: point (x0 + 1 + m % 8, y0 + 1 + m / 8, z0 + 1)
-    const int m = warp * 32 + lane;
-    const int gx = x0 + 1 + (m & 7), gy = y0 + 1 + (m >> 3), gz = z0 + 1;
-    if (gx < g.X && gy < g.Y) {
-      const long long gi = gx + (long long)g.X * (gy + (long long)g.Y * gz);
+    // warp w reads TMEM lanes 32 (w % 4) .. +31 (its lane quarter) of accumulators
+    // 4 (w / 4) .. +3 and sums them in FP32; the four partial sums of every output
+    // meet in shared memory (the halo's space: the MMAs that read it are complete)
+    const int q = warp & 3, grp = warp >> 2;
+    float sum[32];
 #pragma unroll
-      for (int co = 0; co < 32; ++co) {
-        float v = __uint_as_float(r[co]);
-        if (a.bias) v += a.bias[co];
-        if (a.mask && !(a.mask[b * a.mask_bs + co * g.G + gi] > 0.f)) v = 0.f;
-        a.out[b * a.out_bs + co * g.G + gi] = v;
-      }
+    for (int co = 0; co < 32; ++co) sum[co] = 0.f;
+    for (int acc = grp * 4; acc < grp * 4 + 4; ++acc) {
+      unsigned r[32];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+          "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(tmem + ((unsigned)(q * 32) << 16) + (unsigned)acc * 32));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int co = 0; co < 32; ++co) sum[co] += __uint_as_float(r[co]);
+    }
+    float *red = reinterpret_cast<float *>(tsm);  // [group][co][m], 64 KB
+    const int m = q * 32 + lane;
+#pragma unroll
+    for (int co = 0; co < 32; ++co) red[(grp * 32 + co) * 128 + m] = sum[co];
+  }
+  __syncthreads();
+  if (ok) {
+    // output (co, m) per thread, m fastest: row m of D is the point (x0 + 1 + m % 8, y0 + 1 + m / 8, z0 + 1)
+    const float *red = reinterpret_cast<const float *>(tsm);
+    for (int o = threadIdx.x; o < 32 * 128; o += blockDim.x) {
+      const int co = o >> 7, m = o & 127;
+      const int gx = x0 + 1 + (m & 7), gy = y0 + 1 + (m >> 3), gz = z0 + 1;
+      if (gx >= g.X || gy >= g.Y) continue;
+      const long long gi = gx + (long long)g.X * (gy + (long long)g.Y * gz);
+      float v = ((red[co * 128 + m] + red[(32 + co) * 128 + m]) + red[(64 + co) * 128 + m]) + red[(96 + co) * 128 + m];
+      if (a.bias) v += a.bias[co];
+      if (a.mask && !(a.mask[b * a.mask_bs + co * g.G + gi] > 0.f)) v = 0.f;
+      a.out[b * a.out_bs + co * g.G + gi] = v;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
 }
 
 struct WgArgs {
@@ -870,7 +902,7 @@ int launch_conv(dgx_ctx *c, const ConvArgs &a, int B) {
     if (int e = prep(c, (const void *)k_conv_tc)) return e;
     const int tiles = ((a.g.X + kTcX - 1) / kTcX) * ((a.g.Y + kTcY - 1) / kTcY) * a.g.Z;
     count_launch();
-    k_conv_tc<<<dim3(tiles, 1, B), 128, kTcSmem, c->stream>>>(a, m->tc_err);
+    k_conv_tc<<<dim3(tiles, 1, B), kTcThreads, kTcSmem, c->stream>>>(a, m->tc_err);
     return check_cuda(c, cudaGetLastError(), "k_conv_tc");
   }
   if (a.Co % 8 == 0 && (long long)a.g.tiles() * (a.Co / 8) * B >= 4 * 152) return launch_conv_t<8, 8>(c, a, B);

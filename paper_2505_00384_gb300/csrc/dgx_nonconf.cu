@@ -287,7 +287,8 @@ __global__ void __launch_bounds__(128) k_hang_expl(const OpP<double> P0, const O
 }
 
 template <typename T>
-__global__ void k_fill_dead(T *x, int nf, T v, long long Ntot, int nx, int ny, int n3, int4 lo, int4 ext, long long nd) {
+__global__ void k_fill_dead(T *x, const T *src, int nf, T v, long long Ntot, int nx, int ny, int n3, int4 lo, int4 ext,
+                            long long nd) {
   const long long total = nd * n3 * nf;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const int node = (int)(i % n3);
@@ -295,7 +296,8 @@ __global__ void k_fill_dead(T *x, int nf, T v, long long Ntot, int nx, int ny, i
     const int fld = (int)(i / (n3 * nd));
     const int bx = (int)(dc % ext.x), by = (int)((dc / ext.x) % ext.y), bz = (int)(dc / ((long long)ext.x * ext.y));
     const long long cell = (lo.x + bx) + (long long)nx * ((lo.y + by) + (long long)ny * (lo.z + bz));
-    x[fld * Ntot + cell * n3 + node] = v;
+    const long long i0 = fld * Ntot + cell * n3 + node;
+    x[i0] = src ? src[i0] : v;
   }
 }
 
@@ -378,19 +380,19 @@ int launch_hang_explicit(dgx_ctx *c, const double *rho, const double *u, double 
 }
 
 template <typename T>
-int fill_dead(dgx_ctx *c, T *x, int nf, double v, cudaStream_t s) {
+int fill_dead(dgx_ctx *c, T *x, int nf, double v, cudaStream_t s, const T *src) {
   if (!c->nc) return 0;
   const int *rf = c->mesh.refine;
   const int4 lo = make_int4(rf[0], rf[2], rf[4], 0), ext = make_int4(rf[1] - rf[0], rf[3] - rf[2], rf[5] - rf[4], 0);
   const long long nd = (long long)ext.x * ext.y * ext.z, n3 = (long long)c->n * c->n * c->n;
   const long long blocks = std::min<long long>((nd * n3 * nf + 255) / 256, 4 * 152);
   count_launch();
-  k_fill_dead<T><<<(unsigned)std::max<long long>(blocks, 1), 256, 0, s>>>(x, nf, (T)v, c->N, c->mesh.nx, c->mesh.ny,
-                                                                        (int)n3, lo, ext, nd);
+  k_fill_dead<T><<<(unsigned)std::max<long long>(blocks, 1), 256, 0, s>>>(x, src, nf, (T)v, c->N, c->mesh.nx,
+                                                                        c->mesh.ny, (int)n3, lo, ext, nd);
   return check_cuda(c, cudaGetLastError(), "k_fill_dead launch");
 }
-template int fill_dead<double>(dgx_ctx *, double *, int, double, cudaStream_t);
-template int fill_dead<float>(dgx_ctx *, float *, int, double, cudaStream_t);
+template int fill_dead<double>(dgx_ctx *, double *, int, double, cudaStream_t, const double *);
+template int fill_dead<float>(dgx_ctx *, float *, int, double, cudaStream_t, const float *);
 
 // Hanging-face work list: every live base cell whose face neighbour lies in
 // the box, and every child on the block's surface whose face leaves the block
