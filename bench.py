@@ -1329,6 +1329,11 @@ def main():
                                                    y32.data_ptr()), 3 * R)
     t_expl = time_calls(lambda: dgx.dgx_explicit_tendencies(ctx, rho.data_ptr(), u.data_ptr(), Er.data_ptr(),
                                                             Em.data_ptr(), Ee.data_ptr()), max(2, R // 3))
+    expl_variant = dgx.dgx_explicit_variant(ctx)
+    dgx.dgx_set_explicit_variant(ctx, 1 - expl_variant)  # the other arithmetic, for comparison
+    t_expl_other = time_calls(lambda: dgx.dgx_explicit_tendencies(ctx, rho.data_ptr(), u.data_ptr(), Er.data_ptr(),
+                                                                  Em.data_ptr(), Ee.data_ptr()), max(2, R // 3))
+    dgx.dgx_set_explicit_variant(ctx, expl_variant)
     fl_grad, fl_div, bytes64 = dgx.dgx_operator_cost(ctx)
 
     f64_applies = statistics.mean(i.operator_f64 for i in step_infos)
@@ -1419,6 +1424,7 @@ def main():
         "vmult": {"f64_gdofs": N / t_app64 / 1e9, "f32_gdofs": N / t_app32 / 1e9, "f64_ms": t_app64 * 1e3,
                   "f32_ms": t_app32 * 1e3, "k_grad_f64_ms": t_grad64 * 1e3, "k_div_f64_ms": t_div64 * 1e3,
                   "k_grad_f32_ms": t_grad32 * 1e3, "k_div_f32_ms": t_div32 * 1e3, "k_explicit_ms": t_expl * 1e3,
+                  "k_explicit_variant": expl_variant, "k_explicit_other_variant_ms": t_expl_other * 1e3,
                   "flops_per_apply": fl_grad + fl_div, "hbm_floor_bytes_f64": bytes64,
                   "f64_tflops": (fl_grad + fl_div) / t_app64 / 1e12, "f32_tflops": (fl_grad + fl_div) / t_app32 / 1e12,
                   "fp64_peak_measured_tflops": peak64,

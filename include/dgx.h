@@ -385,6 +385,14 @@ void dgx_default_train_opts(dgx_train_opts *opts);
 #define DGX_NOALLOC_SCRATCH_BYTES (16u << 20)
 int dgx_apply_operator_noalloc(dgx_ctx *ctx, int prec, const void *x, void *y);
 
+/* Arithmetic of the explicit fluxes (dgx_explicit_tendencies and the IMEX
+ * step): 1 (default) double-words on the FP32 pipes (hi + lo float pairs,
+ * compensated line products, about 48 bits; degrees up to 4, higher degrees
+ * use the FP64 pipe), 0 the FP64 pipe.  Both agree with the FP64 oracle to
+ * 1e-12.  DGX_ERR_ARG for another value. */
+int dgx_set_explicit_variant(dgx_ctx *ctx, int variant);
+int dgx_explicit_variant(const dgx_ctx *ctx);
+
 /* Algorithmic work of one dgx_apply_operator call for the current mesh (host
  * pointers, any may be NULL): floating-point operations of the implemented
  * (even-odd) sum-factorisation sweeps and pointwise work of the gradient

@@ -1401,6 +1401,15 @@ int dgx_set_operator_variant(dgx_ctx *c, int prec, int variant) {
   return 0;
 }
 
+int dgx_explicit_variant(const dgx_ctx *c) { return c ? c->explicit_variant : DGX_ERR_ARG; }
+
+int dgx_set_explicit_variant(dgx_ctx *c, int variant) {
+  if (!c) return DGX_ERR_ARG;
+  if (variant != 0 && variant != 1) return set_error(c, DGX_ERR_ARG, "explicit-flux variant %d (0 or 1)", variant);
+  c->explicit_variant = variant;
+  return DGX_OK;
+}
+
 int dgx_operator_cost(const dgx_ctx *c, double *flops_grad, double *flops_div, double *b64) {
   if (!c || !c->has_mesh) return DGX_ERR_STATE;
   const int N = c->n, Q = c->q;

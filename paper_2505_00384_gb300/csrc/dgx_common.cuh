@@ -213,6 +213,9 @@ struct dgx_ctx {
   // default of the degree.  Chosen by the timing autotuner (op_tuned) unless
   // pinned by dgx_set_operator_variant (op_pinned).
   int op_variant[2] = {-1, -1};
+  // arithmetic of the explicit fluxes: 1 double-words on the FP32 pipes (degrees
+  // up to 4), 0 the FP64 pipe
+  int explicit_variant = 1;
   bool op_tuned[2] = {false, false};
   bool op_pinned[2] = {false, false};
 

@@ -85,6 +85,12 @@ __device__ __forceinline__ df64 operator/(df64 x, df64 y) {
   const float d = __fadd_rn(pi.hi, dl);
   return fast_two_sum(th, __fdiv_rn(d, y.hi));
 }
+// |x| and max(a, b) for code written once for double and double-word values
+// (double-words are normalised, |lo| <= ulp(hi)/2: compare hi, then lo)
+__device__ __forceinline__ double tabs(double x) { return fabs(x); }
+__device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ df64 tabs(df64 x) { return (x.hi < 0.f || (x.hi == 0.f && x.lo < 0.f)) ? -x : x; }
+__device__ __forceinline__ df64 tmax(df64 a, df64 b) { return (a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo)) ? a : b; }
 __device__ __forceinline__ df64 &operator+=(df64 &x, df64 y) { return x = x + y; }
 __device__ __forceinline__ df64 &operator-=(df64 &x, df64 y) { return x = x - y; }
 __device__ __forceinline__ df64 &operator*=(df64 &x, df64 y) { return x = x * y; }

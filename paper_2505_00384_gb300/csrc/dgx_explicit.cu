@@ -10,16 +10,20 @@
 // acoustic part is implicit); slip walls by the mirror state rho+ = rho-,
 // u+ = u- - 2 (u-.n) n; far-field faces with rho+ = rho_bar, u+ = (u_bar, 0, 0).
 #include "dgx_common.cuh"
-#include "dgx_sweep.cuh"
+#include "dgx_fused.cuh"  // the double-word tables and line product (dgx_sweep.cuh's sweeps in double-words)
 
 namespace dgx {
 namespace {
 
 constexpr int cmax2(int a, int b) { return a > b ? a : b; }
 
+// T: the arithmetic, double (FP64 pipe) or df64 (double-words on the FP32
+// pipes); the arrays are FP64 either way.
+template <typename T>
 struct ExP {
-  OpP<double> P;
-  double g, ubar;
+  OpP<T> P;
+  T g, ubar;
+  const double *tab64;  // the 1D tables in FP64 (double-words convert them while staging)
 };
 
 template <int N, int Q>
@@ -40,15 +44,14 @@ struct ExL {
   static_assert(3 * Q * N2 <= 4 * N2 * Q && 3 * Q2 * N <= 4 * N * Q2, "layout");
 };
 
-template <int N, int Q, bool CURVED>
-__global__ void __launch_bounds__(256) k_explicit(const ExP X, const double *__restrict__ rho,
+template <typename T, int N, int Q, bool CURVED>
+__global__ void __launch_bounds__(256) k_explicit(const ExP<T> X, const double *__restrict__ rho,
                                                   const double *__restrict__ u, const double *__restrict__ rho_bar,
                                                   double *__restrict__ Erho, double *__restrict__ Em,
                                                   double *__restrict__ Ee, long long Ntot) {
-  using T = double;
   using L = ExL<N, Q>;
   constexpr int N2 = L::N2, N3 = L::N3, Q2 = L::Q2, Q3 = L::Q3;
-  const OpP<double> &P = X.P;
+  const OpP<T> &P = X.P;
   extern __shared__ __align__(16) unsigned char smraw[];
   T *sm = reinterpret_cast<T *>(smraw);
   T *tab = sm, *s_in = sm + L::oIn, *s_out = sm + L::oOut, *R1 = sm + L::oR1, *R2 = sm + L::oR2, *VQ = sm + L::oVQ,
@@ -61,7 +64,11 @@ __global__ void __launch_bounds__(256) k_explicit(const ExP X, const double *__r
   const T *colp = CURVED ? P.col + (long long)(cp.cx + P.nx * cp.cy) * col_size(N, Q) : nullptr;
   const T zeta0 = T(cp.cz) * P.dz;
 
-  load_tables<T, N, Q>(P.tab, tab);
+  if constexpr (std::is_same<T, df64>::value) {
+    for (int i = threadIdx.x; i < tab_size(N, Q); i += blockDim.x) tab[i] = T(X.tab64[i]);
+  } else {
+    load_tables<T, N, Q>(P.tab, tab);
+  }
   for (int i = threadIdx.x; i < N3; i += blockDim.x) {
     s_in[i] = rho[cell * N3 + i];
     s_in[N3 + i] = u[cell * N3 + i];
@@ -176,7 +183,7 @@ __global__ void __launch_bounds__(256) k_explicit(const ExP X, const double *__r
       }
       const T unm = vm0 * nA[0] + vm1 * nA[1] + vm2 * nA[2];
       const T unp = vp0 * nA[0] + vp1 * nA[1] + vp2 * nA[2];
-      const T lam = fmax(fabs(unm), fabs(unp));  // lambda |nA|
+      const T lam = tmax(tabs(unm), tabs(unp));  // lambda |nA|
       const T km = T(0.5) * (vm0 * vm0 + vm1 * vm1 + vm2 * vm2), kp = T(0.5) * (vp0 * vp0 + vp1 * vp1 + vp2 * vp2);
       const T qm[5] = {rm, rm * vm0, rm * vm1, rm * vm2, rm * km};
       const T qp[5] = {rp, rp * vp0, rp * vp1, rp * vp2, rp * kp};
@@ -197,11 +204,11 @@ __global__ void __launch_bounds__(256) k_explicit(const ExP X, const double *__r
     __syncthreads();
   }
   for (int i = threadIdx.x; i < N3; i += blockDim.x) {
-    Erho[cell * N3 + i] = s_out[i];
-    Em[cell * N3 + i] = s_out[N3 + i];
-    Em[Ntot + cell * N3 + i] = s_out[2 * N3 + i];
-    Em[2 * Ntot + cell * N3 + i] = s_out[3 * N3 + i];
-    Ee[cell * N3 + i] = s_out[4 * N3 + i];
+    Erho[cell * N3 + i] = static_cast<double>(s_out[i]);
+    Em[cell * N3 + i] = static_cast<double>(s_out[N3 + i]);
+    Em[Ntot + cell * N3 + i] = static_cast<double>(s_out[2 * N3 + i]);
+    Em[2 * Ntot + cell * N3 + i] = static_cast<double>(s_out[3 * N3 + i]);
+    Ee[cell * N3 + i] = static_cast<double>(s_out[4 * N3 + i]);
   }
 }
 
@@ -330,20 +337,40 @@ int prep2(dgx_ctx *c, Kern k, size_t smem) {
   return check_cuda(c, e, "cudaFuncSetAttribute");
 }
 
-template <int N, bool CURVED>
-int explicit_impl(dgx_ctx *c, const double *rho, const double *u, const double *rho_bar, double *Er, double *Em,
-                  double *Ee, cudaStream_t s) {
+template <typename T, int N, bool CURVED>
+int explicit_go(dgx_ctx *c, const double *rho, const double *u, const double *rho_bar, double *Er, double *Em,
+                double *Ee, cudaStream_t s) {
   constexpr int Q = 2 * N - 1;
-  const size_t smem = sizeof(double) * ExL<N, Q>::total;
-  auto k = k_explicit<N, Q, CURVED>;
+  const size_t smem = sizeof(T) * ExL<N, Q>::total;
+  auto k = k_explicit<T, N, Q, CURVED>;
   if (int e = prep2(c, k, smem)) return e;
   for (int pi = 0; pi < num_patches(c); ++pi) {
-    ExP X{make_params<double>(c, pi), c->bg.g, c->bg.u_bar};
+    ExP<T> X{make_params<T>(c, pi), T(c->bg.g), T(c->bg.u_bar), c->tab64};
     const long long o = patch_cell0(c, pi) * N * N * N;
     count_launch();
     k<<<(unsigned)patch_ncell(c, pi), 256, smem, s>>>(X, rho + o, u + o, rho_bar + o, Er + o, Em + o, Ee + o, c->N);
   }
-  if (int e = check_cuda(c, cudaGetLastError(), "k_explicit launch")) return e;
+  return 0;
+}
+
+// The explicit fluxes in double-words (c->explicit_variant 1, degrees up to 4)
+// or on the FP64 pipe.
+template <int N, bool CURVED>
+int explicit_impl(dgx_ctx *c, const double *rho, const double *u, const double *rho_bar, double *Er, double *Em,
+                  double *Ee, cudaStream_t s) {
+  int e;
+  if constexpr (N <= 5) {
+    if (c->explicit_variant == 1) {
+      if ((e = upload_fused_tables(c))) return e;
+      e = explicit_go<df64, N, CURVED>(c, rho, u, rho_bar, Er, Em, Ee, s);
+    } else {
+      e = explicit_go<double, N, CURVED>(c, rho, u, rho_bar, Er, Em, Ee, s);
+    }
+  } else {
+    e = explicit_go<double, N, CURVED>(c, rho, u, rho_bar, Er, Em, Ee, s);
+  }
+  if (e) return e;
+  if ((e = check_cuda(c, cudaGetLastError(), "k_explicit launch"))) return e;
   return c->nc ? launch_hang_explicit(c, rho, u, Er, Em, Ee, s) : 0;
 }
 

@@ -7,6 +7,7 @@
 
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "dgx_common.cuh"
@@ -65,6 +66,28 @@ __device__ __forceinline__ void line_eo(const T *src, int ss, T *dst, int ds) {
   }
 }
 
+// Double-word line product (compensated dot products; defined with the fused
+// kernels' double-word tables in dgx_fused.cuh, which a translation unit that
+// sweeps double-words includes).
+template <int NN, int MAT, int MO, int MI>
+__device__ __forceinline__ void line_dw(const df64 *x, df64 *y);
+
+// One line of a sweep: the even-odd product, or for double-words the line
+// gathered into registers and multiplied by line_dw.
+template <typename T, int NN, int MAT, int MO, int MI>
+__device__ __forceinline__ void line_any(const T *src, int ss, T *dst, int ds) {
+  if constexpr (std::is_same<T, df64>::value) {
+    df64 x[MI], y[MO];
+#pragma unroll
+    for (int m = 0; m < MI; ++m) x[m] = src[m * ss];
+    line_dw<NN, MAT, MO, MI>(x, y);
+#pragma unroll
+    for (int o = 0; o < MO; ++o) dst[o * ds] = y[o];
+  } else {
+    line_eo<T, NN, MAT, MO, MI>(src, ss, dst, ds);
+  }
+}
+
 // One sum-factorisation sweep along direction DIR of `nf` fields stored back
 // to back.  Input field shape (S0, S1, S2), x fastest, with S_DIR == MI; the
 // output replaces that extent by MO.  One thread per 1D line; field f uses the
@@ -112,14 +135,14 @@ __device__ __forceinline__ void sweep(int nf, unsigned sel, const T *__restrict_
     const T *src = in + f * IT + io;
     T *dst = out + f * OT + oo;
     if constexpr (MAT0 == MAT1 && MAT1 == MAT2) {  // one matrix: one copy of the line code
-      line_eo<T, NN, MAT0, MO, MI>(src, ss, dst, ds);
+      line_any<T, NN, MAT0, MO, MI>(src, ss, dst, ds);
     } else if constexpr (MAT1 == MAT2) {
-      if (g < c0) line_eo<T, NN, MAT0, MO, MI>(src, ss, dst, ds);
-      else line_eo<T, NN, MAT1, MO, MI>(src, ss, dst, ds);
+      if (g < c0) line_any<T, NN, MAT0, MO, MI>(src, ss, dst, ds);
+      else line_any<T, NN, MAT1, MO, MI>(src, ss, dst, ds);
     } else {
-      if (g < c0) line_eo<T, NN, MAT0, MO, MI>(src, ss, dst, ds);
-      else if (g < c01) line_eo<T, NN, MAT1, MO, MI>(src, ss, dst, ds);
-      else line_eo<T, NN, MAT2, MO, MI>(src, ss, dst, ds);
+      if (g < c0) line_any<T, NN, MAT0, MO, MI>(src, ss, dst, ds);
+      else if (g < c01) line_any<T, NN, MAT1, MO, MI>(src, ss, dst, ds);
+      else line_any<T, NN, MAT2, MO, MI>(src, ss, dst, ds);
     }
   }
 }

@@ -107,6 +107,8 @@ SIGNATURES = [
     ("dgx_mg_levels", C.c_int, [_P, C.POINTER(C.c_int), _P, C.c_int]),
     ("dgx_operator_variant", C.c_int, [_P, C.c_int]),
     ("dgx_set_operator_variant", C.c_int, [_P, C.c_int, C.c_int]),
+    ("dgx_set_explicit_variant", C.c_int, [_P, C.c_int]),
+    ("dgx_explicit_variant", C.c_int, [_P]),
     ("dgx_basis_tables", C.c_int, [C.c_int, _P, C.c_int]),
     ("dgx_set_mass_rule", C.c_int, [_P, C.c_int, C.c_double, C.c_int]),
     ("dgx_mass_cg_stats", C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
@@ -545,6 +547,15 @@ DGX_OP_VARIANTS = 7
 def dgx_operator_variant(ctx, prec):
     """Launch variant of the operator kernels in use for prec (-1: the default)."""
     return load().dgx_operator_variant(ctx, prec)
+
+
+def dgx_set_explicit_variant(ctx, variant):
+    """Explicit fluxes in double-words (1, default) or on the FP64 pipe (0)."""
+    return _check(ctx, load().dgx_set_explicit_variant(ctx, int(variant)))
+
+
+def dgx_explicit_variant(ctx):
+    return load().dgx_explicit_variant(ctx)
 
 
 def dgx_set_operator_variant(ctx, prec, variant):

@@ -76,8 +76,12 @@ def test_background_fields_match(case):
         assert rel_max_err(host(r), rb) <= 1e-13 and rel_max_err(host(p), pb) <= 1e-13
 
 
-def test_explicit_tendencies(case):
+@pytest.mark.parametrize("variant", [1, 0], ids=["double_words", "fp64_pipe"])
+def test_explicit_tendencies(case, variant):
+    """Both arithmetics of the explicit fluxes (double-words on the FP32 pipes,
+    the default up to degree 4, and the FP64 pipe) against the oracle."""
     import torch
+    dgx.dgx_set_explicit_variant(case.ctx, variant)
     obg, rb, pb = _with_bg(case)
     rho, u, _ = _state(case, rb, pb, 101)
     rd, ud = dev(rho), dev(u)
