@@ -385,8 +385,10 @@ void dgx_default_train_opts(dgx_train_opts *opts);
 #define DGX_NOALLOC_SCRATCH_BYTES (16u << 20)
 int dgx_apply_operator_noalloc(dgx_ctx *ctx, int prec, const void *x, void *y);
 
-/* Arithmetic of the explicit fluxes (dgx_explicit_tendencies and the IMEX
- * step): 1 (default) double-words on the FP32 pipes (hi + lo float pairs,
+/* Arithmetic of the explicit side of the step: the explicit fluxes
+ * (dgx_explicit_tendencies) and the consistent-rule mass terms of the stage
+ * right-hand sides (dgx_kinetic_mass and the IMEX step's rho' g and kinetic
+ * terms): 1 (default) double-words on the FP32 pipes (hi + lo float pairs,
  * compensated line products, about 48 bits; degrees up to 4, higher degrees
  * use the FP64 pipe), 0 the FP64 pipe.  Both agree with the FP64 oracle to
  * 1e-12.  DGX_ERR_ARG for another value. */

@@ -21,14 +21,62 @@
 
 namespace dgx {
 
+struct df64;
+#ifdef __CUDACC__
+__device__ __forceinline__ df64 dw_split_device(double d);
+#endif
+
 struct df64 {
   float hi, lo;
   df64() = default;
   __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
-  __host__ __device__ df64(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  // hi = RN(d) to 24 bits, lo = RN(d - hi)
+  __host__ __device__ df64(double d);
   __host__ __device__ df64(int i) : df64((double)i) {}
   __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
 };
+
+#ifdef __CUDACC__
+// The split of a double into a double-word without the FP64 pipe (its
+// conversions run at 1/64 of the FP32 rate on this GPU): the 53-bit
+// significand is rounded to 24 bits to nearest even with integer operations,
+// and the remainder (at most 29 bits, signed) is converted to float and scaled
+// by a power of two.  The result equals the FP64-pipe split bit for bit:
+// d - hi is exact, and RN of the scaled remainder is the scaled RN.  Doubles
+// whose hi or lo would leave the normal float range (|d| outside [2^-74,
+// 2^127)), zeros, subnormals, infinities and NaNs take the FP64 path.
+__device__ __forceinline__ df64 dw_split_device(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e < 949 || e > 1149) {
+    const float h = __double2float_rn(d);
+    return df64(h, __double2float_rn(d - (double)h));
+  }
+  const unsigned sgn = (unsigned)(b >> 63) << 31;
+  const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);  // 53-bit significand
+  long long mh = m >> 29;
+  const long long rem = m & 0x1FFFFFFFll, half = 1ll << 28;
+  if (rem > half || (rem == half && (mh & 1))) ++mh;  // round to nearest even
+  const int r = (int)(m - (mh << 29));                // d - hi in units of 2^(e - 1075), |r| <= 2^28
+  int eh = e - 1023 + 127;
+  if (mh == (1ll << 24)) {  // rounded up into the next binade
+    mh >>= 1;
+    ++eh;
+  }
+  const float hi = __uint_as_float(sgn | ((unsigned)eh << 23) | ((unsigned)mh & 0x7FFFFFu));
+  const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);  // 2^(e - 1075), normal for e >= 949
+  return df64(hi, __fmul_rn(__int2float_rn(sgn ? -r : r), scale));
+}
+#endif
+
+__host__ __device__ inline df64::df64(double d) {
+#ifdef __CUDA_ARCH__
+  *this = dw_split_device(d);
+#else
+  hi = (float)d;
+  lo = (float)(d - (double)(float)d);
+#endif
+}
 
 // storage type of a compute type: double-word kernels read and write FP64 arrays
 template <typename T>

@@ -222,11 +222,10 @@ struct CmL {
                        oZ = oR3 + 4 * Q3, oY = oZ + Q2 * N, oX = oY + Q * N2, total = oX + N3;
 };
 
-template <int N, int Q, bool CURVED, int MODE>
-__global__ void __launch_bounds__(256) k_cmass(const OpP<double> P, double scale, const double *__restrict__ f0,
-                                               const double *__restrict__ fv, double *__restrict__ out,
-                                               long long Ntot) {
-  using T = double;
+template <typename T, int N, int Q, bool CURVED, int MODE>
+__global__ void __launch_bounds__(256) k_cmass(const OpP<T> P, T scale, const double *__restrict__ tab64,
+                                               const double *__restrict__ f0, const double *__restrict__ fv,
+                                               double *__restrict__ out, long long Ntot) {
   using L = CmL<N, Q>;
   constexpr int N3 = L::N3, Q2 = L::Q2, Q3 = L::Q3;
   constexpr int NF = MODE == 0 ? 1 : 4;
@@ -237,7 +236,11 @@ __global__ void __launch_bounds__(256) k_cmass(const OpP<double> P, double scale
   const long long cell = blockIdx.x;
   const CellPos cp = cell_pos(P, cell);
   const T *colp = CURVED ? P.col + (long long)(cp.cx + P.nx * cp.cy) * col_size(N, Q) : nullptr;
-  load_tables<T, N, Q>(P.tab, tab);
+  if constexpr (std::is_same<T, df64>::value) {
+    for (int i = threadIdx.x; i < tab_size(N, Q); i += blockDim.x) tab[i] = T(tab64[i]);
+  } else {
+    load_tables<T, N, Q>(P.tab, tab);
+  }
   for (int i = threadIdx.x; i < N3; i += blockDim.x) {
     s_in[i] = f0[cell * N3 + i];
     if (MODE == 1) {
@@ -271,7 +274,7 @@ __global__ void __launch_bounds__(256) k_cmass(const OpP<double> P, double scale
   __syncthreads();
   sweep<T, N, 0, N, Q, Q, N, N, M_IT, M_IT, M_IT>(1, 0u, Wy, Wx);
   __syncthreads();
-  for (int i = threadIdx.x; i < N3; i += blockDim.x) out[cell * N3 + i] = Wx[i];
+  for (int i = threadIdx.x; i < N3; i += blockDim.x) out[cell * N3 + i] = static_cast<double>(Wx[i]);
 }
 
 // Forward fast density-weighted mass A(rho) v = Ia^T J Ia v (r+1 Gauss points,
@@ -377,16 +380,26 @@ int explicit_impl(dgx_ctx *c, const double *rho, const double *u, const double *
 template <int N, bool CURVED>
 int cmass_impl(dgx_ctx *c, int mode, double scale, const double *f0, const double *fv, double *out, cudaStream_t s) {
   constexpr int Q = 2 * N - 1;
-  const size_t smem = sizeof(double) * CmL<N, Q>::total;
-  auto k = mode == 0 ? k_cmass<N, Q, CURVED, 0> : k_cmass<N, Q, CURVED, 1>;
-  if (int e = prep2(c, k, smem)) return e;
-  for (int pi = 0; pi < num_patches(c); ++pi) {
-    const long long o = patch_cell0(c, pi) * N * N * N;
-    count_launch();
-    k<<<(unsigned)patch_ncell(c, pi), 128, smem, s>>>(make_params<double>(c, pi), scale, f0 + o, fv ? fv + o : nullptr,
-                                                      out + o, c->N);
+  auto go = [&](auto tag) -> int {
+    using T = decltype(tag);
+    const size_t smem = sizeof(T) * CmL<N, Q>::total;
+    auto k = mode == 0 ? k_cmass<T, N, Q, CURVED, 0> : k_cmass<T, N, Q, CURVED, 1>;
+    if (int e = prep2(c, k, smem)) return e;
+    for (int pi = 0; pi < num_patches(c); ++pi) {
+      const long long o = patch_cell0(c, pi) * N * N * N;
+      count_launch();
+      k<<<(unsigned)patch_ncell(c, pi), 128, smem, s>>>(make_params<T>(c, pi), T(scale), c->tab64, f0 + o,
+                                                        fv ? fv + o : nullptr, out + o, c->N);
+    }
+    return check_cuda(c, cudaGetLastError(), "k_cmass launch");
+  };
+  if constexpr (N <= 5) {  // the explicit side's arithmetic (dgx_set_explicit_variant)
+    if (c->explicit_variant == 1) {
+      if (int e = upload_fused_tables(c)) return e;
+      return go(df64{});
+    }
   }
-  return check_cuda(c, cudaGetLastError(), "k_cmass launch");
+  return go(double{});
 }
 
 template <int N, bool CURVED>

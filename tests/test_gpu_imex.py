@@ -95,8 +95,10 @@ def test_explicit_tendencies(case, variant):
     assert rel_max_err(host(Ee), ee) <= 1e-12
 
 
-def test_mass_terms(case):
+@pytest.mark.parametrize("variant", [1, 0], ids=["double_words", "fp64_pipe"])
+def test_mass_terms(case, variant):
     import torch
+    dgx.dgx_set_explicit_variant(case.ctx, variant)
     _, rb, pb = _with_bg(case)
     rho, u, _ = _state(case, rb, pb, 111)
     rd, ud = dev(rho), dev(u)
