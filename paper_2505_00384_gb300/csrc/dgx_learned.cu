@@ -391,6 +391,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(ConvArgs a, int *err)
       a.out[b * a.out_bs + co * g.G + gi] = v;
     }
   }
+  // after a timeout the MMAs may still be writing TMEM: give them a second
+  // bounded wait before the columns are freed
+  if (!ok && warp == 0) tc_wait(smem_u32(bar), 0, 1 << 22);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
