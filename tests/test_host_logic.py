@@ -81,3 +81,62 @@ def test_bench_oracle_baseline_on_one_core():
     v1, sample1, threads1 = bench.oracle_step_cost(w, budget_s=0.5, threads=1)
     assert v > 0 and v1 > 0 and threads == before and threads1 == 1 and O.max_threads() == before
     assert "random cells" in sample and "random cells" in sample1
+
+
+def _default_args(bench):
+    import sys
+    argv = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        return bench.parse()
+    finally:
+        sys.argv = argv
+
+
+def _reference_line(bench, monkeypatch, capsys, rank):
+    """Run the reference arm's driver with the oracle timing replaced by a
+    fixed cost (the arm's JSON line, not the oracle, is under test here)."""
+    import sys
+    calls = []
+
+    def fake_cost(work, budget_s=15.0, threads=None):
+        calls.append(budget_s)
+        return 123.0 + len(calls), "fixed sample", 4
+
+    monkeypatch.setattr(bench, "oracle_step_cost", fake_cost)
+    monkeypatch.setenv("RANK", str(rank))
+    monkeypatch.setenv("LOCAL_RANK", str(rank))
+    monkeypatch.setenv("WORLD_SIZE", "2" if rank else "1")
+    argv = sys.argv
+    try:
+        sys.argv = ["bench.py", "--impl", "reference", "--steps", "3", "--warmup", "2"]
+        assert bench.main() == 0
+    finally:
+        sys.argv = argv
+    return calls, capsys.readouterr().out
+
+
+def test_bench_reference_arm_line(monkeypatch, capsys):
+    """Rank 0 prints one JSON line with the contract's keys; the value is the
+    median of the timed steps only (warm-up steps excluded)."""
+    import json
+    bench = _bench()
+    calls, out = _reference_line(bench, monkeypatch, capsys, 0)
+    lines = [l for l in out.splitlines() if l.strip()]
+    assert len(calls) == 5 and len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["higher_is_better"] is False and d["steps"] == 3 and d["warmup"] == 2
+    assert d["value"] == 127.0 and abs(d["ms_per_step"] - 127000.0) < 1e-9  # median of 126, 127, 128
+    assert d["config"] == {"workload": bench.workload(_default_args(bench))["name"]}
+    cb = d["cpu_baseline"]
+    assert cb["value"] == d["value"] and cb["cores"] == 4 and cb["kind"] == "oracle" and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_bench_reference_arm_other_ranks_do_no_work(monkeypatch, capsys):
+    bench = _bench()
+    calls, out = _reference_line(bench, monkeypatch, capsys, 1)
+    assert calls == [] and out.strip() == ""
